@@ -1,0 +1,275 @@
+"""Pins of the CPU oracle against facts fixed outside it.
+
+Each test ties the oracle to something it does not compute itself: published
+known-answer vectors, closed forms of the 1-lane circle (Sec. 5), hand-derived
+trajectories of the car-following rules (Sec. 3), conservation and exclusion
+invariants, and a second naive restatement of the rules on tiny networks.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from brute import Brute
+from helpers import check_invariants, digest, make_scenario, positions, splitmix64
+from paper_cs_0105004_gb300.inputs import networks as N
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ------------------------------------------------------------------ generators
+
+def test_philox_known_answers():
+    for r in _rows("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in r]
+        assert list(oracle.philox4x32_10(v[0:4], v[4:6])) == v[6:10]
+
+
+def test_splitmix64_known_answers():
+    for k, r in enumerate(_rows("splitmix64_seed0.txt")):
+        z = (k * 0x9E3779B97F4A7C15) % 2**64
+        assert oracle.splitmix64(z) == int(r[0], 16)
+        assert splitmix64(z) == int(r[0], 16)
+
+
+# ------------------------------------------------------------------ hand-derived trajectories
+
+def test_single_car_trajectory():
+    sc = make_scenario([(0, 1, 200, 1)], 2, [[0]], [0], p=0)
+    o = oracle.Oracle(sc)
+    for step, x, v in _rows("single_car_p0.txt"):
+        o.step(1)
+        pos = positions(o.get_state(), sc.net)
+        assert pos[0] == (0, 0, int(x), int(v)), step
+
+
+def test_car_decelerates_to_link_end_and_arrives():
+    # 12-cell last link: cells 0,1,3,6,10 after steps 0..4; at cell 10 the gap is
+    # 1 free cell + 1 (exit open on the last link) = 2, so it reaches 12 = L and
+    # leaves to parking in step 5.
+    sc = make_scenario([(0, 1, 12, 1)], 2, [[0]], [0], p=0)
+    o = oracle.Oracle(sc)
+    st = o.step(6)
+    assert [int(s["arrived"]) for s in st] == [0, 0, 0, 0, 0, 1]
+    assert int(st[4]["sum_v"]) == 4 and int(st[5]["active"]) == 0
+
+
+def test_transfer_keeps_velocity_and_then_arrives():
+    # link 0 (0->1) then link 1 (1->2), 12 cells each.  Step 5: v = 2 reaches the
+    # end of link 0, enters the empty buffer and crosses to cell 0 of link 1
+    # with v = 2 in the same step.  Steps 6,7: cells 3 (v 3), 7 (v 4).  Step 8:
+    # 4 free cells + exit open = 5 -> reaches 12 and arrives.
+    sc = make_scenario([(0, 1, 12, 1), (1, 2, 12, 1)], 3, [[0, 1]], [0], p=0)
+    o = oracle.Oracle(sc)
+    o.step(6)
+    assert positions(o.get_state(), sc.net)[0] == (1, 0, 0, 2)
+    st = o.step(3)
+    assert positions(o.get_state(), sc.net) == {}
+    assert int(st[0]["transfers"]) == 0 and int(st[2]["arrived"]) == 1
+    assert [int(s["sum_v"]) for s in st[:2]] == [3, 4]
+
+
+def test_intersection_priority_lower_link_id_first():
+    # Two one-lane links (0: 0->2, 1: 1->2) feed link 2 (2->3).  Both vehicles
+    # run identical trajectories and reach their link ends in step 5; the one
+    # on the lower link id takes cell 0 of link 2, the other waits in its
+    # buffer and crosses one step later keeping v = 2.
+    links = [(0, 2, 12, 1), (1, 2, 12, 1), (2, 3, 12, 1)]
+    sc = make_scenario(links, 4, [[0, 2], [1, 2]], [0, 0], p=0)
+    o = oracle.Oracle(sc)
+    st = o.step(6)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (2, 0, 0, 2) and pos[1] == (1, 0, 12, 2)
+    assert int(st[5]["transfers"]) == 1 and int(st[5]["buffered"]) == 1
+    o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (2, 0, 3, 3) and pos[1] == (2, 0, 0, 2)
+    o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    # vehicle 1: v 3 wanted, 2 free cells before vehicle 0 (at 3 after the
+    # lane-change sub-step, there is one lane) -> v 2, cell 2
+    assert pos[0] == (2, 0, 7, 4) and pos[1] == (2, 0, 2, 2)
+
+
+def test_transfer_lane_preference():
+    # Buffered vehicle on lane 1 of a 2-lane link moves to lane 1 of a 3-lane
+    # next link; with that cell taken it takes the lowest free lane (0).
+    links = [(0, 1, 20, 2), (1, 2, 20, 3), (3, 1, 20, 1)]
+    routes = [[0, 1], [2, 1]]
+    sc = make_scenario(links, 4, routes, [0, 0], p=0, bufs=[(0, 0, 1, 3)], placed=[(1, 2, 0, 5, 0)])
+    o = oracle.Oracle(sc)
+    o.step(1)
+    assert positions(o.get_state(), sc.net)[0] == (1, 1, 0, 3)
+    sc2 = make_scenario(links + [(4, 1, 20, 1)], 5, routes + [[3, 1]], [0, 0, 0], p=0,
+                        bufs=[(0, 0, 1, 3), (2, 3, 0, 1)], placed=[(1, 2, 0, 5, 0)])
+    # link 3 (higher id) buffered vehicle targets link 1 too, but after link 0
+    o2 = oracle.Oracle(sc2)
+    o2.step(1)
+    pos = positions(o2.get_state(), sc2.net)
+    assert pos[0] == (1, 1, 0, 3) and pos[2] == (1, 0, 0, 1)
+
+
+def _lane_change_case(start_step, blocker_behind=False):
+    placed = [(0, 0, 0, 10, 3), (1, 0, 0, 12, 0)]
+    routes = [[0], [0]]
+    if blocker_behind:
+        placed.append((2, 0, 1, 7, 0))
+        routes.append([0])
+    return make_scenario([(0, 1, 40, 2)], 2, routes, [0] * len(routes), p=0, placed=placed,
+                         start_step=start_step)
+
+
+def test_lane_change_even_step_moves_up():
+    # Step 0 (d=+1): vehicle 0 at lane 0 cell 10, v 3, sees 1 free cell before
+    # vehicle 1; lane 1 offers 5 > 1 and its cells 5..10 are empty -> it
+    # changes to lane 1, then accelerates to 4 and lands on cell 14.
+    sc = _lane_change_case(0)
+    o = oracle.Oracle(sc)
+    st = o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (0, 1, 14, 4) and pos[1] == (0, 0, 13, 1)
+    assert int(st[0]["lane_changes"]) == 1
+
+
+def test_lane_change_odd_step_has_no_target_from_lane0():
+    sc = _lane_change_case(1)
+    o = oracle.Oracle(sc)
+    st = o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (0, 0, 11, 1) and pos[1] == (0, 0, 13, 1)
+    assert int(st[0]["lane_changes"]) == 0
+
+
+def test_lane_change_needs_room_behind():
+    sc = _lane_change_case(0, blocker_behind=True)
+    o = oracle.Oracle(sc)
+    st = o.step(1)
+    assert int(st[0]["lane_changes"]) == 0
+    assert positions(o.get_state(), sc.net)[0] == (0, 0, 11, 1)
+
+
+# ------------------------------------------------------------------ 1-lane circle (Sec. 5)
+
+def _ring(L, n, mode, v0=0, lanes=1, p=0, vmax=5, seed=3, rng_seed=0):
+    net = N.ring_network(L, lanes)
+    dem, init = N.ring_initial_state(net, n, mode, v0, np.random.default_rng(rng_seed))
+    return N.Scenario("ring", net, dem, 0, seed, vmax, p, 1, init)
+
+
+def test_ring_free_flow_exact():
+    # gaps >= vmax at v = vmax: every vehicle keeps vmax; flow = rho * vmax exactly
+    sc = _ring(320, 32, "uniform", v0=5)
+    st = oracle.Oracle(sc).step(200)
+    assert np.all(st["sum_v"] == 5 * 32)
+
+
+def test_ring_jam_exact():
+    # L = N (g+1), all gaps g < vmax, v = g: stationary, sum v = L - N
+    for g in (1, 2, 3, 4):
+        n = 40
+        sc = _ring(n * (g + 1), n, "uniform", v0=g)
+        st = oracle.Oracle(sc).step(100)
+        assert np.all(st["sum_v"] == n * g)
+
+
+@pytest.mark.parametrize("rho", [0.05, 0.1, 0.3, 0.5, 0.8])
+def test_ring_deterministic_fundamental_diagram(rho):
+    # p = 0: J = min(rho vmax, 1 - rho) after transients (NaSch deterministic limit)
+    L = 640
+    n = int(round(rho * L))
+    sc = _ring(L, n, "random", rng_seed=int(rho * 1000))
+    o = oracle.Oracle(sc)
+    o.step(10 * L)
+    st = o.step(2 * L)
+    J = st["sum_v"].astype(np.float64).mean() / L
+    Jth = min(n / L * 5, 1 - n / L)
+    assert abs(J - Jth) <= 2.0 / L + 1e-9
+
+
+@pytest.mark.parametrize("rho", [0.1, 0.3, 0.5, 0.7])
+def test_ring_vmax1_stochastic_exact_flow(rho):
+    # vmax = 1 with parallel update: J = (1 - sqrt(1 - 4 (1-p) rho (1-rho))) / 2
+    # (Schreckenberg, Schadschneider, Nagel, Ito, Phys. Rev. E 51, 1995)
+    L = 9984
+    n = int(round(rho * L))
+    thr = N.P_THRESHOLD_0_2
+    sc = _ring(L, n, "random", vmax=1, p=thr, rng_seed=7)
+    o = oracle.Oracle(sc)
+    o.step(500)
+    st = o.step(3000)
+    J = st["sum_v"].astype(np.float64).mean() / L
+    q = 1 - thr / 2**32
+    r = n / L
+    Jth = (1 - math.sqrt(1 - 4 * q * r * (1 - r))) / 2
+    assert abs(J - Jth) / Jth < 0.01
+
+
+def test_three_lane_ring_lane_changes_alternate_and_conserve():
+    sc = _ring(320, 300, "random", lanes=3, p=N.P_THRESHOLD_0_2, rng_seed=5)
+    o = oracle.Oracle(sc)
+    prev = positions(o.get_state(), sc.net)
+    total_lc = 0
+    for t in range(200):
+        st = o.step(1)[0]
+        s = o.get_state()
+        pos = positions(s, sc.net)
+        assert len(pos) == 300 and int(st["active"]) == 300
+        d = 1 if t % 2 == 0 else -1
+        for i, p in pos.items():
+            assert p[1] - prev[i][1] in (0, d)
+        total_lc += int(st["lane_changes"])
+        assert int(st["lane_changes"]) == sum(1 for i in pos if pos[i][1] != prev[i][1])
+        prev = pos
+    assert total_lc > 0
+
+
+# ------------------------------------------------------------------ invariants and the naive restatement
+
+def test_invariants_on_grid():
+    sc = N.small_grid_scenario(4, 2, 25, n_trips=400, window=100, steps=400, gen_seed=5, seed=9)
+    o = oracle.Oracle(sc)
+    prev = None
+    for t in range(400):
+        row = o.step(1)[0]
+        s = o.get_state()
+        prev = check_invariants(sc, s, row, prev)
+        assert int(row["state_hash"]) == digest(s, sc.net)
+    assert int(row["arrived"]) > 0
+
+
+@pytest.mark.parametrize("case", [(3, 2, 20, 60, 0, 5, 1), (3, 3, 12, 150, 1, 5, 1), (2, 1, 8, 40, 2, 3, 1),
+                                  (3, 2, 15, 200, 3, 7, 1), (3, 2, 15, 120, 4, 5, 0)])
+def test_oracle_matches_naive_restatement(case):
+    side, lanes, cells, trips, seed, vmax, lc = case
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 60, 250, gen_seed=seed, seed=seed + 11, vmax=vmax)
+    sc.lane_change = lc
+    o, b = oracle.Oracle(sc), Brute(sc)
+    for t in range(250):
+        so = o.step(1)[0]
+        sb = b.step()
+        for k, v in sb.items():
+            assert int(so[k]) == v, (t, k)
+        st = o.get_state()
+        ci, cv, bi, bv = b.state(sc.net)
+        assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
+        assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
+
+
+def test_oracle_matches_naive_restatement_on_rings():
+    for lanes in (1, 2, 3):
+        sc = _ring(96, 40 * lanes, "random", lanes=lanes, p=N.P_THRESHOLD_0_2, rng_seed=lanes)
+        o, b = oracle.Oracle(sc), Brute(sc)
+        for t in range(150):
+            so = o.step(1)[0]
+            sb = b.step()
+            assert int(so["sum_v"]) == sb["sum_v"] and int(so["lane_changes"]) == sb["lane_changes"]
+            ci, cv, _, _ = b.state(sc.net)
+            st = o.get_state()
+            assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)

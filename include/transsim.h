@@ -1,0 +1,216 @@
+/* transsim.h -- C ABI of the GB300 TRANSIMS cellular-automaton step library.
+ *
+ * One time step of the TRANSIMS micro-simulation (Nagel & Rickert,
+ * "Parallel implementation of the TRANSIMS micro-simulation"):
+ *   1. lane change, a sideways move decided on the start-of-step state
+ *      (Sec. 3: two sub-time-steps per step, lane changes first; symmetric
+ *      rules made of a reason to change and a gap check);
+ *   2. velocity update: accelerate by one up to vmax, limit to the free
+ *      cells ahead (interaction range vmax = 5 cells, Sec. 3 and Sec. 4),
+ *      random slowdown by one with probability p (Sec. 3 rule (iii));
+ *   3. move: every vehicle hops v cells at once (Sec. 3); a vehicle that
+ *      reaches the end of its link enters that lane's one-vehicle link-end
+ *      buffer, or leaves to parking on the last link of its route (Sec. 4);
+ *   4. node transfer: buffered vehicles move to cell 0 of the next link of
+ *      their route in a fixed intersection priority (ascending incoming link
+ *      id, then lane), then travellers whose departure time has come enter
+ *      cell 0 of their first link from parking (Sec. 4).
+ * The readings the paper leaves open are fixed as follows: lane-change
+ * direction +1 on even steps and -1 on odd steps; a vehicle changes when
+ * its own gap is below min(v+1, vmax) and the target lane's gap is larger,
+ * and the target cell plus the vmax cells behind it are empty; at a link end
+ * the gap counts one extra cell when the lane's buffer is empty or the link
+ * is the vehicle's last; a transferred vehicle keeps its velocity and tries
+ * the lane with its current index (capped to the next link's lanes) first,
+ * then the others ascending; departures enter with velocity 0 in the first
+ * free lane, in (departure step, id) order.
+ * Randomness: vehicle `id` slows down at step t iff word 0 of
+ * Philox-4x32-10 with counter (t, id, 0, 0) and key (seed & 0xffffffff,
+ * seed >> 32) is below p_threshold, so results do not depend on the
+ * parallel schedule and are bit-identical to a sequential implementation.
+ *
+ * Conventions for every call:
+ *   - Every call returns ts_status.  TS_OK is 0.  Nothing aborts or throws
+ *     across this boundary.  ts_last_error() gives a thread-local message.
+ *   - After TS_ERR_CUDA or TS_ERR_DEVICE_CHECK a context is unusable
+ *     ("sticky") except for ts_destroy.
+ *   - Pointers named host_* or passed in descriptor structs are HOST
+ *     pointers; the library deep-copies them before returning, so the
+ *     caller may free them at once.  Device memory is owned by the context.
+ *   - A context is used by one host thread at a time.
+ *   - cuda_stream arguments are cudaStream_t values passed as void*; NULL
+ *     means the context's own stream.  Stepping is asynchronous on that
+ *     stream; read calls synchronise with a bounded wait.
+ */
+#ifndef TRANSSIM_H
+#define TRANSSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ts_ctx ts_ctx;
+typedef struct ts_batch ts_batch;
+
+typedef enum {
+    TS_OK = 0,
+    TS_ERR_INVALID = 1,      /* bad argument or malformed network / routes / state */
+    TS_ERR_OOM = 2,          /* device allocation failed                            */
+    TS_ERR_CUDA = 3,         /* a CUDA runtime call failed (sticky)                 */
+    TS_ERR_TIMEOUT = 4,      /* a bounded wait ran out; the work may still finish   */
+    TS_ERR_STATE = 5,        /* call not valid in the current state                 */
+    TS_ERR_DEVICE_CHECK = 6  /* a kernel found an impossible state (sticky)         */
+} ts_status;
+
+/* Driving-rule parameters (Sec. 3).  vmax in cells per 1 s step, 1..15
+ * (5 = 135 km/h with 7.5 m cells).  p_threshold = floor(p * 2^32): the
+ * random slowdown fires when the 32-bit Philox word is below it.
+ * lane_change = 0 disables sub-step 1.  debug_checks is reserved (the
+ * device-side consistency checks are always on). */
+typedef struct {
+    uint32_t vmax;
+    uint32_t p_threshold;
+    uint64_t seed;
+    uint32_t lane_change;
+    uint32_t debug_checks;
+} ts_params;
+
+/* Road network: directed links between nodes.  Link l runs from node
+ * link_from[l] to node link_to[l], has link_cells[l] cells of 7.5 m
+ * (>= 2*vmax+2) and link_lanes[l] lanes (1..4).  link_ring may be NULL; a
+ * link with link_ring[l] = 1 is a periodic circle road (Sec. 5) with no
+ * nodes: its from/to are ignored, it must not appear in a multi-link route,
+ * and its cell count must be a multiple of 32.  Intersection priority is
+ * ascending incoming link id, then lane. */
+typedef struct {
+    uint32_t n_nodes, n_links;
+    const uint32_t *link_from, *link_to, *link_cells, *link_lanes;
+    const uint8_t *link_ring;
+} ts_network_desc;
+
+/* Statistics of the state after step `step` (0-based).  active: vehicles
+ * in cells; buffered: vehicles in link-end buffers; waiting: departure time
+ * reached but not yet on a link; arrived: cumulative arrivals; lane_changes,
+ * transfers (buffer -> next link), inserted (from parking): counts within
+ * this step; sum_v: sum of velocities of vehicles in cells; vehicle_updates:
+ * vehicles that went through the velocity update this step; state_hash: sum
+ * modulo 2^64 over vehicles on links of splitmix64(A ^ splitmix64(B)),
+ * A = id << 32 | link, B = cell << 16 | lane << 8 | v, with cell = link
+ * length for a buffered vehicle (splitmix64 as published by Steele, Lea and
+ * Flood, 2014). */
+typedef struct {
+    uint64_t step, active, buffered, waiting, arrived, lane_changes, transfers, inserted, sum_v,
+        vehicle_updates, state_hash;
+} ts_stats;
+
+/* Optional device-memory provider (for example a framework's caching
+ * allocator).  alloc returns device memory of at least `bytes` bytes, 256-byte
+ * aligned, or NULL; free releases it.  stream is the context stream. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} ts_allocator;
+
+/* Canonical host-side state, used to read a state out, to start from a
+ * given state (ring experiments, checkpoints) and for parity checks.
+ * cell_id/cell_v: one entry per lane-cell in (link, lane, cell) order,
+ * -1 = empty.  buf_id/buf_v: one entry per lane in (link, lane) order.
+ * cursor: index of each vehicle's current link within its route.
+ * dep_head: per link, how many entries of its departure queue (ordered by
+ * departure step, then id) have entered the network.  Sizes come from
+ * ts_state_sizes.  All pointers are host pointers owned by the caller. */
+typedef struct {
+    int32_t *cell_id;
+    int8_t *cell_v;
+    int32_t *buf_id;
+    int8_t *buf_v;
+    uint32_t *cursor;
+    uint32_t *dep_head;
+    uint64_t step, arrived, inserted;
+} ts_state;
+
+/* Builds the device layout of one network on the current CUDA device.
+ * desc arrays are host pointers, deep-copied.  allocator may be NULL
+ * (cudaMalloc).  On success *out owns all device memory.  Errors:
+ * TS_ERR_INVALID (lanes outside 1..4, too-short link, bad node id, ring
+ * length not a multiple of 32, vmax outside 1..15), TS_ERR_OOM, TS_ERR_CUDA. */
+ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params,
+                            const ts_allocator *allocator, ts_ctx **out);
+
+/* Loads n travellers (once per context): host_depart_step[n],
+ * host_route_offsets[n+1] (route i = host_route_links[offsets[i] ..
+ * offsets[i+1])), each route a connected, non-empty list of link ids (Sec. 1:
+ * plans come precomputed from the route-choice module).  Resets the state to
+ * the empty network at step 0.  TS_ERR_INVALID on a malformed route or n
+ * above 2^31-2. */
+ts_status ts_load_vehicles(ts_ctx *ctx, uint32_t n, const uint32_t *host_depart_step,
+                           const uint32_t *host_route_offsets, const uint32_t *host_route_links);
+
+/* Enqueues n_steps time steps on cuda_stream (asynchronous; captured CUDA
+ * graphs of the per-step kernels). */
+ts_status ts_step(ts_ctx *ctx, uint32_t n_steps, void *cuda_stream);
+
+/* Waits (at most timeout_ms) for the context's queued work, then returns
+ * the statistics of the last completed step.  TS_ERR_STATE before the first
+ * step, TS_ERR_TIMEOUT if the wait runs out. */
+ts_status ts_read_stats(ts_ctx *ctx, ts_stats *out, uint32_t timeout_ms);
+
+/* Like ts_read_stats for steps first_step .. first_step+n-1 (the context
+ * keeps the last 4096 steps).  TS_ERR_STATE if a step is not available. */
+ts_status ts_read_stats_range(ts_ctx *ctx, uint64_t first_step, uint32_t n, ts_stats *out,
+                              uint32_t timeout_ms);
+
+/* Number of lane-cells, lanes, vehicles and links of the canonical state. */
+ts_status ts_state_sizes(const ts_ctx *ctx, uint64_t *n_lane_cells, uint32_t *n_lanes,
+                         uint32_t *n_vehicles, uint32_t *n_links);
+
+/* Copies the current state into caller-owned host arrays (bounded wait). */
+ts_status ts_read_state(ts_ctx *ctx, ts_state *out, uint32_t timeout_ms);
+
+/* Replaces the current state by a caller-given canonical state (host
+ * arrays).  TS_ERR_INVALID if ids repeat, a vehicle sits on a link its
+ * cursor does not name, or a velocity is outside 0..vmax. */
+ts_status ts_write_state(ts_ctx *ctx, const ts_state *in);
+
+/* Device bytes a context would hold for a network of this shape with
+ * n_vehicles travellers and route_len route entries in total (admission
+ * control for the job server). */
+size_t ts_footprint_bytes(const ts_network_desc *desc, uint32_t n_vehicles, uint64_t route_len);
+
+/* Thread-local description of the last error. */
+const char *ts_last_error(void);
+
+/* Frees the context and its device memory (waits for its stream). */
+void ts_destroy(ts_ctx *ctx);
+
+/* ---- batching: many independent scenarios advanced by the same kernels.
+ * A batch references contexts (it does not own them).  Every member
+ * advances by one step per batch step until it reaches its own target step
+ * (set by ts_batch_add / ts_batch_set_target); members that reached their
+ * target are skipped.  Membership changes take effect at the next
+ * ts_batch_step and need no re-capture. */
+ts_status ts_batch_create(uint32_t capacity, ts_batch **out);
+ts_status ts_batch_add(ts_batch *b, ts_ctx *ctx, uint64_t target_step);
+ts_status ts_batch_remove(ts_batch *b, ts_ctx *ctx);
+ts_status ts_batch_step(ts_batch *b, uint32_t n_steps, void *cuda_stream);
+/* Waits (bounded) for queued batch work; *done_mask_words receives one bit
+ * per member slot that reached its target. */
+ts_status ts_batch_sync(ts_batch *b, uint32_t timeout_ms);
+/* Current step of a member (after ts_batch_sync). */
+ts_status ts_ctx_step(ts_ctx *ctx, uint64_t *step);
+void ts_batch_destroy(ts_batch *b);
+
+/* Kernel launch shape: columns of 32 cells per link tile (32..128). */
+ts_status ts_set_tile_columns(ts_ctx *ctx, uint32_t columns);
+
+/* Number of kernel launches one time step of this context enqueues. */
+uint32_t ts_launches_per_step(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

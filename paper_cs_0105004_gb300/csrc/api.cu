@@ -1,0 +1,948 @@
+// Host side of the C ABI declared in include/transsim.h: input validation,
+// device layout, CUDA-graph stepping, batching and state conversion.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+#include "transsim.h"
+
+using namespace tsim;
+
+namespace {
+
+thread_local std::string g_err;
+
+ts_status fail(ts_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+ts_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(TS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Polls an event until it completes or the deadline passes.
+ts_status wait_event(cudaEvent_t ev, uint32_t timeout_ms) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return TS_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if ((uint64_t)ms >= timeout_ms) return fail(TS_ERR_TIMEOUT, "timed out waiting for the device");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ world (a set of scenarios stepped together)
+
+struct World {
+    int device = 0;
+    cudaStream_t cap_stream = nullptr;  // used only for graph capture
+    uint32_t capacity = 0;
+    std::vector<ts_ctx *> members;      // slot -> context
+    std::vector<uint64_t> targets;
+    ScenDev *d_table = nullptr;
+    WorldDev *d_wd = nullptr;
+    uint4 *d_link_tiles = nullptr, *d_node_tiles = nullptr;
+    size_t link_cap = 0, node_cap = 0;
+    uint32_t n_link_tiles = 0, n_node_tiles = 0;
+    int grid_l = 0, grid_n = 0;
+    std::map<uint32_t, cudaGraphExec_t> graphs;
+    ~World();
+    ts_status init(uint32_t cap);
+    ts_status rebuild();
+    ts_status run(uint32_t n, cudaStream_t s);
+    void drop_graphs();
+};
+
+struct ts_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    ts_allocator alloc{};
+    bool has_alloc = false;
+    ts_params params{};
+    // network (host copies)
+    uint32_t n_nodes = 0, n_links = 0, n_ring = 0, n_nodes_total = 0;
+    std::vector<uint32_t> from, to, cells, lanes, ncols, wbase, bpos, lane_base;
+    std::vector<uint8_t> ring;
+    std::vector<uint64_t> cell_base;
+    std::vector<uint32_t> node_in_off, node_out_off, node_out_link;
+    uint32_t n_words = 0, n_slots = 0, n_lanes = 0;
+    uint64_t n_lane_cells = 0;
+    uint32_t tile_cols = 64;
+    std::vector<uint4> link_tiles, node_tiles;
+    // vehicles
+    bool loaded = false;
+    uint32_t n_veh = 0;
+    std::vector<uint32_t> route_off, route_links, depart, dep_off, dep_ids;
+    // device
+    ScenDev sd{};
+    std::vector<std::pair<void *, size_t>> allocs;
+    std::vector<std::pair<void *, size_t>> veh_allocs;
+    World *own = nullptr;
+    ts_batch *batch = nullptr;
+    uint64_t host_step = 0;
+    bool stepped = false;
+    bool sticky = false;
+
+    void *dalloc(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        void *p = nullptr;
+        if (has_alloc) {
+            p = alloc.alloc(bytes, (void *)stream, alloc.user);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return p;
+    }
+    void dfree(void *p, size_t bytes) {
+        if (!p) return;
+        if (has_alloc) alloc.free(p, bytes, (void *)stream, alloc.user);
+        else cudaFree(p);
+    }
+};
+
+struct ts_batch {
+    World w;
+    cudaEvent_t ev = nullptr;
+};
+
+World::~World() {
+    drop_graphs();
+    if (d_table) cudaFree(d_table);
+    if (d_wd) cudaFree(d_wd);
+    if (d_link_tiles) cudaFree(d_link_tiles);
+    if (d_node_tiles) cudaFree(d_node_tiles);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+void World::drop_graphs() {
+    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    graphs.clear();
+}
+
+ts_status World::init(uint32_t cap) {
+    capacity = cap;
+    members.assign(cap, nullptr);
+    targets.assign(cap, 0);
+    CK(cudaGetDevice(&device));
+    CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    CK(cudaMalloc(&d_table, sizeof(ScenDev) * cap));
+    CK(cudaMemset(d_table, 0, sizeof(ScenDev) * cap));
+    CK(cudaMalloc(&d_wd, sizeof(WorldDev)));
+    WorldDev wd{0u, 0u, 0u, cap};
+    CK(cudaMemcpy(d_wd, &wd, sizeof(wd), cudaMemcpyHostToDevice));
+    return TS_OK;
+}
+
+// Re-uploads the scenario table and the concatenated tile lists (synchronous).
+ts_status World::rebuild() {
+    std::vector<ScenDev> table(capacity);
+    std::vector<uint4> lt, nt;
+    for (uint32_t s = 0; s < capacity; ++s) {
+        memset(&table[s], 0, sizeof(ScenDev));
+        ts_ctx *c = members[s];
+        if (!c) continue;
+        table[s] = c->sd;
+        for (uint4 t : c->link_tiles) { t.x = s; lt.push_back(t); }
+        for (uint4 t : c->node_tiles) { t.x = s; nt.push_back(t); }
+    }
+    CK(cudaMemcpy(d_table, table.data(), sizeof(ScenDev) * capacity, cudaMemcpyHostToDevice));
+    if (lt.size() > link_cap) {
+        drop_graphs();  // captured launches hold the old pointer
+        if (d_link_tiles) cudaFree(d_link_tiles);
+        link_cap = std::max<size_t>(lt.size(), 2 * link_cap);
+        CK(cudaMalloc(&d_link_tiles, sizeof(uint4) * link_cap));
+    }
+    if (nt.size() > node_cap) {
+        drop_graphs();
+        if (d_node_tiles) cudaFree(d_node_tiles);
+        node_cap = std::max<size_t>(nt.size(), 2 * node_cap);
+        CK(cudaMalloc(&d_node_tiles, sizeof(uint4) * node_cap));
+    }
+    if (!lt.empty()) CK(cudaMemcpy(d_link_tiles, lt.data(), sizeof(uint4) * lt.size(), cudaMemcpyHostToDevice));
+    if (!nt.empty()) CK(cudaMemcpy(d_node_tiles, nt.data(), sizeof(uint4) * nt.size(), cudaMemcpyHostToDevice));
+    n_link_tiles = (uint32_t)lt.size();
+    n_node_tiles = (uint32_t)nt.size();
+    WorldDev wd{0u, n_link_tiles, n_node_tiles, capacity};
+    CK(cudaMemcpy(d_wd, &wd, sizeof(wd), cudaMemcpyHostToDevice));
+    const int gl = std::max(1, std::min<int>((int)n_link_tiles, max_link_blocks()));
+    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
+    if (gl != grid_l || gn != grid_n) {
+        drop_graphs();
+        grid_l = gl;
+        grid_n = gn;
+    }
+    return TS_OK;
+}
+
+// Enqueues n steps of every active member on stream s as CUDA graphs of up
+// to 32 steps (two kernel nodes per step).
+ts_status World::run(uint32_t n, cudaStream_t s) {
+    const uint32_t chunk = 32;
+    while (n > 0) {
+        const uint32_t g = std::min(n, chunk);
+        auto it = graphs.find(g);
+        if (it == graphs.end()) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (uint32_t i = 0; i < g; ++i) {
+                launch_link_kernel(d_table, d_link_tiles, d_wd, grid_l, cap_stream);
+                launch_node_kernel(d_table, d_node_tiles, d_wd, grid_n, cap_stream);
+            }
+            CK(cudaStreamEndCapture(cap_stream, &graph));
+            cudaGraphExec_t exec;
+            const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            it = graphs.emplace(g, exec).first;
+        }
+        CK(cudaGraphLaunch(it->second, s));
+        n -= g;
+    }
+    return TS_OK;
+}
+
+// ------------------------------------------------------------------ helpers
+
+namespace {
+
+ts_status check_ctx(ts_ctx *c) {
+    if (!c) return fail(TS_ERR_INVALID, "null context");
+    if (c->sticky) return fail(TS_ERR_CUDA, "context is in an error state");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    return TS_OK;
+}
+
+void free_list(ts_ctx *c, std::vector<std::pair<void *, size_t>> &lst) {
+    for (auto &a : lst) c->dfree(a.first, a.second);
+    lst.clear();
+}
+
+template <typename T>
+T *alloc_in(ts_ctx *c, std::vector<std::pair<void *, size_t>> &lst, size_t count) {
+    const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+    void *p = c->dalloc(bytes);
+    if (p) lst.emplace_back(p, bytes);
+    return reinterpret_cast<T *>(p);
+}
+
+// Reads the control block (after the context's work is complete).
+ts_status read_ctrl(ts_ctx *c, Ctrl *out) {
+    CK(cudaMemcpyAsync(out, c->sd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (out->error) {
+        c->sticky = true;
+        char buf[96];
+        snprintf(buf, sizeof(buf), "device consistency check failed (flags 0x%x)", out->error);
+        return fail(TS_ERR_DEVICE_CHECK, buf);
+    }
+    return TS_OK;
+}
+
+ts_status wait_ctx(ts_ctx *c, uint32_t timeout_ms) {
+    ts_status s = wait_event(c->ev, timeout_ms);
+    if (s == TS_ERR_CUDA) c->sticky = true;
+    return s;
+}
+
+void build_tiles(ts_ctx *c) {
+    const uint32_t TW = c->tile_cols, vmax = c->params.vmax;
+    c->link_tiles.clear();
+    uint32_t start = 0, count = 0, cols = 0;
+    auto flush = [&]() {
+        if (count) c->link_tiles.push_back(make_uint4(0u, start, count, 0u));
+        count = 0;
+        cols = 0;
+    };
+    for (uint32_t l = 0; l < c->n_links; ++l) {
+        const uint32_t nc = c->ncols[l];
+        if (nc > TW) {
+            flush();
+            uint32_t j = 0;
+            while (j < nc) {
+                uint32_t je = std::min(nc, j + TW);
+                // a split must leave more than 2*vmax cells after it, so that the
+                // tile before it never sees the link end
+                if (!c->ring[l] && je < nc && c->cells[l] - 32u * je < 2u * vmax + 1u) je = nc;
+                c->link_tiles.push_back(make_uint4(0u, l, kPartial | j, je));
+                j = je;
+            }
+            start = l + 1;
+            continue;
+        }
+        if (count == 0) start = l;
+        if (cols + nc > TW) {
+            flush();
+            start = l;
+        }
+        ++count;
+        cols += nc;
+    }
+    flush();
+    c->node_tiles.clear();
+    for (uint32_t n = 0; n < c->n_nodes_total; n += kNodeThreads)
+        c->node_tiles.push_back(make_uint4(0u, n, std::min(c->n_nodes_total, n + (uint32_t)kNodeThreads), 0u));
+}
+
+ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
+    if (!d || !p) return fail(TS_ERR_INVALID, "null descriptor");
+    if (p->vmax < 1 || p->vmax > (uint32_t)kMaxVmax) return fail(TS_ERR_INVALID, "vmax must be 1..15");
+    if (d->n_links == 0) return fail(TS_ERR_INVALID, "network has no links");
+    if (!d->link_cells || !d->link_lanes || !d->link_from || !d->link_to) return fail(TS_ERR_INVALID, "null link array");
+    for (uint32_t l = 0; l < d->n_links; ++l) {
+        const bool ring = d->link_ring && d->link_ring[l];
+        if (d->link_lanes[l] < 1 || d->link_lanes[l] > (uint32_t)kMaxLanes) return fail(TS_ERR_INVALID, "lanes must be 1..4");
+        if (d->link_cells[l] < 1 || d->link_cells[l] > (1u << 24)) return fail(TS_ERR_INVALID, "bad cell count");
+        if (ring) {
+            if (d->link_cells[l] % 32u != 0u) return fail(TS_ERR_INVALID, "ring length must be a multiple of 32 cells");
+        } else if (d->link_from[l] >= d->n_nodes || d->link_to[l] >= d->n_nodes) {
+            return fail(TS_ERR_INVALID, "link node id out of range");
+        }
+    }
+    return TS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char *ts_last_error(void) { return g_err.c_str(); }
+
+uint32_t ts_launches_per_step(void) { return 2u; }
+
+size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_t route_len) {
+    if (!d) return 0;
+    uint64_t words = 0, slots = 0, nodes = d->n_nodes, outs = 0;
+    uint32_t max_dep = 10800;
+    for (uint32_t l = 0; l < d->n_links; ++l) {
+        const bool ring = d->link_ring && d->link_ring[l];
+        words += (uint64_t)((d->link_cells[l] + 31u) / 32u) * d->link_lanes[l];
+        if (!ring) slots += d->link_lanes[l];
+        if (ring) ++nodes;
+        ++outs;
+    }
+    size_t b = 0;
+    b += 16ull * d->n_links + 8ull * (nodes + 1) + 4ull * outs;
+    b += words * (4 + 32 + 128) * 2;
+    b += 16ull * slots + 8ull * n_vehicles + 4ull * route_len;
+    b += 4ull * (d->n_links + 1) + 8ull * n_vehicles + 4ull * d->n_links + 4ull * (max_dep + 1);
+    b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing;
+    return b;
+}
+
+ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params, const ts_allocator *allocator,
+                            ts_ctx **out) {
+    if (!out) return fail(TS_ERR_INVALID, "null output");
+    *out = nullptr;
+    ts_status st = validate_desc(desc, params);
+    if (st != TS_OK) return st;
+    std::unique_ptr<ts_ctx> c(new (std::nothrow) ts_ctx());
+    if (!c) return fail(TS_ERR_OOM, "host allocation failed");
+    CK(cudaGetDevice(&c->device));
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+    if (allocator && allocator->alloc && allocator->free) {
+        c->alloc = *allocator;
+        c->has_alloc = true;
+    }
+    c->params = *params;
+    const uint32_t L = desc->n_links;
+    c->n_nodes = desc->n_nodes;
+    c->n_links = L;
+    c->from.assign(desc->link_from, desc->link_from + L);
+    c->to.assign(desc->link_to, desc->link_to + L);
+    c->cells.assign(desc->link_cells, desc->link_cells + L);
+    c->lanes.assign(desc->link_lanes, desc->link_lanes + L);
+    c->ring.assign(L, 0);
+    if (desc->link_ring)
+        for (uint32_t l = 0; l < L; ++l) c->ring[l] = desc->link_ring[l] ? 1 : 0;
+    for (uint32_t l = 0; l < L; ++l) c->n_ring += c->ring[l];
+    c->n_nodes_total = c->n_nodes + c->n_ring;
+    // words, lanes, canonical cells
+    c->ncols.resize(L);
+    c->wbase.resize(L);
+    c->lane_base.resize(L + 1);
+    uint64_t w = 0;
+    c->lane_base[0] = 0;
+    for (uint32_t l = 0; l < L; ++l) {
+        c->ncols[l] = (c->cells[l] + 31u) / 32u;
+        c->wbase[l] = (uint32_t)w;
+        w += (uint64_t)c->ncols[l] * c->lanes[l];
+        c->lane_base[l + 1] = c->lane_base[l] + c->lanes[l];
+    }
+    if (w >= (1ull << 31) / 32ull) return fail(TS_ERR_INVALID, "network too large");
+    c->n_words = (uint32_t)w;
+    c->n_lanes = c->lane_base[L];
+    c->cell_base.resize(c->n_lanes + 1);
+    c->cell_base[0] = 0;
+    for (uint32_t l = 0; l < L; ++l)
+        for (uint32_t k = 0; k < c->lanes[l]; ++k) {
+            const uint32_t ln = c->lane_base[l] + k;
+            c->cell_base[ln + 1] = c->cell_base[ln] + c->cells[l];
+        }
+    c->n_lane_cells = c->cell_base[c->n_lanes];
+    // link-end buffers grouped by node in priority order
+    c->node_in_off.assign(c->n_nodes_total + 1, 0);
+    for (uint32_t l = 0; l < L; ++l)
+        if (!c->ring[l]) c->node_in_off[c->to[l] + 1] += c->lanes[l];
+    for (uint32_t n = 0; n < c->n_nodes_total; ++n) c->node_in_off[n + 1] += c->node_in_off[n];
+    c->n_slots = c->node_in_off[c->n_nodes_total];
+    c->bpos.assign(L, 0);
+    {
+        std::vector<uint32_t> fill(c->node_in_off.begin(), c->node_in_off.end() - 1);
+        for (uint32_t l = 0; l < L; ++l)
+            if (!c->ring[l]) {
+                c->bpos[l] = fill[c->to[l]];
+                fill[c->to[l]] += c->lanes[l];
+            }
+    }
+    // outgoing links (departure owners); ring link r belongs to pseudo node n_nodes + r
+    c->node_out_off.assign(c->n_nodes_total + 1, 0);
+    {
+        uint32_t r = 0;
+        std::vector<uint32_t> owner(L);
+        for (uint32_t l = 0; l < L; ++l) owner[l] = c->ring[l] ? c->n_nodes + r++ : c->from[l];
+        for (uint32_t l = 0; l < L; ++l) c->node_out_off[owner[l] + 1]++;
+        for (uint32_t n = 0; n < c->n_nodes_total; ++n) c->node_out_off[n + 1] += c->node_out_off[n];
+        c->node_out_link.resize(L);
+        std::vector<uint32_t> fill(c->node_out_off.begin(), c->node_out_off.end() - 1);
+        for (uint32_t l = 0; l < L; ++l) c->node_out_link[fill[owner[l]]++] = l;
+    }
+    build_tiles(c.get());
+    // device arrays of the network
+    auto &A = c->allocs;
+    uint4 *link_info = alloc_in<uint4>(c.get(), A, L);
+    uint32_t *in_off = alloc_in<uint32_t>(c.get(), A, c->n_nodes_total + 1);
+    uint32_t *out_off = alloc_in<uint32_t>(c.get(), A, c->n_nodes_total + 1);
+    uint32_t *out_link = alloc_in<uint32_t>(c.get(), A, L);
+    uint32_t *occ0 = alloc_in<uint32_t>(c.get(), A, c->n_words);
+    uint32_t *occ1 = alloc_in<uint32_t>(c.get(), A, c->n_words);
+    int8_t *vel0 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32);
+    int8_t *vel1 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32);
+    uint32_t *vid0 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32);
+    uint32_t *vid1 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32);
+    uint4 *slots = alloc_in<uint4>(c.get(), A, c->n_slots);
+    Ctrl *ctrl = alloc_in<Ctrl>(c.get(), A, 1);
+    StatRec *stats = alloc_in<StatRec>(c.get(), A, kStatsRing);
+    for (auto &a : A)
+        if (!a.first) {
+            free_list(c.get(), A);
+            return fail(TS_ERR_OOM, "device allocation failed");
+        }
+    if (A.size() != 13) {
+        free_list(c.get(), A);
+        return fail(TS_ERR_OOM, "device allocation failed");
+    }
+    std::vector<uint4> li(L);
+    for (uint32_t l = 0; l < L; ++l) li[l] = make_uint4(c->wbase[l], c->cells[l], c->lanes[l] | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
+    CK(cudaMemcpy(link_info, li.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(in_off, c->node_in_off.data(), 4ull * (c->n_nodes_total + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(out_off, c->node_out_off.data(), 4ull * (c->n_nodes_total + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(out_link, c->node_out_link.data(), 4ull * L, cudaMemcpyHostToDevice));
+    ScenDev &sd = c->sd;
+    sd.link_info = link_info;
+    sd.node_in_off = in_off;
+    sd.node_out_off = out_off;
+    sd.node_out_link = out_link;
+    sd.occ[0] = occ0; sd.occ[1] = occ1;
+    sd.vel[0] = vel0; sd.vel[1] = vel1;
+    sd.vid[0] = vid0; sd.vid[1] = vid1;
+    sd.slots = slots;
+    sd.ctrl = ctrl;
+    sd.stats = stats;
+    sd.vmax = params->vmax;
+    sd.p_threshold = params->p_threshold;
+    sd.seed_lo = (uint32_t)(params->seed & 0xFFFFFFFFull);
+    sd.seed_hi = (uint32_t)(params->seed >> 32);
+    sd.lane_change = params->lane_change ? 1u : 0u;
+    sd.n_links = L;
+    sd.n_nodes_total = c->n_nodes_total;
+    CK(cudaMemset(occ0, 0, 4ull * c->n_words));
+    CK(cudaMemset(occ1, 0, 4ull * c->n_words));
+    CK(cudaMemset(slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
+    CK(cudaMemset(ctrl, 0, sizeof(Ctrl)));
+    CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing));
+    *out = c.release();
+    return TS_OK;
+}
+
+static ts_status upload_vehicles(ts_ctx *c) {
+    free_list(c, c->veh_allocs);
+    auto &A = c->veh_allocs;
+    const uint32_t n = c->n_veh;
+    const uint64_t total = c->route_off[n];
+    uint2 *veh = alloc_in<uint2>(c, A, n);
+    uint32_t *routes = alloc_in<uint32_t>(c, A, total);
+    uint32_t *dep_off = alloc_in<uint32_t>(c, A, c->n_links + 1);
+    uint32_t *dep_ids = alloc_in<uint32_t>(c, A, n);
+    uint32_t *dep_steps = alloc_in<uint32_t>(c, A, n);
+    uint32_t *dep_head = alloc_in<uint32_t>(c, A, c->n_links);
+    uint32_t max_dep = 0;
+    for (uint32_t i = 0; i < n; ++i) max_dep = std::max(max_dep, c->depart[i]);
+    const uint32_t n_dep_steps = n ? max_dep + 1 : 0;
+    uint32_t *dep_upto = alloc_in<uint32_t>(c, A, n_dep_steps);
+    for (auto &a : A)
+        if (!a.first) {
+            free_list(c, A);
+            return fail(TS_ERR_OOM, "device allocation failed");
+        }
+    if (A.size() != 7) {
+        free_list(c, A);
+        return fail(TS_ERR_OOM, "device allocation failed");
+    }
+    std::vector<uint2> hv(n);
+    for (uint32_t i = 0; i < n; ++i) hv[i] = make_uint2(c->route_off[i], c->route_off[i + 1]);
+    std::vector<uint32_t> steps(n), upto(n_dep_steps, 0);
+    for (uint32_t q = 0; q < n; ++q) steps[q] = c->depart[c->dep_ids[q]];
+    for (uint32_t i = 0; i < n; ++i) upto[c->depart[i]]++;
+    for (uint32_t t = 1; t < n_dep_steps; ++t) upto[t] += upto[t - 1];
+    if (n) {
+        CK(cudaMemcpy(veh, hv.data(), 8ull * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dep_ids, c->dep_ids.data(), 4ull * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dep_steps, steps.data(), 4ull * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dep_upto, upto.data(), 4ull * n_dep_steps, cudaMemcpyHostToDevice));
+    }
+    if (total) CK(cudaMemcpy(routes, c->route_links.data(), 4ull * total, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dep_off, c->dep_off.data(), 4ull * (c->n_links + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dep_head, c->dep_off.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    ScenDev &sd = c->sd;
+    sd.veh = veh;
+    sd.route_links = routes;
+    sd.dep_off = dep_off;
+    sd.dep_ids = dep_ids;
+    sd.dep_steps = dep_steps;
+    sd.dep_head = dep_head;
+    sd.departed_upto = dep_upto;
+    sd.n_dep_steps = n_dep_steps;
+    return TS_OK;
+}
+
+static ts_status reset_state(ts_ctx *c, uint64_t step, uint64_t arrived, uint64_t inserted) {
+    ScenDev &sd = c->sd;
+    for (int b = 0; b < 2; ++b) CK(cudaMemset(sd.occ[b], 0, 4ull * c->n_words));
+    CK(cudaMemset(sd.slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
+    Ctrl h{};
+    h.step = step;
+    h.target = step;
+    h.arrived = arrived;
+    h.inserted = inserted;
+    CK(cudaMemcpy(sd.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice));
+    CK(cudaMemset(sd.stats, 0, sizeof(StatRec) * kStatsRing));
+    c->host_step = step;
+    c->stepped = false;
+    return TS_OK;
+}
+
+static ts_status ensure_own_world(ts_ctx *c) {
+    if (c->own) {
+        c->own->members[0] = c;
+        return c->own->rebuild();
+    }
+    c->own = new (std::nothrow) World();
+    if (!c->own) return fail(TS_ERR_OOM, "host allocation failed");
+    ts_status s = c->own->init(1);
+    if (s != TS_OK) return s;
+    c->own->members[0] = c;
+    return c->own->rebuild();
+}
+
+ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uint32_t *off, const uint32_t *links) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (c->loaded) return fail(TS_ERR_STATE, "vehicles already loaded");
+    if (n >= 0x7FFFFFFEu) return fail(TS_ERR_INVALID, "too many vehicles");
+    if (n && (!dep || !off || !links)) return fail(TS_ERR_INVALID, "null vehicle array");
+    std::vector<uint32_t> ro(off, off + n + 1);
+    if (ro[0] != 0) return fail(TS_ERR_INVALID, "route offsets must start at 0");
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t a = ro[i], b = ro[i + 1];
+        if (b <= a) return fail(TS_ERR_INVALID, "empty or decreasing route");
+        for (uint32_t j = a; j < b; ++j) {
+            const uint32_t l = links[j];
+            if (l >= c->n_links) return fail(TS_ERR_INVALID, "route link out of range");
+            if (c->ring[l] && b - a != 1) return fail(TS_ERR_INVALID, "a ring link must be the whole route");
+            if (j + 1 < b && c->to[l] != c->from[links[j + 1]]) return fail(TS_ERR_INVALID, "route is not connected");
+        }
+    }
+    c->n_veh = n;
+    c->route_off = std::move(ro);
+    c->route_links.assign(links, links + c->route_off[n]);
+    c->depart.assign(dep, dep + n);
+    // departure queues: per first link, ordered by (departure step, id)
+    c->dep_off.assign(c->n_links + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) c->dep_off[c->route_links[c->route_off[i]] + 1]++;
+    for (uint32_t l = 0; l < c->n_links; ++l) c->dep_off[l + 1] += c->dep_off[l];
+    c->dep_ids.resize(n);
+    {
+        std::vector<uint32_t> fill(c->dep_off.begin(), c->dep_off.end() - 1);
+        for (uint32_t i = 0; i < n; ++i) c->dep_ids[fill[c->route_links[c->route_off[i]]]++] = i;
+        for (uint32_t l = 0; l < c->n_links; ++l)
+            std::stable_sort(c->dep_ids.begin() + c->dep_off[l], c->dep_ids.begin() + c->dep_off[l + 1],
+                             [&](uint32_t a, uint32_t b) { return c->depart[a] < c->depart[b]; });
+    }
+    st = upload_vehicles(c);
+    if (st != TS_OK) return st;
+    st = reset_state(c, 0, 0, 0);
+    if (st != TS_OK) return st;
+    c->loaded = true;
+    return ensure_own_world(c);
+}
+
+ts_status ts_set_tile_columns(ts_ctx *c, uint32_t columns) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (columns < 8 || columns > 128) return fail(TS_ERR_INVALID, "tile columns must be 8..128");
+    if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
+    st = wait_ctx(c, 60000);
+    if (st != TS_OK) return st;
+    c->tile_cols = columns;
+    build_tiles(c);
+    if (c->own) return c->own->rebuild();
+    return TS_OK;
+}
+
+ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (c->batch) return fail(TS_ERR_STATE, "context is stepped by its batch");
+    if (n_steps == 0) return TS_OK;
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+    c->host_step += n_steps;
+    launch_set_target(c->sd.ctrl, c->host_step, s);
+    CK(cudaGetLastError());
+    st = c->own->run(n_steps, s);
+    if (st != TS_OK) {
+        c->sticky = true;
+        return st;
+    }
+    CK(cudaEventRecord(c->ev, s));
+    c->stepped = true;
+    return TS_OK;
+}
+
+ts_status ts_read_stats_range(ts_ctx *c, uint64_t first, uint32_t n, ts_stats *out, uint32_t timeout_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!out && n) return fail(TS_ERR_INVALID, "null output");
+    st = wait_ctx(c, timeout_ms);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    if (n == 0) return TS_OK;
+    if (first + n > h.step || h.step - first > kStatsRing - 1)
+        return fail(TS_ERR_STATE, "requested steps are not available");
+    std::vector<StatRec> tmp(kStatsRing);
+    CK(cudaMemcpy(tmp.data(), c->sd.stats, sizeof(StatRec) * kStatsRing, cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < n; ++i) {
+        const StatRec &r = tmp[(first + i) & (kStatsRing - 1)];
+        if (r.step != first + i) return fail(TS_ERR_STATE, "requested steps are not available");
+        ts_stats &o = out[i];
+        o.step = r.step; o.active = r.active; o.buffered = r.buffered; o.waiting = r.waiting;
+        o.arrived = r.arrived; o.lane_changes = r.lane_changes; o.transfers = r.transfers;
+        o.inserted = r.inserted; o.sum_v = r.sum_v; o.vehicle_updates = r.vehicle_updates;
+        o.state_hash = r.state_hash;
+    }
+    return TS_OK;
+}
+
+ts_status ts_read_stats(ts_ctx *c, ts_stats *out, uint32_t timeout_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!out) return fail(TS_ERR_INVALID, "null output");
+    st = wait_ctx(c, timeout_ms);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    if (!c->stepped || h.step == 0) return fail(TS_ERR_STATE, "no step has completed");
+    StatRec r;
+    CK(cudaMemcpy(&r, c->sd.stats + ((h.step - 1) & (kStatsRing - 1)), sizeof(StatRec), cudaMemcpyDeviceToHost));
+    if (r.step != h.step - 1) return fail(TS_ERR_STATE, "statistics not available");
+    out->step = r.step; out->active = r.active; out->buffered = r.buffered; out->waiting = r.waiting;
+    out->arrived = r.arrived; out->lane_changes = r.lane_changes; out->transfers = r.transfers;
+    out->inserted = r.inserted; out->sum_v = r.sum_v; out->vehicle_updates = r.vehicle_updates;
+    out->state_hash = r.state_hash;
+    return TS_OK;
+}
+
+ts_status ts_state_sizes(const ts_ctx *c, uint64_t *cells, uint32_t *lanes, uint32_t *veh, uint32_t *links) {
+    if (!c) return fail(TS_ERR_INVALID, "null context");
+    if (cells) *cells = c->n_lane_cells;
+    if (lanes) *lanes = c->n_lanes;
+    if (veh) *veh = c->n_veh;
+    if (links) *links = c->n_links;
+    return TS_OK;
+}
+
+ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (!o || !o->cell_id || !o->cell_v || !o->buf_id || !o->buf_v || !o->cursor || !o->dep_head)
+        return fail(TS_ERR_INVALID, "null state array");
+    st = wait_ctx(c, timeout_ms);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    const int cur = (int)(h.step & 1ull);
+    const size_t nw = c->n_words;
+    std::vector<uint32_t> occ(nw), vid(nw * 32), head(c->n_links);
+    std::vector<int8_t> vel(nw * 32);
+    std::vector<uint4> slots(c->n_slots);
+    std::vector<uint2> veh(c->n_veh);
+    CK(cudaMemcpy(occ.data(), c->sd.occ[cur], 4 * nw, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vel.data(), c->sd.vel[cur], nw * 32, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vid.data(), c->sd.vid[cur], 4 * nw * 32, cudaMemcpyDeviceToHost));
+    if (c->n_slots) CK(cudaMemcpy(slots.data(), c->sd.slots, 16ull * c->n_slots, cudaMemcpyDeviceToHost));
+    if (c->n_veh) CK(cudaMemcpy(veh.data(), c->sd.veh, 8ull * c->n_veh, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(head.data(), c->sd.dep_head, 4ull * c->n_links, cudaMemcpyDeviceToHost));
+    for (uint64_t i = 0; i < c->n_lane_cells; ++i) { o->cell_id[i] = -1; o->cell_v[i] = 0; }
+    for (uint32_t i = 0; i < c->n_lanes; ++i) { o->buf_id[i] = -1; o->buf_v[i] = 0; }
+    for (uint32_t l = 0; l < c->n_links; ++l) {
+        const uint32_t nl = c->lanes[l];
+        for (uint32_t j = 0; j < c->ncols[l]; ++j)
+            for (uint32_t k = 0; k < nl; ++k) {
+                const size_t w = (size_t)c->wbase[l] + (size_t)j * nl + k;
+                uint32_t m = occ[w];
+                while (m) {
+                    const int b = __builtin_ctz(m);
+                    m &= m - 1;
+                    const uint64_t x = 32ull * j + (uint64_t)b;
+                    const uint64_t ci = c->cell_base[c->lane_base[l] + k] + x;
+                    o->cell_id[ci] = (int32_t)(vid[w * 32 + b] & kIdMask);
+                    o->cell_v[ci] = vel[w * 32 + b];
+                }
+            }
+        if (!c->ring[l])
+            for (uint32_t k = 0; k < nl; ++k) {
+                const uint4 s = slots[c->bpos[l] + k];
+                if (s.x == kSlotEmpty) continue;
+                o->buf_id[c->lane_base[l] + k] = (int32_t)(s.x & kIdMask);
+                o->buf_v[c->lane_base[l] + k] = (int8_t)(s.w & 0xFFu);
+            }
+    }
+    for (uint32_t i = 0; i < c->n_veh; ++i) o->cursor[i] = veh[i].x - c->route_off[i];
+    for (uint32_t l = 0; l < c->n_links; ++l) o->dep_head[l] = head[l] - c->dep_off[l];
+    o->step = h.step;
+    o->arrived = h.arrived;
+    o->inserted = h.inserted;
+    return TS_OK;
+}
+
+ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (!in || !in->cell_id || !in->cell_v || !in->buf_id || !in->buf_v || !in->cursor || !in->dep_head)
+        return fail(TS_ERR_INVALID, "null state array");
+    st = wait_ctx(c, 60000);
+    if (st != TS_OK) return st;
+    const uint32_t vmax = c->params.vmax;
+    const size_t nw = c->n_words;
+    std::vector<uint32_t> occ(nw, 0), vid(nw * 32, 0);
+    std::vector<int8_t> vel(nw * 32, 0);
+    std::vector<uint4> slots(c->n_slots, make_uint4(kSlotEmpty, 0, 0, 0));
+    std::vector<uint8_t> seen(c->n_veh, 0);
+    std::vector<uint32_t> head(c->n_links);
+    for (uint32_t i = 0; i < c->n_veh; ++i)
+        if (in->cursor[i] >= c->route_off[i + 1] - c->route_off[i]) return fail(TS_ERR_INVALID, "cursor past route end");
+    auto on_route = [&](int32_t id, uint32_t l) {
+        return c->route_links[c->route_off[id] + in->cursor[id]] == l;
+    };
+    for (uint32_t l = 0; l < c->n_links; ++l) {
+        const uint32_t nl = c->lanes[l];
+        for (uint32_t k = 0; k < nl; ++k) {
+            const uint64_t cb = c->cell_base[c->lane_base[l] + k];
+            for (uint32_t x = 0; x < c->cells[l]; ++x) {
+                const int32_t id = in->cell_id[cb + x];
+                if (id < 0) continue;
+                if ((uint32_t)id >= c->n_veh || seen[id]) return fail(TS_ERR_INVALID, "bad or repeated vehicle id");
+                if (!on_route(id, l)) return fail(TS_ERR_INVALID, "vehicle not on the link its cursor names");
+                const int8_t v = in->cell_v[cb + x];
+                if (v < 0 || (uint32_t)v > vmax) return fail(TS_ERR_INVALID, "velocity out of range");
+                seen[id] = 1;
+                const size_t w = (size_t)c->wbase[l] + (size_t)(x / 32) * nl + k;
+                occ[w] |= 1u << (x % 32);
+                vel[w * 32 + x % 32] = v;
+                const bool last = in->cursor[id] + 1 == c->route_off[id + 1] - c->route_off[id];
+                vid[w * 32 + x % 32] = (uint32_t)id | (last ? kLastLinkBit : 0u);
+            }
+            const int32_t b = in->buf_id[c->lane_base[l] + k];
+            if (b >= 0) {
+                if (c->ring[l]) return fail(TS_ERR_INVALID, "ring links have no link-end buffer");
+                if ((uint32_t)b >= c->n_veh || seen[b]) return fail(TS_ERR_INVALID, "bad or repeated vehicle id");
+                if (!on_route(b, l)) return fail(TS_ERR_INVALID, "vehicle not on the link its cursor names");
+                const uint32_t len = c->route_off[b + 1] - c->route_off[b];
+                if (in->cursor[b] + 1 >= len) return fail(TS_ERR_INVALID, "buffered vehicle on its last link");
+                const int8_t v = in->buf_v[c->lane_base[l] + k];
+                if (v < 0 || (uint32_t)v > vmax) return fail(TS_ERR_INVALID, "velocity out of range");
+                seen[b] = 1;
+                const uint32_t p = c->route_off[b] + in->cursor[b];
+                const uint32_t fl = (in->cursor[b] + 2 == len) ? kLastLinkBit : 0u;
+                slots[c->bpos[l] + k] = make_uint4((uint32_t)b | fl, c->route_links[p + 1], l, (uint32_t)v | (k << 8));
+            }
+        }
+    }
+    // vehicles on the network must already have left their departure queue
+    for (uint32_t l = 0; l < c->n_links; ++l) {
+        const uint32_t len = c->dep_off[l + 1] - c->dep_off[l];
+        if (in->dep_head[l] > len) return fail(TS_ERR_INVALID, "dep_head beyond queue");
+        head[l] = c->dep_off[l] + in->dep_head[l];
+        for (uint32_t q = head[l]; q < c->dep_off[l + 1]; ++q)
+            if (seen[c->dep_ids[q]]) return fail(TS_ERR_INVALID, "vehicle on the network is still queued");
+    }
+    std::vector<uint2> veh(c->n_veh);
+    for (uint32_t i = 0; i < c->n_veh; ++i) veh[i] = make_uint2(c->route_off[i] + in->cursor[i], c->route_off[i + 1]);
+    st = reset_state(c, in->step, in->arrived, in->inserted);
+    if (st != TS_OK) return st;
+    const int cur = (int)(in->step & 1ull);
+    CK(cudaMemcpy(c->sd.occ[cur], occ.data(), 4 * nw, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->sd.vel[cur], vel.data(), nw * 32, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->sd.vid[cur], vid.data(), 4 * nw * 32, cudaMemcpyHostToDevice));
+    if (c->n_slots) CK(cudaMemcpy(c->sd.slots, slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
+    if (c->n_veh) CK(cudaMemcpy(c->sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->sd.dep_head, head.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    CK(cudaEventRecord(c->ev, c->stream));
+    return TS_OK;
+}
+
+void ts_destroy(ts_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->ev) cudaEventSynchronize(c->ev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    delete c->own;
+    free_list(c, c->veh_allocs);
+    free_list(c, c->allocs);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// ------------------------------------------------------------------ batching
+
+ts_status ts_batch_create(uint32_t capacity, ts_batch **out) {
+    if (!out || capacity == 0) return fail(TS_ERR_INVALID, "bad batch arguments");
+    *out = nullptr;
+    ts_batch *b = new (std::nothrow) ts_batch();
+    if (!b) return fail(TS_ERR_OOM, "host allocation failed");
+    ts_status st = b->w.init(capacity);
+    if (st != TS_OK) {
+        delete b;
+        return st;
+    }
+    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        delete b;
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    cudaEventRecord(b->ev, b->w.cap_stream);
+    *out = b;
+    return TS_OK;
+}
+
+ts_status ts_batch_add(ts_batch *b, ts_ctx *c, uint64_t target_step) {
+    if (!b) return fail(TS_ERR_INVALID, "null batch");
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (c->batch) return fail(TS_ERR_STATE, "context already in a batch");
+    st = wait_ctx(c, 60000);
+    if (st != TS_OK) return st;
+    st = wait_event(b->ev, 60000);  // the table is rewritten below
+    if (st != TS_OK) return st;
+    uint32_t slot = 0;
+    while (slot < b->w.capacity && b->w.members[slot]) ++slot;
+    if (slot == b->w.capacity) return fail(TS_ERR_STATE, "batch is full");
+    CK(cudaMemcpy(&c->sd.ctrl->target, &target_step, sizeof(target_step), cudaMemcpyHostToDevice));
+    b->w.members[slot] = c;
+    b->w.targets[slot] = target_step;
+    c->batch = b;
+    c->stepped = true;
+    return b->w.rebuild();
+}
+
+ts_status ts_batch_remove(ts_batch *b, ts_ctx *c) {
+    if (!b || !c || c->batch != b) return fail(TS_ERR_INVALID, "context is not in this batch");
+    ts_status st = wait_event(b->ev, 60000);
+    if (st != TS_OK) return st;
+    for (uint32_t s = 0; s < b->w.capacity; ++s)
+        if (b->w.members[s] == c) b->w.members[s] = nullptr;
+    c->batch = nullptr;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    c->host_step = h.step;
+    return b->w.rebuild();
+}
+
+ts_status ts_batch_step(ts_batch *b, uint32_t n_steps, void *cuda_stream) {
+    if (!b) return fail(TS_ERR_INVALID, "null batch");
+    if (n_steps == 0) return TS_OK;
+    CK(cudaSetDevice(b->w.device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s) s = b->w.cap_stream;
+    if (s == b->w.cap_stream) return fail(TS_ERR_INVALID, "pass a stream to ts_batch_step");
+    ts_status st = b->w.run(n_steps, s);
+    if (st != TS_OK) return st;
+    CK(cudaEventRecord(b->ev, s));
+    for (ts_ctx *c : b->w.members)
+        if (c) CK(cudaEventRecord(c->ev, s));
+    return TS_OK;
+}
+
+ts_status ts_batch_sync(ts_batch *b, uint32_t timeout_ms) {
+    if (!b) return fail(TS_ERR_INVALID, "null batch");
+    return wait_event(b->ev, timeout_ms);
+}
+
+ts_status ts_ctx_step(ts_ctx *c, uint64_t *step) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!step) return fail(TS_ERR_INVALID, "null output");
+    st = wait_ctx(c, 60000);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    *step = h.step;
+    return TS_OK;
+}
+
+void ts_batch_destroy(ts_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->w.device);
+    if (b->ev) {
+        cudaEventSynchronize(b->ev);
+        cudaEventDestroy(b->ev);
+    }
+    for (ts_ctx *c : b->w.members)
+        if (c) c->batch = nullptr;
+    delete b;
+}
+
+}  // extern "C"

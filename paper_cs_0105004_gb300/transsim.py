@@ -1,0 +1,284 @@
+"""Python binding of the C ABI in include/transsim.h (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library ``libtranssim.so``;
+this module converts numpy arrays and torch streams to the plain pointers
+and handles the ABI takes.  There is no fallback: if the library is missing
+or no CUDA device is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtranssim.so")
+
+STATS_FIELDS = ("step", "active", "buffered", "waiting", "arrived", "lane_changes", "transfers", "inserted",
+                "sum_v", "vehicle_updates", "state_hash")
+STATS_DTYPE = np.dtype([(f, np.uint64) for f in STATS_FIELDS])
+
+TS_OK, TS_ERR_INVALID, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE, TS_ERR_DEVICE_CHECK = range(7)
+_NAMES = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "STATE", 6: "DEVICE_CHECK"}
+
+u32p = ctypes.POINTER(ctypes.c_uint32)
+u64p = ctypes.POINTER(ctypes.c_uint64)
+i32p = ctypes.POINTER(ctypes.c_int32)
+i8p = ctypes.POINTER(ctypes.c_int8)
+u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class TsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"TS_ERR_{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("vmax", ctypes.c_uint32), ("p_threshold", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("lane_change", ctypes.c_uint32), ("debug_checks", ctypes.c_uint32)]
+
+
+class NetworkDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_uint32), ("n_links", ctypes.c_uint32), ("link_from", u32p),
+                ("link_to", u32p), ("link_cells", u32p), ("link_lanes", u32p), ("link_ring", u8p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in STATS_FIELDS]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("cell_id", i32p), ("cell_v", i8p), ("buf_id", i32p), ("buf_v", i8p), ("cursor", u32p),
+                ("dep_head", u32p), ("step", ctypes.c_uint64), ("arrived", ctypes.c_uint64),
+                ("inserted", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+# The C ABI: name -> (restype, argtypes)
+_API = {
+    "ts_create_network": (ctypes.c_int, [ctypes.POINTER(NetworkDesc), ctypes.POINTER(Params),
+                                         ctypes.POINTER(Allocator), ctypes.POINTER(ctypes.c_void_p)]),
+    "ts_load_vehicles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, u32p, u32p, u32p]),
+    "ts_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "ts_read_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_uint32]),
+    "ts_read_stats_range": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                           ctypes.c_uint32]),
+    "ts_state_sizes": (ctypes.c_int, [ctypes.c_void_p, u64p, u32p, u32p, u32p]),
+    "ts_read_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_uint32]),
+    "ts_write_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State)]),
+    "ts_footprint_bytes": (ctypes.c_size_t, [ctypes.POINTER(NetworkDesc), ctypes.c_uint32, ctypes.c_uint64]),
+    "ts_last_error": (ctypes.c_char_p, []),
+    "ts_destroy": (None, [ctypes.c_void_p]),
+    "ts_batch_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
+    "ts_batch_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "ts_batch_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ts_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "ts_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_ctx_step": (ctypes.c_int, [ctypes.c_void_p, u64p]),
+    "ts_batch_destroy": (None, [ctypes.c_void_p]),
+    "ts_set_tile_columns": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_launches_per_step": (ctypes.c_uint32, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libtranssim.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _API.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_API)
+
+
+def _check(rc):
+    if rc != TS_OK:
+        raise TsError(rc, lib().ts_last_error().decode(errors="replace"))
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class _NetArrays:
+    def __init__(self, net):
+        self.lf = np.ascontiguousarray(net.link_from, np.uint32)
+        self.lt = np.ascontiguousarray(net.link_to, np.uint32)
+        self.lc = np.ascontiguousarray(net.link_cells, np.uint32)
+        self.ll = np.ascontiguousarray(net.link_lanes, np.uint32)
+        self.lr = np.ascontiguousarray(net.link_ring, np.uint8)
+        self.desc = NetworkDesc(net.n_nodes, net.n_links, _p(self.lf, ctypes.c_uint32), _p(self.lt, ctypes.c_uint32),
+                                _p(self.lc, ctypes.c_uint32), _p(self.ll, ctypes.c_uint32), _p(self.lr, ctypes.c_uint8))
+
+
+def footprint_bytes(scenario) -> int:
+    na = _NetArrays(scenario.net)
+    return int(lib().ts_footprint_bytes(ctypes.byref(na.desc), scenario.demand.n,
+                                        int(scenario.demand.route_offsets[-1])))
+
+
+def _torch_allocator():
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    return Allocator(fa, ff, None), (fa, ff)
+
+
+class Simulation:
+    """One scenario on the current CUDA device (wraps a ts_ctx)."""
+
+    def __init__(self, scenario, use_torch_allocator: bool = False, tile_columns: Optional[int] = None):
+        L = lib()
+        self.scenario = scenario
+        net, dem = scenario.net, scenario.demand
+        self._net = _NetArrays(net)
+        params = Params(scenario.vmax, scenario.p_threshold, scenario.seed, scenario.lane_change, 0)
+        self._alloc_keep = None
+        alloc = None
+        if use_torch_allocator:
+            a, keep = _torch_allocator()
+            self._alloc_keep = (a, keep)
+            alloc = ctypes.byref(a)
+        h = ctypes.c_void_p()
+        _check(L.ts_create_network(ctypes.byref(self._net.desc), ctypes.byref(params), alloc, ctypes.byref(h)))
+        self.h = h
+        if tile_columns is not None:
+            _check(L.ts_set_tile_columns(self.h, tile_columns))
+        dep = np.ascontiguousarray(dem.depart_step, np.uint32)
+        off = np.ascontiguousarray(dem.route_offsets, np.uint32)
+        links = np.ascontiguousarray(dem.route_links, np.uint32)
+        _check(L.ts_load_vehicles(self.h, dem.n, _p(dep, ctypes.c_uint32), _p(off, ctypes.c_uint32),
+                                  _p(links, ctypes.c_uint32)))
+        cells, lanes, veh, nl = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(L.ts_state_sizes(self.h, ctypes.byref(cells), ctypes.byref(lanes), ctypes.byref(veh), ctypes.byref(nl)))
+        self.n_lane_cells, self.n_lanes, self.n_veh, self.n_links = cells.value, lanes.value, veh.value, nl.value
+        if scenario.init is not None:
+            self.write_state(scenario.init)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile_columns(self, cols: int):
+        _check(lib().ts_set_tile_columns(self.h, cols))
+
+    def step(self, n: int, stream=None):
+        s = _stream_handle(stream)
+        _check(lib().ts_step(self.h, n, ctypes.c_void_p(s) if s else None))
+
+    def stats(self, timeout_ms: int = 600000) -> dict:
+        st = Stats()
+        _check(lib().ts_read_stats(self.h, ctypes.byref(st), timeout_ms))
+        return {f: getattr(st, f) for f in STATS_FIELDS}
+
+    def stats_range(self, first: int, n: int, timeout_ms: int = 600000) -> np.ndarray:
+        out = np.zeros(n, STATS_DTYPE)
+        _check(lib().ts_read_stats_range(self.h, first, n, out.ctypes.data_as(ctypes.c_void_p), timeout_ms))
+        return out
+
+    def current_step(self) -> int:
+        s = ctypes.c_uint64()
+        _check(lib().ts_ctx_step(self.h, ctypes.byref(s)))
+        return s.value
+
+    def read_state(self, timeout_ms: int = 600000) -> dict:
+        s = dict(cell_id=np.empty(self.n_lane_cells, np.int32), cell_v=np.empty(self.n_lane_cells, np.int8),
+                 buf_id=np.empty(self.n_lanes, np.int32), buf_v=np.empty(self.n_lanes, np.int8),
+                 cursor=np.empty(self.n_veh, np.uint32), dep_head=np.empty(self.n_links, np.uint32))
+        st = State(_p(s["cell_id"], ctypes.c_int32), _p(s["cell_v"], ctypes.c_int8), _p(s["buf_id"], ctypes.c_int32),
+                   _p(s["buf_v"], ctypes.c_int8), _p(s["cursor"], ctypes.c_uint32), _p(s["dep_head"], ctypes.c_uint32),
+                   0, 0, 0)
+        _check(lib().ts_read_state(self.h, ctypes.byref(st), timeout_ms))
+        s["step"], s["arrived"], s["inserted"] = st.step, st.arrived, st.inserted
+        return s
+
+    def write_state(self, init):
+        a = [np.ascontiguousarray(init.cell_id, np.int32), np.ascontiguousarray(init.cell_v, np.int8),
+             np.ascontiguousarray(init.buf_id, np.int32), np.ascontiguousarray(init.buf_v, np.int8),
+             np.ascontiguousarray(init.cursor, np.uint32), np.ascontiguousarray(init.dep_head, np.uint32)]
+        st = State(_p(a[0], ctypes.c_int32), _p(a[1], ctypes.c_int8), _p(a[2], ctypes.c_int32), _p(a[3], ctypes.c_int8),
+                   _p(a[4], ctypes.c_uint32), _p(a[5], ctypes.c_uint32), init.step, init.arrived, init.inserted)
+        _check(lib().ts_write_state(self.h, ctypes.byref(st)))
+
+
+class Batch:
+    """Many scenarios advanced by the same kernel launches (wraps a ts_batch)."""
+
+    def __init__(self, capacity: int):
+        h = ctypes.c_void_p()
+        _check(lib().ts_batch_create(capacity, ctypes.byref(h)))
+        self.h = h
+
+    def add(self, sim: Simulation, target_step: int):
+        _check(lib().ts_batch_add(self.h, sim.h, target_step))
+
+    def remove(self, sim: Simulation):
+        _check(lib().ts_batch_remove(self.h, sim.h))
+
+    def step(self, n: int, stream):
+        s = _stream_handle(stream)
+        _check(lib().ts_batch_step(self.h, n, ctypes.c_void_p(s)))
+
+    def sync(self, timeout_ms: int = 600000):
+        _check(lib().ts_batch_sync(self.h, timeout_ms))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ts_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launches_per_step() -> int:
+    return int(lib().ts_launches_per_step())

@@ -1,0 +1,210 @@
+"""GPU path vs the CPU oracle, bit-exact, through the C ABI.
+
+Every comparison is exact: all arithmetic of the step is integer (cells,
+velocities, 32-bit Philox words against an integer threshold, 64-bit digest
+sums), so the CUDA library and the oracle must agree on every field of every
+step and on the full state.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import check_invariants, make_scenario
+from paper_cs_0105004_gb300 import transsim as T
+from paper_cs_0105004_gb300.inputs import networks as N
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = T.STATS_FIELDS
+
+
+def _cmp_stats(a, b, where=""):
+    for f in FIELDS:
+        if not np.array_equal(a[f], b[f]):
+            bad = np.nonzero(a[f] != b[f])[0]
+            i = int(bad[0])
+            raise AssertionError(f"{where}: field {f} differs first at row {i} (step {int(a['step'][i])}): "
+                                 f"gpu {int(a[f][i])} oracle {int(b[f][i])}")
+
+
+def _cmp_state(g, o, where=""):
+    for k in ("cell_id", "cell_v", "buf_id", "buf_v", "cursor", "dep_head"):
+        if not np.array_equal(g[k], o[k]):
+            i = int(np.nonzero(g[k] != o[k])[0][0])
+            raise AssertionError(f"{where}: state {k} differs at {i}: gpu {g[k][i]} oracle {o[k][i]}")
+    for k in ("step", "arrived", "inserted"):
+        assert g[k] == o[k], (where, k, g[k], o[k])
+
+
+def run_parity(sc, steps, chunk=None, state_every=None, tile_columns=None):
+    sim = T.Simulation(sc, tile_columns=tile_columns)
+    orc = oracle.Oracle(sc)
+    t0 = sc.init.step if sc.init is not None else 0
+    chunk = chunk or min(steps, 4000)
+    done = 0
+    while done < steps:
+        n = min(chunk, steps - done)
+        sim.step(n)
+        g = sim.stats_range(t0 + done, n)
+        o = orc.step(n)
+        _cmp_stats(g, o, f"{sc.name} steps {t0 + done}..{t0 + done + n - 1}")
+        done += n
+        if state_every and (done % state_every == 0 or done == steps):
+            _cmp_state(sim.read_state(), orc.get_state(), f"{sc.name} after step {t0 + done - 1}")
+    _cmp_state(sim.read_state(), orc.get_state(), f"{sc.name} final")
+    sim.close()
+    return o
+
+
+# ------------------------------------------------------------------ hand-built cases
+
+def test_hand_cases_match_oracle():
+    cases = [
+        make_scenario([(0, 1, 200, 1)], 2, [[0]], [0]),
+        make_scenario([(0, 1, 12, 1), (1, 2, 12, 1)], 3, [[0, 1]], [0]),
+        make_scenario([(0, 2, 12, 1), (1, 2, 12, 1), (2, 3, 12, 1)], 4, [[0, 2], [1, 2]], [0, 0]),
+        make_scenario([(0, 1, 40, 2)], 2, [[0], [0]], [0, 0], placed=[(0, 0, 0, 10, 3), (1, 0, 0, 12, 0)]),
+        make_scenario([(0, 1, 40, 2)], 2, [[0], [0]], [0, 0], placed=[(0, 0, 0, 10, 3), (1, 0, 0, 12, 0)],
+                      start_step=1),
+        make_scenario([(0, 1, 20, 2), (1, 2, 20, 3), (3, 1, 20, 1)], 4, [[0, 1], [2, 1]], [0, 0],
+                      bufs=[(0, 0, 1, 3)], placed=[(1, 2, 0, 5, 0)]),
+    ]
+    for sc in cases:
+        run_parity(sc, 40, chunk=1, state_every=1)
+
+
+def test_single_step_granularity_small_grid():
+    sc = N.small_grid_scenario(3, 2, 20, n_trips=80, window=40, steps=120, gen_seed=2, seed=5)
+    run_parity(sc, 120, chunk=1, state_every=1)
+
+
+# ------------------------------------------------------------------ rings (Sec. 5 circle roads)
+
+def _ring(L, n, lanes, p, vmax=5, seed=3, rng_seed=0):
+    net = N.ring_network(L, lanes)
+    dem, init = N.ring_initial_state(net, n, "random", 0, np.random.default_rng(rng_seed))
+    return N.Scenario(f"ring{L}x{lanes}", net, dem, 0, seed, vmax, p, 1, init)
+
+
+@pytest.mark.parametrize("L,lanes,rho", [(64, 1, 0.3), (320, 1, 0.2), (320, 3, 0.25), (9984, 1, 0.15),
+                                         (9984, 3, 0.3), (4128, 2, 0.5)])
+def test_rings_match_oracle(L, lanes, rho):
+    # 9984 and 4128 cells are longer than one tile: the ring is split into
+    # partial tiles whose halos wrap around the ring
+    sc = _ring(L, int(rho * L * lanes), lanes, N.P_THRESHOLD_0_2, rng_seed=L + lanes)
+    run_parity(sc, 300, chunk=100, state_every=100)
+
+
+@pytest.mark.parametrize("vmax", [1, 3, 9, 15])
+def test_rings_other_vmax(vmax):
+    sc = _ring(4160, 2000, 2, N.P_THRESHOLD_0_2, vmax=vmax, rng_seed=vmax)
+    run_parity(sc, 200, chunk=50, state_every=50)
+
+
+# ------------------------------------------------------------------ grids and planar networks
+
+@pytest.mark.parametrize("case", [(3, 1, 20, 100, 1, 5), (4, 2, 25, 400, 2, 5), (4, 3, 15, 500, 3, 5),
+                                  (5, 2, 60, 2000, 4, 5), (3, 2, 40, 300, 5, 7), (4, 2, 33, 300, 6, 15)])
+def test_small_grids_match_oracle(case):
+    side, lanes, cells, trips, seed, vmax = case
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 200, 800, gen_seed=seed, seed=seed * 7 + 1, vmax=vmax)
+    run_parity(sc, 800, chunk=200, state_every=200)
+
+
+def test_long_links_partial_tiles():
+    # links longer than a tile (64 columns = 2048 cells), including tails that
+    # would leave fewer than 2*vmax+1 cells after a split
+    cells = [2048 + 5, 4096 + 3, 2100, 64 * 32 * 2 + 1, 31, 3, 70]
+    links, routes = [], []
+    n = len(cells) + 1
+    for i, c in enumerate(cells):
+        links.append((i, i + 1, c, 1 + i % 3))
+        links.append((i + 1, i, c, 1 + (i + 1) % 3))
+    rng = np.random.default_rng(11)
+    dep = []
+    for v in range(600):
+        a, b = sorted(rng.choice(n, 2, replace=False))
+        if rng.random() < 0.5:
+            routes.append([2 * i for i in range(a, b)])
+        else:
+            routes.append([2 * i + 1 for i in range(b - 1, a - 1, -1)])
+        dep.append(int(rng.integers(0, 300)))
+    sc = make_scenario(links, n, routes, dep, steps=1500, seed=77, p=N.P_THRESHOLD_0_2)
+    for tc in (64, 8):
+        run_parity(sc, 1500, chunk=500, state_every=500, tile_columns=tc)
+
+
+def test_config0_full_run():
+    sc = N.config0()
+    run_parity(sc, sc.steps, chunk=900, state_every=900)
+
+
+def test_config0_tile_shapes_identical():
+    sc = N.config0()
+    ref = None
+    for tc in (8, 16, 32, 64, 128):
+        sim = T.Simulation(sc, tile_columns=tc)
+        sim.step(1200)
+        st = sim.stats_range(0, 1200)
+        if ref is None:
+            ref = st
+        else:
+            _cmp_stats(st, ref, f"tile columns {tc}")
+        sim.close()
+
+
+def test_planar_network_window():
+    sc = N._planar_config("planar-small", 900, 1060, 20000, 5, steps=1200)
+    run_parity(sc, 1200, chunk=400, state_every=400)
+
+
+def test_config1_first_window():
+    # Portland-shaped network, full size, first 1,200 steps (the oracle's
+    # share of the test); later steps are covered by the invariants test
+    sc = N.config1()
+    run_parity(sc, 1200, chunk=400, state_every=1200)
+
+
+def test_invariants_hold_on_gpu_config1():
+    sc = N.config1()
+    sim = T.Simulation(sc)
+    prev = None
+    for k in range(6):
+        sim.step(1000 if k else 3000)
+        st = sim.stats()
+        s = sim.read_state()
+        prev = check_invariants(sc, s, st, None)
+    sim.close()
+
+
+# ------------------------------------------------------------------ batching
+
+def test_batch_equals_alone():
+    scs = [N.small_grid_scenario(3 + i % 3, 1 + i % 3, 20 + 5 * i, 100 + 40 * i, 100, 400, gen_seed=20 + i,
+                                 seed=100 + i) for i in range(6)]
+    alone = []
+    for sc in scs:
+        sim = T.Simulation(sc)
+        sim.step(400)
+        alone.append(sim.stats_range(0, 400))
+        sim.close()
+    import torch
+    stream = torch.cuda.Stream()
+    b = T.Batch(8)
+    sims = [T.Simulation(sc) for sc in scs]
+    targets = [400, 400, 250, 400, 123, 400]
+    for s, tgt in zip(sims, targets):
+        b.add(s, tgt)
+    b.step(450, stream)
+    b.sync()
+    for s, tgt, ref in zip(sims, targets, alone):
+        assert s.current_step() == tgt
+        _cmp_stats(s.stats_range(0, tgt), ref[:tgt], "batch member")
+    # continue two members alone after removing them from the batch
+    b.remove(sims[2])
+    sims[2].step(150)
+    sc2 = scs[2]
+    full = T.Simulation(sc2)
+    full.step(400)
+    _cmp_stats(sims[2].stats_range(250, 150), full.stats_range(250, 150), "resumed member")
+    b.close()

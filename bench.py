@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the TRANSIMS cellular-automaton step on one GB300.
+
+One benchmark step is one whole simulation job: the Portland-shaped
+network (20,024 directed links, 8,500 nodes, 300,000 trips with
+shortest-path routes) simulated for 10,800 one-second time steps from the
+empty network, i.e. 3 simulated hours with lane change, velocity update,
+move and node transfer for every vehicle in every step.  Inputs are resident
+in device memory when the timed region starts; each timed job begins with a
+device-side reset to the empty network.
+
+Printed metric: vehicle-updates/s (vehicles that went through the velocity
+update, summed over steps, per second), with the multiple of real time
+(simulated seconds per wall-clock second, the paper's real-time ratio of
+Sec. 8) alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the plain CPU oracle (single thread) on bounded
+samples of the same workload.  With N > 1 (torchrun) every rank runs an
+independent replica of the job; there is no exchange between GPUs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vehicle-updates/s"
+L2_FLUSH_BYTES = 512 << 20
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _workload(name):
+    from paper_cs_0105004_gb300.inputs import networks as N
+    sc = {"config1": N.config1, "config2": N.config2, "config0": N.config0}[name]()
+    desc = {
+        "config0": "5x5 grid, 80 links of 2 lanes x 60 cells, 2,000 trips",
+        "config1": "Portland-shaped planar network, 20,024 links, 8,500 nodes, 300,000 trips",
+        "config2": "scale-up planar network, 200,000 links, 85,000 nodes, 2,000,000 trips",
+    }[name]
+    return sc, desc
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _cpu_baseline(sc, sample_steps):
+    """The oracle as it stands, single thread, on the first sample_steps steps."""
+    import oracle
+    orc = oracle.Oracle(sc)
+    t0 = time.perf_counter()
+    st = orc.step(sample_steps)
+    dt = time.perf_counter() - t0
+    upd = int(st["vehicle_updates"].sum())
+    orc.close()
+    return {"value": upd / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{sc.name} steps 0..{sample_steps - 1} from the empty network, one thread, "
+                      f"{upd} vehicle updates in {dt:.1f} s",
+            "x_real_time": sample_steps / dt}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the plain CPU oracle timed on bounded samples."""
+    if rank != 0:
+        return
+    import oracle
+    sc, desc = _workload(args.workload)
+    orc = oracle.Oracle(sc)
+    per = args.ref_sample_steps
+    for _ in range(args.warmup):
+        orc.step(per)
+    upd, dt = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = orc.step(per)
+        dt += time.perf_counter() - t0
+        upd += int(st["vehicle_updates"].sum())
+    value = upd / dt
+    sample = (f"{sc.name}: {args.steps} samples of {per} consecutive steps after {args.warmup * per} warm-up "
+              f"steps from the empty network, one thread")
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "x_real_time": per * args.steps / dt,
+            "config": {"workload": desc, "steps_per_sample": per},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_cs_0105004_gb300 import transsim as T
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    sc, desc = _workload(args.workload)
+    steps_per_job = sc.steps if args.job_steps is None else args.job_steps
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    sim = T.Simulation(sc)
+    net = sc.net
+    C = net.n_lane_cells
+
+    def job(s):
+        sim.reset(s)
+        sim.step(steps_per_job, s)
+
+    # warm-up jobs (also capture the CUDA graphs)
+    ref_tot = None
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            job(stream)
+        stream.synchronize()
+        tot = sim.totals()
+        if ref_tot is not None and tot != ref_tot:
+            raise RuntimeError("two runs of the same job differ")
+        ref_tot = tot
+
+    sampler = ClockSampler(local_rank)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.start()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # evict the L2 before every job
+            starts[k].record(stream)
+            job(stream)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot = sim.totals()
+    if ref_tot is not None and tot != ref_tot:
+        raise RuntimeError("timed run differs from the warm-up run")
+    job_ms = float(np.mean(times_ms))
+    updates = tot["vehicle_updates"]
+    # max over ranks of the timed region, sum of the work
+    t_region = sum(times_ms) / 1000.0
+    work = float(updates) * args.steps
+    if dist:
+        tt = torch.tensor([t_region], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ww = torch.tensor([work], dtype=torch.float64, device=dev)
+        dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+        t_region, work = float(tt.item()), float(ww.item())
+    value = work / t_region
+
+    # per-kernel durations with CUDA events on the launching stream (one extra job)
+    sim.reset(stream)
+    link_ms, node_ms = sim.step_timed(steps_per_job, stream)
+    prof_tot = sim.totals()
+    if prof_tot != tot:
+        raise RuntimeError("profiled run differs from the timed run")
+    # algorithmic bytes: link kernel reads+writes v (1 B) and id (4 B) of every
+    # vehicle and one occupancy bit per lane-cell; node kernel ~20 B per transfer
+    # and ~10 B per insertion
+    link_bytes = 10.0 * updates + 0.25 * C * steps_per_job
+    node_bytes = 20.0 * tot["transfers"] + 10.0 * tot["inserted"]
+    link_s = float(link_ms.sum()) / 1000.0
+    node_s = float(node_ms.sum()) / 1000.0
+    peak, peak_kind = _peaks()
+    achieved = link_bytes / link_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "link_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": args.traffic,
+                "avg_launch_us": 1e3 * float(link_ms.mean()),
+                "algorithmic_bytes_per_launch": link_bytes / steps_per_job,
+                "share_of_step_time": link_s / (link_s + node_s),
+                "node_kernel": {"achieved": node_bytes / node_s / 1e9, "avg_launch_us": 1e3 * float(node_ms.mean())}}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_jobs > 0 and rank == 0:
+        dem = sc.demand
+        h2d = (net.link_from.nbytes + net.link_to.nbytes + net.link_cells.nbytes + net.link_lanes.nbytes
+               + net.link_ring.nbytes + dem.depart_step.nbytes + dem.route_offsets.nbytes + dem.route_links.nbytes)
+        d2h = 7 * 8
+        times = []
+        for k in range(args.e2e_jobs + 1):
+            t0 = time.perf_counter()
+            s2 = T.Simulation(sc)
+            s2.step(steps_per_job)
+            t2 = s2.totals()
+            s2.close()
+            dt = time.perf_counter() - t0
+            if t2 != tot:
+                raise RuntimeError("end-to-end run differs")
+            if k > 0:
+                times.append(dt)
+        e2e = {"value": updates / float(np.mean(times)), "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": d2h, "seconds_per_job": float(np.mean(times))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(sc, args.cpu_sample_steps)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": job_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "x_real_time": steps_per_job / (job_ms / 1000.0),
+                "config": {"workload": desc, "steps_per_job": steps_per_job, "links": net.n_links,
+                           "nodes": net.n_nodes, "trips": sc.demand.n, "lane_cells": C,
+                           "vehicle_updates_per_job": updates, "l2": "flushed (512 MB write) before every job; "
+                           "the simulation state stays resident across the steps of a job",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "bit_exact_hash": str(tot["last_state_hash"])},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * (2 * steps_per_job + 1),
+                "clocks": clocks, "wall_s_timed_region": wall}
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2"])
+    ap.add_argument("--job-steps", type=int, default=None, help="steps per job (default: the config's)")
+    ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=1800)
+    ap.add_argument("--ref-sample-steps", type=int, default=300)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per link_kernel launch from an ncu capture of this kernel")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

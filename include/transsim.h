@@ -80,7 +80,7 @@ typedef struct {
 
 /* Road network: directed links between nodes.  Link l runs from node
  * link_from[l] to node link_to[l], has link_cells[l] cells of 7.5 m
- * (>= 2*vmax+2) and link_lanes[l] lanes (1..4).  link_ring may be NULL; a
+ * (1 .. 2^24) and link_lanes[l] lanes (1..4).  link_ring may be NULL; a
  * link with link_ring[l] = 1 is a periodic circle road (Sec. 5) with no
  * nodes: its from/to are ignored, it must not appear in a multi-link route,
  * and its cell count must be a multiple of 32.  Intersection priority is
@@ -105,6 +105,14 @@ typedef struct {
     uint64_t step, active, buffered, waiting, arrived, lane_changes, transfers, inserted, sum_v,
         vehicle_updates, state_hash;
 } ts_stats;
+
+/* Totals since the last ts_load_vehicles / ts_reset / ts_write_state:
+ * steps run, vehicle updates, lane changes and transfers summed over those
+ * steps; inserted and arrived are the cumulative counts of the state;
+ * last_state_hash is the digest after the last step. */
+typedef struct {
+    uint64_t steps, vehicle_updates, lane_changes, transfers, inserted, arrived, last_state_hash;
+} ts_totals;
 
 /* Optional device-memory provider (for example a framework's caching
  * allocator).  alloc returns device memory of at least `bytes` bytes, 256-byte
@@ -154,6 +162,17 @@ ts_status ts_load_vehicles(ts_ctx *ctx, uint32_t n, const uint32_t *host_depart_
  * graphs of the per-step kernels). */
 ts_status ts_step(ts_ctx *ctx, uint32_t n_steps, void *cuda_stream);
 
+/* Enqueues a return to the empty network at step 0 (all travellers back
+ * in their departure queues) on cuda_stream, without host transfers. */
+ts_status ts_reset(ts_ctx *ctx, void *cuda_stream);
+
+/* Runs n_steps steps with plain launches (no graph) and a CUDA event around
+ * each kernel; waits for them and writes the per-step durations of the
+ * link kernel and the node kernel to host arrays link_ms[n], node_ms[n].
+ * For measurement only. */
+ts_status ts_step_timed(ts_ctx *ctx, uint32_t n_steps, void *cuda_stream, float *host_link_ms,
+                        float *host_node_ms);
+
 /* Waits (at most timeout_ms) for the context's queued work, then returns
  * the statistics of the last completed step.  TS_ERR_STATE before the first
  * step, TS_ERR_TIMEOUT if the wait runs out. */
@@ -163,6 +182,9 @@ ts_status ts_read_stats(ts_ctx *ctx, ts_stats *out, uint32_t timeout_ms);
  * keeps the last 4096 steps).  TS_ERR_STATE if a step is not available. */
 ts_status ts_read_stats_range(ts_ctx *ctx, uint64_t first_step, uint32_t n, ts_stats *out,
                               uint32_t timeout_ms);
+
+/* Waits (bounded) and returns the run totals (see ts_totals). */
+ts_status ts_read_totals(ts_ctx *ctx, ts_totals *out, uint32_t timeout_ms);
 
 /* Number of lane-cells, lanes, vehicles and links of the canonical state. */
 ts_status ts_state_sizes(const ts_ctx *ctx, uint64_t *n_lane_cells, uint32_t *n_lanes,
@@ -197,15 +219,15 @@ ts_status ts_batch_create(uint32_t capacity, ts_batch **out);
 ts_status ts_batch_add(ts_batch *b, ts_ctx *ctx, uint64_t target_step);
 ts_status ts_batch_remove(ts_batch *b, ts_ctx *ctx);
 ts_status ts_batch_step(ts_batch *b, uint32_t n_steps, void *cuda_stream);
-/* Waits (bounded) for queued batch work; *done_mask_words receives one bit
- * per member slot that reached its target. */
+/* Waits (bounded) for the batch's queued work. */
 ts_status ts_batch_sync(ts_batch *b, uint32_t timeout_ms);
 /* Current step of a member (after ts_batch_sync). */
 ts_status ts_ctx_step(ts_ctx *ctx, uint64_t *step);
 void ts_batch_destroy(ts_batch *b);
 
-/* Kernel launch shape: columns of 32 cells per link tile (32..128). */
-ts_status ts_set_tile_columns(ts_ctx *ctx, uint32_t columns);
+/* Kernel launch shape: occupancy words (32-cell columns times lanes) per
+ * link tile, 8..128 (default 128).  Results do not depend on it. */
+ts_status ts_set_tile_words(ts_ctx *ctx, uint32_t words);
 
 /* Number of kernel launches one time step of this context enqueues. */
 uint32_t ts_launches_per_step(void);

@@ -29,9 +29,9 @@ ts_status cuda_fail(cudaError_t e, const char *what) {
     return fail(TS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define CK(call)                                         \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
@@ -42,7 +42,8 @@ ts_status wait_event(cudaEvent_t ev, uint32_t timeout_ms) {
         const cudaError_t e = cudaEventQuery(ev);
         if (e == cudaSuccess) return TS_OK;
         if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
-        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        const auto ms =
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
         if ((uint64_t)ms >= timeout_ms) return fail(TS_ERR_TIMEOUT, "timed out waiting for the device");
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
@@ -50,20 +51,19 @@ ts_status wait_event(cudaEvent_t ev, uint32_t timeout_ms) {
 
 }  // namespace
 
-// ------------------------------------------------------------------ world (a set of scenarios stepped together)
+// ------------------------------------------------------------------ world (scenarios stepped together)
 
 struct World {
     int device = 0;
     cudaStream_t cap_stream = nullptr;  // used only for graph capture
     uint32_t capacity = 0;
     std::vector<ts_ctx *> members;      // slot -> context
-    std::vector<uint64_t> targets;
     ScenDev *d_table = nullptr;
-    WorldDev *d_wd = nullptr;
-    uint4 *d_link_tiles = nullptr, *d_node_tiles = nullptr;
+    LinkTile *d_link_tiles = nullptr;
+    uint4 *d_node_tiles = nullptr;
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
-    int grid_l = 0, grid_n = 0;
+    int grid_l = 1, grid_n = 1;
     std::map<uint32_t, cudaGraphExec_t> graphs;
     ~World();
     ts_status init(uint32_t cap);
@@ -80,27 +80,31 @@ struct ts_ctx {
     bool has_alloc = false;
     ts_params params{};
     // network (host copies)
-    uint32_t n_nodes = 0, n_links = 0, n_ring = 0, n_nodes_total = 0;
-    std::vector<uint32_t> from, to, cells, lanes, ncols, wbase, bpos, lane_base;
+    uint32_t n_nodes = 0, n_links = 0, n_ring = 0;
+    std::vector<uint32_t> from, to, cells, lanes, ncols, wbase, bpos, lane_base, col_in_tile;
     std::vector<uint8_t> ring;
     std::vector<uint64_t> cell_base;
-    std::vector<uint32_t> node_in_off, node_out_off, node_out_link;
+    std::vector<uint32_t> node_in_off;
     uint32_t n_words = 0, n_slots = 0, n_lanes = 0;
     uint64_t n_lane_cells = 0;
-    uint32_t tile_cols = 64;
-    std::vector<uint4> link_tiles, node_tiles;
+    uint32_t tile_words = kTileWords;
+    std::vector<LinkTile> link_tiles;
+    std::vector<uint4> node_tiles;
+    uint32_t n_sub = 1, sub_cap = 1;  // statistics sub-records per step (used, allocated)
     // vehicles
     bool loaded = false;
     uint32_t n_veh = 0;
-    std::vector<uint32_t> route_off, route_links, depart, dep_off, dep_ids;
+    std::vector<uint32_t> route_off, route_links, depart, depart_sorted, dep_off, dep_ids;
     // device
     ScenDev sd{};
-    std::vector<std::pair<void *, size_t>> allocs;
-    std::vector<std::pair<void *, size_t>> veh_allocs;
+    uint4 *d_lk_info = nullptr;
+    uint32_t *d_link_exit0 = nullptr;  // all buffers empty, for resets
+    uint2 *d_veh0 = nullptr;           // route starts, for resets
+    uint32_t *d_dep_head0 = nullptr;   // queue starts, for resets
+    std::vector<std::pair<void *, size_t>> allocs, veh_allocs;
     World *own = nullptr;
     ts_batch *batch = nullptr;
     uint64_t host_step = 0;
-    bool stepped = false;
     bool sticky = false;
 
     void *dalloc(size_t bytes) {
@@ -129,7 +133,6 @@ struct ts_batch {
 World::~World() {
     drop_graphs();
     if (d_table) cudaFree(d_table);
-    if (d_wd) cudaFree(d_wd);
     if (d_link_tiles) cudaFree(d_link_tiles);
     if (d_node_tiles) cudaFree(d_node_tiles);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -143,72 +146,70 @@ void World::drop_graphs() {
 ts_status World::init(uint32_t cap) {
     capacity = cap;
     members.assign(cap, nullptr);
-    targets.assign(cap, 0);
     CK(cudaGetDevice(&device));
     CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     CK(cudaMalloc(&d_table, sizeof(ScenDev) * cap));
     CK(cudaMemset(d_table, 0, sizeof(ScenDev) * cap));
-    CK(cudaMalloc(&d_wd, sizeof(WorldDev)));
-    WorldDev wd{0u, 0u, 0u, cap};
-    CK(cudaMemcpy(d_wd, &wd, sizeof(wd), cudaMemcpyHostToDevice));
     return TS_OK;
 }
 
-// Re-uploads the scenario table and the concatenated tile lists (synchronous).
+// Re-uploads the scenario table and the concatenated tile lists
+// (synchronous; callers make sure no work of this world is in flight).
 ts_status World::rebuild() {
     std::vector<ScenDev> table(capacity);
-    std::vector<uint4> lt, nt;
+    std::vector<LinkTile> lt;
+    std::vector<uint4> nt;
     for (uint32_t s = 0; s < capacity; ++s) {
         memset(&table[s], 0, sizeof(ScenDev));
         ts_ctx *c = members[s];
         if (!c) continue;
         table[s] = c->sd;
-        for (uint4 t : c->link_tiles) { t.x = s; lt.push_back(t); }
-        for (uint4 t : c->node_tiles) { t.x = s; nt.push_back(t); }
+        for (LinkTile t : c->link_tiles) {
+            t.a.x = s;
+            lt.push_back(t);
+        }
+        for (uint4 t : c->node_tiles) {
+            t.x = s;
+            nt.push_back(t);
+        }
     }
+    drop_graphs();
     CK(cudaMemcpy(d_table, table.data(), sizeof(ScenDev) * capacity, cudaMemcpyHostToDevice));
     if (lt.size() > link_cap) {
-        drop_graphs();  // captured launches hold the old pointer
         if (d_link_tiles) cudaFree(d_link_tiles);
+        d_link_tiles = nullptr;
         link_cap = std::max<size_t>(lt.size(), 2 * link_cap);
-        CK(cudaMalloc(&d_link_tiles, sizeof(uint4) * link_cap));
+        CK(cudaMalloc(&d_link_tiles, sizeof(LinkTile) * link_cap));
     }
     if (nt.size() > node_cap) {
-        drop_graphs();
         if (d_node_tiles) cudaFree(d_node_tiles);
+        d_node_tiles = nullptr;
         node_cap = std::max<size_t>(nt.size(), 2 * node_cap);
         CK(cudaMalloc(&d_node_tiles, sizeof(uint4) * node_cap));
     }
-    if (!lt.empty()) CK(cudaMemcpy(d_link_tiles, lt.data(), sizeof(uint4) * lt.size(), cudaMemcpyHostToDevice));
+    if (!lt.empty()) CK(cudaMemcpy(d_link_tiles, lt.data(), sizeof(LinkTile) * lt.size(), cudaMemcpyHostToDevice));
     if (!nt.empty()) CK(cudaMemcpy(d_node_tiles, nt.data(), sizeof(uint4) * nt.size(), cudaMemcpyHostToDevice));
     n_link_tiles = (uint32_t)lt.size();
     n_node_tiles = (uint32_t)nt.size();
-    WorldDev wd{0u, n_link_tiles, n_node_tiles, capacity};
-    CK(cudaMemcpy(d_wd, &wd, sizeof(wd), cudaMemcpyHostToDevice));
-    const int gl = std::max(1, std::min<int>((int)n_link_tiles, max_link_blocks()));
-    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
-    if (gl != grid_l || gn != grid_n) {
-        drop_graphs();
-        grid_l = gl;
-        grid_n = gn;
-    }
+    grid_l = std::max(1, std::min<int>((int)n_link_tiles, max_link_blocks()));
+    grid_n = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
     return TS_OK;
 }
 
-// Enqueues n steps of every active member on stream s as CUDA graphs of up
-// to 32 steps (two kernel nodes per step).
+// Enqueues n steps of every active member on stream s, as CUDA graphs of up
+// to kChunk steps: two kernels per step, then the chunk-closing kernel.
 ts_status World::run(uint32_t n, cudaStream_t s) {
-    const uint32_t chunk = 32;
     while (n > 0) {
-        const uint32_t g = std::min(n, chunk);
+        const uint32_t g = std::min(n, kChunk);
         auto it = graphs.find(g);
         if (it == graphs.end()) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
-                launch_link_kernel(d_table, d_link_tiles, d_wd, grid_l, cap_stream);
-                launch_node_kernel(d_table, d_node_tiles, d_wd, grid_n, cap_stream);
+                launch_link_kernel(d_table, d_link_tiles, n_link_tiles, i, grid_l, cap_stream);
+                launch_node_kernel(d_table, d_node_tiles, n_node_tiles, i, grid_n, cap_stream);
             }
+            launch_advance_kernel(d_table, capacity, g, cap_stream);
             CK(cudaStreamEndCapture(cap_stream, &graph));
             cudaGraphExec_t exec;
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
@@ -239,10 +240,11 @@ void free_list(ts_ctx *c, std::vector<std::pair<void *, size_t>> &lst) {
 }
 
 template <typename T>
-T *alloc_in(ts_ctx *c, std::vector<std::pair<void *, size_t>> &lst, size_t count) {
+T *alloc_in(ts_ctx *c, std::vector<std::pair<void *, size_t>> &lst, size_t count, bool &ok) {
     const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
     void *p = c->dalloc(bytes);
     if (p) lst.emplace_back(p, bytes);
+    else ok = false;
     return reinterpret_cast<T *>(p);
 }
 
@@ -260,48 +262,73 @@ ts_status read_ctrl(ts_ctx *c, Ctrl *out) {
 }
 
 ts_status wait_ctx(ts_ctx *c, uint32_t timeout_ms) {
-    ts_status s = wait_event(c->ev, timeout_ms);
+    const ts_status s = wait_event(c->ev, timeout_ms);
     if (s == TS_ERR_CUDA) c->sticky = true;
     return s;
 }
 
+// Link tiles: runs of whole links with at most tile_words occupancy words
+// (all lanes), or, for a longer link, runs of its columns.  A split of a
+// non-periodic link must leave more than 2*vmax cells after it, so the tile
+// before a split never sees the link end; a too-short tail column is merged
+// into the tile before it.
 void build_tiles(ts_ctx *c) {
-    const uint32_t TW = c->tile_cols, vmax = c->params.vmax;
+    const uint32_t TW = c->tile_words, vmax = c->params.vmax;
     c->link_tiles.clear();
-    uint32_t start = 0, count = 0, cols = 0;
+    c->col_in_tile.assign(c->n_links, 0);
+    uint32_t start = 0, count = 0, words = 0, cols = 0;
     auto flush = [&]() {
-        if (count) c->link_tiles.push_back(make_uint4(0u, start, count, 0u));
-        count = 0;
-        cols = 0;
+        if (count) {
+            LinkTile t;
+            t.a = make_uint4(0u, start, count, 0u);
+            t.b = make_uint4(c->wbase[start], c->wbase[start] + words, 0u, 0u);
+            c->link_tiles.push_back(t);
+        }
+        count = words = cols = 0;
     };
     for (uint32_t l = 0; l < c->n_links; ++l) {
-        const uint32_t nc = c->ncols[l];
-        if (nc > TW) {
+        const uint32_t nc = c->ncols[l], nw = nc * c->lanes[l];
+        if (nw > TW) {
             flush();
+            const uint32_t per = std::max(1u, TW / c->lanes[l]);
             uint32_t j = 0;
             while (j < nc) {
-                uint32_t je = std::min(nc, j + TW);
-                // a split must leave more than 2*vmax cells after it, so that the
-                // tile before it never sees the link end
+                uint32_t je = std::min(nc, j + per);
                 if (!c->ring[l] && je < nc && c->cells[l] - 32u * je < 2u * vmax + 1u) je = nc;
-                c->link_tiles.push_back(make_uint4(0u, l, kPartial | j, je));
+                LinkTile t;
+                t.a = make_uint4(0u, l, kPartial | j, je);
+                t.b = make_uint4(c->wbase[l], c->cells[l], c->lanes[l] | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
+                c->link_tiles.push_back(t);
                 j = je;
             }
             start = l + 1;
             continue;
         }
         if (count == 0) start = l;
-        if (cols + nc > TW) {
+        if (words + nw > TW) {
             flush();
             start = l;
         }
+        c->col_in_tile[l] = cols;
         ++count;
+        words += nw;
         cols += nc;
     }
     flush();
     c->node_tiles.clear();
-    for (uint32_t n = 0; n < c->n_nodes_total; n += kNodeThreads)
-        c->node_tiles.push_back(make_uint4(0u, n, std::min(c->n_nodes_total, n + (uint32_t)kNodeThreads), 0u));
+    for (uint32_t m = 0; m < c->n_links; m += kNodeThreads)
+        c->node_tiles.push_back(make_uint4(0u, m, std::min(c->n_links, m + (uint32_t)kNodeThreads), 0u));
+    c->n_sub = std::min(c->sub_cap, c->link_tiles.size() >= 64 ? 8u : 1u);
+}
+
+ts_status upload_lk_info(ts_ctx *c) {
+    std::vector<uint4> li(c->n_links);
+    for (uint32_t l = 0; l < c->n_links; ++l)
+        li[l] = make_uint4(c->wbase[l], c->cells[l],
+                           c->lanes[l] | ((uint32_t)c->ring[l] << 8) | (c->col_in_tile[l] << 16), c->bpos[l]);
+    CK(cudaMemcpy(c->d_lk_info, li.data(), sizeof(uint4) * c->n_links, cudaMemcpyHostToDevice));
+    c->sd.n_sub = c->n_sub;
+    return TS_OK;
 }
 
 ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
@@ -312,7 +339,7 @@ ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
     for (uint32_t l = 0; l < d->n_links; ++l) {
         const bool ring = d->link_ring && d->link_ring[l];
         if (d->link_lanes[l] < 1 || d->link_lanes[l] > (uint32_t)kMaxLanes) return fail(TS_ERR_INVALID, "lanes must be 1..4");
-        if (d->link_cells[l] < 1 || d->link_cells[l] > (1u << 24)) return fail(TS_ERR_INVALID, "bad cell count");
+        if (d->link_cells[l] < 1 || d->link_cells[l] >= kMaxCells) return fail(TS_ERR_INVALID, "cells must be 1..2^22-1");
         if (ring) {
             if (d->link_cells[l] % 32u != 0u) return fail(TS_ERR_INVALID, "ring length must be a multiple of 32 cells");
         } else if (d->link_from[l] >= d->n_nodes || d->link_to[l] >= d->n_nodes) {
@@ -320,6 +347,24 @@ ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
         }
     }
     return TS_OK;
+}
+
+// Zeroes the statistics ring and sets the control block.
+ts_status reset_ctrl(ts_ctx *c, uint64_t step, uint64_t arrived, uint64_t inserted, cudaStream_t s) {
+    Ctrl h{};
+    h.base = step;
+    h.target = step;
+    h.arrived = arrived;
+    h.inserted = inserted;
+    CK(cudaMemcpyAsync(c->sd.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->sd.stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub, s));
+    CK(cudaStreamSynchronize(s));
+    c->host_step = step;
+    return TS_OK;
+}
+
+uint64_t departed_upto(const ts_ctx *c, uint64_t t) {
+    return (uint64_t)(std::upper_bound(c->depart_sorted.begin(), c->depart_sorted.end(), t) - c->depart_sorted.begin());
 }
 
 }  // namespace
@@ -334,21 +379,18 @@ uint32_t ts_launches_per_step(void) { return 2u; }
 
 size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_t route_len) {
     if (!d) return 0;
-    uint64_t words = 0, slots = 0, nodes = d->n_nodes, outs = 0;
-    uint32_t max_dep = 10800;
+    uint64_t words = 0, slots = 0;
     for (uint32_t l = 0; l < d->n_links; ++l) {
         const bool ring = d->link_ring && d->link_ring[l];
         words += (uint64_t)((d->link_cells[l] + 31u) / 32u) * d->link_lanes[l];
         if (!ring) slots += d->link_lanes[l];
-        if (ring) ++nodes;
-        ++outs;
     }
     size_t b = 0;
-    b += 16ull * d->n_links + 8ull * (nodes + 1) + 4ull * outs;
-    b += words * (4 + 32 + 128) * 2;
-    b += 16ull * slots + 8ull * n_vehicles + 4ull * route_len;
-    b += 4ull * (d->n_links + 1) + 8ull * n_vehicles + 4ull * d->n_links + 4ull * (max_dep + 1);
-    b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing;
+    b += 16ull * d->n_links * 2 + 4ull * d->n_links * 2;      // lk_info, nd_info, link_exit (+ reset copy)
+    b += words * (4 + 32 + 128) * 2;                          // occupancy, velocity, id (double-buffered)
+    b += 16ull * slots + 8ull * n_vehicles * 2 + 4ull * route_len;
+    b += 8ull * n_vehicles + 4ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
+    b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
     return b;
 }
 
@@ -363,6 +405,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     CK(cudaGetDevice(&c->device));
     CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->ev, c->stream));
     if (allocator && allocator->alloc && allocator->free) {
         c->alloc = *allocator;
         c->has_alloc = true;
@@ -379,7 +422,6 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     if (desc->link_ring)
         for (uint32_t l = 0; l < L; ++l) c->ring[l] = desc->link_ring[l] ? 1 : 0;
     for (uint32_t l = 0; l < L; ++l) c->n_ring += c->ring[l];
-    c->n_nodes_total = c->n_nodes + c->n_ring;
     // words, lanes, canonical cells
     c->ncols.resize(L);
     c->wbase.resize(L);
@@ -403,12 +445,12 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
             c->cell_base[ln + 1] = c->cell_base[ln] + c->cells[l];
         }
     c->n_lane_cells = c->cell_base[c->n_lanes];
-    // link-end buffers grouped by node in priority order
-    c->node_in_off.assign(c->n_nodes_total + 1, 0);
+    // link-end buffers grouped by the node the link ends at, priority order
+    c->node_in_off.assign(c->n_nodes + 1, 0);
     for (uint32_t l = 0; l < L; ++l)
         if (!c->ring[l]) c->node_in_off[c->to[l] + 1] += c->lanes[l];
-    for (uint32_t n = 0; n < c->n_nodes_total; ++n) c->node_in_off[n + 1] += c->node_in_off[n];
-    c->n_slots = c->node_in_off[c->n_nodes_total];
+    for (uint32_t n = 0; n < c->n_nodes; ++n) c->node_in_off[n + 1] += c->node_in_off[n];
+    c->n_slots = c->node_in_off[c->n_nodes];
     c->bpos.assign(L, 0);
     {
         std::vector<uint32_t> fill(c->node_in_off.begin(), c->node_in_off.end() - 1);
@@ -418,58 +460,43 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
                 fill[c->to[l]] += c->lanes[l];
             }
     }
-    // outgoing links (departure owners); ring link r belongs to pseudo node n_nodes + r
-    c->node_out_off.assign(c->n_nodes_total + 1, 0);
-    {
-        uint32_t r = 0;
-        std::vector<uint32_t> owner(L);
-        for (uint32_t l = 0; l < L; ++l) owner[l] = c->ring[l] ? c->n_nodes + r++ : c->from[l];
-        for (uint32_t l = 0; l < L; ++l) c->node_out_off[owner[l] + 1]++;
-        for (uint32_t n = 0; n < c->n_nodes_total; ++n) c->node_out_off[n + 1] += c->node_out_off[n];
-        c->node_out_link.resize(L);
-        std::vector<uint32_t> fill(c->node_out_off.begin(), c->node_out_off.end() - 1);
-        for (uint32_t l = 0; l < L; ++l) c->node_out_link[fill[owner[l]]++] = l;
-    }
+    for (uint32_t n = 0; n < c->n_nodes; ++n)
+        if (c->node_in_off[n + 1] - c->node_in_off[n] > 255u)
+            return fail(TS_ERR_INVALID, "more than 255 lanes end at one node");
+    c->sub_cap = 8;
     build_tiles(c.get());
+    c->sub_cap = c->n_sub;  // small networks keep one sub-record per step
     // device arrays of the network
+    bool ok = true;
     auto &A = c->allocs;
-    uint4 *link_info = alloc_in<uint4>(c.get(), A, L);
-    uint32_t *in_off = alloc_in<uint32_t>(c.get(), A, c->n_nodes_total + 1);
-    uint32_t *out_off = alloc_in<uint32_t>(c.get(), A, c->n_nodes_total + 1);
-    uint32_t *out_link = alloc_in<uint32_t>(c.get(), A, L);
-    uint32_t *occ0 = alloc_in<uint32_t>(c.get(), A, c->n_words);
-    uint32_t *occ1 = alloc_in<uint32_t>(c.get(), A, c->n_words);
-    int8_t *vel0 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32);
-    int8_t *vel1 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32);
-    uint32_t *vid0 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32);
-    uint32_t *vid1 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32);
-    uint4 *slots = alloc_in<uint4>(c.get(), A, c->n_slots);
-    Ctrl *ctrl = alloc_in<Ctrl>(c.get(), A, 1);
-    StatRec *stats = alloc_in<StatRec>(c.get(), A, kStatsRing);
-    for (auto &a : A)
-        if (!a.first) {
-            free_list(c.get(), A);
-            return fail(TS_ERR_OOM, "device allocation failed");
-        }
-    if (A.size() != 13) {
+    c->d_lk_info = alloc_in<uint4>(c.get(), A, L, ok);
+    uint4 *nd_info = alloc_in<uint4>(c.get(), A, L, ok);
+    uint32_t *occ0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
+    uint32_t *occ1 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
+    int8_t *vel0 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32, ok);
+    int8_t *vel1 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32, ok);
+    uint32_t *vid0 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32, ok);
+    uint32_t *vid1 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32, ok);
+    uint4 *slots = alloc_in<uint4>(c.get(), A, c->n_slots, ok);
+    uint32_t *link_exit = alloc_in<uint32_t>(c.get(), A, L, ok);
+    c->d_link_exit0 = alloc_in<uint32_t>(c.get(), A, L, ok);
+    Ctrl *ctrl = alloc_in<Ctrl>(c.get(), A, 1, ok);
+    StatRec *stats = alloc_in<StatRec>(c.get(), A, (size_t)kStatsRing * c->sub_cap, ok);
+    if (!ok) {
         free_list(c.get(), A);
         return fail(TS_ERR_OOM, "device allocation failed");
     }
-    std::vector<uint4> li(L);
-    for (uint32_t l = 0; l < L; ++l) li[l] = make_uint4(c->wbase[l], c->cells[l], c->lanes[l] | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
-    CK(cudaMemcpy(link_info, li.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(in_off, c->node_in_off.data(), 4ull * (c->n_nodes_total + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(out_off, c->node_out_off.data(), 4ull * (c->n_nodes_total + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(out_link, c->node_out_link.data(), 4ull * L, cudaMemcpyHostToDevice));
     ScenDev &sd = c->sd;
-    sd.link_info = link_info;
-    sd.node_in_off = in_off;
-    sd.node_out_off = out_off;
-    sd.node_out_link = out_link;
-    sd.occ[0] = occ0; sd.occ[1] = occ1;
-    sd.vel[0] = vel0; sd.vel[1] = vel1;
-    sd.vid[0] = vid0; sd.vid[1] = vid1;
+    sd.lk_info = c->d_lk_info;
+    sd.nd_info = nd_info;
+    sd.occ[0] = occ0;
+    sd.occ[1] = occ1;
+    sd.vel[0] = vel0;
+    sd.vel[1] = vel1;
+    sd.vid[0] = vid0;
+    sd.vid[1] = vid1;
     sd.slots = slots;
+    sd.link_exit = link_exit;
     sd.ctrl = ctrl;
     sd.stats = stats;
     sd.vmax = params->vmax;
@@ -478,12 +505,17 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.seed_hi = (uint32_t)(params->seed >> 32);
     sd.lane_change = params->lane_change ? 1u : 0u;
     sd.n_links = L;
-    sd.n_nodes_total = c->n_nodes_total;
+    st = upload_lk_info(c.get());
+    if (st != TS_OK) return st;
+    std::vector<uint32_t> ex(L);
+    for (uint32_t l = 0; l < L; ++l) ex[l] = c->ring[l] ? 0u : ((1u << c->lanes[l]) - 1u);
+    CK(cudaMemcpy(c->d_link_exit0, ex.data(), 4ull * L, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(link_exit, ex.data(), 4ull * L, cudaMemcpyHostToDevice));
     CK(cudaMemset(occ0, 0, 4ull * c->n_words));
     CK(cudaMemset(occ1, 0, 4ull * c->n_words));
     CK(cudaMemset(slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(ctrl, 0, sizeof(Ctrl)));
-    CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing));
+    CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing * c->sub_cap));
     *out = c.release();
     return TS_OK;
 }
@@ -491,79 +523,78 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
 static ts_status upload_vehicles(ts_ctx *c) {
     free_list(c, c->veh_allocs);
     auto &A = c->veh_allocs;
-    const uint32_t n = c->n_veh;
+    const uint32_t n = c->n_veh, L = c->n_links;
     const uint64_t total = c->route_off[n];
-    uint2 *veh = alloc_in<uint2>(c, A, n);
-    uint32_t *routes = alloc_in<uint32_t>(c, A, total);
-    uint32_t *dep_off = alloc_in<uint32_t>(c, A, c->n_links + 1);
-    uint32_t *dep_ids = alloc_in<uint32_t>(c, A, n);
-    uint32_t *dep_steps = alloc_in<uint32_t>(c, A, n);
-    uint32_t *dep_head = alloc_in<uint32_t>(c, A, c->n_links);
-    uint32_t max_dep = 0;
-    for (uint32_t i = 0; i < n; ++i) max_dep = std::max(max_dep, c->depart[i]);
-    const uint32_t n_dep_steps = n ? max_dep + 1 : 0;
-    uint32_t *dep_upto = alloc_in<uint32_t>(c, A, n_dep_steps);
-    for (auto &a : A)
-        if (!a.first) {
-            free_list(c, A);
-            return fail(TS_ERR_OOM, "device allocation failed");
-        }
-    if (A.size() != 7) {
+    bool ok = true;
+    uint2 *veh = alloc_in<uint2>(c, A, n, ok);
+    c->d_veh0 = alloc_in<uint2>(c, A, n, ok);
+    uint32_t *routes = alloc_in<uint32_t>(c, A, total, ok);
+    uint32_t *dep_ids = alloc_in<uint32_t>(c, A, n, ok);
+    uint32_t *dep_steps = alloc_in<uint32_t>(c, A, n, ok);
+    uint32_t *dep_head = alloc_in<uint32_t>(c, A, L, ok);
+    c->d_dep_head0 = alloc_in<uint32_t>(c, A, L, ok);
+    if (!ok) {
         free_list(c, A);
         return fail(TS_ERR_OOM, "device allocation failed");
     }
     std::vector<uint2> hv(n);
     for (uint32_t i = 0; i < n; ++i) hv[i] = make_uint2(c->route_off[i], c->route_off[i + 1]);
-    std::vector<uint32_t> steps(n), upto(n_dep_steps, 0);
-    for (uint32_t q = 0; q < n; ++q) steps[q] = c->depart[c->dep_ids[q]];
-    for (uint32_t i = 0; i < n; ++i) upto[c->depart[i]]++;
-    for (uint32_t t = 1; t < n_dep_steps; ++t) upto[t] += upto[t - 1];
+    std::vector<uint32_t> ids(n), steps(n);
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint32_t id = c->dep_ids[q];
+        steps[q] = c->depart[id];
+        ids[q] = id | (c->route_off[id + 1] - c->route_off[id] == 1 ? kLastLinkBit : 0u);
+    }
+    // per link: first slot of its upstream node, word of its column 0, slot
+    // count, lanes and end of its departure queue
+    std::vector<uint4> nd(L);
+    for (uint32_t m = 0; m < L; ++m) {
+        uint32_t lo = 0, cnt = 0;
+        if (!c->ring[m]) {
+            lo = c->node_in_off[c->from[m]];
+            cnt = c->node_in_off[c->from[m] + 1] - lo;
+        }
+        nd[m] = make_uint4(lo, c->wbase[m], cnt | (c->lanes[m] << 8), c->dep_off[m + 1]);
+    }
     if (n) {
         CK(cudaMemcpy(veh, hv.data(), 8ull * n, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(dep_ids, c->dep_ids.data(), 4ull * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_veh0, hv.data(), 8ull * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dep_ids, ids.data(), 4ull * n, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(dep_steps, steps.data(), 4ull * n, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(dep_upto, upto.data(), 4ull * n_dep_steps, cudaMemcpyHostToDevice));
     }
     if (total) CK(cudaMemcpy(routes, c->route_links.data(), 4ull * total, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dep_off, c->dep_off.data(), 4ull * (c->n_links + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dep_head, c->dep_off.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(const_cast<uint4 *>(c->sd.nd_info), nd.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dep_head, c->dep_off.data(), 4ull * L, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_dep_head0, c->dep_off.data(), 4ull * L, cudaMemcpyHostToDevice));
     ScenDev &sd = c->sd;
     sd.veh = veh;
     sd.route_links = routes;
-    sd.dep_off = dep_off;
     sd.dep_ids = dep_ids;
     sd.dep_steps = dep_steps;
     sd.dep_head = dep_head;
-    sd.departed_upto = dep_upto;
-    sd.n_dep_steps = n_dep_steps;
     return TS_OK;
 }
 
-static ts_status reset_state(ts_ctx *c, uint64_t step, uint64_t arrived, uint64_t inserted) {
+// Device-side return to the empty network at step 0.
+static ts_status reset_device_state(ts_ctx *c, cudaStream_t s) {
     ScenDev &sd = c->sd;
-    for (int b = 0; b < 2; ++b) CK(cudaMemset(sd.occ[b], 0, 4ull * c->n_words));
-    CK(cudaMemset(sd.slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
-    Ctrl h{};
-    h.step = step;
-    h.target = step;
-    h.arrived = arrived;
-    h.inserted = inserted;
-    CK(cudaMemcpy(sd.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice));
-    CK(cudaMemset(sd.stats, 0, sizeof(StatRec) * kStatsRing));
-    c->host_step = step;
-    c->stepped = false;
+    for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(sd.occ[b], 0, 4ull * c->n_words, s));
+    CK(cudaMemsetAsync(sd.slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1), s));
+    CK(cudaMemcpyAsync(sd.link_exit, c->d_link_exit0, 4ull * c->n_links, cudaMemcpyDeviceToDevice, s));
+    if (c->n_veh) CK(cudaMemcpyAsync(sd.veh, c->d_veh0, 8ull * c->n_veh, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(sd.dep_head, c->d_dep_head0, 4ull * c->n_links, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(sd.ctrl, 0, sizeof(Ctrl), s));
+    CK(cudaMemsetAsync(sd.stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub, s));
     return TS_OK;
 }
 
 static ts_status ensure_own_world(ts_ctx *c) {
-    if (c->own) {
-        c->own->members[0] = c;
-        return c->own->rebuild();
+    if (!c->own) {
+        c->own = new (std::nothrow) World();
+        if (!c->own) return fail(TS_ERR_OOM, "host allocation failed");
+        const ts_status s = c->own->init(1);
+        if (s != TS_OK) return s;
     }
-    c->own = new (std::nothrow) World();
-    if (!c->own) return fail(TS_ERR_OOM, "host allocation failed");
-    ts_status s = c->own->init(1);
-    if (s != TS_OK) return s;
     c->own->members[0] = c;
     return c->own->rebuild();
 }
@@ -590,6 +621,8 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
     c->route_off = std::move(ro);
     c->route_links.assign(links, links + c->route_off[n]);
     c->depart.assign(dep, dep + n);
+    c->depart_sorted = c->depart;
+    std::sort(c->depart_sorted.begin(), c->depart_sorted.end());
     // departure queues: per first link, ordered by (departure step, id)
     c->dep_off.assign(c->n_links + 1, 0);
     for (uint32_t i = 0; i < n; ++i) c->dep_off[c->route_links[c->route_off[i]] + 1]++;
@@ -604,22 +637,36 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
     }
     st = upload_vehicles(c);
     if (st != TS_OK) return st;
-    st = reset_state(c, 0, 0, 0);
+    st = reset_device_state(c, c->stream);
     if (st != TS_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    c->host_step = 0;
     c->loaded = true;
+    CK(cudaEventRecord(c->ev, c->stream));
     return ensure_own_world(c);
 }
 
-ts_status ts_set_tile_columns(ts_ctx *c, uint32_t columns) {
+ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
     ts_status st = check_ctx(c);
     if (st != TS_OK) return st;
-    if (columns < 8 || columns > 128) return fail(TS_ERR_INVALID, "tile columns must be 8..128");
+    if (words < 8 || words > (uint32_t)kTileWords) return fail(TS_ERR_INVALID, "tile words must be 8..128");
     if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
     st = wait_ctx(c, 60000);
     if (st != TS_OK) return st;
-    c->tile_cols = columns;
+    c->tile_words = words;
+    const uint32_t old_sub = c->n_sub;
     build_tiles(c);
-    if (c->own) return c->own->rebuild();
+    if (c->n_sub != old_sub) {
+        // the statistics ring layout depends on the tile count; keep the state
+        Ctrl h;
+        st = read_ctrl(c, &h);
+        if (st != TS_OK) return st;
+        st = reset_ctrl(c, h.base, h.arrived, h.inserted, c->stream);
+        if (st != TS_OK) return st;
+    }
+    st = upload_lk_info(c);
+    if (st != TS_OK) return st;
+    if (c->own) return ensure_own_world(c);
     return TS_OK;
 }
 
@@ -639,7 +686,71 @@ ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
         return st;
     }
     CK(cudaEventRecord(c->ev, s));
-    c->stepped = true;
+    return TS_OK;
+}
+
+ts_status ts_reset(ts_ctx *c, void *cuda_stream) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (c->batch) return fail(TS_ERR_STATE, "context is stepped by its batch");
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+    st = reset_device_state(c, s);
+    if (st != TS_OK) return st;
+    CK(cudaEventRecord(c->ev, s));
+    c->host_step = 0;
+    return TS_OK;
+}
+
+ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *link_ms, float *node_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (c->batch) return fail(TS_ERR_STATE, "context is stepped by its batch");
+    if (!link_ms || !node_ms) return fail(TS_ERR_INVALID, "null output");
+    if (n_steps == 0) return TS_OK;
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+    World *w = c->own;
+    std::vector<cudaEvent_t> ev(3ull * n_steps);
+    size_t made = 0;
+    ts_status rs = TS_OK;
+    for (; made < ev.size(); ++made)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) {
+            rs = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+            break;
+        }
+    if (rs == TS_OK) {
+        c->host_step += n_steps;
+        launch_set_target(c->sd.ctrl, c->host_step, s);
+        for (uint32_t b = 0; b < n_steps && rs == TS_OK; b += kChunk) {
+            const uint32_t g = std::min(kChunk, n_steps - b);
+            for (uint32_t i = 0; i < g; ++i) {
+                const size_t e = 3ull * (b + i);
+                cudaEventRecord(ev[e], s);
+                launch_link_kernel(w->d_table, w->d_link_tiles, w->n_link_tiles, i, w->grid_l, s);
+                cudaEventRecord(ev[e + 1], s);
+                launch_node_kernel(w->d_table, w->d_node_tiles, w->n_node_tiles, i, w->grid_n, s);
+                cudaEventRecord(ev[e + 2], s);
+            }
+            launch_advance_kernel(w->d_table, w->capacity, g, s);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rs = cuda_fail(e, "kernel launch");
+        }
+    }
+    if (rs == TS_OK) {
+        const cudaError_t e = cudaEventSynchronize(ev[3ull * n_steps - 1]);
+        if (e != cudaSuccess) rs = cuda_fail(e, "cudaEventSynchronize");
+    }
+    for (uint32_t i = 0; i < n_steps && rs == TS_OK; ++i) {
+        cudaEventElapsedTime(&link_ms[i], ev[3ull * i], ev[3ull * i + 1]);
+        cudaEventElapsedTime(&node_ms[i], ev[3ull * i + 1], ev[3ull * i + 2]);
+    }
+    for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    if (rs != TS_OK) {
+        c->sticky = true;
+        return rs;
+    }
+    CK(cudaEventRecord(c->ev, s));
     return TS_OK;
 }
 
@@ -653,18 +764,43 @@ ts_status ts_read_stats_range(ts_ctx *c, uint64_t first, uint32_t n, ts_stats *o
     st = read_ctrl(c, &h);
     if (st != TS_OK) return st;
     if (n == 0) return TS_OK;
-    if (first + n > h.step || h.step - first > kStatsRing - 1)
+    // the ring keeps the last kStatsRing - kChunk completed steps
+    if (first + n > h.base || h.base - first > kStatsRing - kChunk || first < h.base - h.steps_run)
         return fail(TS_ERR_STATE, "requested steps are not available");
-    std::vector<StatRec> tmp(kStatsRing);
-    CK(cudaMemcpy(tmp.data(), c->sd.stats, sizeof(StatRec) * kStatsRing, cudaMemcpyDeviceToHost));
-    for (uint32_t i = 0; i < n; ++i) {
-        const StatRec &r = tmp[(first + i) & (kStatsRing - 1)];
-        if (r.step != first + i) return fail(TS_ERR_STATE, "requested steps are not available");
+    const uint32_t nsub = c->n_sub;
+    std::vector<StatRec> ring((size_t)kStatsRing * nsub);
+    CK(cudaMemcpy(ring.data(), c->sd.stats, sizeof(StatRec) * ring.size(), cudaMemcpyDeviceToHost));
+    auto sum = [&](uint64_t t, int f) {
+        unsigned long long s = 0;
+        for (uint32_t u = 0; u < nsub; ++u) {
+            const unsigned long long *r =
+                reinterpret_cast<const unsigned long long *>(&ring[(size_t)(t & (kStatsRing - 1)) * nsub + u]);
+            s += r[f];
+        }
+        return (uint64_t)s;
+    };
+    // cumulative arrivals and insertions after step t, counted back from the totals
+    uint64_t arr = h.arrived, ins = h.inserted;
+    for (uint64_t t = h.base - 1; t + 1 > first + n; --t) {
+        arr -= sum(t, 8);
+        ins -= sum(t, 4);
+    }
+    for (uint32_t i = n; i-- > 0;) {
+        const uint64_t t = first + i;
         ts_stats &o = out[i];
-        o.step = r.step; o.active = r.active; o.buffered = r.buffered; o.waiting = r.waiting;
-        o.arrived = r.arrived; o.lane_changes = r.lane_changes; o.transfers = r.transfers;
-        o.inserted = r.inserted; o.sum_v = r.sum_v; o.vehicle_updates = r.vehicle_updates;
-        o.state_hash = r.state_hash;
+        o.step = t;
+        o.active = sum(t, 0);
+        o.buffered = sum(t, 1);
+        o.lane_changes = sum(t, 2);
+        o.transfers = sum(t, 3);
+        o.inserted = sum(t, 4);
+        o.sum_v = sum(t, 5);
+        o.vehicle_updates = sum(t, 6);
+        o.state_hash = sum(t, 7);
+        o.arrived = arr;
+        o.waiting = departed_upto(c, t) - ins;
+        arr -= sum(t, 8);
+        ins -= o.inserted;
     }
     return TS_OK;
 }
@@ -678,14 +814,26 @@ ts_status ts_read_stats(ts_ctx *c, ts_stats *out, uint32_t timeout_ms) {
     Ctrl h;
     st = read_ctrl(c, &h);
     if (st != TS_OK) return st;
-    if (!c->stepped || h.step == 0) return fail(TS_ERR_STATE, "no step has completed");
-    StatRec r;
-    CK(cudaMemcpy(&r, c->sd.stats + ((h.step - 1) & (kStatsRing - 1)), sizeof(StatRec), cudaMemcpyDeviceToHost));
-    if (r.step != h.step - 1) return fail(TS_ERR_STATE, "statistics not available");
-    out->step = r.step; out->active = r.active; out->buffered = r.buffered; out->waiting = r.waiting;
-    out->arrived = r.arrived; out->lane_changes = r.lane_changes; out->transfers = r.transfers;
-    out->inserted = r.inserted; out->sum_v = r.sum_v; out->vehicle_updates = r.vehicle_updates;
-    out->state_hash = r.state_hash;
+    if (h.steps_run == 0) return fail(TS_ERR_STATE, "no step has completed");
+    return ts_read_stats_range(c, h.base - 1, 1, out, timeout_ms);
+}
+
+ts_status ts_read_totals(ts_ctx *c, ts_totals *out, uint32_t timeout_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!out) return fail(TS_ERR_INVALID, "null output");
+    st = wait_ctx(c, timeout_ms);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    out->steps = h.steps_run;
+    out->vehicle_updates = h.tot_updates;
+    out->lane_changes = h.tot_lane_changes;
+    out->transfers = h.tot_transfers;
+    out->inserted = h.inserted;
+    out->arrived = h.arrived;
+    out->last_state_hash = h.last_hash;
     return TS_OK;
 }
 
@@ -709,7 +857,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     Ctrl h;
     st = read_ctrl(c, &h);
     if (st != TS_OK) return st;
-    const int cur = (int)(h.step & 1ull);
+    const int cur = (int)(h.base & 1ull);
     const size_t nw = c->n_words;
     std::vector<uint32_t> occ(nw), vid(nw * 32), head(c->n_links);
     std::vector<int8_t> vel(nw * 32);
@@ -721,8 +869,14 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     if (c->n_slots) CK(cudaMemcpy(slots.data(), c->sd.slots, 16ull * c->n_slots, cudaMemcpyDeviceToHost));
     if (c->n_veh) CK(cudaMemcpy(veh.data(), c->sd.veh, 8ull * c->n_veh, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(head.data(), c->sd.dep_head, 4ull * c->n_links, cudaMemcpyDeviceToHost));
-    for (uint64_t i = 0; i < c->n_lane_cells; ++i) { o->cell_id[i] = -1; o->cell_v[i] = 0; }
-    for (uint32_t i = 0; i < c->n_lanes; ++i) { o->buf_id[i] = -1; o->buf_v[i] = 0; }
+    for (uint64_t i = 0; i < c->n_lane_cells; ++i) {
+        o->cell_id[i] = -1;
+        o->cell_v[i] = 0;
+    }
+    for (uint32_t i = 0; i < c->n_lanes; ++i) {
+        o->buf_id[i] = -1;
+        o->buf_v[i] = 0;
+    }
     for (uint32_t l = 0; l < c->n_links; ++l) {
         const uint32_t nl = c->lanes[l];
         for (uint32_t j = 0; j < c->ncols[l]; ++j)
@@ -733,6 +887,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
                     const int b = __builtin_ctz(m);
                     m &= m - 1;
                     const uint64_t x = 32ull * j + (uint64_t)b;
+                    if (x >= c->cells[l]) return fail(TS_ERR_DEVICE_CHECK, "occupancy bit past the link end");
                     const uint64_t ci = c->cell_base[c->lane_base[l] + k] + x;
                     o->cell_id[ci] = (int32_t)(vid[w * 32 + b] & kIdMask);
                     o->cell_v[ci] = vel[w * 32 + b];
@@ -748,7 +903,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     }
     for (uint32_t i = 0; i < c->n_veh; ++i) o->cursor[i] = veh[i].x - c->route_off[i];
     for (uint32_t l = 0; l < c->n_links; ++l) o->dep_head[l] = head[l] - c->dep_off[l];
-    o->step = h.step;
+    o->step = h.base;
     o->arrived = h.arrived;
     o->inserted = h.inserted;
     return TS_OK;
@@ -758,24 +913,24 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     ts_status st = check_ctx(c);
     if (st != TS_OK) return st;
     if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
     if (!in || !in->cell_id || !in->cell_v || !in->buf_id || !in->buf_v || !in->cursor || !in->dep_head)
         return fail(TS_ERR_INVALID, "null state array");
     st = wait_ctx(c, 60000);
     if (st != TS_OK) return st;
     const uint32_t vmax = c->params.vmax;
     const size_t nw = c->n_words;
-    std::vector<uint32_t> occ(nw, 0), vid(nw * 32, 0);
+    std::vector<uint32_t> occ(nw, 0), vid(nw * 32, 0), exit_bits(c->n_links, 0);
     std::vector<int8_t> vel(nw * 32, 0);
     std::vector<uint4> slots(c->n_slots, make_uint4(kSlotEmpty, 0, 0, 0));
     std::vector<uint8_t> seen(c->n_veh, 0);
     std::vector<uint32_t> head(c->n_links);
     for (uint32_t i = 0; i < c->n_veh; ++i)
         if (in->cursor[i] >= c->route_off[i + 1] - c->route_off[i]) return fail(TS_ERR_INVALID, "cursor past route end");
-    auto on_route = [&](int32_t id, uint32_t l) {
-        return c->route_links[c->route_off[id] + in->cursor[id]] == l;
-    };
+    auto on_route = [&](int32_t id, uint32_t l) { return c->route_links[c->route_off[id] + in->cursor[id]] == l; };
     for (uint32_t l = 0; l < c->n_links; ++l) {
         const uint32_t nl = c->lanes[l];
+        if (!c->ring[l]) exit_bits[l] = (1u << nl) - 1u;
         for (uint32_t k = 0; k < nl; ++k) {
             const uint64_t cb = c->cell_base[c->lane_base[l] + k];
             for (uint32_t x = 0; x < c->cells[l]; ++x) {
@@ -804,7 +959,9 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
                 seen[b] = 1;
                 const uint32_t p = c->route_off[b] + in->cursor[b];
                 const uint32_t fl = (in->cursor[b] + 2 == len) ? kLastLinkBit : 0u;
-                slots[c->bpos[l] + k] = make_uint4((uint32_t)b | fl, c->route_links[p + 1], l, (uint32_t)v | (k << 8));
+                slots[c->bpos[l] + k] =
+                    make_uint4((uint32_t)b | fl, c->route_links[p + 1], l, (uint32_t)v | (k << 8) | (c->cells[l] << 10));
+                exit_bits[l] &= ~(1u << k);
             }
         }
     }
@@ -818,15 +975,18 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     }
     std::vector<uint2> veh(c->n_veh);
     for (uint32_t i = 0; i < c->n_veh; ++i) veh[i] = make_uint2(c->route_off[i] + in->cursor[i], c->route_off[i + 1]);
-    st = reset_state(c, in->step, in->arrived, in->inserted);
-    if (st != TS_OK) return st;
     const int cur = (int)(in->step & 1ull);
-    CK(cudaMemcpy(c->sd.occ[cur], occ.data(), 4 * nw, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->sd.vel[cur], vel.data(), nw * 32, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->sd.vid[cur], vid.data(), 4 * nw * 32, cudaMemcpyHostToDevice));
-    if (c->n_slots) CK(cudaMemcpy(c->sd.slots, slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
-    if (c->n_veh) CK(cudaMemcpy(c->sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->sd.dep_head, head.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    ScenDev &sd = c->sd;
+    CK(cudaMemset(sd.occ[cur ^ 1], 0, 4 * nw));
+    CK(cudaMemcpy(sd.occ[cur], occ.data(), 4 * nw, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.vel[cur], vel.data(), nw * 32, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.vid[cur], vid.data(), 4 * nw * 32, cudaMemcpyHostToDevice));
+    if (c->n_slots) CK(cudaMemcpy(sd.slots, slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.link_exit, exit_bits.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    if (c->n_veh) CK(cudaMemcpy(sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.dep_head, head.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    st = reset_ctrl(c, in->step, in->arrived, in->inserted, c->stream);
+    if (st != TS_OK) return st;
     CK(cudaEventRecord(c->ev, c->stream));
     return TS_OK;
 }
@@ -880,9 +1040,7 @@ ts_status ts_batch_add(ts_batch *b, ts_ctx *c, uint64_t target_step) {
     if (slot == b->w.capacity) return fail(TS_ERR_STATE, "batch is full");
     CK(cudaMemcpy(&c->sd.ctrl->target, &target_step, sizeof(target_step), cudaMemcpyHostToDevice));
     b->w.members[slot] = c;
-    b->w.targets[slot] = target_step;
     c->batch = b;
-    c->stepped = true;
     return b->w.rebuild();
 }
 
@@ -896,7 +1054,7 @@ ts_status ts_batch_remove(ts_batch *b, ts_ctx *c) {
     Ctrl h;
     st = read_ctrl(c, &h);
     if (st != TS_OK) return st;
-    c->host_step = h.step;
+    c->host_step = h.base;
     return b->w.rebuild();
 }
 
@@ -905,8 +1063,7 @@ ts_status ts_batch_step(ts_batch *b, uint32_t n_steps, void *cuda_stream) {
     if (n_steps == 0) return TS_OK;
     CK(cudaSetDevice(b->w.device));
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (!s) s = b->w.cap_stream;
-    if (s == b->w.cap_stream) return fail(TS_ERR_INVALID, "pass a stream to ts_batch_step");
+    if (!s || s == b->w.cap_stream) return fail(TS_ERR_INVALID, "pass a stream to ts_batch_step");
     ts_status st = b->w.run(n_steps, s);
     if (st != TS_OK) return st;
     CK(cudaEventRecord(b->ev, s));
@@ -929,7 +1086,7 @@ ts_status ts_ctx_step(ts_ctx *c, uint64_t *step) {
     Ctrl h;
     st = read_ctrl(c, &h);
     if (st != TS_OK) return st;
-    *step = h.step;
+    *step = h.base;
     return TS_OK;
 }
 

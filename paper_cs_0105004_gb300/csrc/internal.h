@@ -6,15 +6,16 @@
 //     lanes of one column are adjacent and a link's columns are contiguous
 //     (link-major, lane-interleaved).  Bit i of that word is cell 32j+i.
 //   * occ[2][n_words]: occupancy bitmasks, double-buffered by step parity
-//     (state at step t lives in buffer t&1).
+//     (the state at step t lives in buffer t&1).
 //   * vel[2][32*n_words] (int8) and vid[2][32*n_words] (uint32): velocity and
 //     vehicle id of the cell with the same bit index; vid bit 31 marks a
 //     vehicle driving the last link of its route.  Payload of empty cells is
 //     never read.
 //   * slots[n_slots]: one link-end buffer per lane, grouped by the node the
-//     link ends at (node_in_off), in priority order (link id, then lane).
-//     x = id | last-link-next flag << 31 (0xffffffff = empty), y = next link,
-//     z = current link, w = v | lane << 8.
+//     link ends at, in intersection priority order (link id, then lane):
+//     x = id | next-link-is-last << 31 (0xffffffff = empty), y = next link,
+//     z = current link, w = v | lane << 8 | current link cells << 10.
+//   * link_exit[n_links]: bit k set while lane k's buffer is empty.
 //   * veh[n_vehicles]: {absolute index of the current route entry, end of the
 //     vehicle's route}.
 #pragma once
@@ -28,70 +29,76 @@ constexpr int kMaxVmax = 15;
 constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kLastLinkBit = 0x80000000u;
 constexpr uint32_t kIdMask = 0x7FFFFFFFu;
-constexpr int kMaxTileCols = 129;          // columns of a link tile (128 + one merged tail column)
-constexpr int kTileSlots = kMaxTileCols + 2;  // plus a halo column on each side
+constexpr uint32_t kMaxCells = 1u << 22;      // cells per link (buffer digest packs 22 bits)
+constexpr int kTileWords = 128;               // occupancy words per link tile (all lanes)
+constexpr int kTileMaxCols = 129;             // columns per tile (one-lane links, plus a merged tail)
+constexpr int kTileSmemWords = kTileWords + 4 + 2 * kMaxLanes;  // core + merged tail + halos
 constexpr int kLinkThreads = 256;
 constexpr int kNodeThreads = 128;
-constexpr int kListCap = 4096;             // vehicles staged per round in shared memory
-constexpr uint32_t kStatsRing = 4096;      // per-step statistics kept on the device
-constexpr uint32_t kNoNode = 0xFFFFFFFFu;
+constexpr int kListCap = kTileSmemWords * 32;  // every cell of a tile can hold a vehicle
+constexpr uint32_t kStatsRing = 4096;         // steps of statistics kept on the device
+constexpr uint32_t kChunk = 32;               // steps per captured graph
+constexpr uint32_t kNoLink = 0xFFFFFFFFu;
 
 struct Ctrl {
-    unsigned long long step;      // next step to run
+    unsigned long long base;      // steps completed (first step of the next chunk)
     unsigned long long target;    // run while step < target
-    unsigned long long arrived;   // cumulative arrivals
-    unsigned long long inserted;  // cumulative departures inserted
-    unsigned int error;           // device-check flags (bitwise or)
+    unsigned long long arrived;   // cumulative arrivals up to base
+    unsigned long long inserted;  // cumulative departures inserted up to base
+    unsigned long long tot_updates, tot_lane_changes, tot_transfers;  // since the last reset
+    unsigned long long steps_run, last_hash;
+    unsigned int error;  // device-check flags (bitwise or)
     unsigned int pad;
 };
 
 // error flags
-constexpr unsigned kErrCellTaken = 1u;   // two vehicles for one cell
-constexpr unsigned kErrSlotTaken = 2u;   // buffer entry into an occupied buffer
-constexpr unsigned kErrRoute = 4u;       // route cursor past the route end
-constexpr unsigned kErrListCap = 8u;     // internal: list round bookkeeping
+constexpr unsigned kErrCellTaken = 1u;  // two vehicles for one cell
+constexpr unsigned kErrSlotTaken = 2u;  // buffer entry into an occupied buffer
+constexpr unsigned kErrRoute = 4u;      // route cursor past the route end
+constexpr unsigned kErrGeometry = 8u;   // a vehicle left the tile geometry
 
+// One statistics sub-record per step; n_sub of them per step, each on its own
+// 128-byte line, so that block flushes spread over L2 slices.
 struct StatRec {
-    unsigned long long step, active, buffered, waiting, arrived, lane_changes, transfers, inserted, sum_v,
-        vehicle_updates, state_hash, arrived_step;
+    unsigned long long active, buffered, lane_changes, transfers, inserted, sum_v, vehicle_updates, state_hash,
+        arrived_step;
+    unsigned long long pad[7];
 };
+static_assert(sizeof(StatRec) == 128, "StatRec is one line");
 
 struct ScenDev {
-    const uint4 *link_info;       // x wbase, y cells, z lanes | ring << 8, w first slot (bpos)
-    const uint32_t *node_in_off;  // [n_nodes_total + 1] slot ranges per node
-    const uint32_t *node_out_off; // [n_nodes_total + 1]
-    const uint32_t *node_out_link;
+    const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8 | column in tile << 16, w slot base
+    const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8, w dep end
     uint32_t *occ[2];
     int8_t *vel[2];
     uint32_t *vid[2];
     uint4 *slots;
+    uint32_t *link_exit;
     uint2 *veh;
     const uint32_t *route_links;
-    const uint32_t *dep_off;      // [n_links + 1]
-    const uint32_t *dep_ids;
+    const uint32_t *dep_ids;      // id | last-link flag << 31, queue order
     const uint32_t *dep_steps;
     uint32_t *dep_head;           // [n_links] absolute queue index
-    const uint32_t *departed_upto;
-    uint32_t n_dep_steps;
     Ctrl *ctrl;                   // nullptr marks an unused table entry
-    StatRec *stats;               // [kStatsRing]
+    StatRec *stats;               // [kStatsRing * n_sub]
+    uint32_t n_sub;               // sub-records per step (power of two)
     uint32_t vmax, p_threshold, seed_lo, seed_hi, lane_change;
-    uint32_t n_links, n_nodes_total;
+    uint32_t n_links;
 };
 
-struct WorldDev {
-    unsigned int ticket;
-    unsigned int n_link_tiles;
-    unsigned int n_node_tiles;
-    unsigned int n_scen;
-};
-
-// link tile: x scenario slot, y first link, z link count (whole links) or
-// kPartial | first column (one link), w end column (partial tiles)
+// link tile, two uint4: whole links  {scen, l0, nl, 0}            {w_begin, w_end, 0, 0}
+//                       part of one link {scen, l, kPartial | j0, j1} {wbase, cells, lanes | ring << 8, slot base}
 constexpr uint32_t kPartial = 0x80000000u;
+struct LinkTile {
+    uint4 a, b;
+};
+// node tile: {scen, first link, end link, 0}
 
-void launch_link_kernel(const ScenDev *table, const uint4 *tiles, WorldDev *wd, int grid, cudaStream_t s);
-void launch_node_kernel(const ScenDev *table, const uint4 *tiles, WorldDev *wd, int grid, cudaStream_t s);
+void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, uint32_t n_tiles, uint32_t i, int grid,
+                        cudaStream_t s);
+void launch_node_kernel(const ScenDev *table, const uint4 *tiles, uint32_t n_tiles, uint32_t i, int grid,
+                        cudaStream_t s);
+void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 int max_link_blocks();
 int max_node_blocks();

@@ -3,23 +3,27 @@
 // One time step (Sec. 3 and Sec. 4 of Nagel & Rickert) is two launches:
 //
 //   link_kernel  lane change (sub-step 1), velocity update and move
-//                (sub-step 2) of every vehicle on every lane, reading the
-//                state of step t (buffer t&1) and writing the cells of step
-//                t+1 (buffer (t+1)&1); vehicles reaching a link end enter the
-//                lane's link-end buffer or arrive.
-//   node_kernel  node transfer from the link-end buffers to cell 0 of the
-//                next link in fixed priority order, then departures from
-//                parking; the last block to finish closes the step's
-//                statistics and advances the step counter.
+//                (sub-step 2) of every vehicle on every lane.  It reads the
+//                state of step t (buffer t&1) and writes the cells of step
+//                t+1 (buffer (t+1)&1); a vehicle reaching its link end enters
+//                the lane's link-end buffer, or leaves on its last link.
+//   node_kernel  node transfer: for every link m, the buffered vehicles at
+//                m's upstream node whose next link is m, in fixed priority
+//                order (incoming link id, then lane), move to cell 0 of m;
+//                then departures from parking enter m.
+// Once per captured chunk of steps, advance_kernel closes the chunk's
+// statistics and moves the step counter; inside a chunk the step index of a
+// launch is the chunk base plus the launch's position.
 //
-// The paper's split-link boundary exchange (Sec. 4: the first five cells of
-// each half are sent to the other CPU) becomes a one-column halo here: a
-// block owns a tile of 32-cell columns and re-computes the lane-change
-// decisions of the vehicles in the neighbouring column that can influence
-// its own cells, instead of exchanging them.  Work inside a tile is one
-// thread per vehicle: occupancy words are staged in shared memory and the
-// vehicles are compacted into a list, so the cost follows the number of
-// vehicles, not the number of cells.  Gaps come from a 64-bit funnel of two
+// The paper's split-link boundary exchange (Sec. 4: each CPU sends the
+// first five cells of its half of a split link to the other) becomes a
+// one-column halo here: a block owns a tile of 32-cell columns and
+// re-computes the lane-change decisions of the vehicles in the neighbouring
+// column that can influence its own cells instead of exchanging them.  Work
+// inside a tile is one thread per vehicle: occupancy words are staged in
+// shared memory, the vehicles are compacted into a list with their
+// velocity and id loaded once, so the cost follows the number of vehicles
+// and not the number of cells.  Gaps come from a 64-bit funnel of two
 // occupancy words and one find-first-set.
 #include "internal.h"
 
@@ -61,10 +65,14 @@ __device__ __forceinline__ unsigned long long vehicle_term(uint32_t id, uint32_t
     return mix64(a ^ mix64(b));
 }
 
-// Sum of NF per-thread counters over the block, added to dst[f] once.
+__device__ __forceinline__ StatRec *stat_rec(const ScenDev &D, unsigned long long t) {
+    return D.stats + (size_t)(t & (kStatsRing - 1)) * D.n_sub + (blockIdx.x & (D.n_sub - 1));
+}
+
+// Sum of NF per-thread counters over the block, added to base[field[f]] once.
 template <int NF, int NT>
-__device__ __forceinline__ void block_flush(unsigned long long (&acc)[NF], unsigned long long *const (&dst)[NF],
-                                            unsigned long long (*red)[NF]) {
+__device__ __forceinline__ void block_flush(unsigned long long (&acc)[NF], unsigned long long *base,
+                                            const int (&field)[NF], unsigned long long (*red)[NF]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -79,7 +87,7 @@ __device__ __forceinline__ void block_flush(unsigned long long (&acc)[NF], unsig
         unsigned long long s = 0;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-        if (s) atomicAdd(dst[threadIdx.x], s);
+        if (s) atomicAdd(base + field[threadIdx.x], s);
     }
     __syncthreads();
 }
@@ -104,7 +112,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *a, int m, uin
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+        const uint32_t w = lane < nw ? s_warp[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -112,7 +120,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *a, int m, uin
             if (lane >= o) wi += y;
         }
         if (lane < nw) s_warp[lane] = wi - w;  // exclusive warp offsets
-        if (lane == nw - 1) s_warp[31] = wi;     // total
+        if (lane == nw - 1) s_warp[31] = wi;   // total
     }
     __syncthreads();
     uint32_t run = s_warp[warp] + inc - sum;
@@ -129,98 +137,77 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *a, int m, uin
 
 // ------------------------------------------------------------------ link kernel
 
+constexpr int kCols = kTileMaxCols + 2;
+
 struct LinkSmem {
-    uint32_t occ0[kTileSlots][kMaxLanes];  // state of step t
-    uint32_t mv[kTileSlots][kMaxLanes];    // vehicles that changed INTO this lane
-    uint32_t occ1[kTileSlots][kMaxLanes];  // after the lane-change sub-step
-    uint32_t out[kTileSlots][kMaxLanes];   // step t+1, core columns only
-    uint32_t cword[kTileSlots];            // word index of lane 0 of the column
-    uint32_t cx0[kTileSlots];              // first cell of the column within its link
-    int16_t right[kTileSlots], left[kTileSlots];
-    uint8_t clink[kTileSlots], cncell[kTileSlots], clast[kTileSlots], ckind[kTileSlots];
-    uint32_t lcells[kMaxTileCols], lbpos[kMaxTileCols], lid[kMaxTileCols], lcol0[kMaxTileCols];
-    uint32_t lwbase[kMaxTileCols];
-    uint8_t llanes[kMaxTileCols], lring[kMaxTileCols], lopen[kMaxTileCols];
-    uint32_t wpre[kTileSlots * kMaxLanes + 4];
-    uint16_t list[kListCap];
+    uint32_t occ0[kTileSmemWords];  // state of step t (local word index)
+    uint32_t mv[kTileSmemWords];    // vehicles that changed INTO the word's lane
+    uint32_t occ1[kTileSmemWords];  // after the lane-change sub-step
+    uint32_t out[kTileSmemWords];   // step t+1 (core words)
+    uint32_t gw[kTileSmemWords];    // global word index of each local word
+    uint8_t wcol[kTileSmemWords], wlane[kTileSmemWords];
+    uint16_t cw[kCols];             // local word of lane 0 of each column
+    uint32_t cx0[kCols];            // first cell of the column within its link
+    int16_t right[kCols], left[kCols];
+    uint8_t clink[kCols], ckind[kCols];  // ckind: 0 core, 1 left halo, 2 right halo
+    uint32_t lcells[kTileMaxCols], lid[kTileMaxCols], lbpos[kTileMaxCols];
+    uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];
+    uint32_t lentered[kTileMaxCols];  // lanes whose buffer received a vehicle
+    uint32_t wpre[kTileSmemWords + 4];
+    uint16_t code[kListCap];        // (local word << 5) | bit
+    uint8_t ev[kListCap];           // velocity at step t
+    uint8_t eflag[kListCap];        // 1: changed lane in sub-step 1
+    uint32_t eid[kListCap];         // id word (id | last-link flag)
     uint32_t warp_tmp[32];
     unsigned long long red[kLinkThreads / 32][6];
-    int ncore, ncols, nlinks;
+    int ncols, nwords, ncore_words, nlinks;
 };
 
-__device__ __forceinline__ uint32_t gap_ahead(const uint32_t (*O)[kMaxLanes], const int16_t *right, int c, int k,
-                                              int i, uint32_t dist, uint32_t open, uint32_t vmax) {
-    const uint32_t w0 = O[c][k];
-    const int r = right[c];
-    const uint32_t w1 = r >= 0 ? O[r][k] : 0u;
+__device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const LinkSmem &S, int c, int k, int i,
+                                              uint32_t dist, uint32_t open, uint32_t vmax) {
+    const uint32_t w0 = O[S.cw[c] + k];
+    const int r = S.right[c];
+    const uint32_t w1 = r >= 0 ? O[S.cw[r] + k] : 0u;
     const unsigned long long win = (((unsigned long long)w1 << 32) | w0) >> (i + 1);
     uint32_t g = win ? (uint32_t)(__ffsll((long long)win) - 1) : 64u;
     if (g > dist) g = dist + open;
     return g < vmax ? g : vmax;
 }
 
-__device__ __forceinline__ bool room_behind(const uint32_t (*O)[kMaxLanes], const int16_t *left, int c, int k, int i,
+__device__ __forceinline__ bool room_behind(const uint32_t *O, const LinkSmem &S, int c, int k, int i,
                                             uint32_t vmax) {
-    const int l = left[c];
-    const unsigned long long back = ((unsigned long long)O[c][k] << 32) | (l >= 0 ? O[l][k] : 0u);
+    const int l = S.left[c];
+    const unsigned long long back = ((unsigned long long)O[S.cw[c] + k] << 32) | (l >= 0 ? O[S.cw[l] + k] : 0u);
     const unsigned long long mask = ((2ull << vmax) - 1ull) << (32 + i - (int)vmax);
     return (back & mask) == 0ull;
 }
 
-__device__ __forceinline__ uint32_t lc_mask(uint8_t kind, uint32_t vmax) {
-    // core: all; left halo: the last vmax cells; right halo: the first vmax cells
+// Vehicles a tile must look at: every one in its core columns, the last vmax
+// cells of a left halo column (they can move into the core) and the first
+// vmax cells of a right halo column (their lane changes shape the cells the
+// core vehicles look ahead into).
+__device__ __forceinline__ uint32_t list_mask(uint8_t kind, uint32_t vmax) {
     return kind == 0 ? 0xFFFFFFFFu : (kind == 1 ? ~((1u << (32 - vmax)) - 1u) : ((1u << vmax) - 1u));
 }
 
-__device__ __forceinline__ uint32_t mv_mask(uint8_t kind, uint32_t vmax) {
-    return kind == 0 ? 0xFFFFFFFFu : (kind == 1 ? ~((1u << (32 - vmax)) - 1u) : 0u);
-}
-
-// Fills list[] with the vehicles of rank [base, base+kListCap) among the set
-// bits of masked words (word w = column w>>2, lane w&3); wpre holds the
-// exclusive prefix of the per-word counts.
-template <typename MaskFn>
-__device__ __forceinline__ void fill_list(LinkSmem &S, int nwords, uint32_t base, MaskFn maskof) {
-    for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-        uint32_t m = maskof(w);
-        if (!m) continue;
-        const uint32_t r0 = S.wpre[w];
-        const uint32_t cnt = __popc(m);
-        if (r0 + cnt <= base || r0 >= base + kListCap) continue;
-        uint32_t r = r0;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            if (r >= base && r < base + kListCap) S.list[r - base] = (uint16_t)((w << 5) | b);
-            ++r;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kLinkThreads) link_kernel(const ScenDev *__restrict__ table,
-                                                            const uint4 *__restrict__ tiles,
-                                                            const WorldDev *__restrict__ wd) {
+__global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__restrict__ table,
+                                                            const LinkTile *__restrict__ tiles, uint32_t n_tiles,
+                                                            uint32_t pos) {
     __shared__ LinkSmem S;
-    // per-thread counters: lane_changes, vehicle_updates, active, sum_v, state_hash, arrived_step
+    // lane_changes, vehicle_updates, active, sum_v, state_hash, arrived_step
+    static constexpr int kField[6] = {2, 6, 0, 5, 7, 8};
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
-    StatRec *cur_rec = nullptr;
-    const uint32_t n_tiles = wd->n_link_tiles;
+    unsigned long long *cur_rec = nullptr;
 
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint4 td = tiles[tile];
-        const ScenDev &D = table[td.x];
-        const Ctrl *ctrl = D.ctrl;
-        if (ctrl == nullptr) continue;
-        const unsigned long long step = ctrl->step;
-        if (step >= ctrl->target) continue;
-        StatRec *rec = D.stats + (step & (kStatsRing - 1));
+        const LinkTile td = tiles[tile];
+        const ScenDev &D = table[td.a.x];
+        if (D.ctrl == nullptr) continue;
+        const unsigned long long step = D.ctrl->base + pos;
+        if (step >= D.ctrl->target) continue;
+        unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) {
-                unsigned long long *const dst[6] = {&cur_rec->lane_changes, &cur_rec->vehicle_updates,
-                                                    &cur_rec->active, &cur_rec->sum_v, &cur_rec->state_hash,
-                                                    &cur_rec->arrived_step};
-                block_flush<6, kLinkThreads>(acc, dst, S.red);
-            }
+            if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
             cur_rec = rec;
         }
         const uint32_t t = (uint32_t)step;
@@ -228,409 +215,452 @@ __global__ void __launch_bounds__(kLinkThreads) link_kernel(const ScenDev *__res
         const uint32_t vmax = D.vmax;
         const int d = (t & 1u) ? -1 : 1;
         const uint32_t *__restrict__ occ_in = D.occ[cur];
-        const int8_t *__restrict__ vel_in = D.vel[cur];
-        const uint32_t *__restrict__ vid_in = D.vid[cur];
 
-        // ---------------- tile geometry
-        const bool partial = (td.z & kPartial) != 0u;
+        // ---------------- tile geometry and the occupancy of step t
+        const bool partial = (td.a.z & kPartial) != 0u;
         if (!partial) {
-            const int nl = (int)td.z;
+            const int nl = (int)td.a.z;
+            const uint32_t wb = td.b.x;
+            const int nw = (int)(td.b.y - td.b.x);
             for (int q = threadIdx.x; q < nl; q += blockDim.x) {
-                const uint4 li = D.link_info[td.y + q];
+                const uint4 li = D.lk_info[td.a.y + q];
                 S.lcells[q] = li.y;
                 S.llanes[q] = (uint8_t)(li.z & 0xFFu);
                 S.lring[q] = (uint8_t)((li.z >> 8) & 1u);
+                S.lid[q] = td.a.y + q;
                 S.lbpos[q] = li.w;
-                S.lid[q] = td.y + q;
-                S.lwbase[q] = li.x;
-                S.lcol0[q] = (li.y + 31u) >> 5;
-            }
-            __syncthreads();
-            const uint32_t ncore = block_exclusive_scan(S.lcol0, nl, S.warp_tmp);
-            for (int q = threadIdx.x; q < nl; q += blockDim.x) {
-                const uint32_t cells = S.lcells[q], lanes = S.llanes[q], ring = S.lring[q];
-                const int ncol = (int)((cells + 31u) >> 5), c0 = (int)S.lcol0[q];
+                S.lexit[q] = (uint8_t)D.link_exit[td.a.y + q];
+                S.lentered[q] = 0;
+                const int ncol = (int)((li.y + 31u) >> 5), c0 = (int)((li.z >> 16) & 0xFFu);
+                const uint32_t lanes = li.z & 0xFFu, ring = (li.z >> 8) & 1u;
                 for (int j = 0; j < ncol; ++j) {
                     const int c = c0 + j;
-                    S.cword[c] = S.lwbase[q] + (uint32_t)j * lanes;
+                    const uint32_t lw = li.x - wb + (uint32_t)j * lanes;
+                    S.cw[c] = (uint16_t)lw;
                     S.cx0[c] = 32u * (uint32_t)j;
                     S.clink[c] = (uint8_t)q;
-                    S.cncell[c] = (uint8_t)min(32u, cells - 32u * (uint32_t)j);
-                    S.clast[c] = (uint8_t)(!ring && j == ncol - 1);
                     S.ckind[c] = 0;
                     S.right[c] = (int16_t)(j + 1 < ncol ? c + 1 : (ring ? c0 : -1));
                     S.left[c] = (int16_t)(j > 0 ? c - 1 : (ring ? c0 + ncol - 1 : -1));
-                }
-                uint8_t open = 0;
-                if (!ring) {
-                    const uint32_t *sx = reinterpret_cast<const uint32_t *>(D.slots + S.lbpos[q]);
-                    for (uint32_t k = 0; k < lanes; ++k) open |= (uint8_t)((sx[4 * k] == kSlotEmpty) << k);
-                }
-                S.lopen[q] = open;
-            }
-            if (threadIdx.x == 0) { S.ncore = (int)ncore; S.ncols = (int)ncore; S.nlinks = nl; }
-        } else {
-            if (threadIdx.x == 0) {
-                const uint4 li = D.link_info[td.y];
-                const uint32_t cells = li.y, lanes = li.z & 0xFFu, ring = (li.z >> 8) & 1u;
-                const int ncol = (int)((cells + 31u) >> 5);
-                const int j0 = (int)(td.z & ~kPartial), j1 = (int)td.w;
-                S.lcells[0] = cells; S.llanes[0] = (uint8_t)lanes; S.lring[0] = (uint8_t)ring;
-                S.lbpos[0] = li.w; S.lid[0] = td.y; S.lwbase[0] = li.x;
-                uint8_t open = 0;
-                if (!ring && j1 == ncol) {
-                    const uint32_t *sx = reinterpret_cast<const uint32_t *>(D.slots + li.w);
-                    for (uint32_t k = 0; k < lanes; ++k) open |= (uint8_t)((sx[4 * k] == kSlotEmpty) << k);
-                }
-                S.lopen[0] = open;
-                const int ncore = j1 - j0;
-                const bool has_l = j0 > 0 || ring;
-                const bool has_r = j1 < ncol || ring;
-                int nc = ncore;
-                const int hl = has_l ? nc++ : -1;
-                const int hr = has_r ? nc++ : -1;
-                for (int c = 0; c < ncore; ++c) {
-                    const int j = j0 + c;
-                    S.cword[c] = li.x + (uint32_t)j * lanes;
-                    S.cx0[c] = 32u * (uint32_t)j;
-                    S.clink[c] = 0;
-                    S.cncell[c] = (uint8_t)min(32u, cells - 32u * (uint32_t)j);
-                    S.clast[c] = (uint8_t)(!ring && j == ncol - 1);
-                    S.ckind[c] = 0;
-                    S.right[c] = (int16_t)(c + 1 < ncore ? c + 1 : hr);
-                    S.left[c] = (int16_t)(c > 0 ? c - 1 : hl);
-                }
-                if (hl >= 0) {
-                    const int j = j0 > 0 ? j0 - 1 : ncol - 1;
-                    S.cword[hl] = li.x + (uint32_t)j * lanes;
-                    S.cx0[hl] = 32u * (uint32_t)j;
-                    S.clink[hl] = 0;
-                    S.cncell[hl] = (uint8_t)min(32u, cells - 32u * (uint32_t)j);
-                    S.clast[hl] = 0;
-                    S.ckind[hl] = 1;
-                    S.right[hl] = 0;
-                    S.left[hl] = -1;
-                }
-                if (hr >= 0) {
-                    const int j = j1 < ncol ? j1 : 0;
-                    S.cword[hr] = li.x + (uint32_t)j * lanes;
-                    S.cx0[hr] = 32u * (uint32_t)j;
-                    S.clink[hr] = 0;
-                    S.cncell[hr] = (uint8_t)min(32u, cells - 32u * (uint32_t)j);
-                    S.clast[hr] = 0;
-                    S.ckind[hr] = 2;
-                    S.right[hr] = -1;
-                    S.left[hr] = (int16_t)(ncore - 1);
-                }
-                S.ncore = ncore; S.ncols = nc; S.nlinks = 1;
-            }
-        }
-        __syncthreads();
-        const int ncore = S.ncore, ncols = S.ncols;
-        const int nwords = ncols * kMaxLanes;
-
-        // ---------------- stage occupancy of step t
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-            const int c = w >> 2, k = w & 3;
-            const uint32_t lanes = S.llanes[S.clink[c]];
-            S.occ0[c][k] = k < (int)lanes ? occ_in[S.cword[c] + k] : 0u;
-            S.mv[c][k] = 0u;
-            S.out[c][k] = 0u;
-        }
-        __syncthreads();
-
-        // ---------------- sub-step 1: lane changes on the state of step t
-        const bool lc_on = D.lane_change != 0u;
-        if (lc_on) {
-            auto lcword = [&](int w) -> uint32_t {
-                const int c = w >> 2, k = w & 3, kt = k + d;
-                const int lanes = S.llanes[S.clink[c]];
-                if (k >= lanes || kt < 0 || kt >= lanes) return 0u;
-                return S.occ0[c][k] & lc_mask(S.ckind[c], vmax);
-            };
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.wpre[w] = __popc(lcword(w));
-            __syncthreads();
-            const uint32_t total = block_exclusive_scan(S.wpre, nwords, S.warp_tmp);
-            for (uint32_t base = 0; base < total; base += kListCap) {
-                fill_list(S, nwords, base, lcword);
-                __syncthreads();
-                const uint32_t n = min((uint32_t)kListCap, total - base);
-                for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-                    const uint32_t code = S.list[e];
-                    const int i = code & 31, w = code >> 5, c = w >> 2, k = w & 3, kt = k + d;
-                    const int q = S.clink[c];
-                    const uint32_t ring = S.lring[q];
-                    const uint32_t x = S.cx0[c] + (uint32_t)i;
-                    const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
-                    const size_t p = (size_t)(S.cword[c] + (uint32_t)k) * 32u + (uint32_t)i;
-                    const uint32_t v = (uint32_t)vel_in[p];
-                    uint32_t last = 0u;
-                    if (dist < vmax) last = vid_in[p] >> 31;
-                    const uint32_t open_own = ((S.lopen[q] >> k) & 1u) | last;
-                    const uint32_t open_tgt = ((S.lopen[q] >> kt) & 1u) | last;
-                    const uint32_t g_own = gap_ahead(S.occ0, S.right, c, k, i, dist, open_own, vmax);
-                    const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
-                    if (g_own < want) {
-                        const uint32_t g_tgt = gap_ahead(S.occ0, S.right, c, kt, i, dist, open_tgt, vmax);
-                        if (g_tgt > g_own && room_behind(S.occ0, S.left, c, kt, i, vmax)) {
-                            atomicOr(&S.mv[c][kt], 1u << i);
-                            if (S.ckind[c] == 0) acc[0] += 1;
-                        }
+                    for (uint32_t k = 0; k < lanes; ++k) {
+                        S.wcol[lw + k] = (uint8_t)c;
+                        S.wlane[lw + k] = (uint8_t)k;
                     }
                 }
-                __syncthreads();
+                if (q == nl - 1) S.ncols = c0 + ncol;
             }
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-                const int c = w >> 2, k = w & 3, kf = k + d;
-                const uint32_t leaving = (kf >= 0 && kf < kMaxLanes) ? S.mv[c][kf] : 0u;
-                S.occ1[c][k] = (S.occ0[c][k] & ~leaving) | S.mv[c][k];
+            for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+                S.occ0[w] = occ_in[wb + w];
+                S.gw[w] = wb + w;
+                S.mv[w] = 0u;
+                S.out[w] = 0u;
+            }
+            if (threadIdx.x == 0) {
+                S.nwords = nw;
+                S.ncore_words = nw;
+                S.nlinks = nl;
             }
         } else {
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.occ1[w >> 2][w & 3] = S.occ0[w >> 2][w & 3];
+            const uint32_t l = td.a.y, wbase = td.b.x, cells = td.b.y;
+            const uint32_t lanes = td.b.z & 0xFFu, ring = (td.b.z >> 8) & 1u;
+            const int ncol = (int)((cells + 31u) >> 5);
+            const int j0 = (int)(td.a.z & ~kPartial), j1 = (int)td.a.w;
+            const int ncore = j1 - j0;
+            const bool has_l = j0 > 0 || ring, has_r = j1 < ncol || ring;
+            const int hl = has_l ? ncore : -1;
+            const int hr = has_r ? ncore + (has_l ? 1 : 0) : -1;
+            const int ncols = ncore + (has_l ? 1 : 0) + (has_r ? 1 : 0);
+            for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+                int j;
+                uint8_t kind;
+                int16_t rr, ll;
+                if (c < ncore) {
+                    j = j0 + c;
+                    kind = 0;
+                    rr = (int16_t)(c + 1 < ncore ? c + 1 : hr);
+                    ll = (int16_t)(c > 0 ? c - 1 : hl);
+                } else if (c == hl) {
+                    j = j0 > 0 ? j0 - 1 : ncol - 1;
+                    kind = 1;
+                    rr = 0;
+                    ll = -1;
+                } else {
+                    j = j1 < ncol ? j1 : 0;
+                    kind = 2;
+                    rr = -1;
+                    ll = (int16_t)(ncore - 1);
+                }
+                const uint32_t lw = (uint32_t)c * lanes;
+                S.cw[c] = (uint16_t)lw;
+                S.cx0[c] = 32u * (uint32_t)j;
+                S.clink[c] = 0;
+                S.ckind[c] = kind;
+                S.right[c] = rr;
+                S.left[c] = ll;
+                for (uint32_t k = 0; k < lanes; ++k) {
+                    const uint32_t g = wbase + (uint32_t)j * lanes + k;
+                    S.gw[lw + k] = g;
+                    S.occ0[lw + k] = occ_in[g];
+                    S.mv[lw + k] = 0u;
+                    S.out[lw + k] = 0u;
+                    S.wcol[lw + k] = (uint8_t)c;
+                    S.wlane[lw + k] = (uint8_t)k;
+                }
+            }
+            if (threadIdx.x == 0) {
+                S.lcells[0] = cells;
+                S.llanes[0] = (uint8_t)lanes;
+                S.lring[0] = (uint8_t)ring;
+                S.lid[0] = l;
+                S.lbpos[0] = td.b.w;
+                S.lexit[0] = (!ring && j1 == ncol) ? (uint8_t)D.link_exit[l] : (uint8_t)0;
+                S.lentered[0] = 0;
+                S.ncols = ncols;
+                S.nwords = ncols * (int)lanes;
+                S.ncore_words = ncore * (int)lanes;
+                S.nlinks = 1;
+            }
+        }
+        __syncthreads();
+        const int nwords = S.nwords, ncore_words = S.ncore_words;
+
+        // ---------------- compact the vehicles; load their velocity and id once
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x)
+            S.wpre[w] = __popc(S.occ0[w] & list_mask(S.ckind[S.wcol[w]], vmax));
+        __syncthreads();
+        const uint32_t total = block_exclusive_scan(S.wpre, nwords, S.warp_tmp);
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+            uint32_t m = S.occ0[w] & list_mask(S.ckind[S.wcol[w]], vmax);
+            uint32_t r = S.wpre[w];
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                S.code[r++] = (uint16_t)((w << 5) | b);
+            }
+        }
+        __syncthreads();
+        {
+            const int8_t *__restrict__ vel_in = D.vel[cur];
+            const uint32_t *__restrict__ vid_in = D.vid[cur];
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const uint32_t code = S.code[e];
+                const size_t p = (size_t)S.gw[code >> 5] * 32u + (code & 31u);
+                S.ev[e] = (uint8_t)vel_in[p];
+                S.eid[e] = vid_in[p];
+                S.eflag[e] = 0;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- sub-step 1: lane changes, decided on the state of step t
+        const bool lc_on = D.lane_change != 0u;
+        if (lc_on) {
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const uint32_t code = S.code[e];
+                const int w = code >> 5, i = code & 31;
+                const int c = S.wcol[w], k = S.wlane[w], kt = k + d;
+                const int q = S.clink[c];
+                if (kt < 0 || kt >= (int)S.llanes[q]) continue;
+                const uint32_t ring = S.lring[q];
+                const uint32_t x = S.cx0[c] + (uint32_t)i;
+                const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
+                const uint32_t v = S.ev[e];
+                const uint32_t last = S.eid[e] >> 31;
+                const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
+                const uint32_t g_own =
+                    gap_ahead(S.occ0, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
+                if (g_own >= want) continue;
+                const uint32_t g_tgt =
+                    gap_ahead(S.occ0, S, c, kt, i, dist, ((S.lexit[q] >> kt) & 1u) | last, vmax);
+                if (g_tgt > g_own && room_behind(S.occ0, S, c, kt, i, vmax)) {
+                    atomicOr(&S.mv[S.cw[c] + kt], 1u << i);
+                    S.eflag[e] = 1;
+                    if (S.ckind[c] == 0) acc[0] += 1;
+                }
+            }
+            __syncthreads();
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+                const int c = S.wcol[w], k = S.wlane[w], kf = k + d;
+                const uint32_t leaving = (kf >= 0 && kf < (int)S.llanes[S.clink[c]]) ? S.mv[S.cw[c] + kf] : 0u;
+                S.occ1[w] = (S.occ0[w] & ~leaving) | S.mv[w];
+            }
+        } else {
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.occ1[w] = S.occ0[w];
         }
         __syncthreads();
 
         // ---------------- sub-step 2: velocity update and move
         {
-            auto mvword = [&](int w) -> uint32_t {
-                const int c = w >> 2, k = w & 3;
-                return S.occ1[c][k] & mv_mask(S.ckind[c], vmax);
-            };
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.wpre[w] = __popc(mvword(w));
-            __syncthreads();
-            const uint32_t total = block_exclusive_scan(S.wpre, nwords, S.warp_tmp);
             int8_t *__restrict__ vel_out = D.vel[nxt];
             uint32_t *__restrict__ vid_out = D.vid[nxt];
             const uint32_t key0 = D.seed_lo, key1 = D.seed_hi, pthr = D.p_threshold;
-            for (uint32_t base = 0; base < total; base += kListCap) {
-                fill_list(S, nwords, base, mvword);
-                __syncthreads();
-                const uint32_t n = min((uint32_t)kListCap, total - base);
-                for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-                    const uint32_t code = S.list[e];
-                    const int i = code & 31, w = code >> 5, c = w >> 2, k = w & 3;
-                    const int q = S.clink[c];
-                    const int ks = (lc_on && ((S.mv[c][k] >> i) & 1u)) ? k - d : k;
-                    const size_t p = (size_t)(S.cword[c] + (uint32_t)ks) * 32u + (uint32_t)i;
-                    const uint32_t v0 = (uint32_t)vel_in[p];
-                    const uint32_t idw = vid_in[p];
-                    const uint32_t id = idw & kIdMask, last = idw >> 31;
-                    const uint32_t ring = S.lring[q];
-                    const uint32_t x = S.cx0[c] + (uint32_t)i;
-                    const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
-                    const uint32_t open = ((S.lopen[q] >> k) & 1u) | last;
-                    uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;                            // (i)
-                    const uint32_t g = gap_ahead(S.occ1, S.right, c, k, i, dist, open, vmax);
-                    if (v > g) v = g;                                                         // (ii)
-                    if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;           // (iii)
-                    const bool core = S.ckind[c] == 0;
-                    if (core) acc[1] += 1;
-                    int ni = i + (int)v;
-                    if (!ring && x + v >= S.lcells[q]) {
-                        // reaches the link end (only possible for a vehicle owned by
-                        // this tile: a split leaves more than 2*vmax cells after it)
-                        if (!core) {
-                            atomicOr(&D.ctrl->error, kErrCellTaken);
-                        } else if (last) {
-                            acc[5] += 1;  // leaves to parking
-                        } else {
-                            const uint32_t s = S.lbpos[q] + (uint32_t)k;
-                            const uint2 ve = D.veh[id];
-                            if (ve.x + 1u >= ve.y) {
-                                atomicOr(&D.ctrl->error, kErrRoute);
-                            } else {
-                                const uint32_t m = D.route_links[ve.x + 1u];
-                                const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
-                                uint32_t *sx = reinterpret_cast<uint32_t *>(D.slots + s);
-                                if (*sx != kSlotEmpty) atomicOr(&D.ctrl->error, kErrSlotTaken);
-                                D.slots[s] = make_uint4(id | fl, m, S.lid[q], v | ((uint32_t)k << 8));
-                            }
-                        }
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const uint32_t code = S.code[e];
+                const int w = code >> 5, i = code & 31;
+                const int c = S.wcol[w];
+                const uint8_t kind = S.ckind[c];
+                if (kind == 2 || (kind == 1 && i < 32 - (int)vmax)) continue;
+                const int k = S.wlane[w] + (S.eflag[e] ? d : 0);
+                const int q = S.clink[c];
+                const uint32_t idw = S.eid[e];
+                const uint32_t id = idw & kIdMask, last = idw >> 31;
+                const uint32_t ring = S.lring[q];
+                const uint32_t x = S.cx0[c] + (uint32_t)i;
+                const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
+                const uint32_t v0 = S.ev[e];
+                uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;  // (i) accelerate
+                const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
+                if (v > g) v = g;                                                 // (ii) gap
+                if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;  // (iii) random
+                const bool core = kind == 0;
+                if (core) acc[1] += 1;
+                if (!ring && x + v >= S.lcells[q]) {
+                    // reaches the link end; a split leaves more than 2*vmax cells
+                    // after it, so such a vehicle is always in this tile's core
+                    if (!core) {
+                        atomicOr(&D.ctrl->error, kErrGeometry);
+                    } else if (last) {
+                        acc[5] += 1;  // leaves to parking
                     } else {
-                        int dc = c;
-                        if (ni >= 32) { dc = S.right[c]; ni -= 32; }
-                        if (dc < 0) {
-                            atomicOr(&D.ctrl->error, kErrCellTaken);
-                        } else if (S.ckind[dc] == 0) {
-                            const size_t pd = (size_t)(S.cword[dc] + (uint32_t)k) * 32u + (uint32_t)ni;
-                            vel_out[pd] = (int8_t)v;
-                            vid_out[pd] = idw;
-                            const uint32_t old = atomicOr(&S.out[dc][k], 1u << ni);
-                            if (old & (1u << ni)) atomicOr(&D.ctrl->error, kErrCellTaken);
-                            acc[2] += 1;
-                            acc[3] += v;
-                            acc[4] += vehicle_term(id, S.lid[q], (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v);
+                        const uint2 ve = D.veh[id];
+                        if (ve.x + 1u >= ve.y) {
+                            atomicOr(&D.ctrl->error, kErrRoute);
+                        } else {
+                            const uint32_t m = D.route_links[ve.x + 1u];
+                            const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
+                            uint4 *slot = D.slots + S.lbpos[q] + (uint32_t)k;
+                            if (!((S.lexit[q] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
+                            *slot = make_uint4(id | fl, m, S.lid[q], v | ((uint32_t)k << 8) | (S.lcells[q] << 10));
+                            atomicOr(&S.lentered[q], 1u << k);
                         }
                     }
+                } else {
+                    int ni = i + (int)v;
+                    int dc = c;
+                    if (ni >= 32) {
+                        dc = S.right[c];
+                        ni -= 32;
+                    }
+                    if (dc < 0) {
+                        atomicOr(&D.ctrl->error, kErrGeometry);
+                    } else if (S.ckind[dc] == 0) {
+                        const int dw = S.cw[dc] + k;
+                        const size_t pd = (size_t)S.gw[dw] * 32u + (uint32_t)ni;
+                        vel_out[pd] = (int8_t)v;
+                        vid_out[pd] = idw;
+                        const uint32_t old = atomicOr(&S.out[dw], 1u << ni);
+                        if (old & (1u << ni)) atomicOr(&D.ctrl->error, kErrCellTaken);
+                        acc[2] += 1;
+                        acc[3] += v;
+                        acc[4] += vehicle_term(id, S.lid[q], (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v);
+                    }
                 }
-                __syncthreads();
-            }
-        }
-
-        // ---------------- write the occupancy of step t+1 for the core columns
-        {
-            uint32_t *__restrict__ occ_out = D.occ[nxt];
-            for (int w = threadIdx.x; w < ncore * kMaxLanes; w += blockDim.x) {
-                const int c = w >> 2, k = w & 3;
-                if (k < (int)S.llanes[S.clink[c]]) occ_out[S.cword[c] + k] = S.out[c][k];
             }
         }
         __syncthreads();
+
+        // ---------------- write the occupancy of step t+1 and the buffer states
+        {
+            uint32_t *__restrict__ occ_out = D.occ[nxt];
+            for (int w = threadIdx.x; w < ncore_words; w += blockDim.x) occ_out[S.gw[w]] = S.out[w];
+            for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x)
+                if (S.lentered[q]) D.link_exit[S.lid[q]] = (uint32_t)S.lexit[q] & ~S.lentered[q];
+        }
+        __syncthreads();
     }
-    if (cur_rec) {
-        unsigned long long *const dst[6] = {&cur_rec->lane_changes, &cur_rec->vehicle_updates, &cur_rec->active,
-                                            &cur_rec->sum_v, &cur_rec->state_hash, &cur_rec->arrived_step};
-        block_flush<6, kLinkThreads>(acc, dst, S.red);
-    }
+    if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
 }
 
 // ------------------------------------------------------------------ node kernel
 
+constexpr int kSlotPrefetch = 8;
+
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
-                                                            const uint4 *__restrict__ tiles, WorldDev *wd) {
+                                                            const uint4 *__restrict__ tiles, uint32_t n_tiles,
+                                                            uint32_t pos) {
     __shared__ unsigned long long red[kNodeThreads / 32][6];
-    __shared__ bool am_last;
     // transfers, inserted, buffered, active, sum_v, state_hash
+    static constexpr int kField[6] = {3, 4, 1, 0, 5, 7};
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
-    StatRec *cur_rec = nullptr;
-    const uint32_t n_tiles = wd->n_node_tiles;
+    unsigned long long *cur_rec = nullptr;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint4 td = tiles[tile];
         const ScenDev &D = table[td.x];
         if (D.ctrl == nullptr) continue;
-        const unsigned long long step = D.ctrl->step;
+        const unsigned long long step = D.ctrl->base + pos;
         if (step >= D.ctrl->target) continue;
-        StatRec *rec = D.stats + (step & (kStatsRing - 1));
+        unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) {
-                unsigned long long *const dst[6] = {&cur_rec->transfers, &cur_rec->inserted, &cur_rec->buffered,
-                                                    &cur_rec->active, &cur_rec->sum_v, &cur_rec->state_hash};
-                block_flush<6, kNodeThreads>(acc, dst, red);
-            }
+            if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
             cur_rec = rec;
         }
         const uint32_t t = (uint32_t)step;
         const int nxt = (int)((step + 1ull) & 1ull);
-        uint32_t *occ = D.occ[nxt];
-        int8_t *vel = D.vel[nxt];
-        uint32_t *vid = D.vid[nxt];
-        const uint32_t n = td.y + threadIdx.x;
-        if (n < td.z) {
-            // node transfer, priority = slot order (incoming link id, then lane)
-            const uint32_t s_end = D.node_in_off[n + 1];
-            for (uint32_t s = D.node_in_off[n]; s < s_end; ++s) {
-                const uint4 sl = D.slots[s];
-                if (sl.x == kSlotEmpty) continue;
-                const uint32_t id = sl.x & kIdMask, m = sl.y, l = sl.z;
-                const uint32_t v = sl.w & 0xFFu, ks = (sl.w >> 8) & 0xFFu;
-                const uint4 mi = D.link_info[m];
-                const uint32_t lanes = mi.z & 0xFFu;
+        const uint32_t m = td.y + threadIdx.x;
+        if (m < td.z) {
+            uint32_t *occ = D.occ[nxt];
+            int8_t *vel = D.vel[nxt];
+            uint32_t *vid = D.vid[nxt];
+            const uint4 nd = D.nd_info[m];
+            uint32_t h = D.dep_head[m];
+            const uint32_t slot_lo = nd.x, wbase = nd.y, cnt = nd.z & 0xFFu, lanes = (nd.z >> 8) & 0xFFu;
+            const uint32_t dep_end = nd.w;
+            // occupancy of cell 0 of every lane of m after the move
+            uint32_t o[kMaxLanes];
+            uint32_t free_mask = 0;
+#pragma unroll
+            for (int k = 0; k < kMaxLanes; ++k) {
+                o[k] = (uint32_t)k < lanes ? occ[wbase + k] : 1u;
+                free_mask |= (uint32_t)(!(o[k] & 1u)) << k;
+            }
+            uint4 sl[kSlotPrefetch];
+#pragma unroll
+            for (int s = 0; s < kSlotPrefetch; ++s)
+                sl[s] = (uint32_t)s < cnt ? D.slots[slot_lo + s] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+            // node transfer in priority order (slot order)
+            for (uint32_t s = 0; s < cnt; ++s) {
+                uint4 x;
+                if (s < (uint32_t)kSlotPrefetch) {
+                    // select the prefetched slot without dynamic register indexing
+                    x = sl[0];
+#pragma unroll
+                    for (int u = 1; u < kSlotPrefetch; ++u)
+                        if ((uint32_t)u == s) x = sl[u];
+                } else {
+                    x = D.slots[slot_lo + s];
+                }
+                if (x.x == kSlotEmpty || x.y != m) continue;
+                const uint32_t id = x.x & kIdMask, l = x.z;
+                const uint32_t v = x.w & 0xFFu, ks = (x.w >> 8) & 3u, cells_l = x.w >> 10;
                 const uint32_t pref = ks < lanes - 1u ? ks : lanes - 1u;
-                bool placed = false;
-                for (uint32_t tr = 0; tr < lanes; ++tr) {
-                    const uint32_t qn = tr == 0 ? pref : (tr - 1u < pref ? tr - 1u : tr);
-                    const uint32_t w = mi.x + qn;  // column 0, lane qn
-                    const uint32_t o = occ[w];
-                    if (!(o & 1u)) {
-                        occ[w] = o | 1u;
-                        vel[(size_t)w * 32u] = (int8_t)v;
-                        vid[(size_t)w * 32u] = sl.x;  // id with the last-link flag of the next link
-                        D.veh[id].x += 1u;
-                        D.slots[s].x = kSlotEmpty;
-                        acc[0] += 1; acc[3] += 1; acc[4] += v;
-                        acc[5] += vehicle_term(id, m, qn, 0u, v);
-                        placed = true;
-                        break;
-                    }
+                uint32_t qn = 0xFFu;
+                if ((free_mask >> pref) & 1u) {
+                    qn = pref;
+                } else {
+                    const uint32_t rest = free_mask & ~(1u << pref);
+                    if (rest) qn = (uint32_t)(__ffs(rest) - 1);
                 }
-                if (!placed) {
+                if (qn != 0xFFu) {
+                    free_mask &= ~(1u << qn);
+                    const uint32_t w = wbase + qn;  // column 0 of lane qn
+                    occ[w] = o[qn & 3] | 1u;
+                    vel[(size_t)w * 32u] = (int8_t)v;
+                    vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
+                    atomicAdd(&D.veh[id].x, 1u);
+                    D.slots[slot_lo + s].x = kSlotEmpty;
+                    atomicOr(&D.link_exit[l], 1u << ks);
+                    acc[0] += 1;
+                    acc[3] += 1;
+                    acc[4] += v;
+                    acc[5] += vehicle_term(id, m, qn, 0u, v);
+                } else {
                     acc[2] += 1;
-                    acc[5] += vehicle_term(id, l, ks, D.link_info[l].y, v);
+                    acc[5] += vehicle_term(id, l, ks, cells_l, v);
                 }
             }
-            // departures from parking onto the links leaving this node
-            const uint32_t a_end = D.node_out_off[n + 1];
-            for (uint32_t a = D.node_out_off[n]; a < a_end; ++a) {
-                const uint32_t m = D.node_out_link[a];
-                uint32_t h = D.dep_head[m];
-                const uint32_t e = D.dep_off[m + 1];
-                if (h >= e || D.dep_steps[h] > t) continue;
-                const uint4 mi = D.link_info[m];
-                const uint32_t lanes = mi.z & 0xFFu;
-                while (h < e && D.dep_steps[h] <= t) {
-                    uint32_t qn = 0;
-                    for (; qn < lanes; ++qn)
-                        if (!(occ[mi.x + qn] & 1u)) break;
-                    if (qn == lanes) break;
-                    const uint32_t id = D.dep_ids[h];
-                    const uint2 ve = D.veh[id];
-                    const uint32_t w = mi.x + qn;
-                    occ[w] |= 1u;
-                    vel[(size_t)w * 32u] = 0;
-                    vid[(size_t)w * 32u] = id | ((ve.x + 1u == ve.y) ? kLastLinkBit : 0u);
-                    acc[1] += 1; acc[3] += 1;
-                    acc[5] += vehicle_term(id, m, qn, 0u, 0u);
-                    ++h;
-                }
-                D.dep_head[m] = h;
+            // departures from parking onto m
+            const uint32_t h0 = h;
+            while (h < dep_end && free_mask && D.dep_steps[h] <= t) {
+                const uint32_t qn = (uint32_t)(__ffs(free_mask) - 1);
+                free_mask &= ~(1u << qn);
+                const uint32_t w = wbase + qn;
+                occ[w] = o[qn & 3] | 1u;
+                vel[(size_t)w * 32u] = 0;
+                const uint32_t idw = D.dep_ids[h];
+                vid[(size_t)w * 32u] = idw;
+                acc[1] += 1;
+                acc[3] += 1;
+                acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
+                ++h;
             }
+            if (h != h0) D.dep_head[m] = h;
         }
     }
-    if (cur_rec) {
-        unsigned long long *const dst[6] = {&cur_rec->transfers, &cur_rec->inserted, &cur_rec->buffered,
-                                            &cur_rec->active, &cur_rec->sum_v, &cur_rec->state_hash};
-        block_flush<6, kNodeThreads>(acc, dst, red);
+    if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
+}
+
+// ------------------------------------------------------------------ chunk close
+
+// One block per scenario: sums the statistics of the g steps just run,
+// moves the step counter and clears the records of the next chunk.
+__global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict__ table, uint32_t g_max) {
+    const ScenDev &D = table[blockIdx.x];
+    Ctrl *c = D.ctrl;
+    if (c == nullptr) return;
+    __shared__ unsigned long long red[4][6];
+    __shared__ unsigned long long s_base;
+    const unsigned long long base = c->base, target = c->target;
+    const uint32_t g = base < target ? (uint32_t)min((unsigned long long)g_max, target - base) : 0u;
+    const uint32_t nsub = D.n_sub;
+    // vehicle_updates, lane_changes, transfers, arrived_step, inserted, last-step hash
+    unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
+    for (uint32_t r = threadIdx.x; r < g * nsub; r += blockDim.x) {
+        const unsigned long long t = base + r / nsub;
+        const StatRec &R = D.stats[(size_t)(t & (kStatsRing - 1)) * nsub + r % nsub];
+        a[0] += R.vehicle_updates;
+        a[1] += R.lane_changes;
+        a[2] += R.transfers;
+        a[3] += R.arrived_step;
+        a[4] += R.inserted;
+        if (t == base + g - 1) a[5] += R.state_hash;
     }
-    // The last block to finish closes the step of every active scenario.
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        unsigned long long v = a[f];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][f] = v;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int tk = atomicAdd(&wd->ticket, 1u);
-        am_last = (tk == gridDim.x - 1u);
+        unsigned long long s[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < 4; ++w)
+            for (int f = 0; f < 6; ++f) s[f] += red[w][f];
+        if (g) {
+            c->tot_updates += s[0];
+            c->tot_lane_changes += s[1];
+            c->tot_transfers += s[2];
+            c->arrived += s[3];
+            c->inserted += s[4];
+            c->last_hash = s[5];
+            c->steps_run += g;
+            c->base = base + g;
+        }
+        s_base = base + g;
     }
     __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    const uint32_t n_scen = wd->n_scen;
-    for (uint32_t s = threadIdx.x; s < n_scen; s += blockDim.x) {
-        const ScenDev &D = table[s];
-        Ctrl *c = D.ctrl;
-        if (c == nullptr) continue;
-        const unsigned long long step = __ldcg(&c->step);
-        if (step >= __ldcg(&c->target)) continue;
-        StatRec *r = D.stats + (step & (kStatsRing - 1));
-        const unsigned long long arrived = __ldcg(&c->arrived) + __ldcg(&r->arrived_step);
-        const unsigned long long inserted = __ldcg(&c->inserted) + __ldcg(&r->inserted);
-        unsigned long long departed = 0;
-        if (D.n_dep_steps) departed = D.departed_upto[step < D.n_dep_steps ? step : D.n_dep_steps - 1];
-        r->step = step;
-        r->arrived = arrived;
-        r->waiting = departed - inserted;
-        c->arrived = arrived;
-        c->inserted = inserted;
-        StatRec *nr = D.stats + ((step + 1ull) & (kStatsRing - 1));
-        unsigned long long *z = reinterpret_cast<unsigned long long *>(nr);
-        for (int f = 0; f < (int)(sizeof(StatRec) / 8); ++f) z[f] = 0ull;
-        c->step = step + 1ull;
+    if (g == 0) return;
+    // clear the records of the next chunk
+    const unsigned long long nb = s_base;
+    const uint32_t per = nsub * (uint32_t)(sizeof(StatRec) / 8);
+    for (uint32_t u = threadIdx.x; u < kChunk * per; u += blockDim.x) {
+        const unsigned long long t = nb + u / per;
+        unsigned long long *z = reinterpret_cast<unsigned long long *>(D.stats + (size_t)(t & (kStatsRing - 1)) * nsub);
+        z[u % per] = 0ull;
     }
-    if (threadIdx.x == 0) wd->ticket = 0u;
 }
 
 __global__ void set_target_kernel(Ctrl *ctrl, unsigned long long target) { ctrl->target = target; }
 
-void launch_link_kernel(const ScenDev *table, const uint4 *tiles, WorldDev *wd, int grid, cudaStream_t s) {
-    link_kernel<<<grid, kLinkThreads, 0, s>>>(table, tiles, wd);
+void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, uint32_t n_tiles, uint32_t i, int grid,
+                        cudaStream_t s) {
+    link_kernel<<<grid, kLinkThreads, 0, s>>>(table, tiles, n_tiles, i);
 }
 
-void launch_node_kernel(const ScenDev *table, const uint4 *tiles, WorldDev *wd, int grid, cudaStream_t s) {
-    node_kernel<<<grid, kNodeThreads, 0, s>>>(table, tiles, wd);
+void launch_node_kernel(const ScenDev *table, const uint4 *tiles, uint32_t n_tiles, uint32_t i, int grid,
+                        cudaStream_t s) {
+    node_kernel<<<grid, kNodeThreads, 0, s>>>(table, tiles, n_tiles, i);
+}
+
+void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s) {
+    advance_kernel<<<n_scen, 128, 0, s>>>(table, g);
 }
 
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s) {
     set_target_kernel<<<1, 1, 0, s>>>(ctrl, target);
 }
 
-static int blocks_per_sm(const void *fn, int threads) {
+static int resident_blocks(const void *fn, int threads) {
     int dev = 0, n = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -638,7 +668,7 @@ static int blocks_per_sm(const void *fn, int threads) {
     return (n > 0 ? n : 1) * (sms > 0 ? sms : 1);
 }
 
-int max_link_blocks() { return blocks_per_sm((const void *)link_kernel, kLinkThreads); }
-int max_node_blocks() { return blocks_per_sm((const void *)node_kernel, kNodeThreads); }
+int max_link_blocks() { return resident_blocks((const void *)link_kernel, kLinkThreads); }
+int max_node_blocks() { return resident_blocks((const void *)node_kernel, kNodeThreads); }
 
 }  // namespace tsim

@@ -50,6 +50,13 @@ class Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in STATS_FIELDS]
 
 
+TOTALS_FIELDS = ("steps", "vehicle_updates", "lane_changes", "transfers", "inserted", "arrived", "last_state_hash")
+
+
+class Totals(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in TOTALS_FIELDS]
+
+
 class State(ctypes.Structure):
     _fields_ = [("cell_id", i32p), ("cell_v", i8p), ("buf_id", i32p), ("buf_v", i8p), ("cursor", u32p),
                 ("dep_head", u32p), ("step", ctypes.c_uint64), ("arrived", ctypes.c_uint64),
@@ -70,9 +77,13 @@ _API = {
                                          ctypes.POINTER(Allocator), ctypes.POINTER(ctypes.c_void_p)]),
     "ts_load_vehicles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, u32p, u32p, u32p]),
     "ts_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "ts_reset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ts_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
     "ts_read_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_uint32]),
     "ts_read_stats_range": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                            ctypes.c_uint32]),
+    "ts_read_totals": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Totals), ctypes.c_uint32]),
     "ts_state_sizes": (ctypes.c_int, [ctypes.c_void_p, u64p, u32p, u32p, u32p]),
     "ts_read_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_uint32]),
     "ts_write_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State)]),
@@ -86,7 +97,7 @@ _API = {
     "ts_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_ctx_step": (ctypes.c_int, [ctypes.c_void_p, u64p]),
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
-    "ts_set_tile_columns": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
 }
 
@@ -166,7 +177,7 @@ def _torch_allocator():
 class Simulation:
     """One scenario on the current CUDA device (wraps a ts_ctx)."""
 
-    def __init__(self, scenario, use_torch_allocator: bool = False, tile_columns: Optional[int] = None):
+    def __init__(self, scenario, use_torch_allocator: bool = False, tile_words: Optional[int] = None):
         L = lib()
         self.scenario = scenario
         net, dem = scenario.net, scenario.demand
@@ -181,8 +192,8 @@ class Simulation:
         h = ctypes.c_void_p()
         _check(L.ts_create_network(ctypes.byref(self._net.desc), ctypes.byref(params), alloc, ctypes.byref(h)))
         self.h = h
-        if tile_columns is not None:
-            _check(L.ts_set_tile_columns(self.h, tile_columns))
+        if tile_words is not None:
+            _check(L.ts_set_tile_words(self.h, tile_words))
         dep = np.ascontiguousarray(dem.depart_step, np.uint32)
         off = np.ascontiguousarray(dem.route_offsets, np.uint32)
         links = np.ascontiguousarray(dem.route_links, np.uint32)
@@ -205,17 +216,36 @@ class Simulation:
         except Exception:
             pass
 
-    def set_tile_columns(self, cols: int):
-        _check(lib().ts_set_tile_columns(self.h, cols))
+    def set_tile_words(self, words: int):
+        _check(lib().ts_set_tile_words(self.h, words))
 
     def step(self, n: int, stream=None):
         s = _stream_handle(stream)
         _check(lib().ts_step(self.h, n, ctypes.c_void_p(s) if s else None))
 
+    def reset(self, stream=None):
+        s = _stream_handle(stream)
+        _check(lib().ts_reset(self.h, ctypes.c_void_p(s) if s else None))
+
+    def step_timed(self, n: int, stream=None):
+        """Runs n steps with a CUDA event around every kernel; returns the
+        per-step durations (ms) of the link kernel and the node kernel."""
+        s = _stream_handle(stream)
+        a = np.zeros(n, np.float32)
+        b = np.zeros(n, np.float32)
+        _check(lib().ts_step_timed(self.h, n, ctypes.c_void_p(s) if s else None, a.ctypes.data_as(ctypes.c_void_p),
+                                   b.ctypes.data_as(ctypes.c_void_p)))
+        return a, b
+
     def stats(self, timeout_ms: int = 600000) -> dict:
         st = Stats()
         _check(lib().ts_read_stats(self.h, ctypes.byref(st), timeout_ms))
         return {f: getattr(st, f) for f in STATS_FIELDS}
+
+    def totals(self, timeout_ms: int = 600000) -> dict:
+        t = Totals()
+        _check(lib().ts_read_totals(self.h, ctypes.byref(t), timeout_ms))
+        return {f: getattr(t, f) for f in TOTALS_FIELDS}
 
     def stats_range(self, first: int, n: int, timeout_ms: int = 600000) -> np.ndarray:
         out = np.zeros(n, STATS_DTYPE)

@@ -36,8 +36,8 @@ def _cmp_state(g, o, where=""):
         assert g[k] == o[k], (where, k, g[k], o[k])
 
 
-def run_parity(sc, steps, chunk=None, state_every=None, tile_columns=None):
-    sim = T.Simulation(sc, tile_columns=tile_columns)
+def run_parity(sc, steps, chunk=None, state_every=None, tile_words=None):
+    sim = T.Simulation(sc, tile_words=tile_words)
     orc = oracle.Oracle(sc)
     t0 = sc.init.step if sc.init is not None else 0
     chunk = chunk or min(steps, 4000)
@@ -112,7 +112,7 @@ def test_small_grids_match_oracle(case):
 
 
 def test_long_links_partial_tiles():
-    # links longer than a tile (64 columns = 2048 cells), including tails that
+    # links longer than a tile (128 words = 4096 one-lane cells), including tails that
     # would leave fewer than 2*vmax+1 cells after a split
     cells = [2048 + 5, 4096 + 3, 2100, 64 * 32 * 2 + 1, 31, 3, 70]
     links, routes = [], []
@@ -130,8 +130,8 @@ def test_long_links_partial_tiles():
             routes.append([2 * i + 1 for i in range(b - 1, a - 1, -1)])
         dep.append(int(rng.integers(0, 300)))
     sc = make_scenario(links, n, routes, dep, steps=1500, seed=77, p=N.P_THRESHOLD_0_2)
-    for tc in (64, 8):
-        run_parity(sc, 1500, chunk=500, state_every=500, tile_columns=tc)
+    for tc in (128, 8):
+        run_parity(sc, 1500, chunk=500, state_every=500, tile_words=tc)
 
 
 def test_config0_full_run():
@@ -143,7 +143,7 @@ def test_config0_tile_shapes_identical():
     sc = N.config0()
     ref = None
     for tc in (8, 16, 32, 64, 128):
-        sim = T.Simulation(sc, tile_columns=tc)
+        sim = T.Simulation(sc, tile_words=tc)
         sim.step(1200)
         st = sim.stats_range(0, 1200)
         if ref is None:

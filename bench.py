@@ -164,7 +164,7 @@ def run_ours(args, rank, world, local_rank):
     steps_per_job = sc.steps if args.job_steps is None else args.job_steps
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    sim = T.Simulation(sc)
+    sim = T.Simulation(sc, tile_words=args.tile_words)
     net = sc.net
     C = net.n_lane_cells
 
@@ -239,7 +239,10 @@ def run_ours(args, rank, world, local_rank):
                 "avg_launch_us": 1e3 * float(link_ms.mean()),
                 "algorithmic_bytes_per_launch": link_bytes / steps_per_job,
                 "share_of_step_time": link_s / (link_s + node_s),
-                "node_kernel": {"achieved": node_bytes / node_s / 1e9, "avg_launch_us": 1e3 * float(node_ms.mean())}}
+                "launch_us_p50_p90_max": [round(1e3 * float(np.percentile(link_ms, q)), 2) for q in (50, 90, 100)],
+                "node_kernel": {"achieved": node_bytes / node_s / 1e9, "avg_launch_us": 1e3 * float(node_ms.mean()),
+                                "launch_us_p50_p90_max": [round(1e3 * float(np.percentile(node_ms, q)), 2)
+                                                          for q in (50, 90, 100)]}}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -277,6 +280,7 @@ def run_ours(args, rank, world, local_rank):
                            "vehicle_updates_per_job": updates, "l2": "flushed (512 MB write) before every job; "
                            "the simulation state stays resident across the steps of a job",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "tile_words": args.tile_words or 128,
                            "bit_exact_hash": str(tot["last_state_hash"])},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (2 * steps_per_job + 1),
@@ -297,6 +301,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1800)
     ap.add_argument("--ref-sample-steps", type=int, default=300)
+    ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..128)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per link_kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

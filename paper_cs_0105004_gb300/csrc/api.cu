@@ -206,10 +206,10 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
-                launch_link_kernel(d_table, d_link_tiles, n_link_tiles, i, grid_l, cap_stream);
-                launch_node_kernel(d_table, d_node_tiles, n_node_tiles, i, grid_n, cap_stream);
+                launch_link_kernel(d_table, d_link_tiles, n_link_tiles, i, grid_l, cap_stream, i > 0);
+                launch_node_kernel(d_table, d_node_tiles, n_node_tiles, i, grid_n, cap_stream, true);
             }
-            launch_advance_kernel(d_table, capacity, g, cap_stream);
+            launch_advance_kernel(d_table, capacity, g, cap_stream, true);
             CK(cudaStreamEndCapture(cap_stream, &graph));
             cudaGraphExec_t exec;
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
@@ -727,12 +727,12 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
             for (uint32_t i = 0; i < g; ++i) {
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
-                launch_link_kernel(w->d_table, w->d_link_tiles, w->n_link_tiles, i, w->grid_l, s);
+                launch_link_kernel(w->d_table, w->d_link_tiles, w->n_link_tiles, i, w->grid_l, s, false);
                 cudaEventRecord(ev[e + 1], s);
-                launch_node_kernel(w->d_table, w->d_node_tiles, w->n_node_tiles, i, w->grid_n, s);
+                launch_node_kernel(w->d_table, w->d_node_tiles, w->n_node_tiles, i, w->grid_n, s, false);
                 cudaEventRecord(ev[e + 2], s);
             }
-            launch_advance_kernel(w->d_table, w->capacity, g, s);
+            launch_advance_kernel(w->d_table, w->capacity, g, s, false);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) rs = cuda_fail(e, "kernel launch");
         }

@@ -94,11 +94,13 @@ struct LinkTile {
 };
 // node tile: {scen, first link, end link, 0}
 
+// pdl: launch with programmatic stream serialization (overlaps this launch
+// with the tail of the previous kernel in the stream)
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, uint32_t n_tiles, uint32_t i, int grid,
-                        cudaStream_t s);
+                        cudaStream_t s, bool pdl);
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, uint32_t n_tiles, uint32_t i, int grid,
-                        cudaStream_t s);
-void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s);
+                        cudaStream_t s, bool pdl);
+void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 int max_link_blocks();
 int max_node_blocks();

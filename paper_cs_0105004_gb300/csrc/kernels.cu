@@ -65,6 +65,28 @@ __device__ __forceinline__ unsigned long long vehicle_term(uint32_t id, uint32_t
     return mix64(a ^ mix64(b));
 }
 
+#ifdef TS_PHASE_TIMING
+// Debug builds only: %globaltimer stamps at the phase boundaries of the first
+// tile of every link_kernel block of the last launch.
+constexpr int kPhases = 10;
+constexpr int kPhaseBlocks = 4096;
+__device__ unsigned long long g_phase[kPhases][kPhaseBlocks];
+__device__ __forceinline__ void stamp(int ph, bool first) {
+    if (first && threadIdx.x == 0 && blockIdx.x < kPhaseBlocks) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        g_phase[ph][blockIdx.x] = t;
+    }
+}
+#else
+__device__ __forceinline__ void stamp(int, bool) {}
+#endif
+
+// Programmatic dependent launch: a kernel lets the next one in its stream
+// launch at once, and waits for its predecessor only before touching state.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ StatRec *stat_rec(const ScenDev &D, unsigned long long t) {
     return D.stats + (size_t)(t & (kStatsRing - 1)) * D.n_sub + (blockIdx.x & (D.n_sub - 1));
 }
@@ -199,24 +221,17 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
 
+    pdl_trigger();
+    bool waited = false;
+    bool first = true;
+    stamp(0, true);
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const LinkTile td = tiles[tile];
         const ScenDev &D = table[td.a.x];
         if (D.ctrl == nullptr) continue;
-        const unsigned long long step = D.ctrl->base + pos;
-        if (step >= D.ctrl->target) continue;
-        unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
-        if (rec != cur_rec) {
-            if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
-            cur_rec = rec;
-        }
-        const uint32_t t = (uint32_t)step;
-        const int cur = (int)(step & 1ull), nxt = cur ^ 1;
-        const uint32_t vmax = D.vmax;
-        const int d = (t & 1u) ? -1 : 1;
-        const uint32_t *__restrict__ occ_in = D.occ[cur];
+        stamp(1, first);
 
-        // ---------------- tile geometry and the occupancy of step t
+        // ---------------- tile geometry (static data: read before waiting)
         const bool partial = (td.a.z & kPartial) != 0u;
         if (!partial) {
             const int nl = (int)td.a.z;
@@ -229,7 +244,6 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.lring[q] = (uint8_t)((li.z >> 8) & 1u);
                 S.lid[q] = td.a.y + q;
                 S.lbpos[q] = li.w;
-                S.lexit[q] = (uint8_t)D.link_exit[td.a.y + q];
                 S.lentered[q] = 0;
                 const int ncol = (int)((li.y + 31u) >> 5), c0 = (int)((li.z >> 16) & 0xFFu);
                 const uint32_t lanes = li.z & 0xFFu, ring = (li.z >> 8) & 1u;
@@ -250,7 +264,6 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 if (q == nl - 1) S.ncols = c0 + ncol;
             }
             for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-                S.occ0[w] = occ_in[wb + w];
                 S.gw[w] = wb + w;
                 S.mv[w] = 0u;
                 S.out[w] = 0u;
@@ -300,7 +313,6 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 for (uint32_t k = 0; k < lanes; ++k) {
                     const uint32_t g = wbase + (uint32_t)j * lanes + k;
                     S.gw[lw + k] = g;
-                    S.occ0[lw + k] = occ_in[g];
                     S.mv[lw + k] = 0u;
                     S.out[lw + k] = 0u;
                     S.wcol[lw + k] = (uint8_t)c;
@@ -313,7 +325,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.lring[0] = (uint8_t)ring;
                 S.lid[0] = l;
                 S.lbpos[0] = td.b.w;
-                S.lexit[0] = (!ring && j1 == ncol) ? (uint8_t)D.link_exit[l] : (uint8_t)0;
+                S.lexit[0] = (!ring && j1 == ncol) ? 1u : 0u;  // marks that the link end is in this tile
                 S.lentered[0] = 0;
                 S.ncols = ncols;
                 S.nwords = ncols * (int)lanes;
@@ -322,7 +334,36 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             }
         }
         __syncthreads();
+        stamp(2, first);
+        if (!waited) {
+            pdl_wait();
+            waited = true;
+        }
+        stamp(3, first);
+        const unsigned long long step = D.ctrl->base + pos;
+        if (step >= D.ctrl->target) continue;
+        unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
+        if (rec != cur_rec) {
+            if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
+            cur_rec = rec;
+        }
+        const uint32_t t = (uint32_t)step;
+        const int cur = (int)(step & 1ull), nxt = cur ^ 1;
+        const uint32_t vmax = D.vmax;
+        const int d = (t & 1u) ? -1 : 1;
         const int nwords = S.nwords, ncore_words = S.ncore_words;
+
+        // ---------------- occupancy of step t and the link-end buffer states
+        {
+            const uint32_t *__restrict__ occ_in = D.occ[cur];
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.occ0[w] = occ_in[S.gw[w]];
+            for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x) {
+                const bool end_here = partial ? S.lexit[0] != 0 : !S.lring[q];
+                S.lexit[q] = end_here ? (uint8_t)D.link_exit[S.lid[q]] : (uint8_t)0;
+            }
+        }
+        __syncthreads();
+        stamp(4, first);
 
         // ---------------- compact the vehicles; load their velocity and id once
         for (int w = threadIdx.x; w < nwords; w += blockDim.x)
@@ -351,6 +392,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             }
         }
         __syncthreads();
+        stamp(5, first);
 
         // ---------------- sub-step 1: lane changes, decided on the state of step t
         const bool lc_on = D.lane_change != 0u;
@@ -388,6 +430,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.occ1[w] = S.occ0[w];
         }
         __syncthreads();
+        stamp(6, first);
 
         // ---------------- sub-step 2: velocity update and move
         {
@@ -458,6 +501,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             }
         }
         __syncthreads();
+        stamp(7, first);
 
         // ---------------- write the occupancy of step t+1 and the buffer states
         {
@@ -467,8 +511,11 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 if (S.lentered[q]) D.link_exit[S.lid[q]] = (uint32_t)S.lexit[q] & ~S.lentered[q];
         }
         __syncthreads();
+        stamp(8, first);
+        first = false;
     }
     if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
+    stamp(9, true);
 }
 
 // ------------------------------------------------------------------ node kernel
@@ -483,10 +530,18 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
     static constexpr int kField[6] = {3, 4, 1, 0, 5, 7};
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
+    pdl_trigger();
+    bool waited = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint4 td = tiles[tile];
         const ScenDev &D = table[td.x];
         if (D.ctrl == nullptr) continue;
+        const uint32_t m = td.y + threadIdx.x;
+        const uint4 nd = m < td.z ? D.nd_info[m] : make_uint4(0u, 0u, 0u, 0u);  // static
+        if (!waited) {
+            pdl_wait();
+            waited = true;
+        }
         const unsigned long long step = D.ctrl->base + pos;
         if (step >= D.ctrl->target) continue;
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
@@ -496,12 +551,10 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
         }
         const uint32_t t = (uint32_t)step;
         const int nxt = (int)((step + 1ull) & 1ull);
-        const uint32_t m = td.y + threadIdx.x;
         if (m < td.z) {
             uint32_t *occ = D.occ[nxt];
             int8_t *vel = D.vel[nxt];
             uint32_t *vid = D.vid[nxt];
-            const uint4 nd = D.nd_info[m];
             uint32_t h = D.dep_head[m];
             const uint32_t slot_lo = nd.x, wbase = nd.y, cnt = nd.z & 0xFFu, lanes = (nd.z >> 8) & 0xFFu;
             const uint32_t dep_end = nd.w;
@@ -584,6 +637,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
 // One block per scenario: sums the statistics of the g steps just run,
 // moves the step counter and clears the records of the next chunk.
 __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict__ table, uint32_t g_max) {
+    pdl_wait();
     const ScenDev &D = table[blockIdx.x];
     Ctrl *c = D.ctrl;
     if (c == nullptr) return;
@@ -642,18 +696,33 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
 
 __global__ void set_target_kernel(Ctrl *ctrl, unsigned long long target) { ctrl->target = target; }
 
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, uint32_t n_tiles, uint32_t i, int grid,
-                        cudaStream_t s) {
-    link_kernel<<<grid, kLinkThreads, 0, s>>>(table, tiles, n_tiles, i);
+                        cudaStream_t s, bool pdl) {
+    launch_pdl(link_kernel, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, uint32_t n_tiles, uint32_t i, int grid,
-                        cudaStream_t s) {
-    node_kernel<<<grid, kNodeThreads, 0, s>>>(table, tiles, n_tiles, i);
+                        cudaStream_t s, bool pdl) {
+    launch_pdl(node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i);
 }
 
-void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s) {
-    advance_kernel<<<n_scen, 128, 0, s>>>(table, g);
+void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl) {
+    launch_pdl(advance_kernel, (int)n_scen, 128, pdl, s, table, g);
 }
 
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s) {
@@ -667,6 +736,17 @@ static int resident_blocks(const void *fn, int threads) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0);
     return (n > 0 ? n : 1) * (sms > 0 ? sms : 1);
 }
+
+#ifdef TS_PHASE_TIMING
+extern "C" int ts_debug_phase_times(unsigned long long *out, int n_blocks) {
+    if (n_blocks > kPhaseBlocks) n_blocks = kPhaseBlocks;
+    for (int p = 0; p < kPhases; ++p)
+        if (cudaMemcpyFromSymbol(out + (size_t)p * n_blocks, g_phase, sizeof(unsigned long long) * n_blocks,
+                                 sizeof(unsigned long long) * kPhaseBlocks * p) != cudaSuccess)
+            return -1;
+    return n_blocks;
+}
+#endif
 
 int max_link_blocks() { return resident_blocks((const void *)link_kernel, kLinkThreads); }
 int max_node_blocks() { return resident_blocks((const void *)node_kernel, kNodeThreads); }

@@ -229,6 +229,35 @@ void ts_batch_destroy(ts_batch *b);
  * link tile, 8..128 (default 128).  Results do not depend on it. */
 ts_status ts_set_tile_words(ts_ctx *ctx, uint32_t words);
 
+/* Advances a periodic ring road held in caller-owned device buffers by
+ * n_steps steps, without allocating any device memory.  The paper has no
+ * counterpart to this call: it exists for callers that cannot let a
+ * library allocate GPU memory (a framework that owns all device memory
+ * through its own pool, a plugin given fixed buffers).  It runs the same
+ * step kernel as ts_step on one ring link of `cells` cells (a multiple of
+ * 32, at most 131072) and `lanes` lanes (1..4); n_steps at most 1024.
+ * Layout of the caller's buffers, W = cells/32 * lanes words: dev_occ0/1
+ * [W] uint32 occupancy words, word (column j, lane k) = j*lanes + k, bit i =
+ * cell 32j+i; dev_vel0/1 [32*W] int8 velocities and dev_vid0/1 [32*W]
+ * uint32 vehicle ids (below 2^31) at word*32 + bit.  The state of step
+ * first_step is read from buffer set (first_step & 1) and the state after
+ * the last step is written to set ((first_step + n_steps) & 1); the other
+ * set is overwritten.  dev_stats_out [n_steps] (device memory) receives the
+ * statistics of steps first_step .. first_step+n_steps-1 (buffered, waiting,
+ * arrived, transfers and inserted are 0 on a ring).  Asynchronous on
+ * cuda_stream; device consistency flags are not reported by this call.
+ * Scratch: a fixed array of about 530 KB in device memory, held by every
+ * device that loads the library until the process exits.  All calls share
+ * it, so calls that overlap on the GPU (other streams, other threads) race;
+ * each call rewrites and clears what it uses.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Returns TS_ERR_INVALID for sizes
+ * beyond the limits above, TS_ERR_CUDA if a copy or launch fails. */
+ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *params, uint64_t first_step,
+                               uint32_t n_steps, uint32_t *dev_occ0, uint32_t *dev_occ1, int8_t *dev_vel0,
+                               int8_t *dev_vel1, uint32_t *dev_vid0, uint32_t *dev_vid1, ts_stats *dev_stats_out,
+                               void *cuda_stream);
+
 /* Number of kernel launches one time step of this context enqueues. */
 uint32_t ts_launches_per_step(void);
 

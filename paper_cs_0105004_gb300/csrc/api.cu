@@ -51,6 +51,8 @@ ts_status wait_event(cudaEvent_t ev, uint32_t timeout_ms) {
 
 }  // namespace
 
+void tsim::set_last_error(const char *msg) { g_err = msg; }
+
 // ------------------------------------------------------------------ world (scenarios stepped together)
 
 struct World {

@@ -104,5 +104,7 @@ void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cu
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 int max_link_blocks();
 int max_node_blocks();
+// Sets the thread-local message returned by ts_last_error.
+void set_last_error(const char *msg);
 
 }  // namespace tsim

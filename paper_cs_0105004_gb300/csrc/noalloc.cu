@@ -1,0 +1,172 @@
+// Ring-road stepping on caller-owned device buffers, without any device
+// allocation by the library.
+//
+// Some callers cannot let a library call cudaMalloc: code that runs inside a
+// framework which owns every byte of device memory through its own pool,
+// plugins that are handed fixed buffers and must not grow the process's
+// footprint, or hosts that pre-plan all memory before a long run.  For them
+// ts_ring_step_noalloc advances a periodic circle road (the 1-lane and
+// 3-lane circles of Sec. 5) whose state the caller keeps in its own device
+// buffers.  It runs the same link kernel as ts_step; what that kernel needs
+// besides the caller's buffers (the scenario table, the tile list, the
+// control block and the per-step partial statistics) lives in one file-scope
+// __device__ array, fixed in size, that every device which loads this
+// library holds until the process exits.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+#include "transsim.h"
+
+namespace tsim {
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxCells = 1u << 17;  // cells per lane
+constexpr uint32_t kNoAllocMaxSteps = 1024;      // steps per call
+constexpr uint32_t kNoAllocMaxTiles = 132;  // 4096 columns in runs of at least 32
+
+// Byte offsets inside the scratch array.
+constexpr size_t kOffTable = 0;
+constexpr size_t kOffCtrl = 256;
+constexpr size_t kOffLink = 512;
+constexpr size_t kOffTiles = 1024;
+constexpr size_t kOffStats = kOffTiles + ((sizeof(LinkTile) * kNoAllocMaxTiles + 255u) / 256u) * 256u;
+constexpr size_t kScratchBytes = kOffStats + sizeof(StatRec) * kStatsRing;
+
+static_assert(sizeof(ScenDev) <= 256, "table entry fits its slot");
+static_assert(sizeof(Ctrl) <= 256, "control block fits its slot");
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+std::vector<unsigned char *> g_scratch_ptr;  // per device ordinal, from cudaGetSymbolAddress
+
+ts_status bad(ts_status s, const char *msg) {
+    set_last_error(msg);
+    return s;
+}
+
+// Sums the partial records of each step into the caller's statistics array.
+__global__ void gather_ring_stats(const StatRec *recs, unsigned long long first, uint32_t n, ts_stats *out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const StatRec &r = recs[(first + i) & (kStatsRing - 1)];
+    ts_stats o;
+    o.step = first + i;
+    o.active = r.active;
+    o.buffered = 0;
+    o.waiting = 0;
+    o.arrived = 0;
+    o.lane_changes = r.lane_changes;
+    o.transfers = 0;
+    o.inserted = 0;
+    o.sum_v = r.sum_v;
+    o.vehicle_updates = r.vehicle_updates;
+    o.state_hash = r.state_hash;
+    out[i] = o;
+}
+
+}  // namespace
+}  // namespace tsim
+
+using namespace tsim;
+
+extern "C" {
+
+// Declared in include/transsim.h; see the comment there.
+ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *params, uint64_t first_step,
+                               uint32_t n_steps, uint32_t *dev_occ0, uint32_t *dev_occ1, int8_t *dev_vel0,
+                               int8_t *dev_vel1, uint32_t *dev_vid0, uint32_t *dev_vid1, ts_stats *dev_stats_out,
+                               void *cuda_stream) {
+    if (!params) return bad(TS_ERR_INVALID, "null params");
+    if (cells < 32 || cells > kNoAllocMaxCells || cells % 32u != 0u)
+        return bad(TS_ERR_INVALID, "ring cells must be a multiple of 32 in 32..131072");
+    if (lanes < 1 || lanes > (uint32_t)kMaxLanes) return bad(TS_ERR_INVALID, "lanes must be 1..4");
+    if (params->vmax < 1 || params->vmax > (uint32_t)kMaxVmax) return bad(TS_ERR_INVALID, "vmax must be 1..15");
+    if (n_steps > kNoAllocMaxSteps) return bad(TS_ERR_INVALID, "at most 1024 steps per call");
+    if (!dev_occ0 || !dev_occ1 || !dev_vel0 || !dev_vel1 || !dev_vid0 || !dev_vid1 || !dev_stats_out)
+        return bad(TS_ERR_INVALID, "null buffer");
+    if (n_steps == 0) return TS_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return bad(TS_ERR_CUDA, "cudaGetDevice failed");
+    unsigned char *base = nullptr;
+    {
+        // once per device, with that device current: the host-side name of the
+        // array is not a device address, so ask the runtime for it
+        std::lock_guard<std::mutex> lock(g_mu);
+        if ((size_t)dev >= g_scratch_ptr.size()) g_scratch_ptr.resize((size_t)dev + 1, nullptr);
+        if (!g_scratch_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+                return bad(TS_ERR_CUDA, "cudaGetSymbolAddress failed");
+            g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+        }
+        base = g_scratch_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    ScenDev *d_table = reinterpret_cast<ScenDev *>(base + kOffTable);
+    Ctrl *d_ctrl = reinterpret_cast<Ctrl *>(base + kOffCtrl);
+    uint4 *d_link = reinterpret_cast<uint4 *>(base + kOffLink);
+    LinkTile *d_tiles = reinterpret_cast<LinkTile *>(base + kOffTiles);
+    StatRec *d_stats = reinterpret_cast<StatRec *>(base + kOffStats);
+
+    // tiles: the whole ring if it fits one tile, else runs of columns whose
+    // halos wrap around the ring
+    const uint32_t ncols = cells / 32u, words = ncols * lanes;
+    std::vector<LinkTile> tiles;
+    if (words <= (uint32_t)kTileWords) {
+        LinkTile t;
+        t.a = make_uint4(0u, 0u, 1u, 0u);
+        t.b = make_uint4(0u, words, 0u, 0u);
+        tiles.push_back(t);
+    } else {
+        const uint32_t per = (uint32_t)kTileWords / lanes;
+        for (uint32_t j = 0; j < ncols; j += per) {
+            LinkTile t;
+            t.a = make_uint4(0u, 0u, kPartial | j, j + per < ncols ? j + per : ncols);
+            t.b = make_uint4(0u, cells, lanes | (1u << 8), 0u);
+            tiles.push_back(t);
+        }
+    }
+    if (tiles.size() > kNoAllocMaxTiles) return bad(TS_ERR_INVALID, "ring too large");
+    ScenDev sd{};
+    sd.lk_info = d_link;
+    sd.occ[0] = dev_occ0;
+    sd.occ[1] = dev_occ1;
+    sd.vel[0] = dev_vel0;
+    sd.vel[1] = dev_vel1;
+    sd.vid[0] = dev_vid0;
+    sd.vid[1] = dev_vid1;
+    sd.ctrl = d_ctrl;
+    sd.stats = d_stats;
+    sd.n_sub = 1;
+    sd.vmax = params->vmax;
+    sd.p_threshold = params->p_threshold;
+    sd.seed_lo = (uint32_t)(params->seed & 0xFFFFFFFFull);
+    sd.seed_hi = (uint32_t)(params->seed >> 32);
+    sd.lane_change = params->lane_change ? 1u : 0u;
+    sd.n_links = 1;
+    Ctrl ctrl{};
+    ctrl.base = first_step;
+    ctrl.target = first_step + n_steps;
+    const uint4 link = make_uint4(0u, cells, lanes | (1u << 8), 0u);
+    // the scratch keeps the previous call's contents: rewrite all of it that
+    // this call reads, and clear the statistics it accumulates into
+    if (cudaMemcpyAsync(d_table, &sd, sizeof(sd), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_ctrl, &ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_link, &link, sizeof(link), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(LinkTile) * tiles.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(d_stats, 0, sizeof(StatRec) * kStatsRing, s) != cudaSuccess)
+        return bad(TS_ERR_CUDA, "scratch set-up copy failed");
+    const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks()));
+    for (uint32_t i = 0; i < n_steps; ++i)
+        launch_link_kernel(d_table, d_tiles, (uint32_t)tiles.size(), i, grid, s, false);
+    gather_ring_stats<<<(n_steps + 127) / 128, 128, 0, s>>>(d_stats, first_step, n_steps, dev_stats_out);
+    if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");
+    return TS_OK;
+}
+
+}  // extern "C"

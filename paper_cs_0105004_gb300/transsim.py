@@ -99,6 +99,8 @@ _API = {
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
+    "ts_ring_step_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Params), ctypes.c_uint64,
+                                            ctypes.c_uint32] + [ctypes.c_void_p] * 8),
 }
 
 _lib = None

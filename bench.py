@@ -165,6 +165,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sim = T.Simulation(sc, tile_words=args.tile_words)
+    if args.load_balance:
+        sim.set_load_balance(args.load_balance, args.tile_vehicles)
     net = sc.net
     C = net.n_lane_cells
 
@@ -281,6 +283,7 @@ def run_ours(args, rank, world, local_rank):
                            "the simulation state stays resident across the steps of a job",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "tile_words": args.tile_words or 128,
+                           "load_balance": {"every_steps": args.load_balance, "vehicles_per_tile": args.tile_vehicles},
                            "bit_exact_hash": str(tot["last_state_hash"])},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (2 * steps_per_job + 1),
@@ -302,6 +305,8 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=1800)
     ap.add_argument("--ref-sample-steps", type=int, default=300)
     ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..128)")
+    ap.add_argument("--load-balance", type=int, default=512, help="re-tile from the occupancy every N steps (0 = off)")
+    ap.add_argument("--tile-vehicles", type=int, default=768, help="vehicle budget per tile when re-tiling")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per link_kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

@@ -258,6 +258,14 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
                                int8_t *dev_vel1, uint32_t *dev_vid0, uint32_t *dev_vid1, ts_stats *dev_stats_out,
                                void *cuda_stream);
 
+/* Load balancing (the counterpart of feeding measured per-link load back
+ * into the partition): every `every_steps` steps of a ts_step call
+ * (0 = never; otherwise at least 32) the link tiles are rebuilt from the
+ * current occupancy so that a tile holds at most `vehicles_per_tile`
+ * vehicles (0 = no budget).  Each pass waits for the queued work and reads
+ * the occupancy to the host.  Results do not depend on it. */
+ts_status ts_set_load_balance(ts_ctx *ctx, uint32_t every_steps, uint32_t vehicles_per_tile);
+
 /* Number of kernel launches one time step of this context enqueues. */
 uint32_t ts_launches_per_step(void);
 

@@ -63,6 +63,7 @@ struct World {
     ScenDev *d_table = nullptr;
     LinkTile *d_link_tiles = nullptr;
     uint4 *d_node_tiles = nullptr;
+    uint32_t *d_counts = nullptr;  // [0] link tiles, [1] node tiles, read by the kernels
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1;
@@ -92,7 +93,9 @@ struct ts_ctx {
     uint32_t tile_words = kTileWords;
     std::vector<LinkTile> link_tiles;
     std::vector<uint4> node_tiles;
-    uint32_t n_sub = 1, sub_cap = 1;  // statistics sub-records per step (used, allocated)
+    uint32_t n_sub = 1;                // statistics sub-records per step (fixed at creation)
+    uint32_t tile_vehicles = 1024;     // vehicle budget per tile when re-tiling from occupancy
+    uint32_t retile_every = 0;         // steps between load-balancing passes (0 = static tiles)
     // vehicles
     bool loaded = false;
     uint32_t n_veh = 0;
@@ -135,6 +138,7 @@ struct ts_batch {
 World::~World() {
     drop_graphs();
     if (d_table) cudaFree(d_table);
+    if (d_counts) cudaFree(d_counts);
     if (d_link_tiles) cudaFree(d_link_tiles);
     if (d_node_tiles) cudaFree(d_node_tiles);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -152,11 +156,14 @@ ts_status World::init(uint32_t cap) {
     CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     CK(cudaMalloc(&d_table, sizeof(ScenDev) * cap));
     CK(cudaMemset(d_table, 0, sizeof(ScenDev) * cap));
+    CK(cudaMalloc(&d_counts, 2 * sizeof(uint32_t)));
+    CK(cudaMemset(d_counts, 0, 2 * sizeof(uint32_t)));
     return TS_OK;
 }
 
-// Re-uploads the scenario table and the concatenated tile lists
-// (synchronous; callers make sure no work of this world is in flight).
+// Re-uploads the scenario table, the concatenated tile lists and their
+// counts (synchronous; callers make sure no work of this world is in
+// flight).  Captured graphs stay valid unless a tile array has to grow.
 ts_status World::rebuild() {
     std::vector<ScenDev> table(capacity);
     std::vector<LinkTile> lt;
@@ -175,15 +182,16 @@ ts_status World::rebuild() {
             nt.push_back(t);
         }
     }
-    drop_graphs();
     CK(cudaMemcpy(d_table, table.data(), sizeof(ScenDev) * capacity, cudaMemcpyHostToDevice));
     if (lt.size() > link_cap) {
+        drop_graphs();
         if (d_link_tiles) cudaFree(d_link_tiles);
         d_link_tiles = nullptr;
-        link_cap = std::max<size_t>(lt.size(), 2 * link_cap);
+        link_cap = std::max<size_t>(2 * lt.size(), lt.size() + 1024);
         CK(cudaMalloc(&d_link_tiles, sizeof(LinkTile) * link_cap));
     }
     if (nt.size() > node_cap) {
+        drop_graphs();
         if (d_node_tiles) cudaFree(d_node_tiles);
         d_node_tiles = nullptr;
         node_cap = std::max<size_t>(nt.size(), 2 * node_cap);
@@ -193,8 +201,17 @@ ts_status World::rebuild() {
     if (!nt.empty()) CK(cudaMemcpy(d_node_tiles, nt.data(), sizeof(uint4) * nt.size(), cudaMemcpyHostToDevice));
     n_link_tiles = (uint32_t)lt.size();
     n_node_tiles = (uint32_t)nt.size();
-    grid_l = std::max(1, std::min<int>((int)n_link_tiles, max_link_blocks()));
-    grid_n = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
+    const uint32_t counts[2] = {n_link_tiles, n_node_tiles};
+    CK(cudaMemcpy(d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
+    // persistent grids: at most the resident blocks, and room for the tile
+    // count to double through load balancing before blocks loop over tiles
+    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks()));
+    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
+    if (gl > grid_l || gn != grid_n || gl < grid_l / 2) {
+        drop_graphs();
+        grid_l = gl;
+        grid_n = gn;
+    }
     return TS_OK;
 }
 
@@ -208,8 +225,8 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
-                launch_link_kernel(d_table, d_link_tiles, n_link_tiles, i, grid_l, cap_stream, i > 0);
-                launch_node_kernel(d_table, d_node_tiles, n_node_tiles, i, grid_n, cap_stream, true);
+                launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0);
+                launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true);
             }
             launch_advance_kernel(d_table, capacity, g, cap_stream, true);
             CK(cudaStreamEndCapture(cap_stream, &graph));
@@ -270,15 +287,25 @@ ts_status wait_ctx(ts_ctx *c, uint32_t timeout_ms) {
 }
 
 // Link tiles: runs of whole links with at most tile_words occupancy words
-// (all lanes), or, for a longer link, runs of its columns.  A split of a
-// non-periodic link must leave more than 2*vmax cells after it, so the tile
-// before a split never sees the link end; a too-short tail column is merged
-// into the tile before it.
-void build_tiles(ts_ctx *c) {
-    const uint32_t TW = c->tile_words, vmax = c->params.vmax;
+// (all lanes), at most 128 columns and 128 links, or, for a longer link, runs
+// of its columns.  With per-word vehicle counts (wcount), a tile also holds at
+// most tile_vehicles vehicles, so jammed stretches get smaller tiles.  A split
+// of a non-periodic link must leave more than 2*vmax cells after it, so the
+// tile before a split never sees the link end; a too-short tail column is
+// merged into the tile before it.  Results do not depend on the tiling.
+void build_tiles(ts_ctx *c, const std::vector<uint32_t> *wcount) {
+    const uint32_t TW = c->tile_words, vmax = c->params.vmax, maxc = (uint32_t)kTileMaxCols - 1u;
+    const uint32_t VT = (wcount && c->tile_vehicles) ? c->tile_vehicles : 0xFFFFFFFFu;
+    auto col_veh = [&](uint32_t l, uint32_t j) -> uint32_t {
+        if (!wcount) return 0u;
+        uint32_t s = 0;
+        const uint32_t w0 = c->wbase[l] + j * c->lanes[l];
+        for (uint32_t k = 0; k < c->lanes[l]; ++k) s += (*wcount)[w0 + k];
+        return s;
+    };
     c->link_tiles.clear();
     c->col_in_tile.assign(c->n_links, 0);
-    uint32_t start = 0, count = 0, words = 0, cols = 0;
+    uint32_t start = 0, count = 0, words = 0, cols = 0, veh = 0;
     auto flush = [&]() {
         if (count) {
             LinkTile t;
@@ -286,41 +313,45 @@ void build_tiles(ts_ctx *c) {
             t.b = make_uint4(c->wbase[start], c->wbase[start] + words, 0u, 0u);
             c->link_tiles.push_back(t);
         }
-        count = words = cols = 0;
+        count = words = cols = veh = 0;
     };
     for (uint32_t l = 0; l < c->n_links; ++l) {
-        const uint32_t nc = c->ncols[l], nw = nc * c->lanes[l];
-        if (nw > TW) {
+        const uint32_t nc = c->ncols[l], lanes = c->lanes[l], nw = nc * lanes;
+        uint32_t vl = 0;
+        if (wcount)
+            for (uint32_t j = 0; j < nc; ++j) vl += col_veh(l, j);
+        if (nw > TW || nc > maxc || vl > VT) {
             flush();
-            const uint32_t per = std::max(1u, TW / c->lanes[l]);
             uint32_t j = 0;
             while (j < nc) {
-                uint32_t je = std::min(nc, j + per);
+                uint32_t je = j + 1, v = col_veh(l, j);
+                while (je < nc && (je + 1 - j) * lanes <= TW && je + 1 - j <= maxc) {
+                    const uint32_t vn = col_veh(l, je);
+                    if (v + vn > VT) break;
+                    v += vn;
+                    ++je;
+                }
                 if (!c->ring[l] && je < nc && c->cells[l] - 32u * je < 2u * vmax + 1u) je = nc;
                 LinkTile t;
                 t.a = make_uint4(0u, l, kPartial | j, je);
-                t.b = make_uint4(c->wbase[l], c->cells[l], c->lanes[l] | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
+                t.b = make_uint4(c->wbase[l], c->cells[l], lanes | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
                 c->link_tiles.push_back(t);
                 j = je;
             }
-            start = l + 1;
             continue;
         }
+        if (count > 0 && (words + nw > TW || cols + nc > maxc || veh + vl > VT || count == maxc)) flush();
         if (count == 0) start = l;
-        if (words + nw > TW) {
-            flush();
-            start = l;
-        }
         c->col_in_tile[l] = cols;
         ++count;
         words += nw;
         cols += nc;
+        veh += vl;
     }
     flush();
     c->node_tiles.clear();
     for (uint32_t m = 0; m < c->n_links; m += kNodeThreads)
         c->node_tiles.push_back(make_uint4(0u, m, std::min(c->n_links, m + (uint32_t)kNodeThreads), 0u));
-    c->n_sub = std::min(c->sub_cap, c->link_tiles.size() >= 64 ? 8u : 1u);
 }
 
 ts_status upload_lk_info(ts_ctx *c) {
@@ -329,7 +360,6 @@ ts_status upload_lk_info(ts_ctx *c) {
         li[l] = make_uint4(c->wbase[l], c->cells[l],
                            c->lanes[l] | ((uint32_t)c->ring[l] << 8) | (c->col_in_tile[l] << 16), c->bpos[l]);
     CK(cudaMemcpy(c->d_lk_info, li.data(), sizeof(uint4) * c->n_links, cudaMemcpyHostToDevice));
-    c->sd.n_sub = c->n_sub;
     return TS_OK;
 }
 
@@ -465,9 +495,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     for (uint32_t n = 0; n < c->n_nodes; ++n)
         if (c->node_in_off[n + 1] - c->node_in_off[n] > 255u)
             return fail(TS_ERR_INVALID, "more than 255 lanes end at one node");
-    c->sub_cap = 8;
-    build_tiles(c.get());
-    c->sub_cap = c->n_sub;  // small networks keep one sub-record per step
+    build_tiles(c.get(), nullptr);
+    c->n_sub = c->link_tiles.size() >= 64 ? 8u : 1u;  // small networks keep one sub-record per step
     // device arrays of the network
     bool ok = true;
     auto &A = c->allocs;
@@ -483,7 +512,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     uint32_t *link_exit = alloc_in<uint32_t>(c.get(), A, L, ok);
     c->d_link_exit0 = alloc_in<uint32_t>(c.get(), A, L, ok);
     Ctrl *ctrl = alloc_in<Ctrl>(c.get(), A, 1, ok);
-    StatRec *stats = alloc_in<StatRec>(c.get(), A, (size_t)kStatsRing * c->sub_cap, ok);
+    StatRec *stats = alloc_in<StatRec>(c.get(), A, (size_t)kStatsRing * c->n_sub, ok);
     if (!ok) {
         free_list(c.get(), A);
         return fail(TS_ERR_OOM, "device allocation failed");
@@ -507,6 +536,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.seed_hi = (uint32_t)(params->seed >> 32);
     sd.lane_change = params->lane_change ? 1u : 0u;
     sd.n_links = L;
+    sd.n_sub = c->n_sub;
     st = upload_lk_info(c.get());
     if (st != TS_OK) return st;
     std::vector<uint32_t> ex(L);
@@ -517,7 +547,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     CK(cudaMemset(occ1, 0, 4ull * c->n_words));
     CK(cudaMemset(slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(ctrl, 0, sizeof(Ctrl)));
-    CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing * c->sub_cap));
+    CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub));
     *out = c.release();
     return TS_OK;
 }
@@ -656,20 +686,30 @@ ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
     st = wait_ctx(c, 60000);
     if (st != TS_OK) return st;
     c->tile_words = words;
-    const uint32_t old_sub = c->n_sub;
-    build_tiles(c);
-    if (c->n_sub != old_sub) {
-        // the statistics ring layout depends on the tile count; keep the state
-        Ctrl h;
-        st = read_ctrl(c, &h);
-        if (st != TS_OK) return st;
-        st = reset_ctrl(c, h.base, h.arrived, h.inserted, c->stream);
-        if (st != TS_OK) return st;
-    }
+    build_tiles(c, nullptr);
     st = upload_lk_info(c);
     if (st != TS_OK) return st;
     if (c->own) return ensure_own_world(c);
     return TS_OK;
+}
+
+// Load balancing between chunks: the tiles are rebuilt from the current
+// occupancy so that no tile carries more than tile_vehicles vehicles (the
+// counterpart of feeding measured load back into the partition).
+static ts_status retile(ts_ctx *c, cudaStream_t s) {
+    CK(cudaEventRecord(c->ev, s));
+    ts_status st = wait_ctx(c, 600000);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);
+    if (st != TS_OK) return st;
+    std::vector<uint32_t> occ(c->n_words);
+    CK(cudaMemcpy(occ.data(), c->sd.occ[h.base & 1ull], 4ull * c->n_words, cudaMemcpyDeviceToHost));
+    for (auto &w : occ) w = (uint32_t)__builtin_popcount(w);
+    build_tiles(c, &occ);
+    st = upload_lk_info(c);
+    if (st != TS_OK) return st;
+    return c->own->rebuild();
 }
 
 ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
@@ -679,15 +719,37 @@ ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
     if (c->batch) return fail(TS_ERR_STATE, "context is stepped by its batch");
     if (n_steps == 0) return TS_OK;
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+    const uint64_t start = c->host_step;
     c->host_step += n_steps;
     launch_set_target(c->sd.ctrl, c->host_step, s);
     CK(cudaGetLastError());
-    st = c->own->run(n_steps, s);
-    if (st != TS_OK) {
-        c->sticky = true;
-        return st;
+    const uint64_t R = c->retile_every;
+    uint64_t done = 0;
+    while (done < n_steps) {
+        uint64_t seg = n_steps - done;
+        if (R) seg = std::min<uint64_t>(seg, ((start + done) / R + 1) * R - (start + done));
+        st = c->own->run((uint32_t)seg, s);
+        if (st != TS_OK) {
+            c->sticky = true;
+            return st;
+        }
+        done += seg;
+        if (R && done < n_steps && (start + done) % R == 0) {
+            st = retile(c, s);
+            if (st != TS_OK) return st;
+        }
     }
     CK(cudaEventRecord(c->ev, s));
+    return TS_OK;
+}
+
+ts_status ts_set_load_balance(ts_ctx *c, uint32_t every_steps, uint32_t vehicles_per_tile) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (every_steps && every_steps < kChunk) return fail(TS_ERR_INVALID, "load balancing at most every 32 steps");
+    if (vehicles_per_tile && vehicles_per_tile < 128) return fail(TS_ERR_INVALID, "vehicle budget below 128");
+    c->retile_every = every_steps;
+    c->tile_vehicles = vehicles_per_tile;
     return TS_OK;
 }
 
@@ -729,9 +791,9 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
             for (uint32_t i = 0; i < g; ++i) {
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
-                launch_link_kernel(w->d_table, w->d_link_tiles, w->n_link_tiles, i, w->grid_l, s, false);
+                launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false);
                 cudaEventRecord(ev[e + 1], s);
-                launch_node_kernel(w->d_table, w->d_node_tiles, w->n_node_tiles, i, w->grid_n, s, false);
+                launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false);
                 cudaEventRecord(ev[e + 2], s);
             }
             launch_advance_kernel(w->d_table, w->capacity, g, s, false);

@@ -96,9 +96,11 @@ struct LinkTile {
 
 // pdl: launch with programmatic stream serialization (overlaps this launch
 // with the tail of the previous kernel in the stream)
-void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, uint32_t n_tiles, uint32_t i, int grid,
+// n_tiles points to the tile count in device memory; it may change between
+// graph launches (load balancing) without a new capture
+void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl);
-void launch_node_kernel(const ScenDev *table, const uint4 *tiles, uint32_t n_tiles, uint32_t i, int grid,
+void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl);
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);

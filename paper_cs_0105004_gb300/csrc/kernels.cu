@@ -78,8 +78,19 @@ __device__ __forceinline__ void stamp(int ph, bool first) {
         g_phase[ph][blockIdx.x] = t;
     }
 }
+// [launch position * 3 + kernel kind][first block entry, last block exit]
+__device__ unsigned long long g_span[128][2];
+__device__ __forceinline__ void span_mark(int slot, bool enter) {
+    if (threadIdx.x == 0 && slot < 128) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (enter) atomicMin(&g_span[slot][0], t);
+        else atomicMax(&g_span[slot][1], t);
+    }
+}
 #else
 __device__ __forceinline__ void stamp(int, bool) {}
+__device__ __forceinline__ void span_mark(int, bool) {}
 #endif
 
 // Programmatic dependent launch: a kernel lets the next one in its stream
@@ -114,49 +125,6 @@ __device__ __forceinline__ void block_flush(unsigned long long (&acc)[NF], unsig
     __syncthreads();
 }
 
-// Exclusive prefix sum of a[0..m) in place (m <= 3 * blockDim.x); returns the total.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *a, int m, uint32_t *s_warp) {
-    constexpr int PER = 3;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-    uint32_t v[PER], sum = 0;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int i = t * PER + q;
-        v[q] = i < m ? a[i] : 0u;
-        sum += v[q];
-    }
-    uint32_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < nw ? s_warp[lane] : 0u;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < nw) s_warp[lane] = wi - w;  // exclusive warp offsets
-        if (lane == nw - 1) s_warp[31] = wi;   // total
-    }
-    __syncthreads();
-    uint32_t run = s_warp[warp] + inc - sum;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int i = t * PER + q;
-        if (i < m) a[i] = run;
-        run += v[q];
-    }
-    const uint32_t total = s_warp[31];
-    __syncthreads();
-    return total;
-}
-
 // ------------------------------------------------------------------ link kernel
 
 constexpr int kCols = kTileMaxCols + 2;
@@ -175,12 +143,11 @@ struct LinkSmem {
     uint32_t lcells[kTileMaxCols], lid[kTileMaxCols], lbpos[kTileMaxCols];
     uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];
     uint32_t lentered[kTileMaxCols];  // lanes whose buffer received a vehicle
-    uint32_t wpre[kTileSmemWords + 4];
+    uint32_t nlist;                 // vehicles in the list
     uint16_t code[kListCap];        // (local word << 5) | bit
     uint8_t ev[kListCap];           // velocity at step t
     uint8_t eflag[kListCap];        // 1: changed lane in sub-step 1
     uint32_t eid[kListCap];         // id word (id | last-link flag)
-    uint32_t warp_tmp[32];
     unsigned long long red[kLinkThreads / 32][6];
     int ncols, nwords, ncore_words, nlinks;
 };
@@ -213,15 +180,17 @@ __device__ __forceinline__ uint32_t list_mask(uint8_t kind, uint32_t vmax) {
 }
 
 __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__restrict__ table,
-                                                            const LinkTile *__restrict__ tiles, uint32_t n_tiles,
-                                                            uint32_t pos) {
+                                                            const LinkTile *__restrict__ tiles,
+                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
     __shared__ LinkSmem S;
+    const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
     // lane_changes, vehicle_updates, active, sum_v, state_hash, arrived_step
     static constexpr int kField[6] = {2, 6, 0, 5, 7, 8};
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
 
     pdl_trigger();
+    span_mark((int)pos * 3, true);
     bool waited = false;
     bool first = true;
     stamp(0, true);
@@ -333,15 +302,20 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.nlinks = 1;
             }
         }
+        // The step base and target change only between captured chunks (the
+        // chunk-closing kernel has finished before a chunk's first launch), so
+        // they may be read before waiting for the previous kernel.
+        const unsigned long long step = D.ctrl->base + pos;
+        const bool active = step < D.ctrl->target;
+        if (threadIdx.x == 0) S.nlist = 0u;
         __syncthreads();
         stamp(2, first);
+        if (!active) continue;
         if (!waited) {
             pdl_wait();
             waited = true;
         }
         stamp(3, first);
-        const unsigned long long step = D.ctrl->base + pos;
-        if (step >= D.ctrl->target) continue;
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
             if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
@@ -353,10 +327,35 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         const int d = (t & 1u) ? -1 : 1;
         const int nwords = S.nwords, ncore_words = S.ncore_words;
 
-        // ---------------- occupancy of step t and the link-end buffer states
+        // ---------------- occupancy of step t, buffer states, and the vehicle list
         {
+            // one word per thread (a tile has fewer words than the block has
+            // threads); each warp reserves its part of the list at once
+            static_assert(kTileSmemWords <= kLinkThreads, "one word per thread");
             const uint32_t *__restrict__ occ_in = D.occ[cur];
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.occ0[w] = occ_in[S.gw[w]];
+            const int w = threadIdx.x, lane = threadIdx.x & 31;
+            uint32_t m = 0u;
+            if (w < nwords) {
+                const uint32_t o = occ_in[S.gw[w]];
+                S.occ0[w] = o;
+                m = o & list_mask(S.ckind[S.wcol[w]], vmax);
+            }
+            const uint32_t cnt = (uint32_t)__popc(m);
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            uint32_t wbase = 0u;
+            if (lane == 31 && inc) wbase = atomicAdd(&S.nlist, inc);
+            wbase = __shfl_sync(0xffffffffu, wbase, 31);
+            uint32_t r = wbase + inc - cnt;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                S.code[r++] = (uint16_t)((w << 5) | b);
+            }
             for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x) {
                 const bool end_here = partial ? S.lexit[0] != 0 : !S.lring[q];
                 S.lexit[q] = end_here ? (uint8_t)D.link_exit[S.lid[q]] : (uint8_t)0;
@@ -364,22 +363,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         }
         __syncthreads();
         stamp(4, first);
-
-        // ---------------- compact the vehicles; load their velocity and id once
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x)
-            S.wpre[w] = __popc(S.occ0[w] & list_mask(S.ckind[S.wcol[w]], vmax));
-        __syncthreads();
-        const uint32_t total = block_exclusive_scan(S.wpre, nwords, S.warp_tmp);
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-            uint32_t m = S.occ0[w] & list_mask(S.ckind[S.wcol[w]], vmax);
-            uint32_t r = S.wpre[w];
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                S.code[r++] = (uint16_t)((w << 5) | b);
-            }
-        }
-        __syncthreads();
+        const uint32_t total = S.nlist;
         {
             const int8_t *__restrict__ vel_in = D.vel[cur];
             const uint32_t *__restrict__ vid_in = D.vid[cur];
@@ -516,6 +500,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
     }
     if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
     stamp(9, true);
+    span_mark((int)pos * 3, false);
 }
 
 // ------------------------------------------------------------------ node kernel
@@ -523,14 +508,16 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
 constexpr int kSlotPrefetch = 8;
 
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
-                                                            const uint4 *__restrict__ tiles, uint32_t n_tiles,
-                                                            uint32_t pos) {
+                                                            const uint4 *__restrict__ tiles,
+                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
     __shared__ unsigned long long red[kNodeThreads / 32][6];
+    const uint32_t n_tiles = *n_tiles_p;
     // transfers, inserted, buffered, active, sum_v, state_hash
     static constexpr int kField[6] = {3, 4, 1, 0, 5, 7};
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
     pdl_trigger();
+    span_mark((int)pos * 3 + 1, true);
     bool waited = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint4 td = tiles[tile];
@@ -538,12 +525,13 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
         if (D.ctrl == nullptr) continue;
         const uint32_t m = td.y + threadIdx.x;
         const uint4 nd = m < td.z ? D.nd_info[m] : make_uint4(0u, 0u, 0u, 0u);  // static
+        // constant within a captured chunk, like the link descriptors
+        const unsigned long long step = D.ctrl->base + pos;
+        if (step >= D.ctrl->target) continue;
         if (!waited) {
             pdl_wait();
             waited = true;
         }
-        const unsigned long long step = D.ctrl->base + pos;
-        if (step >= D.ctrl->target) continue;
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
             if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
@@ -630,6 +618,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
         }
     }
     if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
+    span_mark((int)pos * 3 + 1, false);
 }
 
 // ------------------------------------------------------------------ chunk close
@@ -637,6 +626,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
 // One block per scenario: sums the statistics of the g steps just run,
 // moves the step counter and clears the records of the next chunk.
 __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict__ table, uint32_t g_max) {
+    span_mark((int)g_max * 3 + 2, true);
     pdl_wait();
     const ScenDev &D = table[blockIdx.x];
     Ctrl *c = D.ctrl;
@@ -692,6 +682,7 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
         unsigned long long *z = reinterpret_cast<unsigned long long *>(D.stats + (size_t)(t & (kStatsRing - 1)) * nsub);
         z[u % per] = 0ull;
     }
+    span_mark((int)g_max * 3 + 2, false);
 }
 
 __global__ void set_target_kernel(Ctrl *ctrl, unsigned long long target) { ctrl->target = target; }
@@ -711,12 +702,12 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, uint32_t n_tiles, uint32_t i, int grid,
+void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl) {
     launch_pdl(link_kernel, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i);
 }
 
-void launch_node_kernel(const ScenDev *table, const uint4 *tiles, uint32_t n_tiles, uint32_t i, int grid,
+void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl) {
     launch_pdl(node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i);
 }
@@ -745,6 +736,17 @@ extern "C" int ts_debug_phase_times(unsigned long long *out, int n_blocks) {
                                  sizeof(unsigned long long) * kPhaseBlocks * p) != cudaSuccess)
             return -1;
     return n_blocks;
+}
+extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
+    if (reset) {
+        unsigned long long init[128][2];
+        for (int i = 0; i < 128; ++i) {
+            init[i][0] = ~0ull;
+            init[i][1] = 0ull;
+        }
+        return cudaMemcpyToSymbol(g_span, init, sizeof(init)) == cudaSuccess ? 0 : -1;
+    }
+    return cudaMemcpyFromSymbol(out, g_span, sizeof(unsigned long long) * 256) == cudaSuccess ? 0 : -1;
 }
 #endif
 

@@ -31,6 +31,7 @@ constexpr uint32_t kNoAllocMaxTiles = 132;  // 4096 columns in runs of at least 
 constexpr size_t kOffTable = 0;
 constexpr size_t kOffCtrl = 256;
 constexpr size_t kOffLink = 512;
+constexpr size_t kOffCount = 768;
 constexpr size_t kOffTiles = 1024;
 constexpr size_t kOffStats = kOffTiles + ((sizeof(LinkTile) * kNoAllocMaxTiles + 255u) / 256u) * 256u;
 constexpr size_t kScratchBytes = kOffStats + sizeof(StatRec) * kStatsRing;
@@ -110,6 +111,7 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     Ctrl *d_ctrl = reinterpret_cast<Ctrl *>(base + kOffCtrl);
     uint4 *d_link = reinterpret_cast<uint4 *>(base + kOffLink);
     LinkTile *d_tiles = reinterpret_cast<LinkTile *>(base + kOffTiles);
+    uint32_t *d_count = reinterpret_cast<uint32_t *>(base + kOffCount);
     StatRec *d_stats = reinterpret_cast<StatRec *>(base + kOffStats);
 
     // tiles: the whole ring if it fits one tile, else runs of columns whose
@@ -152,18 +154,20 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     ctrl.base = first_step;
     ctrl.target = first_step + n_steps;
     const uint4 link = make_uint4(0u, cells, lanes | (1u << 8), 0u);
+    const uint32_t n_tiles = (uint32_t)tiles.size();
     // the scratch keeps the previous call's contents: rewrite all of it that
     // this call reads, and clear the statistics it accumulates into
     if (cudaMemcpyAsync(d_table, &sd, sizeof(sd), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_ctrl, &ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_link, &link, sizeof(link), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_count, &n_tiles, sizeof(n_tiles), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(LinkTile) * tiles.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemsetAsync(d_stats, 0, sizeof(StatRec) * kStatsRing, s) != cudaSuccess)
         return bad(TS_ERR_CUDA, "scratch set-up copy failed");
     const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks()));
     for (uint32_t i = 0; i < n_steps; ++i)
-        launch_link_kernel(d_table, d_tiles, (uint32_t)tiles.size(), i, grid, s, false);
+        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false);
     gather_ring_stats<<<(n_steps + 127) / 128, 128, 0, s>>>(d_stats, first_step, n_steps, dev_stats_out);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");
     return TS_OK;

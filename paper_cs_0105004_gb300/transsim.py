@@ -99,6 +99,7 @@ _API = {
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
+    "ts_set_load_balance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
     "ts_ring_step_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Params), ctypes.c_uint64,
                                             ctypes.c_uint32] + [ctypes.c_void_p] * 8),
 }
@@ -217,6 +218,9 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+    def set_load_balance(self, every_steps: int, vehicles_per_tile: int = 1024):
+        _check(lib().ts_set_load_balance(self.h, every_steps, vehicles_per_tile))
 
     def set_tile_words(self, words: int):
         _check(lib().ts_set_tile_words(self.h, words))

@@ -153,6 +153,19 @@ def test_config0_tile_shapes_identical():
         sim.close()
 
 
+def test_load_balancing_keeps_results():
+    # re-tiling from the occupancy every 64 steps with a small vehicle budget
+    # splits jammed stretches into many partial tiles; results stay identical
+    sc = N.small_grid_scenario(4, 3, 70, n_trips=3000, window=300, steps=1500, gen_seed=8, seed=21)
+    sim = T.Simulation(sc)
+    sim.set_load_balance(64, 128)
+    orc = oracle.Oracle(sc)
+    sim.step(1500)
+    _cmp_stats(sim.stats_range(0, 1500), orc.step(1500), "load balanced")
+    _cmp_state(sim.read_state(), orc.get_state(), "load balanced final")
+    sim.close()
+
+
 def test_planar_network_window():
     sc = N._planar_config("planar-small", 900, 1060, 20000, 5, steps=1200)
     run_parity(sc, 1200, chunk=400, state_every=400)

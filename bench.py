@@ -292,13 +292,113 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
 
 
+def run_config3(args):
+    """Batching: 256 independent grid scenarios in one launch set per phase,
+    against the same scenarios run one after another."""
+    import torch
+    from paper_cs_0105004_gb300 import batching as Bt
+    from paper_cs_0105004_gb300 import transsim as T
+    from paper_cs_0105004_gb300.inputs import networks as N
+    torch.cuda.set_device(0)
+    steps = args.job_steps or 3600
+    scs = [N.config3_scenario(i) for i in range(args.scenarios)]
+    stream = torch.cuda.Stream()
+    best, timings = Bt.autotune_tile_words(scs[:args.tune_sample], stream, window=256)
+    sims = Bt.make_members(scs, tile_words=best)
+    batch = T.Batch(len(sims))
+    batch.add_many(sims, steps)
+    for _ in range(args.warmup):
+        Bt.run_batched(sims, steps, stream, batch)
+    sampler = ClockSampler(0)
+    sampler.start()
+    runs = [Bt.run_batched(sims, steps, stream, batch) for _ in range(args.steps)]
+    clocks = sampler.stop()
+    if len({r.vehicle_updates for r in runs}) != 1:
+        raise RuntimeError("batched runs differ")
+    batch.close()
+    seq = Bt.run_sequential(sims[:args.seq_sample], steps, stream)
+    if seq.per_member_updates != runs[0].per_member_updates[:args.seq_sample]:
+        raise RuntimeError("sequential and batched results differ")
+    sec = sum(r.seconds for r in runs)
+    value = sum(r.vehicle_updates for r in runs) / sec
+    lane_cells = sum(sc.net.n_lane_cells for sc in scs)
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "x_real_time": steps / (sec / args.steps),
+            "config": {"workload": f"{args.scenarios} grid scenarios (side 10-60, 1-3 lanes, 30-120 cells, "
+                                   f"0.1-0.4 trips per lane-cell), {steps} steps each, one batch",
+                       "lane_cells": lane_cells, "trips": int(sum(sc.demand.n for sc in scs)),
+                       "vehicle_updates_per_run": runs[0].vehicle_updates, "tile_words": best,
+                       "autotune_seconds": {str(k): v for k, v in timings.items()},
+                       "l2": "inputs larger than L2"},
+            "sequential": {"value": seq.updates_per_s, "unit": METRIC, "scenarios": args.seq_sample,
+                           "seconds": seq.seconds},
+            "batched_over_sequential": value / seq.updates_per_s,
+            "gpu_launches": args.steps * (2 * steps + steps // 32 + 1 + args.scenarios),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    for s_ in sims:
+        s_.close()
+
+
+def run_config4(args):
+    """Serving: a Poisson stream of simulation jobs admitted by device-memory
+    budget into a continuously running batch."""
+    import torch
+    from paper_cs_0105004_gb300 import serving as Sv
+    from paper_cs_0105004_gb300.inputs import networks as N
+    torch.cuda.set_device(0)
+    steps = args.job_steps or 3600
+    c0 = N.config0()
+    c1 = N.config1() if args.serve_mix[1] > 0 else None
+    grids = [N.config3_scenario(i) for i in range(args.grid_pool)]
+    arrivals = Sv.poisson_arrivals(args.rate, args.duration, seed=7)
+    rng = np.random.default_rng(7)
+    mix = np.array(args.serve_mix, dtype=float)
+    kinds = rng.choice(3, size=arrivals.size, p=mix / mix.sum())
+    jobs = []
+    for jid, (t, kd) in enumerate(zip(arrivals, kinds)):
+        base = [c0, c1, grids[jid % len(grids)]][kd]
+        def make(base=base, jid=jid):
+            return N.Scenario(f"{base.name}/job{jid}", base.net, base.demand, steps, seed=100000 + jid,
+                              vmax=base.vmax, p_threshold=base.p_threshold)
+        jobs.append(Sv.Job(jid, ["config0", "config1", "grid"][kd], float(t), make, steps))
+    srv = Sv.Server(budget_bytes=int(args.budget_gb * 2**30), chunk_steps=args.chunk)
+    sampler = ClockSampler(0)
+    sampler.start()
+    rep = srv.run(jobs, time_scale=args.time_scale)
+    clocks = sampler.stop()
+    srv.close()
+    summ = rep.summary()
+    line = {"metric": METRIC, "value": summ["vehicle_updates_per_s"], "unit": METRIC, "n_gpus": 1,
+            "steps": len(rep.jobs), "warmup": 0, "ms_per_step": 1000.0 * rep.wall_s / max(1, len(rep.jobs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"Poisson {args.rate}/s jobs for {args.duration} s, mix config0:config1:grid = "
+                                   f"{args.serve_mix}, {steps} steps per job, arrival clock x{args.time_scale}",
+                       "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
+            "serving": summ, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4"])
+    ap.add_argument("--scenarios", type=int, default=256, help="config3: batch members")
+    ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
+    ap.add_argument("--seq-sample", type=int, default=256, help="config3: members run one by one for comparison")
+    ap.add_argument("--rate", type=float, default=20.0, help="config4: job arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="config4: seconds of arrivals")
+    ap.add_argument("--time-scale", type=float, default=1.0, help="config4: arrival clock factor")
+    ap.add_argument("--serve-mix", type=float, nargs=3, default=[60, 10, 30], help="config4: config0 config1 grid")
+    ap.add_argument("--grid-pool", type=int, default=16, help="config4: distinct grid networks")
+    ap.add_argument("--budget-gb", type=float, default=160.0, help="config4: device memory for jobs")
+    ap.add_argument("--chunk", type=int, default=128, help="config4: steps per batch step")
     ap.add_argument("--job-steps", type=int, default=None, help="steps per job (default: the config's)")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -315,6 +415,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "config3":
+        if rank == 0:
+            run_config3(args)
+        return
+    if args.workload == "config4":
+        if rank == 0:
+            run_config4(args)
         return
     if world > 1:
         import torch

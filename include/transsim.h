@@ -217,8 +217,13 @@ void ts_destroy(ts_ctx *ctx);
  * ts_batch_step and need no re-capture. */
 ts_status ts_batch_create(uint32_t capacity, ts_batch **out);
 ts_status ts_batch_add(ts_batch *b, ts_ctx *ctx, uint64_t target_step);
+/* Adds n contexts at once (one table rebuild). */
+ts_status ts_batch_add_many(ts_batch *b, ts_ctx *const *ctxs, uint32_t n, uint64_t target_step);
 ts_status ts_batch_remove(ts_batch *b, ts_ctx *ctx);
 ts_status ts_batch_step(ts_batch *b, uint32_t n_steps, void *cuda_stream);
+/* Enqueues, on cuda_stream, a return of every member to the empty network
+ * at step 0 with the new target step; no host transfers, no rebuild. */
+ts_status ts_batch_reset(ts_batch *b, uint64_t target_step, void *cuda_stream);
 /* Waits (bounded) for the batch's queued work. */
 ts_status ts_batch_sync(ts_batch *b, uint32_t timeout_ms);
 /* Current step of a member (after ts_batch_sync). */

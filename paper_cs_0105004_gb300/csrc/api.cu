@@ -675,7 +675,7 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
     c->host_step = 0;
     c->loaded = true;
     CK(cudaEventRecord(c->ev, c->stream));
-    return ensure_own_world(c);
+    return TS_OK;  // the single-scenario launch set is built on first use
 }
 
 ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
@@ -719,6 +719,10 @@ ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
     if (c->batch) return fail(TS_ERR_STATE, "context is stepped by its batch");
     if (n_steps == 0) return TS_OK;
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+    if (!c->own) {
+        st = ensure_own_world(c);
+        if (st != TS_OK) return st;
+    }
     const uint64_t start = c->host_step;
     c->host_step += n_steps;
     launch_set_target(c->sd.ctrl, c->host_step, s);
@@ -774,6 +778,10 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
     if (!link_ms || !node_ms) return fail(TS_ERR_INVALID, "null output");
     if (n_steps == 0) return TS_OK;
     cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
+    if (!c->own) {
+        st = ensure_own_world(c);
+        if (st != TS_OK) return st;
+    }
     World *w = c->own;
     std::vector<cudaEvent_t> ev(3ull * n_steps);
     size_t made = 0;
@@ -1089,24 +1097,36 @@ ts_status ts_batch_create(uint32_t capacity, ts_batch **out) {
     return TS_OK;
 }
 
-ts_status ts_batch_add(ts_batch *b, ts_ctx *c, uint64_t target_step) {
-    if (!b) return fail(TS_ERR_INVALID, "null batch");
-    ts_status st = check_ctx(c);
+ts_status ts_batch_add_many(ts_batch *b, ts_ctx *const *ctxs, uint32_t n, uint64_t target_step) {
+    if (!b || (n && !ctxs)) return fail(TS_ERR_INVALID, "null batch or contexts");
+    ts_status st = wait_event(b->ev, 60000);  // the table is rewritten below
     if (st != TS_OK) return st;
-    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
-    if (c->batch) return fail(TS_ERR_STATE, "context already in a batch");
-    st = wait_ctx(c, 60000);
-    if (st != TS_OK) return st;
-    st = wait_event(b->ev, 60000);  // the table is rewritten below
-    if (st != TS_OK) return st;
-    uint32_t slot = 0;
-    while (slot < b->w.capacity && b->w.members[slot]) ++slot;
-    if (slot == b->w.capacity) return fail(TS_ERR_STATE, "batch is full");
-    CK(cudaMemcpy(&c->sd.ctrl->target, &target_step, sizeof(target_step), cudaMemcpyHostToDevice));
-    b->w.members[slot] = c;
-    c->batch = b;
+    uint32_t free_slots = 0;
+    for (ts_ctx *m : b->w.members) free_slots += m == nullptr;
+    if (n > free_slots) return fail(TS_ERR_STATE, "batch is full");
+    for (uint32_t i = 0; i < n; ++i) {
+        ts_ctx *c = ctxs[i];
+        st = check_ctx(c);
+        if (st != TS_OK) return st;
+        if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+        if (c->batch) return fail(TS_ERR_STATE, "context already in a batch");
+        for (uint32_t j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(TS_ERR_INVALID, "context listed twice");
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        ts_ctx *c = ctxs[i];
+        st = wait_ctx(c, 60000);
+        if (st != TS_OK) return st;
+        CK(cudaMemcpy(&c->sd.ctrl->target, &target_step, sizeof(target_step), cudaMemcpyHostToDevice));
+        uint32_t slot = 0;
+        while (b->w.members[slot]) ++slot;
+        b->w.members[slot] = c;
+        c->batch = b;
+    }
     return b->w.rebuild();
 }
+
+ts_status ts_batch_add(ts_batch *b, ts_ctx *c, uint64_t target_step) { return ts_batch_add_many(b, &c, 1, target_step); }
 
 ts_status ts_batch_remove(ts_batch *b, ts_ctx *c) {
     if (!b || !c || c->batch != b) return fail(TS_ERR_INVALID, "context is not in this batch");
@@ -1130,6 +1150,26 @@ ts_status ts_batch_step(ts_batch *b, uint32_t n_steps, void *cuda_stream) {
     if (!s || s == b->w.cap_stream) return fail(TS_ERR_INVALID, "pass a stream to ts_batch_step");
     ts_status st = b->w.run(n_steps, s);
     if (st != TS_OK) return st;
+    CK(cudaEventRecord(b->ev, s));
+    for (ts_ctx *c : b->w.members)
+        if (c) CK(cudaEventRecord(c->ev, s));
+    return TS_OK;
+}
+
+ts_status ts_batch_reset(ts_batch *b, uint64_t target_step, void *cuda_stream) {
+    if (!b) return fail(TS_ERR_INVALID, "null batch");
+    CK(cudaSetDevice(b->w.device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s || s == b->w.cap_stream) return fail(TS_ERR_INVALID, "pass a stream to ts_batch_reset");
+    for (ts_ctx *c : b->w.members) {
+        if (!c) continue;
+        if (c->sticky) return fail(TS_ERR_CUDA, "a member is in an error state");
+        ts_status st = reset_device_state(c, s);
+        if (st != TS_OK) return st;
+        launch_set_target(c->sd.ctrl, target_step, s);
+        c->host_step = 0;
+    }
+    CK(cudaGetLastError());
     CK(cudaEventRecord(b->ev, s));
     for (ts_ctx *c : b->w.members)
         if (c) CK(cudaEventRecord(c->ev, s));

@@ -92,9 +92,12 @@ _API = {
     "ts_destroy": (None, [ctypes.c_void_p]),
     "ts_batch_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
     "ts_batch_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "ts_batch_add_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
+                                         ctypes.c_uint64]),
     "ts_batch_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ts_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "ts_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_batch_reset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "ts_ctx_step": (ctypes.c_int, [ctypes.c_void_p, u64p]),
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
@@ -164,9 +167,11 @@ def footprint_bytes(scenario) -> int:
 def _torch_allocator():
     import torch
 
+    # all contexts allocate on the calling thread's current stream, so blocks
+    # freed by finished jobs are reused by the next ones
     def _alloc(nbytes, stream, user):
         try:
-            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
         except Exception:
             return None
 
@@ -294,6 +299,10 @@ class Batch:
     def add(self, sim: Simulation, target_step: int):
         _check(lib().ts_batch_add(self.h, sim.h, target_step))
 
+    def add_many(self, sims, target_step: int):
+        arr = (ctypes.c_void_p * len(sims))(*[s.h.value for s in sims])
+        _check(lib().ts_batch_add_many(self.h, arr, len(sims), target_step))
+
     def remove(self, sim: Simulation):
         _check(lib().ts_batch_remove(self.h, sim.h))
 
@@ -303,6 +312,10 @@ class Batch:
 
     def sync(self, timeout_ms: int = 600000):
         _check(lib().ts_batch_sync(self.h, timeout_ms))
+
+    def reset(self, target_step: int, stream):
+        s = _stream_handle(stream)
+        _check(lib().ts_batch_reset(self.h, target_step, ctypes.c_void_p(s)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,0 +1,66 @@
+"""Batching and serving: each job's result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+from paper_cs_0105004_gb300 import batching as Bt
+from paper_cs_0105004_gb300 import serving as Sv
+from paper_cs_0105004_gb300 import transsim as T
+from paper_cs_0105004_gb300.inputs import networks as N
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(i):
+    return N.small_grid_scenario(3 + i % 4, 1 + i % 3, 20 + 3 * i, 60 + 25 * i, 80, 300, gen_seed=40 + i,
+                                 seed=500 + i)
+
+
+def _alone(sc, steps):
+    sim = T.Simulation(sc)
+    sim.step(steps)
+    tot = sim.totals()
+    sim.close()
+    return tot
+
+
+def test_served_jobs_equal_their_single_runs():
+    scs = [_small(i) for i in range(12)]
+    steps = 300
+    alone = [_alone(sc, steps) for sc in scs]
+    # arrivals closer together than a job lasts, so jobs join a running batch
+    jobs = [Sv.Job(i, "grid", 0.002 * i, (lambda sc=sc: sc), steps) for i, sc in enumerate(scs)]
+    jobs.sort(key=lambda j: j.arrival)
+    srv = Sv.Server(budget_bytes=2**30, chunk_steps=32, workers=2)
+    rep = srv.run(jobs)
+    srv.close()
+    assert len(rep.jobs) == len(scs)
+    for j in rep.jobs:
+        a = alone[j.jid]
+        assert j.vehicle_updates == a["vehicle_updates"]
+        assert j.last_state_hash == a["last_state_hash"]
+        assert j.finished >= j.admitted >= j.arrival
+    assert rep.peak_active > 1  # jobs overlapped on the device
+
+
+def test_admission_respects_the_memory_budget():
+    scs = [_small(i) for i in range(6)]
+    fp = max(T.footprint_bytes(sc) for sc in scs)
+    jobs = [Sv.Job(i, "grid", 0.0, (lambda sc=sc: sc), 200) for i, sc in enumerate(scs)]
+    srv = Sv.Server(budget_bytes=2 * fp, chunk_steps=32, workers=2)
+    rep = srv.run(jobs)
+    srv.close()
+    assert len(rep.jobs) == 6 and rep.peak_bytes <= 2 * fp and rep.peak_active <= 2
+
+
+def test_batched_run_equals_sequential_runs():
+    import torch
+    scs = [N.config3_scenario(i, demand_scale=0.05, steps=400) for i in range(4)]
+    stream = torch.cuda.Stream()
+    best, timings = Bt.autotune_tile_words(scs, stream, window=64)
+    assert best in timings
+    sims = Bt.make_members(scs, tile_words=best)
+    b = Bt.run_batched(sims, 400, stream)
+    s = Bt.run_sequential(sims, 400, stream)
+    assert b.per_member_updates == s.per_member_updates
+    for sim in sims:
+        sim.close()

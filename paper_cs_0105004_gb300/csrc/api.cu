@@ -53,6 +53,7 @@ ts_status wait_event(cudaEvent_t ev, uint32_t timeout_ms) {
 
 void tsim::set_last_error(const char *msg) { g_err = msg; }
 
+
 // ------------------------------------------------------------------ world (scenarios stepped together)
 
 struct World {
@@ -382,12 +383,17 @@ ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
 }
 
 // Zeroes the statistics ring and sets the control block.
-ts_status reset_ctrl(ts_ctx *c, uint64_t step, uint64_t arrived, uint64_t inserted, cudaStream_t s) {
+ts_status reset_ctrl(ts_ctx *c, uint64_t step, uint64_t arrived, uint64_t inserted, cudaStream_t s,
+                     uint64_t active = 0, uint64_t buffered = 0, uint64_t sum_v = 0, uint64_t hash = 0) {
     Ctrl h{};
     h.base = step;
     h.target = step;
     h.arrived = arrived;
     h.inserted = inserted;
+    h.active = active;
+    h.buffered = buffered;
+    h.sum_v = sum_v;
+    h.hash = hash;
     CK(cudaMemcpyAsync(c->sd.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->sd.stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub, s));
     CK(cudaStreamSynchronize(s));
@@ -419,7 +425,7 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
     }
     size_t b = 0;
     b += 16ull * d->n_links * 2 + 4ull * d->n_links * 2;      // lk_info, nd_info, link_exit (+ reset copy)
-    b += words * (4 + 32 + 128) * 2;                          // occupancy, velocity, id (double-buffered)
+    b += words * (4 + 4 + 4 + 32 + 128) * 2;                  // occupancy, v>0, location, velocity, id (x2)
     b += 16ull * slots + 8ull * n_vehicles * 2 + 4ull * route_len;
     b += 8ull * n_vehicles + 4ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
     b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
@@ -504,6 +510,10 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     uint4 *nd_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint32_t *occ0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
     uint32_t *occ1 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
+    uint32_t *mov0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
+    uint32_t *mov1 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
+    uint32_t *loc0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
+    uint32_t *loc1 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
     int8_t *vel0 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32, ok);
     int8_t *vel1 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32, ok);
     uint32_t *vid0 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32, ok);
@@ -522,6 +532,10 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.nd_info = nd_info;
     sd.occ[0] = occ0;
     sd.occ[1] = occ1;
+    sd.mov[0] = mov0;
+    sd.mov[1] = mov1;
+    sd.loc[0] = loc0;
+    sd.loc[1] = loc1;
     sd.vel[0] = vel0;
     sd.vel[1] = vel1;
     sd.vid[0] = vid0;
@@ -543,8 +557,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     for (uint32_t l = 0; l < L; ++l) ex[l] = c->ring[l] ? 0u : ((1u << c->lanes[l]) - 1u);
     CK(cudaMemcpy(c->d_link_exit0, ex.data(), 4ull * L, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(link_exit, ex.data(), 4ull * L, cudaMemcpyHostToDevice));
-    CK(cudaMemset(occ0, 0, 4ull * c->n_words));
-    CK(cudaMemset(occ1, 0, 4ull * c->n_words));
+    for (uint32_t *p : {occ0, occ1, mov0, mov1, loc0, loc1}) CK(cudaMemset(p, 0, 4ull * c->n_words));
     CK(cudaMemset(slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(ctrl, 0, sizeof(Ctrl)));
     CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub));
@@ -610,7 +623,11 @@ static ts_status upload_vehicles(ts_ctx *c) {
 // Device-side return to the empty network at step 0.
 static ts_status reset_device_state(ts_ctx *c, cudaStream_t s) {
     ScenDev &sd = c->sd;
-    for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(sd.occ[b], 0, 4ull * c->n_words, s));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaMemsetAsync(sd.occ[b], 0, 4ull * c->n_words, s));
+        CK(cudaMemsetAsync(sd.mov[b], 0, 4ull * c->n_words, s));
+        CK(cudaMemsetAsync(sd.loc[b], 0, 4ull * c->n_words, s));
+    }
     CK(cudaMemsetAsync(sd.slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1), s));
     CK(cudaMemcpyAsync(sd.link_exit, c->d_link_exit0, 4ull * c->n_links, cudaMemcpyDeviceToDevice, s));
     if (c->n_veh) CK(cudaMemcpyAsync(sd.veh, c->d_veh0, 8ull * c->n_veh, cudaMemcpyDeviceToDevice, s));
@@ -851,28 +868,32 @@ ts_status ts_read_stats_range(ts_ctx *c, uint64_t first, uint32_t n, ts_stats *o
         }
         return (uint64_t)s;
     };
-    // cumulative arrivals and insertions after step t, counted back from the totals
-    uint64_t arr = h.arrived, ins = h.inserted;
-    for (uint64_t t = h.base - 1; t + 1 > first + n; --t) {
-        arr -= sum(t, 8);
-        ins -= sum(t, 4);
-    }
+    // running values after step t, counted back from the values at the base
+    uint64_t arr = h.arrived, ins = h.inserted, act = h.active, buf = h.buffered, sv = h.sum_v, hs = h.hash;
+    auto back = [&](uint64_t t) {
+        arr -= sum(t, kArrived);
+        ins -= sum(t, kInserted);
+        act -= sum(t, kDActive);
+        buf -= sum(t, kDBuffered);
+        sv -= sum(t, kDSumV);
+        hs -= sum(t, kDHash);
+    };
+    for (uint64_t t = h.base - 1; t + 1 > first + n; --t) back(t);
     for (uint32_t i = n; i-- > 0;) {
         const uint64_t t = first + i;
         ts_stats &o = out[i];
         o.step = t;
-        o.active = sum(t, 0);
-        o.buffered = sum(t, 1);
-        o.lane_changes = sum(t, 2);
-        o.transfers = sum(t, 3);
-        o.inserted = sum(t, 4);
-        o.sum_v = sum(t, 5);
-        o.vehicle_updates = sum(t, 6);
-        o.state_hash = sum(t, 7);
+        o.active = act;
+        o.buffered = buf;
+        o.lane_changes = sum(t, kLaneChanges);
+        o.transfers = sum(t, kTransfers);
+        o.inserted = sum(t, kInserted);
+        o.sum_v = sv;
+        o.vehicle_updates = sum(t, kUpdates);
+        o.state_hash = hs;
         o.arrived = arr;
         o.waiting = departed_upto(c, t) - ins;
-        arr -= sum(t, 8);
-        ins -= o.inserted;
+        back(t);
     }
     return TS_OK;
 }
@@ -905,7 +926,7 @@ ts_status ts_read_totals(ts_ctx *c, ts_totals *out, uint32_t timeout_ms) {
     out->transfers = h.tot_transfers;
     out->inserted = h.inserted;
     out->arrived = h.arrived;
-    out->last_state_hash = h.last_hash;
+    out->last_state_hash = h.hash;
     return TS_OK;
 }
 
@@ -931,13 +952,16 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     if (st != TS_OK) return st;
     const int cur = (int)(h.base & 1ull);
     const size_t nw = c->n_words;
-    std::vector<uint32_t> occ(nw), vid(nw * 32), head(c->n_links);
-    std::vector<int8_t> vel(nw * 32);
+    std::vector<uint32_t> occ(nw), loc(nw), vid0(nw * 32), vid1(nw * 32), head(c->n_links);
+    std::vector<int8_t> vel0(nw * 32), vel1(nw * 32);
     std::vector<uint4> slots(c->n_slots);
     std::vector<uint2> veh(c->n_veh);
     CK(cudaMemcpy(occ.data(), c->sd.occ[cur], 4 * nw, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(vel.data(), c->sd.vel[cur], nw * 32, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(vid.data(), c->sd.vid[cur], 4 * nw * 32, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(loc.data(), c->sd.loc[cur], 4 * nw, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vel0.data(), c->sd.vel[0], nw * 32, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vel1.data(), c->sd.vel[1], nw * 32, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vid0.data(), c->sd.vid[0], 4 * nw * 32, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vid1.data(), c->sd.vid[1], 4 * nw * 32, cudaMemcpyDeviceToHost));
     if (c->n_slots) CK(cudaMemcpy(slots.data(), c->sd.slots, 16ull * c->n_slots, cudaMemcpyDeviceToHost));
     if (c->n_veh) CK(cudaMemcpy(veh.data(), c->sd.veh, 8ull * c->n_veh, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(head.data(), c->sd.dep_head, 4ull * c->n_links, cudaMemcpyDeviceToHost));
@@ -961,8 +985,9 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
                     const uint64_t x = 32ull * j + (uint64_t)b;
                     if (x >= c->cells[l]) return fail(TS_ERR_DEVICE_CHECK, "occupancy bit past the link end");
                     const uint64_t ci = c->cell_base[c->lane_base[l] + k] + x;
-                    o->cell_id[ci] = (int32_t)(vid[w * 32 + b] & kIdMask);
-                    o->cell_v[ci] = vel[w * 32 + b];
+                    const bool b1 = (loc[w] >> b) & 1u;
+                    o->cell_id[ci] = (int32_t)((b1 ? vid1 : vid0)[w * 32 + b] & kIdMask);
+                    o->cell_v[ci] = (b1 ? vel1 : vel0)[w * 32 + b];
                 }
             }
         if (!c->ring[l])
@@ -992,7 +1017,8 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     if (st != TS_OK) return st;
     const uint32_t vmax = c->params.vmax;
     const size_t nw = c->n_words;
-    std::vector<uint32_t> occ(nw, 0), vid(nw * 32, 0), exit_bits(c->n_links, 0);
+    std::vector<uint32_t> occ(nw, 0), mov(nw, 0), vid(nw * 32, 0), exit_bits(c->n_links, 0);
+    uint64_t n_active = 0, n_buffered = 0, sum_v = 0, hash = 0;
     std::vector<int8_t> vel(nw * 32, 0);
     std::vector<uint4> slots(c->n_slots, make_uint4(kSlotEmpty, 0, 0, 0));
     std::vector<uint8_t> seen(c->n_veh, 0);
@@ -1015,9 +1041,13 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
                 seen[id] = 1;
                 const size_t w = (size_t)c->wbase[l] + (size_t)(x / 32) * nl + k;
                 occ[w] |= 1u << (x % 32);
+                if (v) mov[w] |= 1u << (x % 32);
                 vel[w * 32 + x % 32] = v;
                 const bool last = in->cursor[id] + 1 == c->route_off[id + 1] - c->route_off[id];
                 vid[w * 32 + x % 32] = (uint32_t)id | (last ? kLastLinkBit : 0u);
+                ++n_active;
+                sum_v += (uint64_t)v;
+                hash += vehicle_term((uint32_t)id, l, k, x, (uint32_t)v);
             }
             const int32_t b = in->buf_id[c->lane_base[l] + k];
             if (b >= 0) {
@@ -1034,6 +1064,8 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
                 slots[c->bpos[l] + k] =
                     make_uint4((uint32_t)b | fl, c->route_links[p + 1], l, (uint32_t)v | (k << 8) | (c->cells[l] << 10));
                 exit_bits[l] &= ~(1u << k);
+                ++n_buffered;
+                hash += vehicle_term((uint32_t)b, l, k, c->cells[l], (uint32_t)v);
             }
         }
     }
@@ -1049,15 +1081,20 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     for (uint32_t i = 0; i < c->n_veh; ++i) veh[i] = make_uint2(c->route_off[i] + in->cursor[i], c->route_off[i + 1]);
     const int cur = (int)(in->step & 1ull);
     ScenDev &sd = c->sd;
-    CK(cudaMemset(sd.occ[cur ^ 1], 0, 4 * nw));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaMemset(sd.occ[b], 0, 4 * nw));
+        CK(cudaMemset(sd.mov[b], 0, 4 * nw));
+        CK(cudaMemset(sd.loc[b], 0, 4 * nw));  // all payload in buffer 0
+    }
     CK(cudaMemcpy(sd.occ[cur], occ.data(), 4 * nw, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(sd.vel[cur], vel.data(), nw * 32, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(sd.vid[cur], vid.data(), 4 * nw * 32, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.mov[cur], mov.data(), 4 * nw, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.vel[0], vel.data(), nw * 32, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sd.vid[0], vid.data(), 4 * nw * 32, cudaMemcpyHostToDevice));
     if (c->n_slots) CK(cudaMemcpy(sd.slots, slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(sd.link_exit, exit_bits.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
     if (c->n_veh) CK(cudaMemcpy(sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(sd.dep_head, head.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
-    st = reset_ctrl(c, in->step, in->arrived, in->inserted, c->stream);
+    st = reset_ctrl(c, in->step, in->arrived, in->inserted, c->stream, n_active, n_buffered, sum_v, hash);
     if (st != TS_OK) return st;
     CK(cudaEventRecord(c->ev, c->stream));
     return TS_OK;

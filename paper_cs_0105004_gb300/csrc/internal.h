@@ -6,11 +6,16 @@
 //     lanes of one column are adjacent and a link's columns are contiguous
 //     (link-major, lane-interleaved).  Bit i of that word is cell 32j+i.
 //   * occ[2][n_words]: occupancy bitmasks, double-buffered by step parity
-//     (the state at step t lives in buffer t&1).
-//   * vel[2][32*n_words] (int8) and vid[2][32*n_words] (uint32): velocity and
-//     vehicle id of the cell with the same bit index; vid bit 31 marks a
-//     vehicle driving the last link of its route.  Payload of empty cells is
-//     never read.
+//     (the state at step t lives in occ[t&1]); mov[2][n_words]: bit set when
+//     the vehicle in that cell has v > 0; loc[2][n_words]: which of the two
+//     payload buffers holds the vehicle's velocity and id.
+//   * vel[2][32*n_words] (int8) and vid[2][32*n_words] (uint32): the two
+//     payload buffers, velocity and vehicle id of the cell with the same bit
+//     index; vid bit 31 marks a vehicle driving the last link of its route.
+//     A vehicle that stays where it is with v = 0 keeps its payload where it
+//     is; a vehicle that moves or changes speed writes the buffer that no
+//     reader of the step can be using (the other one than the cell's current
+//     occupant's).  Payload of empty cells is never read.
 //   * slots[n_slots]: one link-end buffer per lane, grouped by the node the
 //     link ends at, in intersection priority order (link id, then lane):
 //     x = id | next-link-is-last << 31 (0xffffffff = empty), y = next link,
@@ -43,10 +48,16 @@ constexpr uint32_t kNoLink = 0xFFFFFFFFu;
 struct Ctrl {
     unsigned long long base;      // steps completed (first step of the next chunk)
     unsigned long long target;    // run while step < target
-    unsigned long long arrived;   // cumulative arrivals up to base
-    unsigned long long inserted;  // cumulative departures inserted up to base
+    // values of the state at `base` (statistics of earlier steps are rebuilt
+    // from these and the per-step changes)
+    unsigned long long arrived;   // cumulative arrivals
+    unsigned long long inserted;  // cumulative departures inserted
+    unsigned long long active;    // vehicles in cells
+    unsigned long long buffered;  // vehicles in link-end buffers
+    unsigned long long sum_v;     // sum of velocities of vehicles in cells
+    unsigned long long hash;      // state digest
     unsigned long long tot_updates, tot_lane_changes, tot_transfers;  // since the last reset
-    unsigned long long steps_run, last_hash;
+    unsigned long long steps_run;
     unsigned int error;  // device-check flags (bitwise or)
     unsigned int pad;
 };
@@ -58,18 +69,22 @@ constexpr unsigned kErrRoute = 4u;      // route cursor past the route end
 constexpr unsigned kErrGeometry = 8u;   // a vehicle left the tile geometry
 
 // One statistics sub-record per step; n_sub of them per step, each on its own
-// 128-byte line, so that block flushes spread over L2 slices.
+// 128-byte line, so that block flushes spread over L2 slices.  Counts of the
+// step, and the changes (modulo 2^64) of the state's running values.
 struct StatRec {
-    unsigned long long active, buffered, lane_changes, transfers, inserted, sum_v, vehicle_updates, state_hash,
-        arrived_step;
+    unsigned long long vehicle_updates, lane_changes, transfers, inserted, arrived, d_active, d_buffered, d_sum_v,
+        d_hash;
     unsigned long long pad[7];
 };
+enum StatField { kUpdates = 0, kLaneChanges, kTransfers, kInserted, kArrived, kDActive, kDBuffered, kDSumV, kDHash };
 static_assert(sizeof(StatRec) == 128, "StatRec is one line");
 
 struct ScenDev {
     const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8 | column in tile << 16, w slot base
     const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8, w dep end
     uint32_t *occ[2];
+    uint32_t *mov[2];
+    uint32_t *loc[2];
     int8_t *vel[2];
     uint32_t *vid[2];
     uint4 *slots;
@@ -108,5 +123,23 @@ int max_link_blocks();
 int max_node_blocks();
 // Sets the thread-local message returned by ts_last_error.
 void set_last_error(const char *msg);
+
+// splitmix64 output function (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Digest term of one vehicle: the state digest is the sum (mod 2^64) of this
+// over all vehicles in cells and buffers (a buffered vehicle has cell = link
+// cells).
+__host__ __device__ __forceinline__ unsigned long long vehicle_term(uint32_t id, uint32_t link, uint32_t lane,
+                                                                    uint32_t cell, uint32_t v) {
+    const unsigned long long a = ((unsigned long long)id << 32) | link;
+    const unsigned long long b = ((unsigned long long)cell << 16) | ((unsigned long long)lane << 8) | v;
+    return mix64(a ^ mix64(b));
+}
 
 }  // namespace tsim

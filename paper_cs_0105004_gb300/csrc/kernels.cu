@@ -50,21 +50,6 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
     return c0;
 }
 
-// splitmix64 output function (Steele, Lea, Flood 2014).
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-    z += 0x9e3779b97f4a7c15ull;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ unsigned long long vehicle_term(uint32_t id, uint32_t link, uint32_t lane, uint32_t cell,
-                                                           uint32_t v) {
-    const unsigned long long a = ((unsigned long long)id << 32) | link;
-    const unsigned long long b = ((unsigned long long)cell << 16) | ((unsigned long long)lane << 8) | v;
-    return mix64(a ^ mix64(b));
-}
-
 #ifdef TS_PHASE_TIMING
 // Debug builds only: %globaltimer stamps at the phase boundaries of the first
 // tile of every link_kernel block of the last launch.
@@ -130,25 +115,30 @@ __device__ __forceinline__ void block_flush(unsigned long long (&acc)[NF], unsig
 constexpr int kCols = kTileMaxCols + 2;
 
 struct LinkSmem {
-    uint32_t occ0[kTileSmemWords];  // state of step t (local word index)
+    uint32_t occ0[kTileSmemWords];  // step t: occupancy, v > 0, payload buffer
+    uint32_t mov0[kTileSmemWords];
+    uint32_t loc0[kTileSmemWords];
     uint32_t mv[kTileSmemWords];    // vehicles that changed INTO the word's lane
     uint32_t occ1[kTileSmemWords];  // after the lane-change sub-step
-    uint32_t out[kTileSmemWords];   // step t+1 (core words)
+    uint32_t mov1[kTileSmemWords];
+    uint32_t oocc[kTileSmemWords];  // step t+1 (core words)
+    uint32_t omov[kTileSmemWords];
+    uint32_t oloc[kTileSmemWords];
     uint32_t gw[kTileSmemWords];    // global word index of each local word
     uint8_t wcol[kTileSmemWords], wlane[kTileSmemWords];
     uint16_t cw[kCols];             // local word of lane 0 of each column
     uint32_t cx0[kCols];            // first cell of the column within its link
+    uint32_t cnear[kCols];          // cells within vmax of a (non-periodic) link end
     int16_t right[kCols], left[kCols];
     uint8_t clink[kCols], ckind[kCols];  // ckind: 0 core, 1 left halo, 2 right halo
     uint32_t lcells[kTileMaxCols], lid[kTileMaxCols], lbpos[kTileMaxCols];
     uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];
     uint32_t lentered[kTileMaxCols];  // lanes whose buffer received a vehicle
-    uint32_t nlist;                 // vehicles in the list
-    uint16_t code[kListCap];        // (local word << 5) | bit
-    uint8_t ev[kListCap];           // velocity at step t
-    uint8_t eflag[kListCap];        // 1: changed lane in sub-step 1
-    uint32_t eid[kListCap];         // id word (id | last-link flag)
-    unsigned long long red[kLinkThreads / 32][6];
+    uint32_t nlist;                   // vehicles in the list
+    uint16_t code[kListCap];          // (local word << 5) | bit
+    uint8_t ev[kListCap];             // velocity at step t
+    uint32_t eid[kListCap];           // id word (id | last-link flag)
+    unsigned long long red[kLinkThreads / 32][7];
     int ncols, nwords, ncore_words, nlinks;
 };
 
@@ -171,12 +161,46 @@ __device__ __forceinline__ bool room_behind(const uint32_t *O, const LinkSmem &S
     return (back & mask) == 0ull;
 }
 
-// Vehicles a tile must look at: every one in its core columns, the last vmax
-// cells of a left halo column (they can move into the core) and the first
-// vmax cells of a right halo column (their lane changes shape the cells the
-// core vehicles look ahead into).
-__device__ __forceinline__ uint32_t list_mask(uint8_t kind, uint32_t vmax) {
+// Bit x of the result: cell x+1 of the same lane is occupied (next word's bit
+// 0 for x = 31).
+__device__ __forceinline__ uint32_t ahead_mask(const uint32_t *O, const LinkSmem &S, int c, int k) {
+    const int r = S.right[c];
+    return (O[S.cw[c] + k] >> 1) | ((r >= 0 ? O[S.cw[r] + k] : 0u) << 31);
+}
+
+// Vehicles a tile must look at for lane changes: every one in its core
+// columns, the last vmax cells of a left halo column (they can move into the
+// core) and the first vmax cells of a right halo column (their lane changes
+// shape the cells the core vehicles look ahead into).
+__device__ __forceinline__ uint32_t lc_mask(uint8_t kind, uint32_t vmax) {
     return kind == 0 ? 0xFFFFFFFFu : (kind == 1 ? ~((1u << (32 - vmax)) - 1u) : ((1u << vmax) - 1u));
+}
+
+// Vehicles a tile moves: its core, and the last vmax cells of a left halo.
+__device__ __forceinline__ uint32_t move_mask(uint8_t kind, uint32_t vmax) {
+    return kind == 0 ? 0xFFFFFFFFu : (kind == 1 ? ~((1u << (32 - vmax)) - 1u) : 0u);
+}
+
+// Appends the set bits of m (word w) to the block's vehicle list; one thread
+// per word, one shared-memory reservation per warp.
+__device__ __forceinline__ void list_append(LinkSmem &S, int w, uint32_t m) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t cnt = (uint32_t)__popc(m);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    uint32_t base = 0u;
+    if (lane == 31 && inc) base = atomicAdd(&S.nlist, inc);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t r = base + inc - cnt;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        S.code[r++] = (uint16_t)((w << 5) | b);
+    }
 }
 
 __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__restrict__ table,
@@ -184,11 +208,12 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
     __shared__ LinkSmem S;
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
-    // lane_changes, vehicle_updates, active, sum_v, state_hash, arrived_step
-    static constexpr int kField[6] = {2, 6, 0, 5, 7, 8};
-    unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
+    static_assert(kTileSmemWords <= kLinkThreads, "one word per thread");
+    // statistics of the block: updates, lane changes, arrivals, and the changes
+    // of active, buffered, sum of velocities and digest
+    static constexpr int kField[7] = {kUpdates, kLaneChanges, kArrived, kDActive, kDBuffered, kDSumV, kDHash};
+    unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
-
     pdl_trigger();
     span_mark((int)pos * 3, true);
     bool waited = false;
@@ -199,9 +224,15 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         const ScenDev &D = table[td.a.x];
         if (D.ctrl == nullptr) continue;
         stamp(1, first);
+        const uint32_t vmax = D.vmax;
 
         // ---------------- tile geometry (static data: read before waiting)
         const bool partial = (td.a.z & kPartial) != 0u;
+        auto near_mask = [&](uint32_t ring, uint32_t cells, uint32_t x0) -> uint32_t {
+            if (ring) return 0u;
+            const int thr = (int)cells - 1 - (int)vmax - (int)x0;  // first cell within vmax of the end
+            return thr <= 0 ? 0xFFFFFFFFu : (thr >= 32 ? 0u : ~((1u << thr) - 1u));
+        };
         if (!partial) {
             const int nl = (int)td.a.z;
             const uint32_t wb = td.b.x;
@@ -221,6 +252,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                     const uint32_t lw = li.x - wb + (uint32_t)j * lanes;
                     S.cw[c] = (uint16_t)lw;
                     S.cx0[c] = 32u * (uint32_t)j;
+                    S.cnear[c] = near_mask(ring, li.y, 32u * (uint32_t)j);
                     S.clink[c] = (uint8_t)q;
                     S.ckind[c] = 0;
                     S.right[c] = (int16_t)(j + 1 < ncol ? c + 1 : (ring ? c0 : -1));
@@ -235,7 +267,9 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             for (int w = threadIdx.x; w < nw; w += blockDim.x) {
                 S.gw[w] = wb + w;
                 S.mv[w] = 0u;
-                S.out[w] = 0u;
+                S.oocc[w] = 0u;
+                S.omov[w] = 0u;
+                S.oloc[w] = 0u;
             }
             if (threadIdx.x == 0) {
                 S.nwords = nw;
@@ -275,15 +309,17 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 const uint32_t lw = (uint32_t)c * lanes;
                 S.cw[c] = (uint16_t)lw;
                 S.cx0[c] = 32u * (uint32_t)j;
+                S.cnear[c] = near_mask(ring, cells, 32u * (uint32_t)j);
                 S.clink[c] = 0;
                 S.ckind[c] = kind;
                 S.right[c] = rr;
                 S.left[c] = ll;
                 for (uint32_t k = 0; k < lanes; ++k) {
-                    const uint32_t g = wbase + (uint32_t)j * lanes + k;
-                    S.gw[lw + k] = g;
+                    S.gw[lw + k] = wbase + (uint32_t)j * lanes + k;
                     S.mv[lw + k] = 0u;
-                    S.out[lw + k] = 0u;
+                    S.oocc[lw + k] = 0u;
+                    S.omov[lw + k] = 0u;
+                    S.oloc[lw + k] = 0u;
                     S.wcol[lw + k] = (uint8_t)c;
                     S.wlane[lw + k] = (uint8_t)k;
                 }
@@ -318,116 +354,167 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         stamp(3, first);
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
+            if (cur_rec) block_flush<7, kLinkThreads>(acc, cur_rec, kField, S.red);
             cur_rec = rec;
         }
         const uint32_t t = (uint32_t)step;
         const int cur = (int)(step & 1ull), nxt = cur ^ 1;
-        const uint32_t vmax = D.vmax;
         const int d = (t & 1u) ? -1 : 1;
         const int nwords = S.nwords, ncore_words = S.ncore_words;
+        const int w = threadIdx.x;  // one word per thread in the word phases
 
-        // ---------------- occupancy of step t, buffer states, and the vehicle list
-        {
-            // one word per thread (a tile has fewer words than the block has
-            // threads); each warp reserves its part of the list at once
-            static_assert(kTileSmemWords <= kLinkThreads, "one word per thread");
-            const uint32_t *__restrict__ occ_in = D.occ[cur];
-            const int w = threadIdx.x, lane = threadIdx.x & 31;
-            uint32_t m = 0u;
-            if (w < nwords) {
-                const uint32_t o = occ_in[S.gw[w]];
-                S.occ0[w] = o;
-                m = o & list_mask(S.ckind[S.wcol[w]], vmax);
-            }
-            const uint32_t cnt = (uint32_t)__popc(m);
-            uint32_t inc = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            uint32_t wbase = 0u;
-            if (lane == 31 && inc) wbase = atomicAdd(&S.nlist, inc);
-            wbase = __shfl_sync(0xffffffffu, wbase, 31);
-            uint32_t r = wbase + inc - cnt;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                S.code[r++] = (uint16_t)((w << 5) | b);
-            }
-            for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x) {
-                const bool end_here = partial ? S.lexit[0] != 0 : !S.lring[q];
-                S.lexit[q] = end_here ? (uint8_t)D.link_exit[S.lid[q]] : (uint8_t)0;
-            }
+        // ---------------- state of step t
+        if (w < nwords) {
+            const uint32_t g = S.gw[w];
+            const uint32_t o = D.occ[cur][g];
+            S.occ0[w] = o;
+            S.mov0[w] = o ? D.mov[cur][g] : 0u;
+            S.loc0[w] = o ? D.loc[cur][g] : 0u;
+            if (S.ckind[S.wcol[w]] == 0) acc[0] += (unsigned long long)__popc(o);  // vehicle updates
+        }
+        for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x) {
+            const bool end_here = partial ? S.lexit[0] != 0 : !S.lring[q];
+            S.lexit[q] = end_here ? (uint8_t)D.link_exit[S.lid[q]] : (uint8_t)0;
         }
         __syncthreads();
         stamp(4, first);
-        const uint32_t total = S.nlist;
-        {
-            const int8_t *__restrict__ vel_in = D.vel[cur];
-            const uint32_t *__restrict__ vid_in = D.vid[cur];
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t code = S.code[e];
-                const size_t p = (size_t)S.gw[code >> 5] * 32u + (code & 31u);
-                S.ev[e] = (uint8_t)vel_in[p];
-                S.eid[e] = vid_in[p];
-                S.eflag[e] = 0;
-            }
-        }
-        __syncthreads();
-        stamp(5, first);
+        const int8_t *__restrict__ vel0 = D.vel[0];
+        const int8_t *__restrict__ vel1 = D.vel[1];
+        const uint32_t *__restrict__ vid0 = D.vid[0];
+        const uint32_t *__restrict__ vid1 = D.vid[1];
 
-        // ---------------- sub-step 1: lane changes, decided on the state of step t
+        // ---------------- sub-step 1: lane changes, decided on the state of step t.
+        // A vehicle with v = 0 and an occupied cell ahead always has a reason to
+        // change (its gap 0 is below min(v+1, vmax) = 1); it changes iff the
+        // target cell and the vmax cells behind it are empty and the target
+        // lane's next cell is free.  That is decided here for whole words.  A
+        // vehicle with v = 0 and a free cell ahead has no reason to change.
+        // Moving vehicles and vehicles near a link end are decided one by one.
         const bool lc_on = D.lane_change != 0u;
         if (lc_on) {
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t code = S.code[e];
-                const int w = code >> 5, i = code & 31;
+            uint32_t listed = 0u;
+            if (w < nwords) {
                 const int c = S.wcol[w], k = S.wlane[w], kt = k + d;
                 const int q = S.clink[c];
-                if (kt < 0 || kt >= (int)S.llanes[q]) continue;
+                if (kt >= 0 && kt < (int)S.llanes[q]) {
+                    const uint32_t o = S.occ0[w] & lc_mask(S.ckind[c], vmax);
+                    if (o) {
+                        const uint32_t near = S.cnear[c];
+                        const uint32_t tw = S.occ0[S.cw[c] + kt];
+                        const int lf = S.left[c];
+                        const unsigned long long tt =
+                            ((unsigned long long)tw << 32) | (lf >= 0 ? S.occ0[S.cw[lf] + kt] : 0u);
+                        uint32_t behind = 0u;
+                        for (uint32_t j = 1; j <= vmax; ++j) behind |= (uint32_t)(tt >> (32 - j));
+                        const uint32_t ok = ahead_mask(S.occ0, S, c, k) & ~tw & ~behind & ~ahead_mask(S.occ0, S, c, kt);
+                        const uint32_t lcv0 = o & ~S.mov0[w] & ~near & ok;
+                        if (lcv0) {
+                            atomicOr(&S.mv[S.cw[c] + kt], lcv0);
+                            if (S.ckind[c] == 0) acc[1] += (unsigned long long)__popc(lcv0);
+                        }
+                        listed = o & (S.mov0[w] | near);
+                    }
+                }
+            }
+            list_append(S, w, listed);
+            __syncthreads();
+            const uint32_t total = S.nlist;
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const uint32_t code = S.code[e];
+                const int ww = code >> 5, i = code & 31;
+                const size_t p = (size_t)S.gw[ww] * 32u + (uint32_t)i;
+                const bool b1 = (S.loc0[ww] >> i) & 1u;
+                S.ev[e] = (uint8_t)(b1 ? vel1[p] : vel0[p]);
+                S.eid[e] = b1 ? vid1[p] : vid0[p];
+            }
+            __syncthreads();
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const uint32_t code = S.code[e];
+                const int ww = code >> 5, i = code & 31;
+                const int c = S.wcol[ww], k = S.wlane[ww], kt = k + d;
+                const int q = S.clink[c];
                 const uint32_t ring = S.lring[q];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
                 const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
                 const uint32_t v = S.ev[e];
                 const uint32_t last = S.eid[e] >> 31;
                 const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
-                const uint32_t g_own =
-                    gap_ahead(S.occ0, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
+                const uint32_t g_own = gap_ahead(S.occ0, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
                 if (g_own >= want) continue;
+                if ((S.occ0[S.cw[c] + kt] >> i) & 1u) continue;  // target cell taken
                 const uint32_t g_tgt =
                     gap_ahead(S.occ0, S, c, kt, i, dist, ((S.lexit[q] >> kt) & 1u) | last, vmax);
                 if (g_tgt > g_own && room_behind(S.occ0, S, c, kt, i, vmax)) {
                     atomicOr(&S.mv[S.cw[c] + kt], 1u << i);
-                    S.eflag[e] = 1;
-                    if (S.ckind[c] == 0) acc[0] += 1;
+                    if (S.ckind[c] == 0) acc[1] += 1;
                 }
             }
             __syncthreads();
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-                const int c = S.wcol[w], k = S.wlane[w], kf = k + d;
-                const uint32_t leaving = (kf >= 0 && kf < (int)S.llanes[S.clink[c]]) ? S.mv[S.cw[c] + kf] : 0u;
-                S.occ1[w] = (S.occ0[w] & ~leaving) | S.mv[w];
+            if (w < nwords) {
+                const int c = S.wcol[w], k = S.wlane[w];
+                const int lanes = S.llanes[S.clink[c]];
+                const int kf = k + d, kb = k - d;
+                const uint32_t leaving = (kf >= 0 && kf < lanes) ? S.mv[S.cw[c] + kf] : 0u;
+                const uint32_t arriving = S.mv[w];
+                const uint32_t src_mov = (arriving && kb >= 0 && kb < lanes) ? S.mov0[S.cw[c] + kb] : 0u;
+                S.occ1[w] = (S.occ0[w] & ~leaving) | arriving;
+                S.mov1[w] = (S.mov0[w] & ~leaving) | (src_mov & arriving);
             }
-        } else {
-            for (int w = threadIdx.x; w < nwords; w += blockDim.x) S.occ1[w] = S.occ0[w];
+            if (threadIdx.x == 0) S.nlist = 0u;
+        } else if (w < nwords) {
+            S.occ1[w] = S.occ0[w];
+            S.mov1[w] = S.mov0[w];
         }
         __syncthreads();
-        stamp(6, first);
+        stamp(5, first);
 
-        // ---------------- sub-step 2: velocity update and move
+        // ---------------- sub-step 2: velocity update and move.  A vehicle with
+        // v = 0, an occupied cell ahead, no lane change and far from the link
+        // end keeps v = 0 and its cell: its bits are copied, its payload stays.
         {
-            int8_t *__restrict__ vel_out = D.vel[nxt];
-            uint32_t *__restrict__ vid_out = D.vid[nxt];
+            uint32_t listed = 0u;
+            if (w < nwords) {
+                const int c = S.wcol[w], k = S.wlane[w];
+                const uint8_t kind = S.ckind[c];
+                const uint32_t o1 = S.occ1[w];
+                const uint32_t free_ahead = ~ahead_mask(S.occ1, S, c, k);
+                const uint32_t busy = S.mov1[w] | free_ahead | S.cnear[c] | S.mv[w];
+                listed = o1 & busy & move_mask(kind, vmax);
+                if (kind == 0) {
+                    const uint32_t inert = o1 & ~busy;
+                    if (inert) {
+                        atomicOr(&S.oocc[w], inert);
+                        atomicOr(&S.oloc[w], inert & S.loc0[w]);
+                    }
+                }
+            }
+            list_append(S, w, listed);
+            __syncthreads();
+            const uint32_t total = S.nlist;
+            // payload of the listed vehicles, from where they were at step t
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                const uint32_t code = S.code[e];
+                const int ww = code >> 5, i = code & 31;
+                const int c = S.wcol[ww];
+                const int ks = ((S.mv[ww] >> i) & 1u) ? (int)S.wlane[ww] - d : (int)S.wlane[ww];
+                const int sw = S.cw[c] + ks;
+                const size_t p = (size_t)S.gw[sw] * 32u + (uint32_t)i;
+                const bool b1 = (S.loc0[sw] >> i) & 1u;
+                S.ev[e] = (uint8_t)(b1 ? vel1[p] : vel0[p]);
+                S.eid[e] = b1 ? vid1[p] : vid0[p];
+            }
+            __syncthreads();
+            int8_t *__restrict__ velw0 = D.vel[0];
+            int8_t *__restrict__ velw1 = D.vel[1];
+            uint32_t *__restrict__ vidw0 = D.vid[0];
+            uint32_t *__restrict__ vidw1 = D.vid[1];
             const uint32_t key0 = D.seed_lo, key1 = D.seed_hi, pthr = D.p_threshold;
             for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
                 const uint32_t code = S.code[e];
-                const int w = code >> 5, i = code & 31;
-                const int c = S.wcol[w];
-                const uint8_t kind = S.ckind[c];
-                if (kind == 2 || (kind == 1 && i < 32 - (int)vmax)) continue;
-                const int k = S.wlane[w] + (S.eflag[e] ? d : 0);
+                const int ww = code >> 5, i = code & 31;
+                const int c = S.wcol[ww];
+                const int k = S.wlane[ww];
+                const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
                 const int q = S.clink[c];
                 const uint32_t idw = S.eid[e];
                 const uint32_t id = idw & kIdMask, last = idw >> 31;
@@ -439,15 +526,20 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
                 if (v > g) v = g;                                                 // (ii) gap
                 if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;  // (iii) random
-                const bool core = kind == 0;
-                if (core) acc[1] += 1;
+                const bool core = S.ckind[c] == 0;
+                const uint32_t lid = S.lid[q];
+                // the tile whose core held the vehicle at step t accounts for it
+                const unsigned long long old_term = core ? vehicle_term(id, lid, (uint32_t)ks, x, v0) : 0ull;
                 if (!ring && x + v >= S.lcells[q]) {
                     // reaches the link end; a split leaves more than 2*vmax cells
                     // after it, so such a vehicle is always in this tile's core
                     if (!core) {
                         atomicOr(&D.ctrl->error, kErrGeometry);
                     } else if (last) {
-                        acc[5] += 1;  // leaves to parking
+                        acc[2] += 1;  // leaves to parking
+                        acc[3] -= 1;
+                        acc[5] -= v0;
+                        acc[6] -= old_term;
                     } else {
                         const uint2 ve = D.veh[id];
                         if (ve.x + 1u >= ve.y) {
@@ -455,10 +547,14 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                         } else {
                             const uint32_t m = D.route_links[ve.x + 1u];
                             const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
-                            uint4 *slot = D.slots + S.lbpos[q] + (uint32_t)k;
                             if (!((S.lexit[q] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
-                            *slot = make_uint4(id | fl, m, S.lid[q], v | ((uint32_t)k << 8) | (S.lcells[q] << 10));
+                            D.slots[S.lbpos[q] + (uint32_t)k] =
+                                make_uint4(id | fl, m, lid, v | ((uint32_t)k << 8) | (S.lcells[q] << 10));
                             atomicOr(&S.lentered[q], 1u << k);
+                            acc[3] -= 1;
+                            acc[4] += 1;
+                            acc[5] -= v0;
+                            acc[6] += vehicle_term(id, lid, (uint32_t)k, S.lcells[q], v) - old_term;
                         }
                     }
                 } else {
@@ -470,35 +566,50 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                     }
                     if (dc < 0) {
                         atomicOr(&D.ctrl->error, kErrGeometry);
-                    } else if (S.ckind[dc] == 0) {
-                        const int dw = S.cw[dc] + k;
-                        const size_t pd = (size_t)S.gw[dw] * 32u + (uint32_t)ni;
-                        vel_out[pd] = (int8_t)v;
-                        vid_out[pd] = idw;
-                        const uint32_t old = atomicOr(&S.out[dw], 1u << ni);
-                        if (old & (1u << ni)) atomicOr(&D.ctrl->error, kErrCellTaken);
-                        acc[2] += 1;
-                        acc[3] += v;
-                        acc[4] += vehicle_term(id, S.lid[q], (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v);
+                    } else {
+                        if (core) {
+                            acc[5] += (unsigned long long)v - v0;
+                            acc[6] += vehicle_term(id, lid, (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v) - old_term;
+                        }
+                        if (S.ckind[dc] == 0) {
+                            const int dw = S.cw[dc] + k;
+                            const uint32_t bit = 1u << ni;
+                            // write the payload buffer that no reader of this step uses
+                            const bool b1 = (S.occ0[dw] & bit) ? !(S.loc0[dw] & bit) : false;
+                            const size_t pd = (size_t)S.gw[dw] * 32u + (uint32_t)ni;
+                            if (b1) {
+                                velw1[pd] = (int8_t)v;
+                                vidw1[pd] = idw;
+                                atomicOr(&S.oloc[dw], bit);
+                            } else {
+                                velw0[pd] = (int8_t)v;
+                                vidw0[pd] = idw;
+                            }
+                            const uint32_t old = atomicOr(&S.oocc[dw], bit);
+                            if (old & bit) atomicOr(&D.ctrl->error, kErrCellTaken);
+                            if (v) atomicOr(&S.omov[dw], bit);
+                        }
                     }
                 }
             }
         }
         __syncthreads();
-        stamp(7, first);
+        stamp(6, first);
 
-        // ---------------- write the occupancy of step t+1 and the buffer states
-        {
-            uint32_t *__restrict__ occ_out = D.occ[nxt];
-            for (int w = threadIdx.x; w < ncore_words; w += blockDim.x) occ_out[S.gw[w]] = S.out[w];
-            for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x)
-                if (S.lentered[q]) D.link_exit[S.lid[q]] = (uint32_t)S.lexit[q] & ~S.lentered[q];
+        // ---------------- write the state of step t+1 and the buffer states
+        if (w < ncore_words) {
+            const uint32_t g = S.gw[w];
+            D.occ[nxt][g] = S.oocc[w];
+            D.mov[nxt][g] = S.omov[w];
+            D.loc[nxt][g] = S.oloc[w];
         }
+        for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x)
+            if (S.lentered[q]) D.link_exit[S.lid[q]] = (uint32_t)S.lexit[q] & ~S.lentered[q];
         __syncthreads();
-        stamp(8, first);
+        stamp(7, first);
         first = false;
     }
-    if (cur_rec) block_flush<6, kLinkThreads>(acc, cur_rec, kField, S.red);
+    if (cur_rec) block_flush<7, kLinkThreads>(acc, cur_rec, kField, S.red);
     stamp(9, true);
     span_mark((int)pos * 3, false);
 }
@@ -512,8 +623,8 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
     __shared__ unsigned long long red[kNodeThreads / 32][6];
     const uint32_t n_tiles = *n_tiles_p;
-    // transfers, inserted, buffered, active, sum_v, state_hash
-    static constexpr int kField[6] = {3, 4, 1, 0, 5, 7};
+    // transfers, insertions and the changes of active, buffered, sum of velocities, digest
+    static constexpr int kField[6] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash};
     unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
     pdl_trigger();
@@ -541,8 +652,9 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
         const int nxt = (int)((step + 1ull) & 1ull);
         if (m < td.z) {
             uint32_t *occ = D.occ[nxt];
-            int8_t *vel = D.vel[nxt];
-            uint32_t *vid = D.vid[nxt];
+            uint32_t *mov = D.mov[nxt];
+            int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
+            uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
             uint32_t h = D.dep_head[m];
             const uint32_t slot_lo = nd.x, wbase = nd.y, cnt = nd.z & 0xFFu, lanes = (nd.z >> 8) & 0xFFu;
             const uint32_t dep_end = nd.w;
@@ -581,23 +693,21 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
                     const uint32_t rest = free_mask & ~(1u << pref);
                     if (rest) qn = (uint32_t)(__ffs(rest) - 1);
                 }
-                if (qn != 0xFFu) {
-                    free_mask &= ~(1u << qn);
-                    const uint32_t w = wbase + qn;  // column 0 of lane qn
-                    occ[w] = o[qn & 3] | 1u;
-                    vel[(size_t)w * 32u] = (int8_t)v;
-                    vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
-                    atomicAdd(&D.veh[id].x, 1u);
-                    D.slots[slot_lo + s].x = kSlotEmpty;
-                    atomicOr(&D.link_exit[l], 1u << ks);
-                    acc[0] += 1;
-                    acc[3] += 1;
-                    acc[4] += v;
-                    acc[5] += vehicle_term(id, m, qn, 0u, v);
-                } else {
-                    acc[2] += 1;
-                    acc[5] += vehicle_term(id, l, ks, cells_l, v);
-                }
+                if (qn == 0xFFu) continue;  // stays buffered: nothing changes
+                free_mask &= ~(1u << qn);
+                const uint32_t w = wbase + qn;  // column 0 of lane qn
+                occ[w] = o[qn & 3] | 1u;
+                if (v) mov[w] |= 1u;
+                vel[(size_t)w * 32u] = (int8_t)v;
+                vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
+                atomicAdd(&D.veh[id].x, 1u);
+                D.slots[slot_lo + s].x = kSlotEmpty;
+                atomicOr(&D.link_exit[l], 1u << ks);
+                acc[0] += 1;
+                acc[2] += 1;
+                acc[3] -= 1;
+                acc[4] += v;
+                acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, l, ks, cells_l, v);
             }
             // departures from parking onto m
             const uint32_t h0 = h;
@@ -610,7 +720,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
                 const uint32_t idw = D.dep_ids[h];
                 vid[(size_t)w * 32u] = idw;
                 acc[1] += 1;
-                acc[3] += 1;
+                acc[2] += 1;
                 acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
                 ++h;
             }
@@ -631,25 +741,23 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
     const ScenDev &D = table[blockIdx.x];
     Ctrl *c = D.ctrl;
     if (c == nullptr) return;
-    __shared__ unsigned long long red[4][6];
+    constexpr int NF = 9;
+    __shared__ unsigned long long red[4][NF];
     __shared__ unsigned long long s_base;
     const unsigned long long base = c->base, target = c->target;
     const uint32_t g = base < target ? (uint32_t)min((unsigned long long)g_max, target - base) : 0u;
     const uint32_t nsub = D.n_sub;
-    // vehicle_updates, lane_changes, transfers, arrived_step, inserted, last-step hash
-    unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
+    // sums of every field of the StatRec over the g steps just run
+    unsigned long long a[NF] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (uint32_t r = threadIdx.x; r < g * nsub; r += blockDim.x) {
         const unsigned long long t = base + r / nsub;
-        const StatRec &R = D.stats[(size_t)(t & (kStatsRing - 1)) * nsub + r % nsub];
-        a[0] += R.vehicle_updates;
-        a[1] += R.lane_changes;
-        a[2] += R.transfers;
-        a[3] += R.arrived_step;
-        a[4] += R.inserted;
-        if (t == base + g - 1) a[5] += R.state_hash;
+        const unsigned long long *R =
+            reinterpret_cast<const unsigned long long *>(&D.stats[(size_t)(t & (kStatsRing - 1)) * nsub + r % nsub]);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a[f] += R[f];
     }
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
+    for (int f = 0; f < NF; ++f) {
         unsigned long long v = a[f];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -657,16 +765,19 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long s[6] = {0, 0, 0, 0, 0, 0};
+        unsigned long long sm[NF] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int w = 0; w < 4; ++w)
-            for (int f = 0; f < 6; ++f) s[f] += red[w][f];
+            for (int f = 0; f < NF; ++f) sm[f] += red[w][f];
         if (g) {
-            c->tot_updates += s[0];
-            c->tot_lane_changes += s[1];
-            c->tot_transfers += s[2];
-            c->arrived += s[3];
-            c->inserted += s[4];
-            c->last_hash = s[5];
+            c->tot_updates += sm[kUpdates];
+            c->tot_lane_changes += sm[kLaneChanges];
+            c->tot_transfers += sm[kTransfers];
+            c->arrived += sm[kArrived];
+            c->inserted += sm[kInserted];
+            c->active += sm[kDActive];
+            c->buffered += sm[kDBuffered];
+            c->sum_v += sm[kDSumV];
+            c->hash += sm[kDHash];
             c->steps_run += g;
             c->base = base + g;
         }

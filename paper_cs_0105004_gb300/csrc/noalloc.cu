@@ -9,9 +9,9 @@
 // 3-lane circles of Sec. 5) whose state the caller keeps in its own device
 // buffers.  It runs the same link kernel as ts_step; what that kernel needs
 // besides the caller's buffers (the scenario table, the tile list, the
-// control block and the per-step partial statistics) lives in one file-scope
-// __device__ array, fixed in size, that every device which loads this
-// library holds until the process exits.
+// control block, the per-step partial statistics and the moving/location
+// bitplanes) lives in one file-scope __device__ array, fixed in size, that
+// every device which loads this library holds until the process exits.
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -26,6 +26,7 @@ namespace {
 constexpr uint32_t kNoAllocMaxCells = 1u << 17;  // cells per lane
 constexpr uint32_t kNoAllocMaxSteps = 1024;      // steps per call
 constexpr uint32_t kNoAllocMaxTiles = 132;  // 4096 columns in runs of at least 32
+constexpr uint32_t kNoAllocMaxWords = kNoAllocMaxCells / 32u * (uint32_t)kMaxLanes;
 
 // Byte offsets inside the scratch array.
 constexpr size_t kOffTable = 0;
@@ -34,7 +35,8 @@ constexpr size_t kOffLink = 512;
 constexpr size_t kOffCount = 768;
 constexpr size_t kOffTiles = 1024;
 constexpr size_t kOffStats = kOffTiles + ((sizeof(LinkTile) * kNoAllocMaxTiles + 255u) / 256u) * 256u;
-constexpr size_t kScratchBytes = kOffStats + sizeof(StatRec) * kStatsRing;
+constexpr size_t kOffPlanes = kOffStats + sizeof(StatRec) * kStatsRing;  // mov0, mov1, loc0, loc1
+constexpr size_t kScratchBytes = kOffPlanes + 4ull * 4ull * kNoAllocMaxWords;
 
 static_assert(sizeof(ScenDev) <= 256, "table entry fits its slot");
 static_assert(sizeof(Ctrl) <= 256, "control block fits its slot");
@@ -49,23 +51,87 @@ ts_status bad(ts_status s, const char *msg) {
     return s;
 }
 
-// Sums the partial records of each step into the caller's statistics array.
-__global__ void gather_ring_stats(const StatRec *recs, unsigned long long first, uint32_t n, ts_stats *out) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// Derives the moving and location bitplanes of the caller's state of step
+// `first` (payload in set cur = first & 1) and adds its vehicle count, speed
+// sum and digest into the control block.
+__global__ void prep_ring(ScenDev D, uint32_t lanes, uint32_t words, uint32_t cur) {
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long act = 0, sv = 0, hs = 0;
+    if (w < words) {
+        const uint32_t o = D.occ[cur][w];
+        uint32_t mv = 0;
+        const uint32_t k = w % lanes, x0 = (w / lanes) * 32u;
+        for (uint32_t m = o; m; m &= m - 1) {
+            const uint32_t i = (uint32_t)__ffs(m) - 1u;
+            const uint32_t v = (uint32_t)D.vel[cur][w * 32u + i];
+            if (v) mv |= 1u << i;
+            sv += v;
+            hs += vehicle_term(D.vid[cur][w * 32u + i] & kIdMask, 0u, k, x0 + i, v);
+        }
+        act = (unsigned long long)__popc(o);
+        D.mov[cur][w] = mv;
+        D.loc[cur][w] = cur ? o : 0u;  // location bit set = payload in set 1
+        D.mov[cur ^ 1u][w] = 0u;
+        D.loc[cur ^ 1u][w] = 0u;
+    }
+    for (int d = 16; d; d >>= 1) {
+        act += __shfl_xor_sync(0xffffffffu, act, d);
+        sv += __shfl_xor_sync(0xffffffffu, sv, d);
+        hs += __shfl_xor_sync(0xffffffffu, hs, d);
+    }
+    if ((threadIdx.x & 31u) == 0u && act) {
+        atomicAdd(&D.ctrl->active, act);
+        atomicAdd(&D.ctrl->sum_v, sv);
+        atomicAdd(&D.ctrl->hash, hs);
+    }
+}
+
+// Moves every vehicle's payload of the final state into set f, where the
+// caller reads it.
+__global__ void finish_ring(ScenDev D, uint32_t words, uint32_t f) {
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= words) return;
+    const uint32_t o = D.occ[f][w], l = D.loc[f][w];
+    const uint32_t away = o & (f ? ~l : l);
+    for (uint32_t m = away; m; m &= m - 1) {
+        const uint32_t i = (uint32_t)__ffs(m) - 1u;
+        D.vel[f][w * 32u + i] = D.vel[f ^ 1u][w * 32u + i];
+        D.vid[f][w * 32u + i] = D.vid[f ^ 1u][w * 32u + i];
+    }
+}
+
+// Per-step statistics from the step records: counts as recorded, running
+// values as the values at `first` plus the changes of steps first..t
+// (inclusive scan, one block of kNoAllocMaxSteps threads).
+__global__ void gather_ring_stats(const StatRec *recs, const Ctrl *ctrl, unsigned long long first, uint32_t n,
+                                  ts_stats *out) {
+    __shared__ unsigned long long sc[3][kNoAllocMaxSteps];
+    const uint32_t i = threadIdx.x;
+    const StatRec *r = recs + ((first + i) & (kStatsRing - 1));
+    sc[0][i] = i < n ? r->d_active : 0ull;
+    sc[1][i] = i < n ? r->d_sum_v : 0ull;
+    sc[2][i] = i < n ? r->d_hash : 0ull;
+    __syncthreads();
+    for (uint32_t d = 1; d < kNoAllocMaxSteps; d <<= 1) {
+        unsigned long long a[3];
+        for (int f = 0; f < 3; ++f) a[f] = i >= d ? sc[f][i - d] : 0ull;
+        __syncthreads();
+        for (int f = 0; f < 3; ++f) sc[f][i] += a[f];
+        __syncthreads();
+    }
     if (i >= n) return;
-    const StatRec &r = recs[(first + i) & (kStatsRing - 1)];
     ts_stats o;
     o.step = first + i;
-    o.active = r.active;
+    o.active = ctrl->active + sc[0][i];
     o.buffered = 0;
     o.waiting = 0;
     o.arrived = 0;
-    o.lane_changes = r.lane_changes;
+    o.lane_changes = r->lane_changes;
     o.transfers = 0;
     o.inserted = 0;
-    o.sum_v = r.sum_v;
-    o.vehicle_updates = r.vehicle_updates;
-    o.state_hash = r.state_hash;
+    o.sum_v = ctrl->sum_v + sc[1][i];
+    o.vehicle_updates = r->vehicle_updates;
+    o.state_hash = ctrl->hash + sc[2][i];
     out[i] = o;
 }
 
@@ -113,6 +179,7 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     LinkTile *d_tiles = reinterpret_cast<LinkTile *>(base + kOffTiles);
     uint32_t *d_count = reinterpret_cast<uint32_t *>(base + kOffCount);
     StatRec *d_stats = reinterpret_cast<StatRec *>(base + kOffStats);
+    uint32_t *d_planes = reinterpret_cast<uint32_t *>(base + kOffPlanes);
 
     // tiles: the whole ring if it fits one tile, else runs of columns whose
     // halos wrap around the ring
@@ -137,6 +204,10 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     sd.lk_info = d_link;
     sd.occ[0] = dev_occ0;
     sd.occ[1] = dev_occ1;
+    sd.mov[0] = d_planes;
+    sd.mov[1] = d_planes + kNoAllocMaxWords;
+    sd.loc[0] = d_planes + 2u * kNoAllocMaxWords;
+    sd.loc[1] = d_planes + 3u * kNoAllocMaxWords;
     sd.vel[0] = dev_vel0;
     sd.vel[1] = dev_vel1;
     sd.vid[0] = dev_vid0;
@@ -156,7 +227,8 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     const uint4 link = make_uint4(0u, cells, lanes | (1u << 8), 0u);
     const uint32_t n_tiles = (uint32_t)tiles.size();
     // the scratch keeps the previous call's contents: rewrite all of it that
-    // this call reads, and clear the statistics it accumulates into
+    // this call reads, and clear the statistics and running values it
+    // accumulates into
     if (cudaMemcpyAsync(d_table, &sd, sizeof(sd), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_ctrl, &ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_link, &link, sizeof(link), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -165,10 +237,13 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
             cudaSuccess ||
         cudaMemsetAsync(d_stats, 0, sizeof(StatRec) * kStatsRing, s) != cudaSuccess)
         return bad(TS_ERR_CUDA, "scratch set-up copy failed");
+    const uint32_t cur = (uint32_t)(first_step & 1ull), fin = (uint32_t)((first_step + n_steps) & 1ull);
+    prep_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, lanes, words, cur);
     const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks()));
     for (uint32_t i = 0; i < n_steps; ++i)
         launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false);
-    gather_ring_stats<<<(n_steps + 127) / 128, 128, 0, s>>>(d_stats, first_step, n_steps, dev_stats_out);
+    finish_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, words, fin);
+    gather_ring_stats<<<1, kNoAllocMaxSteps, 0, s>>>(d_stats, d_ctrl, first_step, n_steps, dev_stats_out);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");
     return TS_OK;
 }

@@ -303,7 +303,10 @@ def run_config3(args):
     steps = args.job_steps or 3600
     scs = [N.config3_scenario(i) for i in range(args.scenarios)]
     stream = torch.cuda.Stream()
-    best, timings = Bt.autotune_tile_words(scs[:args.tune_sample], stream, window=256)
+    if args.tune_sample > 0:
+        best, timings = Bt.autotune_tile_words(scs[:args.tune_sample], stream, window=256)
+    else:
+        best, timings = (args.tile_words or 128), {}
     sims = Bt.make_members(scs, tile_words=best)
     batch = T.Batch(len(sims))
     batch.add_many(sims, steps)
@@ -316,9 +319,11 @@ def run_config3(args):
     if len({r.vehicle_updates for r in runs}) != 1:
         raise RuntimeError("batched runs differ")
     batch.close()
-    seq = Bt.run_sequential(sims[:args.seq_sample], steps, stream)
-    if seq.per_member_updates != runs[0].per_member_updates[:args.seq_sample]:
-        raise RuntimeError("sequential and batched results differ")
+    seq = None
+    if args.seq_sample > 0:
+        seq = Bt.run_sequential(sims[:args.seq_sample], steps, stream)
+        if seq.per_member_updates != runs[0].per_member_updates[:args.seq_sample]:
+            raise RuntimeError("sequential and batched results differ")
     sec = sum(r.seconds for r in runs)
     value = sum(r.vehicle_updates for r in runs) / sec
     lane_cells = sum(sc.net.n_lane_cells for sc in scs)
@@ -332,9 +337,9 @@ def run_config3(args):
                        "vehicle_updates_per_run": runs[0].vehicle_updates, "tile_words": best,
                        "autotune_seconds": {str(k): v for k, v in timings.items()},
                        "l2": "inputs larger than L2"},
-            "sequential": {"value": seq.updates_per_s, "unit": METRIC, "scenarios": args.seq_sample,
-                           "seconds": seq.seconds},
-            "batched_over_sequential": value / seq.updates_per_s,
+            "sequential": None if seq is None else {"value": seq.updates_per_s, "unit": METRIC,
+                                                    "scenarios": args.seq_sample, "seconds": seq.seconds},
+            "batched_over_sequential": None if seq is None else value / seq.updates_per_s,
             "gpu_launches": args.steps * (2 * steps + steps // 32 + 1 + args.scenarios),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
@@ -364,6 +369,8 @@ def run_config4(args):
             return N.Scenario(f"{base.name}/job{jid}", base.net, base.demand, steps, seed=100000 + jid,
                               vmax=base.vmax, p_threshold=base.p_threshold)
         jobs.append(Sv.Job(jid, ["config0", "config1", "grid"][kd], float(t), make, steps))
+    import copy
+    seq_jobs = copy.deepcopy(jobs) if args.serve_compare else None
     srv = Sv.Server(budget_bytes=int(args.budget_gb * 2**30), chunk_steps=args.chunk)
     sampler = ClockSampler(0)
     sampler.start()
@@ -371,6 +378,16 @@ def run_config4(args):
     clocks = sampler.stop()
     srv.close()
     summ = rep.summary()
+    one = None
+    if seq_jobs is not None:
+        # the same stream served one job at a time (each job alone on the GPU)
+        srv1 = Sv.Server(budget_bytes=int(args.budget_gb * 2**30), capacity=1, chunk_steps=args.chunk)
+        rep1 = srv1.run(seq_jobs, time_scale=args.time_scale)
+        srv1.close()
+        one = rep1.summary()
+        by = {j.jid: j for j in rep.jobs}
+        if any(by[j.jid].last_state_hash != j.last_state_hash for j in rep1.jobs):
+            raise RuntimeError("a job differs between the batched and the one-at-a-time server")
     line = {"metric": METRIC, "value": summ["vehicle_updates_per_s"], "unit": METRIC, "n_gpus": 1,
             "steps": len(rep.jobs), "warmup": 0, "ms_per_step": 1000.0 * rep.wall_s / max(1, len(rep.jobs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -378,7 +395,7 @@ def run_config4(args):
             "config": {"workload": f"Poisson {args.rate}/s jobs for {args.duration} s, mix config0:config1:grid = "
                                    f"{args.serve_mix}, {steps} steps per job, arrival clock x{args.time_scale}",
                        "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
-            "serving": summ, "clocks": clocks}
+            "serving": summ, "one_job_at_a_time": one, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -399,6 +416,7 @@ def main():
     ap.add_argument("--grid-pool", type=int, default=16, help="config4: distinct grid networks")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="config4: device memory for jobs")
     ap.add_argument("--chunk", type=int, default=128, help="config4: steps per batch step")
+    ap.add_argument("--serve-compare", type=int, default=1, help="config4: also serve the stream one job at a time")
     ap.add_argument("--job-steps", type=int, default=None, help="steps per job (default: the config's)")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -347,6 +347,64 @@ def run_config3(args):
         s_.close()
 
 
+def run_empty(args):
+    """The config 1 network with no vehicles: the cost of sweeping every
+    lane-cell's occupancy each step, which the step pays at any load (Sec. 9
+    notes the same floor for an empty network)."""
+    import numpy as np
+    import torch
+    from paper_cs_0105004_gb300 import transsim as T
+    from paper_cs_0105004_gb300.inputs import networks as N
+    torch.cuda.set_device(0)
+    full = N.config1()
+    steps = args.job_steps or full.steps
+    none = N.Demand(np.zeros(0, np.uint32), np.zeros(1, np.uint32), np.zeros(0, np.uint32))
+    sc = N.Scenario("config1-empty", full.net, none, steps, full.seed)
+    sim = T.Simulation(sc)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def job():
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.reset(stream)
+        sim.step(steps, stream)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1000.0
+
+    for _ in range(args.warmup):
+        job()
+    sampler = ClockSampler(0)
+    sampler.start()
+    secs = [job() for _ in range(args.steps)]
+    clocks = sampler.stop()
+    sim.reset(stream)
+    lm, nm = sim.step_timed(min(steps, 2048), stream)
+    sec = sum(secs)
+    C = sc.net.n_lane_cells
+    peak, src = _peaks()
+    link_us = float(np.mean(lm)) * 1e3
+    line = {"metric": "lane-cell updates/s", "value": C * steps * args.steps / sec, "unit": "lane-cell updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "x_real_time": steps / (sec / args.steps),
+            "config": {"workload": "config 1 network (20,024 links, 8,500 nodes) with no trips",
+                       "steps_per_job": steps, "lane_cells": C,
+                       "l2": "flushed (512 MB write) before every job"},
+            "us_per_sim_step": 1e6 * sec / (args.steps * steps),
+            "roofline": {"bound": "hbm", "kernel": "link_kernel", "achieved": 0.25 * C / (link_us * 1e-6) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": 0.25 * C / (link_us * 1e-6) / 1e9 / peak,
+                         "peak_source": src, "traffic": None, "avg_launch_us": link_us,
+                         "node_kernel_avg_launch_us": float(np.mean(nm)) * 1e3},
+            "gpu_launches": args.steps * (2 * steps + steps // 32 + 1),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
 def run_config4(args):
     """Serving: a Poisson stream of simulation jobs admitted by device-memory
     budget into a continuously running batch."""
@@ -405,7 +463,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty"])
     ap.add_argument("--scenarios", type=int, default=256, help="config3: batch members")
     ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
     ap.add_argument("--seq-sample", type=int, default=256, help="config3: members run one by one for comparison")
@@ -441,6 +499,10 @@ def main():
     if args.workload == "config4":
         if rank == 0:
             run_config4(args)
+        return
+    if args.workload == "empty":
+        if rank == 0:
+            run_empty(args)
         return
     if world > 1:
         import torch

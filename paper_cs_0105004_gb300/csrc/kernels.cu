@@ -56,11 +56,16 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
 constexpr int kPhases = 10;
 constexpr int kPhaseBlocks = 4096;
 __device__ unsigned long long g_phase[kPhases][kPhaseBlocks];
+// and the time spent in each phase summed over all tiles of all blocks
+__device__ unsigned long long g_phase_sum[kPhases];
+static __shared__ unsigned long long s_phase_last;
 __device__ __forceinline__ void stamp(int ph, bool first) {
-    if (first && threadIdx.x == 0 && blockIdx.x < kPhaseBlocks) {
+    if (threadIdx.x == 0) {
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        g_phase[ph][blockIdx.x] = t;
+        if (first && blockIdx.x < kPhaseBlocks) g_phase[ph][blockIdx.x] = t;
+        if (ph > 0) atomicAdd(&g_phase_sum[ph], t - s_phase_last);
+        s_phase_last = t;
     }
 }
 // [launch position * 3 + kernel kind][first block entry, last block exit]
@@ -136,8 +141,6 @@ struct LinkSmem {
     uint32_t lentered[kTileMaxCols];  // lanes whose buffer received a vehicle
     uint32_t nlist;                   // vehicles in the list
     uint16_t code[kListCap];          // (local word << 5) | bit
-    uint8_t ev[kListCap];             // velocity at step t
-    uint32_t eid[kListCap];           // id word (id | last-link flag)
     unsigned long long red[kLinkThreads / 32][7];
     int ncols, nwords, ncore_words, nlinks;
 };
@@ -422,26 +425,21 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
                 const uint32_t code = S.code[e];
                 const int ww = code >> 5, i = code & 31;
-                const size_t p = (size_t)S.gw[ww] * 32u + (uint32_t)i;
-                const bool b1 = (S.loc0[ww] >> i) & 1u;
-                S.ev[e] = (uint8_t)(b1 ? vel1[p] : vel0[p]);
-                S.eid[e] = b1 ? vid1[p] : vid0[p];
-            }
-            __syncthreads();
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t code = S.code[e];
-                const int ww = code >> 5, i = code & 31;
                 const int c = S.wcol[ww], k = S.wlane[ww], kt = k + d;
+                if ((S.occ0[S.cw[c] + kt] >> i) & 1u) continue;  // target cell taken
                 const int q = S.clink[c];
                 const uint32_t ring = S.lring[q];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
                 const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
-                const uint32_t v = S.ev[e];
-                const uint32_t last = S.eid[e] >> 31;
+                // payload at step t; the last-link flag matters only within
+                // vmax cells of the link end
+                const size_t p = (size_t)S.gw[ww] * 32u + (uint32_t)i;
+                const bool b1 = (S.loc0[ww] >> i) & 1u;
+                const uint32_t v = (uint32_t)(b1 ? vel1[p] : vel0[p]);
+                const uint32_t last = ((S.cnear[c] >> i) & 1u) ? (b1 ? vid1[p] : vid0[p]) >> 31 : 0u;
                 const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
                 const uint32_t g_own = gap_ahead(S.occ0, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
                 if (g_own >= want) continue;
-                if ((S.occ0[S.cw[c] + kt] >> i) & 1u) continue;  // target cell taken
                 const uint32_t g_tgt =
                     gap_ahead(S.occ0, S, c, kt, i, dist, ((S.lexit[q] >> kt) & 1u) | last, vmax);
                 if (g_tgt > g_own && room_behind(S.occ0, S, c, kt, i, vmax)) {
@@ -491,19 +489,6 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             list_append(S, w, listed);
             __syncthreads();
             const uint32_t total = S.nlist;
-            // payload of the listed vehicles, from where they were at step t
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t code = S.code[e];
-                const int ww = code >> 5, i = code & 31;
-                const int c = S.wcol[ww];
-                const int ks = ((S.mv[ww] >> i) & 1u) ? (int)S.wlane[ww] - d : (int)S.wlane[ww];
-                const int sw = S.cw[c] + ks;
-                const size_t p = (size_t)S.gw[sw] * 32u + (uint32_t)i;
-                const bool b1 = (S.loc0[sw] >> i) & 1u;
-                S.ev[e] = (uint8_t)(b1 ? vel1[p] : vel0[p]);
-                S.eid[e] = b1 ? vid1[p] : vid0[p];
-            }
-            __syncthreads();
             int8_t *__restrict__ velw0 = D.vel[0];
             int8_t *__restrict__ velw1 = D.vel[1];
             uint32_t *__restrict__ vidw0 = D.vid[0];
@@ -515,13 +500,18 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 const int c = S.wcol[ww];
                 const int k = S.wlane[ww];
                 const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
+                // payload from where the vehicle was at step t; no thread of
+                // this step writes a buffer that a step-t occupant is read from
+                const int sw = S.cw[c] + ks;
+                const size_t ps = (size_t)S.gw[sw] * 32u + (uint32_t)i;
+                const bool sb1 = (S.loc0[sw] >> i) & 1u;
+                const uint32_t idw = sb1 ? vid1[ps] : vid0[ps];
+                const uint32_t v0 = (uint32_t)(sb1 ? vel1[ps] : vel0[ps]);
                 const int q = S.clink[c];
-                const uint32_t idw = S.eid[e];
                 const uint32_t id = idw & kIdMask, last = idw >> 31;
                 const uint32_t ring = S.lring[q];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
                 const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
-                const uint32_t v0 = S.ev[e];
                 uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;  // (i) accelerate
                 const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
                 if (v > g) v = g;                                                 // (ii) gap
@@ -847,6 +837,13 @@ extern "C" int ts_debug_phase_times(unsigned long long *out, int n_blocks) {
                                  sizeof(unsigned long long) * kPhaseBlocks * p) != cudaSuccess)
             return -1;
     return n_blocks;
+}
+extern "C" int ts_debug_phase_sums(unsigned long long *out, int reset) {
+    if (reset) {
+        unsigned long long z[kPhases] = {};
+        return cudaMemcpyToSymbol(g_phase_sum, z, sizeof(z)) == cudaSuccess ? 0 : -1;
+    }
+    return cudaMemcpyFromSymbol(out, g_phase_sum, sizeof(unsigned long long) * kPhases) == cudaSuccess ? 0 : -1;
 }
 extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
     if (reset) {

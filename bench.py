@@ -38,9 +38,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "vehicle-updates/s"
 L2_FLUSH_BYTES = 512 << 20
+STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _launches(steps, every=0, start=0):
+    """Kernel launches of one ts_step call of `steps` steps: the target-setting
+    kernel, then per chunk (at most 32 steps, never across a load-balancing
+    boundary) one link kernel per step, the node kernel and the chunk close."""
+    n, done = 1, 0
+    while done < steps:
+        seg = steps - done
+        if every:
+            seg = min(seg, ((start + done) // every + 1) * every - (start + done))
+        n += seg + 2 * ((seg + 31) // 32)
+        done += seg
+    return n
 
 
 def _workload(name):
@@ -167,6 +182,7 @@ def run_ours(args, rank, world, local_rank):
     sim = T.Simulation(sc, tile_words=args.tile_words)
     if args.load_balance:
         sim.set_load_balance(args.load_balance, args.tile_vehicles)
+    sim.set_step_mode(STEP_MODES[args.step_mode])
     net = sc.net
     C = net.n_lane_cells
 
@@ -227,13 +243,14 @@ def run_ours(args, rank, world, local_rank):
     prof_tot = sim.totals()
     if prof_tot != tot:
         raise RuntimeError("profiled run differs from the timed run")
-    # algorithmic bytes: link kernel reads+writes v (1 B) and id (4 B) of every
-    # vehicle and one occupancy bit per lane-cell; node kernel ~20 B per transfer
-    # and ~10 B per insertion
-    link_bytes = 10.0 * updates + 0.25 * C * steps_per_job
-    node_bytes = 20.0 * tot["transfers"] + 10.0 * tot["inserted"]
+    # algorithmic bytes: the link kernel reads+writes v (1 B) and id (4 B) of
+    # every vehicle and one occupancy bit per lane-cell, and completes the node
+    # transfers (~20 B each) and insertions (~10 B each) of the step before it
+    # (the node kernel does those of every 32nd step only)
+    link_bytes = 10.0 * updates + 0.25 * C * steps_per_job + 20.0 * tot["transfers"] + 10.0 * tot["inserted"]
+    node_launch_ms = np.concatenate([node_ms[31::32], node_ms[-1:] if steps_per_job % 32 else node_ms[:0]])
     link_s = float(link_ms.sum()) / 1000.0
-    node_s = float(node_ms.sum()) / 1000.0
+    node_s = float(node_launch_ms.sum()) / 1000.0
     peak, peak_kind = _peaks()
     achieved = link_bytes / link_s / 1e9
     roofline = {"bound": "hbm", "kernel": "link_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -242,9 +259,8 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": link_bytes / steps_per_job,
                 "share_of_step_time": link_s / (link_s + node_s),
                 "launch_us_p50_p90_max": [round(1e3 * float(np.percentile(link_ms, q)), 2) for q in (50, 90, 100)],
-                "node_kernel": {"achieved": node_bytes / node_s / 1e9, "avg_launch_us": 1e3 * float(node_ms.mean()),
-                                "launch_us_p50_p90_max": [round(1e3 * float(np.percentile(node_ms, q)), 2)
-                                                          for q in (50, 90, 100)]}}
+                "node_kernel": {"launches": int(node_launch_ms.size),
+                                "avg_launch_us": 1e3 * float(node_launch_ms.mean())}}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -282,11 +298,11 @@ def run_ours(args, rank, world, local_rank):
                            "vehicle_updates_per_job": updates, "l2": "flushed (512 MB write) before every job; "
                            "the simulation state stays resident across the steps of a job",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "tile_words": args.tile_words or 128,
+                           "tile_words": args.tile_words or 128, "step_mode": args.step_mode,
                            "load_balance": {"every_steps": args.load_balance, "vehicles_per_tile": args.tile_vehicles},
                            "bit_exact_hash": str(tot["last_state_hash"])},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * (2 * steps_per_job + 1),
+                "gpu_launches": args.steps * _launches(steps_per_job, args.load_balance),
                 "clocks": clocks, "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     sim.close()
@@ -309,6 +325,7 @@ def run_config3(args):
         best, timings = (args.tile_words or 128), {}
     sims = Bt.make_members(scs, tile_words=best)
     batch = T.Batch(len(sims))
+    batch.set_step_mode(STEP_MODES[args.step_mode])
     batch.add_many(sims, steps)
     for _ in range(args.warmup):
         Bt.run_batched(sims, steps, stream, batch)
@@ -335,12 +352,13 @@ def run_config3(args):
                                    f"0.1-0.4 trips per lane-cell), {steps} steps each, one batch",
                        "lane_cells": lane_cells, "trips": int(sum(sc.demand.n for sc in scs)),
                        "vehicle_updates_per_run": runs[0].vehicle_updates, "tile_words": best,
+                       "step_mode": args.step_mode,
                        "autotune_seconds": {str(k): v for k, v in timings.items()},
                        "l2": "inputs larger than L2"},
             "sequential": None if seq is None else {"value": seq.updates_per_s, "unit": METRIC,
                                                     "scenarios": args.seq_sample, "seconds": seq.seconds},
             "batched_over_sequential": None if seq is None else value / seq.updates_per_s,
-            "gpu_launches": args.steps * (2 * steps + steps // 32 + 1 + args.scenarios),
+            "gpu_launches": args.steps * (_launches(steps) - 1 + args.scenarios),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     for s_ in sims:
@@ -361,6 +379,7 @@ def run_empty(args):
     none = N.Demand(np.zeros(0, np.uint32), np.zeros(1, np.uint32), np.zeros(0, np.uint32))
     sc = N.Scenario("config1-empty", full.net, none, steps, full.seed)
     sim = T.Simulation(sc)
+    sim.set_step_mode(STEP_MODES[args.step_mode])
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -398,8 +417,8 @@ def run_empty(args):
             "roofline": {"bound": "hbm", "kernel": "link_kernel", "achieved": 0.25 * C / (link_us * 1e-6) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": 0.25 * C / (link_us * 1e-6) / 1e9 / peak,
                          "peak_source": src, "traffic": None, "avg_launch_us": link_us,
-                         "node_kernel_avg_launch_us": float(np.mean(nm)) * 1e3},
-            "gpu_launches": args.steps * (2 * steps + steps // 32 + 1),
+                         "node_kernel_avg_launch_us": float(np.mean(nm[31::32])) * 1e3},
+            "gpu_launches": args.steps * _launches(steps),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     sim.close()
@@ -481,6 +500,8 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=1800)
     ap.add_argument("--ref-sample-steps", type=int, default=300)
     ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..128)")
+    ap.add_argument("--step-mode", default="auto", choices=list(STEP_MODES),
+                    help="fused: one launch per step; split: link and node kernel per step")
     ap.add_argument("--load-balance", type=int, default=512, help="re-tile from the occupancy every N steps (0 = off)")
     ap.add_argument("--tile-vehicles", type=int, default=768, help="vehicle budget per tile when re-tiling")
     ap.add_argument("--traffic", type=float, default=None,

@@ -263,6 +263,18 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
                                int8_t *dev_vel1, uint32_t *dev_vid0, uint32_t *dev_vid1, ts_stats *dev_stats_out,
                                void *cuda_stream);
 
+/* Step launch mode.  FUSED: one link-kernel launch per step, each also
+ * completing the node transfers of the step before it (every tile resolves
+ * the transfers that concern its own links; a node kernel completes the last
+ * step of each chunk of up to 32 steps).  SPLIT: a link kernel and a node
+ * kernel per step.  AUTO (default) is SPLIT: resolving an occupied buffer's
+ * transfer inside the link kernel lengthens the step more than the saved
+ * launch shortens it, except on nearly empty networks, where FUSED is
+ * faster.  Results do not depend on the mode. */
+enum { TS_STEP_AUTO = 0, TS_STEP_FUSED = 1, TS_STEP_SPLIT = 2 };
+ts_status ts_set_step_mode(ts_ctx *ctx, uint32_t mode);
+ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode);
+
 /* Load balancing (the counterpart of feeding measured per-link load back
  * into the partition): every `every_steps` steps of a ts_step call
  * (0 = never; otherwise at least 32) the link tiles are rebuilt from the
@@ -271,7 +283,11 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
  * the occupancy to the host.  Results do not depend on it. */
 ts_status ts_set_load_balance(ts_ctx *ctx, uint32_t every_steps, uint32_t vehicles_per_tile);
 
-/* Number of kernel launches one time step of this context enqueues. */
+/* Number of kernel launches one time step enqueues in FUSED mode (1: the
+ * link kernel, which also completes the node transfers of the step before
+ * it; SPLIT mode adds the node kernel: 2).  On top, every chunk of up to 32
+ * steps adds the chunk-closing kernel and, in FUSED mode, the node kernel
+ * of its last step, and every ts_step call one launch (its target step). */
 uint32_t ts_launches_per_step(void);
 
 #ifdef __cplusplus

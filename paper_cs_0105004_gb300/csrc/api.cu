@@ -68,7 +68,9 @@ struct World {
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1;
-    std::map<uint32_t, cudaGraphExec_t> graphs;
+    uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
+    std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
+    bool fused() const;
     ~World();
     ts_status init(uint32_t cap);
     ts_status rebuild();
@@ -97,6 +99,7 @@ struct ts_ctx {
     uint32_t n_sub = 1;                // statistics sub-records per step (fixed at creation)
     uint32_t tile_vehicles = 1024;     // vehicle budget per tile when re-tiling from occupancy
     uint32_t retile_every = 0;         // steps between load-balancing passes (0 = static tiles)
+    uint32_t step_mode = TS_STEP_AUTO; // for the context's own world
     // vehicles
     bool loaded = false;
     uint32_t n_veh = 0;
@@ -104,7 +107,6 @@ struct ts_ctx {
     // device
     ScenDev sd{};
     uint4 *d_lk_info = nullptr;
-    uint32_t *d_link_exit0 = nullptr;  // all buffers empty, for resets
     uint2 *d_veh0 = nullptr;           // route starts, for resets
     uint32_t *d_dep_head0 = nullptr;   // queue starts, for resets
     std::vector<std::pair<void *, size_t>> allocs, veh_allocs;
@@ -216,18 +218,32 @@ ts_status World::rebuild() {
     return TS_OK;
 }
 
+// Fused steps (one launch per step) save the node kernel's launch but make
+// every tile with an occupied lane-end buffer resolve that buffer's node
+// transfer itself (two to three dependent memory round trips before the
+// step can start).  Measured on GB300, that costs more than the launch it
+// saves as soon as buffers are in use (config 1: 16.8 us per step split,
+// 18.3 fused; an empty network: 9.4 us fused, 12.4 split), so AUTO splits.
+bool World::fused() const { return mode == TS_STEP_FUSED; }
+
 // Enqueues n steps of every active member on stream s, as CUDA graphs of up
-// to kChunk steps: two kernels per step, then the chunk-closing kernel.
+// to kChunk steps.  Fused: one link kernel per step, each but the first also
+// completing the node transfers of the step before it, and the node kernel
+// for the chunk's last step.  Split: a link and a node kernel per step.
+// Then the chunk-closing kernel.
 ts_status World::run(uint32_t n, cudaStream_t s) {
+    const bool fu = fused();
     while (n > 0) {
         const uint32_t g = std::min(n, kChunk);
-        auto it = graphs.find(g);
+        const uint32_t key = g | (fu ? 1u << 16 : 0u);
+        auto it = graphs.find(key);
         if (it == graphs.end()) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
-                launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0);
-                launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true);
+                launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0);
+                if (!fu || i + 1 == g)
+                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true);
             }
             launch_advance_kernel(d_table, capacity, g, cap_stream, true);
             CK(cudaStreamEndCapture(cap_stream, &graph));
@@ -235,7 +251,7 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            it = graphs.emplace(g, exec).first;
+            it = graphs.emplace(key, exec).first;
         }
         CK(cudaGraphLaunch(it->second, s));
         n -= g;
@@ -413,7 +429,7 @@ extern "C" {
 
 const char *ts_last_error(void) { return g_err.c_str(); }
 
-uint32_t ts_launches_per_step(void) { return 2u; }
+uint32_t ts_launches_per_step(void) { return 1u; }
 
 size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_t route_len) {
     if (!d) return 0;
@@ -424,9 +440,9 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
         if (!ring) slots += d->link_lanes[l];
     }
     size_t b = 0;
-    b += 16ull * d->n_links * 2 + 4ull * d->n_links * 2;      // lk_info, nd_info, link_exit (+ reset copy)
+    b += 16ull * d->n_links * 2;                              // lk_info, nd_info
     b += words * (4 + 4 + 4 + 32 + 128) * 2;                  // occupancy, v>0, location, velocity, id (x2)
-    b += 16ull * slots + 8ull * n_vehicles * 2 + 4ull * route_len;
+    b += 16ull * slots * 2 + 8ull * n_vehicles * 2 + 4ull * route_len;  // buffers (x2), vehicles, routes
     b += 8ull * n_vehicles + 4ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
     b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
     return b;
@@ -518,9 +534,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     int8_t *vel1 = alloc_in<int8_t>(c.get(), A, (size_t)c->n_words * 32, ok);
     uint32_t *vid0 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32, ok);
     uint32_t *vid1 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32, ok);
-    uint4 *slots = alloc_in<uint4>(c.get(), A, c->n_slots, ok);
-    uint32_t *link_exit = alloc_in<uint32_t>(c.get(), A, L, ok);
-    c->d_link_exit0 = alloc_in<uint32_t>(c.get(), A, L, ok);
+    uint4 *slots0 = alloc_in<uint4>(c.get(), A, c->n_slots, ok);
+    uint4 *slots1 = alloc_in<uint4>(c.get(), A, c->n_slots, ok);
     Ctrl *ctrl = alloc_in<Ctrl>(c.get(), A, 1, ok);
     StatRec *stats = alloc_in<StatRec>(c.get(), A, (size_t)kStatsRing * c->n_sub, ok);
     if (!ok) {
@@ -540,8 +555,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.vel[1] = vel1;
     sd.vid[0] = vid0;
     sd.vid[1] = vid1;
-    sd.slots = slots;
-    sd.link_exit = link_exit;
+    sd.slots[0] = slots0;
+    sd.slots[1] = slots1;
     sd.ctrl = ctrl;
     sd.stats = stats;
     sd.vmax = params->vmax;
@@ -553,12 +568,9 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.n_sub = c->n_sub;
     st = upload_lk_info(c.get());
     if (st != TS_OK) return st;
-    std::vector<uint32_t> ex(L);
-    for (uint32_t l = 0; l < L; ++l) ex[l] = c->ring[l] ? 0u : ((1u << c->lanes[l]) - 1u);
-    CK(cudaMemcpy(c->d_link_exit0, ex.data(), 4ull * L, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(link_exit, ex.data(), 4ull * L, cudaMemcpyHostToDevice));
     for (uint32_t *p : {occ0, occ1, mov0, mov1, loc0, loc1}) CK(cudaMemset(p, 0, 4ull * c->n_words));
-    CK(cudaMemset(slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
+    CK(cudaMemset(slots0, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
+    CK(cudaMemset(slots1, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(ctrl, 0, sizeof(Ctrl)));
     CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub));
     *out = c.release();
@@ -628,8 +640,7 @@ static ts_status reset_device_state(ts_ctx *c, cudaStream_t s) {
         CK(cudaMemsetAsync(sd.mov[b], 0, 4ull * c->n_words, s));
         CK(cudaMemsetAsync(sd.loc[b], 0, 4ull * c->n_words, s));
     }
-    CK(cudaMemsetAsync(sd.slots, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1), s));
-    CK(cudaMemcpyAsync(sd.link_exit, c->d_link_exit0, 4ull * c->n_links, cudaMemcpyDeviceToDevice, s));
+    for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(sd.slots[b], 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1), s));
     if (c->n_veh) CK(cudaMemcpyAsync(sd.veh, c->d_veh0, 8ull * c->n_veh, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(sd.dep_head, c->d_dep_head0, 4ull * c->n_links, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(sd.ctrl, 0, sizeof(Ctrl), s));
@@ -645,6 +656,7 @@ static ts_status ensure_own_world(ts_ctx *c) {
         if (s != TS_OK) return s;
     }
     c->own->members[0] = c;
+    c->own->mode = c->step_mode;
     return c->own->rebuild();
 }
 
@@ -707,6 +719,23 @@ ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
     st = upload_lk_info(c);
     if (st != TS_OK) return st;
     if (c->own) return ensure_own_world(c);
+    return TS_OK;
+}
+
+ts_status ts_set_step_mode(ts_ctx *c, uint32_t mode) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (mode > TS_STEP_SPLIT) return fail(TS_ERR_INVALID, "unknown step mode");
+    if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
+    c->step_mode = mode;
+    if (c->own) c->own->mode = mode;
+    return TS_OK;
+}
+
+ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode) {
+    if (!b) return fail(TS_ERR_INVALID, "null batch");
+    if (mode > TS_STEP_SPLIT) return fail(TS_ERR_INVALID, "unknown step mode");
+    b->w.mode = mode;
     return TS_OK;
 }
 
@@ -813,12 +842,16 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
         launch_set_target(c->sd.ctrl, c->host_step, s);
         for (uint32_t b = 0; b < n_steps && rs == TS_OK; b += kChunk) {
             const uint32_t g = std::min(kChunk, n_steps - b);
+            // the launch sequence of a captured chunk, with events around
+            // every kernel (fused: node time is 0 but for the chunk's last step)
+            const bool fu = w->fused();
             for (uint32_t i = 0; i < g; ++i) {
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
-                launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false);
+                launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0);
                 cudaEventRecord(ev[e + 1], s);
-                launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false);
+                if (!fu || i + 1 == g)
+                    launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false);
                 cudaEventRecord(ev[e + 2], s);
             }
             launch_advance_kernel(w->d_table, w->capacity, g, s, false);
@@ -962,7 +995,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     CK(cudaMemcpy(vel1.data(), c->sd.vel[1], nw * 32, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(vid0.data(), c->sd.vid[0], 4 * nw * 32, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(vid1.data(), c->sd.vid[1], 4 * nw * 32, cudaMemcpyDeviceToHost));
-    if (c->n_slots) CK(cudaMemcpy(slots.data(), c->sd.slots, 16ull * c->n_slots, cudaMemcpyDeviceToHost));
+    if (c->n_slots) CK(cudaMemcpy(slots.data(), c->sd.slots[cur], 16ull * c->n_slots, cudaMemcpyDeviceToHost));
     if (c->n_veh) CK(cudaMemcpy(veh.data(), c->sd.veh, 8ull * c->n_veh, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(head.data(), c->sd.dep_head, 4ull * c->n_links, cudaMemcpyDeviceToHost));
     for (uint64_t i = 0; i < c->n_lane_cells; ++i) {
@@ -1017,7 +1050,7 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     if (st != TS_OK) return st;
     const uint32_t vmax = c->params.vmax;
     const size_t nw = c->n_words;
-    std::vector<uint32_t> occ(nw, 0), mov(nw, 0), vid(nw * 32, 0), exit_bits(c->n_links, 0);
+    std::vector<uint32_t> occ(nw, 0), mov(nw, 0), vid(nw * 32, 0);
     uint64_t n_active = 0, n_buffered = 0, sum_v = 0, hash = 0;
     std::vector<int8_t> vel(nw * 32, 0);
     std::vector<uint4> slots(c->n_slots, make_uint4(kSlotEmpty, 0, 0, 0));
@@ -1028,7 +1061,6 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     auto on_route = [&](int32_t id, uint32_t l) { return c->route_links[c->route_off[id] + in->cursor[id]] == l; };
     for (uint32_t l = 0; l < c->n_links; ++l) {
         const uint32_t nl = c->lanes[l];
-        if (!c->ring[l]) exit_bits[l] = (1u << nl) - 1u;
         for (uint32_t k = 0; k < nl; ++k) {
             const uint64_t cb = c->cell_base[c->lane_base[l] + k];
             for (uint32_t x = 0; x < c->cells[l]; ++x) {
@@ -1063,7 +1095,6 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
                 const uint32_t fl = (in->cursor[b] + 2 == len) ? kLastLinkBit : 0u;
                 slots[c->bpos[l] + k] =
                     make_uint4((uint32_t)b | fl, c->route_links[p + 1], l, (uint32_t)v | (k << 8) | (c->cells[l] << 10));
-                exit_bits[l] &= ~(1u << k);
                 ++n_buffered;
                 hash += vehicle_term((uint32_t)b, l, k, c->cells[l], (uint32_t)v);
             }
@@ -1090,8 +1121,10 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     CK(cudaMemcpy(sd.mov[cur], mov.data(), 4 * nw, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(sd.vel[0], vel.data(), nw * 32, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(sd.vid[0], vid.data(), 4 * nw * 32, cudaMemcpyHostToDevice));
-    if (c->n_slots) CK(cudaMemcpy(sd.slots, slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(sd.link_exit, exit_bits.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    if (c->n_slots) {
+        CK(cudaMemset(sd.slots[cur ^ 1], 0xFF, 16ull * c->n_slots));
+        CK(cudaMemcpy(sd.slots[cur], slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
+    }
     if (c->n_veh) CK(cudaMemcpy(sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(sd.dep_head, head.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
     st = reset_ctrl(c, in->step, in->arrived, in->inserted, c->stream, n_active, n_buffered, sum_v, hash);

@@ -16,11 +16,13 @@
 //     is; a vehicle that moves or changes speed writes the buffer that no
 //     reader of the step can be using (the other one than the cell's current
 //     occupant's).  Payload of empty cells is never read.
-//   * slots[n_slots]: one link-end buffer per lane, grouped by the node the
-//     link ends at, in intersection priority order (link id, then lane):
+//   * slots[2][n_slots]: one link-end buffer per lane, grouped by the node
+//     the link ends at, in intersection priority order (link id, then lane):
 //     x = id | next-link-is-last << 31 (0xffffffff = empty), y = next link,
 //     z = current link, w = v | lane << 8 | current link cells << 10.
-//   * link_exit[n_links]: bit k set while lane k's buffer is empty.
+//     Double-buffered by step parity like the cells: a step reads
+//     slots[t&1] (which every tile may read to resolve node transfers) and
+//     each tile writes its own links' buffers into slots[(t+1)&1].
 //   * veh[n_vehicles]: {absolute index of the current route entry, end of the
 //     vehicle's route}.
 #pragma once
@@ -87,8 +89,7 @@ struct ScenDev {
     uint32_t *loc[2];
     int8_t *vel[2];
     uint32_t *vid[2];
-    uint4 *slots;
-    uint32_t *link_exit;
+    uint4 *slots[2];
     uint2 *veh;
     const uint32_t *route_links;
     const uint32_t *dep_ids;      // id | last-link flag << 31, queue order
@@ -113,8 +114,11 @@ struct LinkTile {
 // with the tail of the previous kernel in the stream)
 // n_tiles points to the tile count in device memory; it may change between
 // graph launches (load balancing) without a new capture
+// xfer: the launch first completes the node transfers and departures of the
+// previous step (the step at position i-1 of the chunk); without it, the
+// previous step must have been completed by node_kernel
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl);
+                        cudaStream_t s, bool pdl, bool xfer);
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl);
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);

@@ -115,6 +115,79 @@ __device__ __forceinline__ void block_flush(unsigned long long (&acc)[NF], unsig
     __syncthreads();
 }
 
+// ------------------------------------------------------------------ node transfer
+
+// Free lanes of link m at cell 0 (bit k set: cell 0 of lane k is empty in
+// occ); the lanes' words are loaded together.
+__device__ __forceinline__ uint32_t free_cell0(const uint32_t *__restrict__ occ, const uint4 &nd) {
+    const uint32_t lanes = (nd.z >> 8) & 0xFFu;
+    uint32_t o[kMaxLanes];
+#pragma unroll
+    for (int k = 0; k < kMaxLanes; ++k) o[k] = (uint32_t)k < lanes ? occ[nd.y + k] : 1u;
+    uint32_t f = 0u;
+#pragma unroll
+    for (int k = 0; k < kMaxLanes; ++k) f |= ((o[k] & 1u) ^ 1u) << k;
+    return f;
+}
+
+constexpr int kSlotPrefetch = 8;  // buffers of a node loaded together before resolving
+
+// Node transfer into link m at the end of a step (Sec. 3): the buffered
+// vehicles at m's upstream node whose next link is m, in slot (priority)
+// order, each take cell 0 of the preferred lane min(k, lanes(m)-1) if it is
+// free, else of the lowest free lane, else stay buffered.  nd = nd_info[m],
+// free_mask from free_cell0 (after the step's moves).  Calls
+// place(slot index, slot, lane) for every placement and returns the lanes
+// still free (for departures).  Any number of threads may evaluate the same
+// m on the same inputs and get the same placements.
+template <class F>
+__device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ slots, const uint4 &nd, uint32_t m,
+                                                      uint32_t free_mask, F &&place) {
+    const uint32_t slot_lo = nd.x, cnt = nd.z & 0xFFu, lanes = (nd.z >> 8) & 0xFFu;
+    auto visit = [&](const uint4 &x, uint32_t si) {
+        if (x.x == kSlotEmpty || x.y != m || !free_mask) return;
+        const uint32_t ks = (x.w >> 8) & 3u;
+        const uint32_t pref = ks < lanes - 1u ? ks : lanes - 1u;
+        uint32_t qn;
+        if ((free_mask >> pref) & 1u) {
+            qn = pref;
+        } else {
+            const uint32_t rest = free_mask & ~(1u << pref);
+            if (!rest) return;
+            qn = (uint32_t)(__ffs(rest) - 1);
+        }
+        free_mask &= ~(1u << qn);
+        place(si, x, qn);
+    };
+    uint4 pre[kSlotPrefetch];
+#pragma unroll
+    for (int s = 0; s < kSlotPrefetch; ++s)
+        pre[s] = (uint32_t)s < cnt ? slots[slot_lo + s] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+#pragma unroll
+    for (int s = 0; s < kSlotPrefetch; ++s) visit(pre[s], slot_lo + (uint32_t)s);
+    for (uint32_t s = kSlotPrefetch; s < cnt && free_mask; ++s) visit(slots[slot_lo + s], slot_lo + s);
+    return free_mask;
+}
+
+// Departures from parking onto link m after the transfers: the head of m's
+// queue enters the lowest free lane with v = 0 while lanes are free and its
+// departure step has come.  Calls insert(queue entry, lane); returns the new
+// queue head.
+template <class F>
+__device__ __forceinline__ uint32_t run_departures(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
+                                                   uint32_t free_mask, F &&insert) {
+    uint32_t h = D.dep_head[m];
+    const uint32_t h0 = h, dep_end = nd.w;
+    while (h < dep_end && free_mask && D.dep_steps[h] <= t) {
+        const uint32_t qn = (uint32_t)(__ffs(free_mask) - 1);
+        free_mask &= ~(1u << qn);
+        insert(D.dep_ids[h], qn);
+        ++h;
+    }
+    if (h != h0) D.dep_head[m] = h;
+    return h;
+}
+
 // ------------------------------------------------------------------ link kernel
 
 constexpr int kCols = kTileMaxCols + 2;
@@ -137,11 +210,13 @@ struct LinkSmem {
     int16_t right[kCols], left[kCols];
     uint8_t clink[kCols], ckind[kCols];  // ckind: 0 core, 1 left halo, 2 right halo
     uint32_t lcells[kTileMaxCols], lid[kTileMaxCols], lbpos[kTileMaxCols];
-    uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];
-    uint32_t lentered[kTileMaxCols];  // lanes whose buffer received a vehicle
+    uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];  // lexit: lanes whose buffer is empty
+    uint8_t lend[kTileMaxCols];       // the link's end (and its buffers) is in this tile
+    uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
     uint32_t nlist;                   // vehicles in the list
     uint16_t code[kListCap];          // (local word << 5) | bit
     unsigned long long red[kLinkThreads / 32][7];
+    unsigned long long xacc[6];       // node-transfer counts of the current previous-step record
     int ncols, nwords, ncore_words, nlinks;
 };
 
@@ -206,17 +281,126 @@ __device__ __forceinline__ void list_append(LinkSmem &S, int w, uint32_t m) {
     }
 }
 
+// The link thread of link q (index in the tile): with do_xfer, completes the
+// node transfers and departures into q (if q starts in this tile) at the end
+// of step t-1; then sets up q's lane-end buffers for step t (if q ends in this
+// tile).  Returns the vehicles placed on q.  Out of line, so that its
+// registers do not weigh on the rest of the step.
+__device__ __noinline__ uint32_t link_buffers_phase(LinkSmem &S, const ScenDev &D, int q, int cur, uint32_t t,
+                                                    bool do_xfer) {
+    const int nxt = cur ^ 1;
+    uint32_t n_placed = 0u;
+    const uint4 *__restrict__ sc = D.slots[cur];
+    uint4 *__restrict__ sn = D.slots[nxt];
+    const uint32_t *__restrict__ oc = D.occ[cur];
+    const uint32_t l = S.lid[q];
+    if (do_xfer && S.lcw0[q] != 0xFFFFu) {
+        // transfers and departures into l at the end of step t-1
+        const uint4 nd = D.nd_info[l];
+        uint32_t placed = 0u, moving = 0u;
+        unsigned long long acc2[6] = {0, 0, 0, 0, 0, 0};
+        int8_t *vel = D.vel[0];  // cell 0 was empty: its payload goes
+        uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
+        uint32_t fr = resolve_transfers(sc, nd, l, free_cell0(oc, nd), [&](uint32_t, const uint4 &x,
+                                                                          uint32_t qn) {
+            const uint32_t id = x.x & kIdMask, v = x.w & 0xFFu, ks = (x.w >> 8) & 3u;
+            placed |= 1u << qn;
+            if (v) moving |= 1u << qn;
+            const size_t pc = (size_t)(nd.y + qn) * 32u;
+            vel[pc] = (int8_t)v;
+            vid[pc] = x.x;  // id with the last-link flag of l
+            atomicAdd(&D.veh[id].x, 1u);
+            acc2[0] += 1;
+            acc2[2] += 1;
+            acc2[3] -= 1;
+            acc2[4] += v;
+            acc2[5] += vehicle_term(id, l, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+        });
+        run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn) {
+            placed |= 1u << qn;
+            const size_t pc = (size_t)(nd.y + qn) * 32u;
+            vel[pc] = 0;
+            vid[pc] = idw;
+            acc2[1] += 1;
+            acc2[2] += 1;
+            acc2[5] += vehicle_term(idw & kIdMask, l, qn, 0u, 0u);
+        });
+        n_placed = (uint32_t)__popc(placed);  // they are updated in step t
+        if (placed)
+            for (int f = 0; f < 6; ++f)
+                if (acc2[f]) atomicAdd(&S.xacc[f], acc2[f]);
+        for (uint32_t m = placed; m; m &= m - 1u) {
+            const uint32_t qn = (uint32_t)(__ffs(m) - 1);
+            atomicOr(&S.occ0[S.lcw0[q] + qn], 1u);
+            if ((moving >> qn) & 1u) atomicOr(&S.mov0[S.lcw0[q] + qn], 1u);
+        }
+    }
+    uint32_t open = 0u;
+    if (S.lend[q]) {
+        // l's lane-end buffers for step t: empty, or emptied by a
+        // transfer of step t-1 (the same resolution as the tile of
+        // the next link computes), or still holding their vehicle
+        const uint32_t nl = S.llanes[q], b0 = S.lbpos[q];
+        uint4 own[kMaxLanes];
+#pragma unroll
+        for (int k = 0; k < kMaxLanes; ++k)
+            own[k] = (uint32_t)k < nl ? sc[b0 + k] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+#pragma unroll
+        for (uint32_t k = 0; k < (uint32_t)kMaxLanes; ++k) {
+            if (k >= nl) break;
+            const uint32_t idx = b0 + k;
+            const uint4 x = own[k];
+            bool empty = x.x == kSlotEmpty;
+            if (!empty && do_xfer) {
+                const uint4 nd = D.nd_info[x.y];
+                resolve_transfers(sc, nd, x.y, free_cell0(oc, nd),
+                                  [&](uint32_t si, const uint4 &, uint32_t) { empty |= si == idx; });
+            }
+            if (empty) open |= 1u << k;
+            sn[idx] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : x;
+        }
+    }
+    S.lexit[q] = (uint8_t)open;
+    return n_placed;
+}
+
 __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__restrict__ table,
                                                             const LinkTile *__restrict__ tiles,
-                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
+                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
+                                                            uint32_t xfer) {
     __shared__ LinkSmem S;
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
     static_assert(kTileSmemWords <= kLinkThreads, "one word per thread");
     // statistics of the block: updates, lane changes, arrivals, and the changes
     // of active, buffered, sum of velocities and digest
     static constexpr int kField[7] = {kUpdates, kLaneChanges, kArrived, kDActive, kDBuffered, kDSumV, kDHash};
-    unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    // counts in 32 bits (per block and step they stay far below 2^31; the
+    // changes are signed), the digest change in 64
+    uint32_t acc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    unsigned long long acc_hash = 0ull;
+    auto flush_acc = [&](unsigned long long *rec) {
+        unsigned long long v[7] = {acc[0], acc[1], acc[2], (unsigned long long)(long long)(int)acc[3],
+                                   (unsigned long long)(long long)(int)acc[4],
+                                   (unsigned long long)(long long)(int)acc[5], acc_hash};
+        block_flush<7, kLinkThreads>(v, rec, kField, S.red);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) acc[f] = 0u;
+        acc_hash = 0ull;
+    };
     unsigned long long *cur_rec = nullptr;
+    // with xfer set, the launch first completes the node transfers and
+    // departures of the previous step (whose record gets these counts):
+    // transfers, insertions and the changes of active, buffered, sum of v, digest
+    static constexpr int kField2[6] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash};
+    unsigned long long *cur_rec2 = nullptr;
+    if (threadIdx.x < 6) S.xacc[threadIdx.x] = 0ull;  // ordered by the first tile's barrier
+    auto flush_xacc = [&]() {
+        if (threadIdx.x < 6 && S.xacc[threadIdx.x]) {
+            atomicAdd(cur_rec2 + kField2[threadIdx.x], S.xacc[threadIdx.x]);
+            S.xacc[threadIdx.x] = 0ull;
+        }
+        __syncthreads();
+    };
     pdl_trigger();
     span_mark((int)pos * 3, true);
     bool waited = false;
@@ -247,9 +431,10 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.lring[q] = (uint8_t)((li.z >> 8) & 1u);
                 S.lid[q] = td.a.y + q;
                 S.lbpos[q] = li.w;
-                S.lentered[q] = 0;
                 const int ncol = (int)((li.y + 31u) >> 5), c0 = (int)((li.z >> 16) & 0xFFu);
                 const uint32_t lanes = li.z & 0xFFu, ring = (li.z >> 8) & 1u;
+                S.lend[q] = (uint8_t)(ring ^ 1u);
+                S.lcw0[q] = ring ? (uint16_t)0xFFFFu : (uint16_t)(li.x - wb);
                 for (int j = 0; j < ncol; ++j) {
                     const int c = c0 + j;
                     const uint32_t lw = li.x - wb + (uint32_t)j * lanes;
@@ -269,6 +454,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             }
             for (int w = threadIdx.x; w < nw; w += blockDim.x) {
                 S.gw[w] = wb + w;
+                S.occ0[w] = 0u;
+                S.mov0[w] = 0u;
                 S.mv[w] = 0u;
                 S.oocc[w] = 0u;
                 S.omov[w] = 0u;
@@ -319,6 +506,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.left[c] = ll;
                 for (uint32_t k = 0; k < lanes; ++k) {
                     S.gw[lw + k] = wbase + (uint32_t)j * lanes + k;
+                    S.occ0[lw + k] = 0u;
+                    S.mov0[lw + k] = 0u;
                     S.mv[lw + k] = 0u;
                     S.oocc[lw + k] = 0u;
                     S.omov[lw + k] = 0u;
@@ -333,8 +522,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.lring[0] = (uint8_t)ring;
                 S.lid[0] = l;
                 S.lbpos[0] = td.b.w;
-                S.lexit[0] = (!ring && j1 == ncol) ? 1u : 0u;  // marks that the link end is in this tile
-                S.lentered[0] = 0;
+                S.lend[0] = (uint8_t)((!ring && j1 == ncol) ? 1u : 0u);
+                S.lcw0[0] = (!ring && j0 == 0) ? (uint16_t)0u : (uint16_t)0xFFFFu;
                 S.ncols = ncols;
                 S.nwords = ncols * (int)lanes;
                 S.ncore_words = ncore * (int)lanes;
@@ -357,7 +546,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         stamp(3, first);
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) block_flush<7, kLinkThreads>(acc, cur_rec, kField, S.red);
+            if (cur_rec) flush_acc(cur_rec);
             cur_rec = rec;
         }
         const uint32_t t = (uint32_t)step;
@@ -366,18 +555,33 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         const int nwords = S.nwords, ncore_words = S.ncore_words;
         const int w = threadIdx.x;  // one word per thread in the word phases
 
-        // ---------------- state of step t
+        // with xfer, memory holds the state after the moves of step t-1 and
+        // the node transfers of t-1 are completed here, before step t
+        const bool do_xfer = xfer != 0u;
+        if (do_xfer) {
+            unsigned long long *rec2 = reinterpret_cast<unsigned long long *>(stat_rec(D, step - 1ull));
+            if (rec2 != cur_rec2) {
+                if (cur_rec2) flush_xacc();
+                cur_rec2 = rec2;
+            }
+        }
+
+        // ---------------- state of step t (occ0/mov0 start at zero: the word
+        // loads and the placements of the node transfers are or-ed in)
         if (w < nwords) {
             const uint32_t g = S.gw[w];
             const uint32_t o = D.occ[cur][g];
-            S.occ0[w] = o;
-            S.mov0[w] = o ? D.mov[cur][g] : 0u;
+            if (o) {
+                atomicOr(&S.occ0[w], o);
+                atomicOr(&S.mov0[w], D.mov[cur][g]);
+            }
             S.loc0[w] = o ? D.loc[cur][g] : 0u;
-            if (S.ckind[S.wcol[w]] == 0) acc[0] += (unsigned long long)__popc(o);  // vehicle updates
+            if (S.ckind[S.wcol[w]] == 0) acc[0] += (uint32_t)__popc(o);  // vehicle updates
         }
-        for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x) {
-            const bool end_here = partial ? S.lexit[0] != 0 : !S.lring[q];
-            S.lexit[q] = end_here ? (uint8_t)D.link_exit[S.lid[q]] : (uint8_t)0;
+        {
+            // link threads, counted down from the last thread
+            const int q = kLinkThreads - 1 - (int)threadIdx.x;
+            if (q < S.nlinks) acc[0] += link_buffers_phase(S, D, q, cur, t, do_xfer);
         }
         __syncthreads();
         stamp(4, first);
@@ -413,7 +617,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                         const uint32_t lcv0 = o & ~S.mov0[w] & ~near & ok;
                         if (lcv0) {
                             atomicOr(&S.mv[S.cw[c] + kt], lcv0);
-                            if (S.ckind[c] == 0) acc[1] += (unsigned long long)__popc(lcv0);
+                            if (S.ckind[c] == 0) acc[1] += (uint32_t)__popc(lcv0);
                         }
                         listed = o & (S.mov0[w] | near);
                     }
@@ -529,7 +733,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                         acc[2] += 1;  // leaves to parking
                         acc[3] -= 1;
                         acc[5] -= v0;
-                        acc[6] -= old_term;
+                        acc_hash -= old_term;
                     } else {
                         const uint2 ve = D.veh[id];
                         if (ve.x + 1u >= ve.y) {
@@ -538,13 +742,12 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                             const uint32_t m = D.route_links[ve.x + 1u];
                             const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
                             if (!((S.lexit[q] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
-                            D.slots[S.lbpos[q] + (uint32_t)k] =
+                            D.slots[nxt][S.lbpos[q] + (uint32_t)k] =
                                 make_uint4(id | fl, m, lid, v | ((uint32_t)k << 8) | (S.lcells[q] << 10));
-                            atomicOr(&S.lentered[q], 1u << k);
                             acc[3] -= 1;
                             acc[4] += 1;
                             acc[5] -= v0;
-                            acc[6] += vehicle_term(id, lid, (uint32_t)k, S.lcells[q], v) - old_term;
+                            acc_hash += vehicle_term(id, lid, (uint32_t)k, S.lcells[q], v) - old_term;
                         }
                     }
                 } else {
@@ -558,8 +761,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                         atomicOr(&D.ctrl->error, kErrGeometry);
                     } else {
                         if (core) {
-                            acc[5] += (unsigned long long)v - v0;
-                            acc[6] += vehicle_term(id, lid, (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v) - old_term;
+                            acc[5] += v - v0;
+                            acc_hash += vehicle_term(id, lid, (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v) - old_term;
                         }
                         if (S.ckind[dc] == 0) {
                             const int dw = S.cw[dc] + k;
@@ -593,21 +796,21 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             D.mov[nxt][g] = S.omov[w];
             D.loc[nxt][g] = S.oloc[w];
         }
-        for (int q = threadIdx.x; q < S.nlinks; q += blockDim.x)
-            if (S.lentered[q]) D.link_exit[S.lid[q]] = (uint32_t)S.lexit[q] & ~S.lentered[q];
         __syncthreads();
         stamp(7, first);
         first = false;
     }
-    if (cur_rec) block_flush<7, kLinkThreads>(acc, cur_rec, kField, S.red);
+    if (cur_rec) flush_acc(cur_rec);
+    if (cur_rec2) flush_xacc();
     stamp(9, true);
     span_mark((int)pos * 3, false);
 }
 
 // ------------------------------------------------------------------ node kernel
 
-constexpr int kSlotPrefetch = 8;
-
+// Completes the node transfers and departures of the last step a chunk ran
+// for each scenario (the link kernel does those of the other steps at the
+// start of the next step).  One thread per link m.
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
                                                             const uint4 *__restrict__ tiles,
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
@@ -626,9 +829,11 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
         if (D.ctrl == nullptr) continue;
         const uint32_t m = td.y + threadIdx.x;
         const uint4 nd = m < td.z ? D.nd_info[m] : make_uint4(0u, 0u, 0u, 0u);  // static
-        // constant within a captured chunk, like the link descriptors
-        const unsigned long long step = D.ctrl->base + pos;
-        if (step >= D.ctrl->target) continue;
+        // constant within a captured chunk, like the link descriptors: the
+        // last step this scenario ran in the chunk
+        const unsigned long long base = D.ctrl->base, target = D.ctrl->target;
+        if (target <= base) continue;
+        const unsigned long long step = min(base + pos, target - 1ull);
         if (!waited) {
             pdl_wait();
             waited = true;
@@ -638,83 +843,39 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
             if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
             cur_rec = rec;
         }
-        const uint32_t t = (uint32_t)step;
         const int nxt = (int)((step + 1ull) & 1ull);
         if (m < td.z) {
             uint32_t *occ = D.occ[nxt];
             uint32_t *mov = D.mov[nxt];
+            uint4 *slots = D.slots[nxt];
             int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
             uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
-            uint32_t h = D.dep_head[m];
-            const uint32_t slot_lo = nd.x, wbase = nd.y, cnt = nd.z & 0xFFu, lanes = (nd.z >> 8) & 0xFFu;
-            const uint32_t dep_end = nd.w;
-            // occupancy of cell 0 of every lane of m after the move
-            uint32_t o[kMaxLanes];
-            uint32_t free_mask = 0;
-#pragma unroll
-            for (int k = 0; k < kMaxLanes; ++k) {
-                o[k] = (uint32_t)k < lanes ? occ[wbase + k] : 1u;
-                free_mask |= (uint32_t)(!(o[k] & 1u)) << k;
-            }
-            uint4 sl[kSlotPrefetch];
-#pragma unroll
-            for (int s = 0; s < kSlotPrefetch; ++s)
-                sl[s] = (uint32_t)s < cnt ? D.slots[slot_lo + s] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
-            // node transfer in priority order (slot order)
-            for (uint32_t s = 0; s < cnt; ++s) {
-                uint4 x;
-                if (s < (uint32_t)kSlotPrefetch) {
-                    // select the prefetched slot without dynamic register indexing
-                    x = sl[0];
-#pragma unroll
-                    for (int u = 1; u < kSlotPrefetch; ++u)
-                        if ((uint32_t)u == s) x = sl[u];
-                } else {
-                    x = D.slots[slot_lo + s];
-                }
-                if (x.x == kSlotEmpty || x.y != m) continue;
-                const uint32_t id = x.x & kIdMask, l = x.z;
-                const uint32_t v = x.w & 0xFFu, ks = (x.w >> 8) & 3u, cells_l = x.w >> 10;
-                const uint32_t pref = ks < lanes - 1u ? ks : lanes - 1u;
-                uint32_t qn = 0xFFu;
-                if ((free_mask >> pref) & 1u) {
-                    qn = pref;
-                } else {
-                    const uint32_t rest = free_mask & ~(1u << pref);
-                    if (rest) qn = (uint32_t)(__ffs(rest) - 1);
-                }
-                if (qn == 0xFFu) continue;  // stays buffered: nothing changes
-                free_mask &= ~(1u << qn);
-                const uint32_t w = wbase + qn;  // column 0 of lane qn
-                occ[w] = o[qn & 3] | 1u;
+            // slots with next link m are written by this thread only
+            const uint32_t fr = resolve_transfers(slots, nd, m, free_cell0(occ, nd), [&](uint32_t si, const uint4 &x,
+                                                                                          uint32_t qn) {
+                const uint32_t id = x.x & kIdMask, v = x.w & 0xFFu, ks = (x.w >> 8) & 3u;
+                const uint32_t w = nd.y + qn;  // column 0 of lane qn
+                occ[w] |= 1u;
                 if (v) mov[w] |= 1u;
                 vel[(size_t)w * 32u] = (int8_t)v;
                 vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
                 atomicAdd(&D.veh[id].x, 1u);
-                D.slots[slot_lo + s].x = kSlotEmpty;
-                atomicOr(&D.link_exit[l], 1u << ks);
+                slots[si].x = kSlotEmpty;
                 acc[0] += 1;
                 acc[2] += 1;
                 acc[3] -= 1;
                 acc[4] += v;
-                acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, l, ks, cells_l, v);
-            }
-            // departures from parking onto m
-            const uint32_t h0 = h;
-            while (h < dep_end && free_mask && D.dep_steps[h] <= t) {
-                const uint32_t qn = (uint32_t)(__ffs(free_mask) - 1);
-                free_mask &= ~(1u << qn);
-                const uint32_t w = wbase + qn;
-                occ[w] = o[qn & 3] | 1u;
+                acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+            });
+            run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn) {
+                const uint32_t w = nd.y + qn;
+                occ[w] |= 1u;
                 vel[(size_t)w * 32u] = 0;
-                const uint32_t idw = D.dep_ids[h];
                 vid[(size_t)w * 32u] = idw;
                 acc[1] += 1;
                 acc[2] += 1;
                 acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
-                ++h;
-            }
-            if (h != h0) D.dep_head[m] = h;
+            });
         }
     }
     if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
@@ -804,8 +965,8 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
 }
 
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl) {
-    launch_pdl(link_kernel, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i);
+                        cudaStream_t s, bool pdl, bool xfer) {
+    launch_pdl(link_kernel, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i, xfer ? 1u : 0u);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,

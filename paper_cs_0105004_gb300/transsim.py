@@ -21,6 +21,7 @@ STATS_FIELDS = ("step", "active", "buffered", "waiting", "arrived", "lane_change
 STATS_DTYPE = np.dtype([(f, np.uint64) for f in STATS_FIELDS])
 
 TS_OK, TS_ERR_INVALID, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE, TS_ERR_DEVICE_CHECK = range(7)
+STEP_AUTO, STEP_FUSED, STEP_SPLIT = range(3)
 _NAMES = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "STATE", 6: "DEVICE_CHECK"}
 
 u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -101,6 +102,8 @@ _API = {
     "ts_ctx_step": (ctypes.c_int, [ctypes.c_void_p, u64p]),
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_batch_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
     "ts_set_load_balance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
     "ts_ring_step_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Params), ctypes.c_uint64,
@@ -230,6 +233,10 @@ class Simulation:
     def set_tile_words(self, words: int):
         _check(lib().ts_set_tile_words(self.h, words))
 
+    def set_step_mode(self, mode: int):
+        """STEP_AUTO, STEP_FUSED or STEP_SPLIT; results do not depend on it."""
+        _check(lib().ts_set_step_mode(self.h, mode))
+
     def step(self, n: int, stream=None):
         s = _stream_handle(stream)
         _check(lib().ts_step(self.h, n, ctypes.c_void_p(s) if s else None))
@@ -309,6 +316,9 @@ class Batch:
     def step(self, n: int, stream):
         s = _stream_handle(stream)
         _check(lib().ts_batch_step(self.h, n, ctypes.c_void_p(s)))
+
+    def set_step_mode(self, mode: int):
+        _check(lib().ts_batch_set_step_mode(self.h, mode))
 
     def sync(self, timeout_ms: int = 600000):
         _check(lib().ts_batch_sync(self.h, timeout_ms))

@@ -36,8 +36,10 @@ def _cmp_state(g, o, where=""):
         assert g[k] == o[k], (where, k, g[k], o[k])
 
 
-def run_parity(sc, steps, chunk=None, state_every=None, tile_words=None):
+def run_parity(sc, steps, chunk=None, state_every=None, tile_words=None, mode=None):
     sim = T.Simulation(sc, tile_words=tile_words)
+    if mode is not None:
+        sim.set_step_mode(mode)
     orc = oracle.Oracle(sc)
     t0 = sc.init.step if sc.init is not None else 0
     chunk = chunk or min(steps, 4000)
@@ -105,10 +107,12 @@ def test_rings_other_vmax(vmax):
 
 @pytest.mark.parametrize("case", [(3, 1, 20, 100, 1, 5), (4, 2, 25, 400, 2, 5), (4, 3, 15, 500, 3, 5),
                                   (5, 2, 60, 2000, 4, 5), (3, 2, 40, 300, 5, 7), (4, 2, 33, 300, 6, 15)])
-def test_small_grids_match_oracle(case):
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_small_grids_match_oracle(case, mode):
     side, lanes, cells, trips, seed, vmax = case
     sc = N.small_grid_scenario(side, lanes, cells, trips, 200, 800, gen_seed=seed, seed=seed * 7 + 1, vmax=vmax)
-    run_parity(sc, 800, chunk=200, state_every=200)
+    # chunks of 200 steps end inside a captured chunk of 32 (200 = 6*32 + 8)
+    run_parity(sc, 800, chunk=200, state_every=200, mode=mode)
 
 
 def test_long_links_partial_tiles():
@@ -130,13 +134,14 @@ def test_long_links_partial_tiles():
             routes.append([2 * i + 1 for i in range(b - 1, a - 1, -1)])
         dep.append(int(rng.integers(0, 300)))
     sc = make_scenario(links, n, routes, dep, steps=1500, seed=77, p=N.P_THRESHOLD_0_2)
-    for tc in (128, 8):
-        run_parity(sc, 1500, chunk=500, state_every=500, tile_words=tc)
+    for tc, mode in ((128, T.STEP_FUSED), (8, T.STEP_FUSED), (8, T.STEP_SPLIT)):
+        run_parity(sc, 1500, chunk=500, state_every=500, tile_words=tc, mode=mode)
 
 
-def test_config0_full_run():
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_AUTO])
+def test_config0_full_run(mode):
     sc = N.config0()
-    run_parity(sc, sc.steps, chunk=900, state_every=900)
+    run_parity(sc, sc.steps, chunk=900, state_every=900, mode=mode)
 
 
 def test_config0_tile_shapes_identical():
@@ -192,7 +197,8 @@ def test_invariants_hold_on_gpu_config1():
 
 # ------------------------------------------------------------------ batching
 
-def test_batch_equals_alone():
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_batch_equals_alone(mode):
     scs = [N.small_grid_scenario(3 + i % 3, 1 + i % 3, 20 + 5 * i, 100 + 40 * i, 100, 400, gen_seed=20 + i,
                                  seed=100 + i) for i in range(6)]
     alone = []
@@ -204,6 +210,7 @@ def test_batch_equals_alone():
     import torch
     stream = torch.cuda.Stream()
     b = T.Batch(8)
+    b.set_step_mode(mode)
     sims = [T.Simulation(sc) for sc in scs]
     targets = [400, 400, 250, 400, 123, 400]
     for s, tgt in zip(sims, targets):

@@ -44,18 +44,30 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
-def _launches(steps, every=0, start=0):
+def _launches(steps, mode, every=0, start=0):
     """Kernel launches of one ts_step call of `steps` steps: the target-setting
     kernel, then per chunk (at most 32 steps, never across a load-balancing
-    boundary) one link kernel per step, the node kernel and the chunk close."""
+    boundary) a link and a node kernel per step (split steps) or one link
+    kernel per step and one node kernel (fused steps), and the chunk close."""
     n, done = 1, 0
     while done < steps:
         seg = steps - done
         if every:
             seg = min(seg, ((start + done) // every + 1) * every - (start + done))
-        n += seg + 2 * ((seg + 31) // 32)
+        chunks = (seg + 31) // 32
+        n += (seg + 2 * chunks) if mode == "fused" else (2 * seg + chunks)
         done += seg
     return n
+
+
+def _node_launch_ms(node_ms, mode):
+    """Durations of the node-kernel launches of a ts_step_timed run (fused
+    steps launch it for the last step of each chunk of 32 only)."""
+    import numpy as np
+    if mode != "fused":
+        return node_ms
+    n = node_ms.size
+    return np.concatenate([node_ms[31::32], node_ms[-1:] if n % 32 else node_ms[:0]])
 
 
 def _workload(name):
@@ -166,6 +178,42 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_window(args):
+    """For profilers started with --profile-from-start off: steps the workload
+    (one scenario, or the config-3 batch) unprofiled to step S, then runs N
+    steps between cudaProfilerStart and cudaProfilerStop."""
+    import torch
+    from paper_cs_0105004_gb300 import transsim as T
+    from paper_cs_0105004_gb300.inputs import networks as N
+    S, n = (int(x) for x in args.profile_window.split(":"))
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    if args.workload == "config3":
+        scs = [N.config3_scenario(i) for i in range(args.scenarios)]
+        sims = [T.Simulation(sc, tile_words=args.tile_words) for sc in scs]
+        runner = T.Batch(len(sims))
+        runner.set_step_mode(STEP_MODES[args.step_mode])
+        runner.add_many(sims, S + n)
+        advance = lambda k: runner.step(k, stream)
+    else:
+        sc, _ = _workload(args.workload)
+        sim = T.Simulation(sc, tile_words=args.tile_words)
+        if args.load_balance:
+            sim.set_load_balance(args.load_balance, args.tile_vehicles)
+        sim.set_step_mode(STEP_MODES[args.step_mode])
+        sims = [sim]
+        advance = lambda k: sim.step(k, stream)
+    advance(S)
+    stream.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    advance(n)
+    stream.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    upd = sum(s.totals()["vehicle_updates"] for s in sims)
+    print(json.dumps({"profile_window": {"workload": args.workload, "first_step": S, "steps": n,
+                                         "vehicle_updates_to_end": upd}}), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_cs_0105004_gb300 import transsim as T
@@ -248,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
     # transfers (~20 B each) and insertions (~10 B each) of the step before it
     # (the node kernel does those of every 32nd step only)
     link_bytes = 10.0 * updates + 0.25 * C * steps_per_job + 20.0 * tot["transfers"] + 10.0 * tot["inserted"]
-    node_launch_ms = np.concatenate([node_ms[31::32], node_ms[-1:] if steps_per_job % 32 else node_ms[:0]])
+    node_launch_ms = _node_launch_ms(node_ms, args.step_mode)
     link_s = float(link_ms.sum()) / 1000.0
     node_s = float(node_launch_ms.sum()) / 1000.0
     peak, peak_kind = _peaks()
@@ -302,7 +350,7 @@ def run_ours(args, rank, world, local_rank):
                            "load_balance": {"every_steps": args.load_balance, "vehicles_per_tile": args.tile_vehicles},
                            "bit_exact_hash": str(tot["last_state_hash"])},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * _launches(steps_per_job, args.load_balance),
+                "gpu_launches": args.steps * _launches(steps_per_job, args.step_mode, args.load_balance),
                 "clocks": clocks, "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     sim.close()
@@ -358,7 +406,7 @@ def run_config3(args):
             "sequential": None if seq is None else {"value": seq.updates_per_s, "unit": METRIC,
                                                     "scenarios": args.seq_sample, "seconds": seq.seconds},
             "batched_over_sequential": None if seq is None else value / seq.updates_per_s,
-            "gpu_launches": args.steps * (_launches(steps) - 1 + args.scenarios),
+            "gpu_launches": args.steps * (_launches(steps, args.step_mode) - 1 + args.scenarios),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     for s_ in sims:
@@ -417,8 +465,8 @@ def run_empty(args):
             "roofline": {"bound": "hbm", "kernel": "link_kernel", "achieved": 0.25 * C / (link_us * 1e-6) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": 0.25 * C / (link_us * 1e-6) / 1e9 / peak,
                          "peak_source": src, "traffic": None, "avg_launch_us": link_us,
-                         "node_kernel_avg_launch_us": float(np.mean(nm[31::32])) * 1e3},
-            "gpu_launches": args.steps * _launches(steps),
+                         "node_kernel_avg_launch_us": float(np.mean(_node_launch_ms(nm, args.step_mode))) * 1e3},
+            "gpu_launches": args.steps * _launches(steps, args.step_mode),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     sim.close()
@@ -500,6 +548,8 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=1800)
     ap.add_argument("--ref-sample-steps", type=int, default=300)
     ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..128)")
+    ap.add_argument("--profile-window", default=None, metavar="S:N",
+                    help="step unprofiled to S, then run N steps inside cudaProfilerStart/Stop, and exit")
     ap.add_argument("--step-mode", default="auto", choices=list(STEP_MODES),
                     help="fused: one launch per step; split: link and node kernel per step")
     ap.add_argument("--load-balance", type=int, default=512, help="re-tile from the occupancy every N steps (0 = off)")
@@ -512,6 +562,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_window:
+        if rank == 0:
+            run_profile_window(args)
         return
     if args.workload == "config3":
         if rank == 0:

@@ -243,7 +243,7 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             for (uint32_t i = 0; i < g; ++i) {
                 launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0);
                 if (!fu || i + 1 == g)
-                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true);
+                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu);
             }
             launch_advance_kernel(d_table, capacity, g, cap_stream, true);
             CK(cudaStreamEndCapture(cap_stream, &graph));
@@ -851,7 +851,7 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
                 launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
-                    launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false);
+                    launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu);
                 cudaEventRecord(ev[e + 2], s);
             }
             launch_advance_kernel(w->d_table, w->capacity, g, s, false);

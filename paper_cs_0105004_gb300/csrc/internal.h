@@ -119,8 +119,10 @@ struct LinkTile {
 // previous step must have been completed by node_kernel
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl, bool xfer);
+// chunk_end: the pass completes the last step each scenario ran in the
+// chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl);
+                        cudaStream_t s, bool pdl, bool chunk_end);
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 int max_link_blocks();

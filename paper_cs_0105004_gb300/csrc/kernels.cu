@@ -808,12 +808,64 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
 
 // ------------------------------------------------------------------ node kernel
 
-// Completes the node transfers and departures of the last step a chunk ran
-// for each scenario (the link kernel does those of the other steps at the
-// start of the next step).  One thread per link m.
+// Node transfers and departures into link m (nd = nd_info[m]) at the end of
+// step `step`, on the state after that step's moves; acc gets the transfers,
+// insertions and the changes of active, buffered, sum of velocities, digest.
+__device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const uint4 &nd, unsigned long long step,
+                                          unsigned long long (&acc)[6]) {
+    const int nxt = (int)((step + 1ull) & 1ull);
+    uint32_t *occ = D.occ[nxt];
+    uint32_t *mov = D.mov[nxt];
+    uint4 *slots = D.slots[nxt];
+    int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
+    uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
+    // slots with next link m, and the cells 0 of m, are written by this thread only
+    const uint32_t fr = resolve_transfers(slots, nd, m, free_cell0(occ, nd), [&](uint32_t si, const uint4 &x,
+                                                                                  uint32_t qn) {
+        const uint32_t id = x.x & kIdMask, v = x.w & 0xFFu, ks = (x.w >> 8) & 3u;
+        const uint32_t w = nd.y + qn;  // column 0 of lane qn
+        occ[w] |= 1u;
+        if (v) mov[w] |= 1u;
+        vel[(size_t)w * 32u] = (int8_t)v;
+        vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
+        atomicAdd(&D.veh[id].x, 1u);
+        slots[si].x = kSlotEmpty;
+        acc[0] += 1;
+        acc[2] += 1;
+        acc[3] -= 1;
+        acc[4] += v;
+        acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+    });
+    run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn) {
+        const uint32_t w = nd.y + qn;
+        occ[w] |= 1u;
+        vel[(size_t)w * 32u] = 0;
+        vid[(size_t)w * 32u] = idw;
+        acc[1] += 1;
+        acc[2] += 1;
+        acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
+    });
+}
+
+// The step of a node pass at chunk position pos: per step (split steps) the
+// step itself if the scenario runs it; at a chunk's end (fused steps) the last
+// step the scenario ran in the chunk.  Returns false if there is none.
+__device__ __forceinline__ bool node_step(const ScenDev &D, uint32_t pos, bool chunk_end, unsigned long long &step) {
+    const unsigned long long base = D.ctrl->base, target = D.ctrl->target;
+    if (target <= base) return false;
+    step = base + pos;
+    if (step >= target) {
+        if (!chunk_end) return false;
+        step = target - 1ull;
+    }
+    return true;
+}
+
+// One thread per link m.
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
                                                             const uint4 *__restrict__ tiles,
-                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos) {
+                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
+                                                            uint32_t chunk_end) {
     __shared__ unsigned long long red[kNodeThreads / 32][6];
     const uint32_t n_tiles = *n_tiles_p;
     // transfers, insertions and the changes of active, buffered, sum of velocities, digest
@@ -829,11 +881,9 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
         if (D.ctrl == nullptr) continue;
         const uint32_t m = td.y + threadIdx.x;
         const uint4 nd = m < td.z ? D.nd_info[m] : make_uint4(0u, 0u, 0u, 0u);  // static
-        // constant within a captured chunk, like the link descriptors: the
-        // last step this scenario ran in the chunk
-        const unsigned long long base = D.ctrl->base, target = D.ctrl->target;
-        if (target <= base) continue;
-        const unsigned long long step = min(base + pos, target - 1ull);
+        // base and target are constant within a captured chunk
+        unsigned long long step;
+        if (!node_step(D, pos, chunk_end != 0u, step)) continue;
         if (!waited) {
             pdl_wait();
             waited = true;
@@ -843,40 +893,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
             if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
             cur_rec = rec;
         }
-        const int nxt = (int)((step + 1ull) & 1ull);
-        if (m < td.z) {
-            uint32_t *occ = D.occ[nxt];
-            uint32_t *mov = D.mov[nxt];
-            uint4 *slots = D.slots[nxt];
-            int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
-            uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
-            // slots with next link m are written by this thread only
-            const uint32_t fr = resolve_transfers(slots, nd, m, free_cell0(occ, nd), [&](uint32_t si, const uint4 &x,
-                                                                                          uint32_t qn) {
-                const uint32_t id = x.x & kIdMask, v = x.w & 0xFFu, ks = (x.w >> 8) & 3u;
-                const uint32_t w = nd.y + qn;  // column 0 of lane qn
-                occ[w] |= 1u;
-                if (v) mov[w] |= 1u;
-                vel[(size_t)w * 32u] = (int8_t)v;
-                vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
-                atomicAdd(&D.veh[id].x, 1u);
-                slots[si].x = kSlotEmpty;
-                acc[0] += 1;
-                acc[2] += 1;
-                acc[3] -= 1;
-                acc[4] += v;
-                acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
-            });
-            run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn) {
-                const uint32_t w = nd.y + qn;
-                occ[w] |= 1u;
-                vel[(size_t)w * 32u] = 0;
-                vid[(size_t)w * 32u] = idw;
-                acc[1] += 1;
-                acc[2] += 1;
-                acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
-            });
-        }
+        if (m < td.z) node_link(D, m, nd, step, acc);
     }
     if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
     span_mark((int)pos * 3 + 1, false);
@@ -970,8 +987,8 @@ void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint3
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl) {
-    launch_pdl(node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i);
+                        cudaStream_t s, bool pdl, bool chunk_end) {
+    launch_pdl(node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i, chunk_end ? 1u : 0u);
 }
 
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl) {

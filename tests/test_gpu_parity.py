@@ -176,11 +176,12 @@ def test_planar_network_window():
     run_parity(sc, 1200, chunk=400, state_every=400)
 
 
-def test_config1_first_window():
+@pytest.mark.parametrize("mode", [T.STEP_AUTO, T.STEP_FUSED])
+def test_config1_first_window(mode):
     # Portland-shaped network, full size, first 1,200 steps (the oracle's
     # share of the test); later steps are covered by the invariants test
     sc = N.config1()
-    run_parity(sc, 1200, chunk=400, state_every=1200)
+    run_parity(sc, 1200, chunk=400, state_every=1200, mode=mode)
 
 
 def test_invariants_hold_on_gpu_config1():

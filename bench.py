@@ -39,6 +39,11 @@ sys.path.insert(0, ROOT)
 METRIC = "vehicle-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
+# dram__bytes_read.sum + dram__bytes_write.sum of one link_kernel launch from
+# an ncu --set full capture (caches flushed) of config 1 at step 5,000
+# (--profile-window 5000:64).  Valid only while link_kernel is unchanged
+# since that capture.
+LINK_TRAFFIC_BYTES = {"config1": 4860160.0 + 2816.0}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -302,7 +307,8 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     achieved = link_bytes / link_s / 1e9
     roofline = {"bound": "hbm", "kernel": "link_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": args.traffic,
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": args.traffic if args.traffic is not None else LINK_TRAFFIC_BYTES.get(args.workload),
                 "avg_launch_us": 1e3 * float(link_ms.mean()),
                 "algorithmic_bytes_per_launch": link_bytes / steps_per_job,
                 "share_of_step_time": link_s / (link_s + node_s),

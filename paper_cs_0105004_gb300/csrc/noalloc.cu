@@ -25,7 +25,8 @@ namespace {
 
 constexpr uint32_t kNoAllocMaxCells = 1u << 17;  // cells per lane
 constexpr uint32_t kNoAllocMaxSteps = 1024;      // steps per call
-constexpr uint32_t kNoAllocMaxTiles = 132;  // 4096 columns in runs of at least 32
+constexpr uint32_t kNoAllocMaxTiles =  // 4096 columns in runs of kTileWords / lanes columns
+    (kNoAllocMaxCells / 32u + (uint32_t)(kTileWords / kMaxLanes) - 1u) / (uint32_t)(kTileWords / kMaxLanes);
 constexpr uint32_t kNoAllocMaxWords = kNoAllocMaxCells / 32u * (uint32_t)kMaxLanes;
 
 // Byte offsets inside the scratch array.

@@ -108,7 +108,7 @@ struct ts_ctx {
     ScenDev sd{};
     uint4 *d_lk_info = nullptr;
     uint2 *d_veh0 = nullptr;           // route starts, for resets
-    uint32_t *d_dep_head0 = nullptr;   // queue starts, for resets
+    uint2 *d_dep_head0 = nullptr;      // queue starts, for resets
     std::vector<std::pair<void *, size_t>> allocs, veh_allocs;
     World *own = nullptr;
     ts_batch *batch = nullptr;
@@ -443,7 +443,7 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
     b += 16ull * d->n_links * 2;                              // lk_info, nd_info
     b += words * (4 + 4 + 4 + 32 + 128) * 2;                  // occupancy, v>0, location, velocity, id (x2)
     b += 16ull * slots * 2 + 8ull * n_vehicles * 2 + 4ull * route_len;  // buffers (x2), vehicles, routes
-    b += 8ull * n_vehicles + 4ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
+    b += 8ull * n_vehicles + 8ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
     b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
     return b;
 }
@@ -577,6 +577,12 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     return TS_OK;
 }
 
+// Departure-queue head of link l at absolute queue index h: {h, departure
+// step of entry h, or ~0 when the queue is exhausted}.
+static uint2 queue_head(const ts_ctx *c, uint32_t l, uint32_t h) {
+    return make_uint2(h, h < c->dep_off[l + 1] ? c->depart[c->dep_ids[h]] : 0xFFFFFFFFu);
+}
+
 static ts_status upload_vehicles(ts_ctx *c) {
     free_list(c, c->veh_allocs);
     auto &A = c->veh_allocs;
@@ -588,8 +594,8 @@ static ts_status upload_vehicles(ts_ctx *c) {
     uint32_t *routes = alloc_in<uint32_t>(c, A, total, ok);
     uint32_t *dep_ids = alloc_in<uint32_t>(c, A, n, ok);
     uint32_t *dep_steps = alloc_in<uint32_t>(c, A, n, ok);
-    uint32_t *dep_head = alloc_in<uint32_t>(c, A, L, ok);
-    c->d_dep_head0 = alloc_in<uint32_t>(c, A, L, ok);
+    uint2 *dep_head = alloc_in<uint2>(c, A, L, ok);
+    c->d_dep_head0 = alloc_in<uint2>(c, A, L, ok);
     if (!ok) {
         free_list(c, A);
         return fail(TS_ERR_OOM, "device allocation failed");
@@ -621,8 +627,10 @@ static ts_status upload_vehicles(ts_ctx *c) {
     }
     if (total) CK(cudaMemcpy(routes, c->route_links.data(), 4ull * total, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(const_cast<uint4 *>(c->sd.nd_info), nd.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dep_head, c->dep_off.data(), 4ull * L, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_dep_head0, c->dep_off.data(), 4ull * L, cudaMemcpyHostToDevice));
+    std::vector<uint2> heads(L);
+    for (uint32_t l = 0; l < L; ++l) heads[l] = queue_head(c, l, c->dep_off[l]);
+    CK(cudaMemcpy(dep_head, heads.data(), 8ull * L, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_dep_head0, heads.data(), 8ull * L, cudaMemcpyHostToDevice));
     ScenDev &sd = c->sd;
     sd.veh = veh;
     sd.route_links = routes;
@@ -642,7 +650,7 @@ static ts_status reset_device_state(ts_ctx *c, cudaStream_t s) {
     }
     for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(sd.slots[b], 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1), s));
     if (c->n_veh) CK(cudaMemcpyAsync(sd.veh, c->d_veh0, 8ull * c->n_veh, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(sd.dep_head, c->d_dep_head0, 4ull * c->n_links, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(sd.dep_head, c->d_dep_head0, 8ull * c->n_links, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(sd.ctrl, 0, sizeof(Ctrl), s));
     CK(cudaMemsetAsync(sd.stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub, s));
     return TS_OK;
@@ -985,7 +993,8 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     if (st != TS_OK) return st;
     const int cur = (int)(h.base & 1ull);
     const size_t nw = c->n_words;
-    std::vector<uint32_t> occ(nw), loc(nw), vid0(nw * 32), vid1(nw * 32), head(c->n_links);
+    std::vector<uint32_t> occ(nw), loc(nw), vid0(nw * 32), vid1(nw * 32);
+    std::vector<uint2> head(c->n_links);
     std::vector<int8_t> vel0(nw * 32), vel1(nw * 32);
     std::vector<uint4> slots(c->n_slots);
     std::vector<uint2> veh(c->n_veh);
@@ -997,7 +1006,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
     CK(cudaMemcpy(vid1.data(), c->sd.vid[1], 4 * nw * 32, cudaMemcpyDeviceToHost));
     if (c->n_slots) CK(cudaMemcpy(slots.data(), c->sd.slots[cur], 16ull * c->n_slots, cudaMemcpyDeviceToHost));
     if (c->n_veh) CK(cudaMemcpy(veh.data(), c->sd.veh, 8ull * c->n_veh, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(head.data(), c->sd.dep_head, 4ull * c->n_links, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(head.data(), c->sd.dep_head, 8ull * c->n_links, cudaMemcpyDeviceToHost));
     for (uint64_t i = 0; i < c->n_lane_cells; ++i) {
         o->cell_id[i] = -1;
         o->cell_v[i] = 0;
@@ -1032,7 +1041,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
             }
     }
     for (uint32_t i = 0; i < c->n_veh; ++i) o->cursor[i] = veh[i].x - c->route_off[i];
-    for (uint32_t l = 0; l < c->n_links; ++l) o->dep_head[l] = head[l] - c->dep_off[l];
+    for (uint32_t l = 0; l < c->n_links; ++l) o->dep_head[l] = head[l].x - c->dep_off[l];
     o->step = h.base;
     o->arrived = h.arrived;
     o->inserted = h.inserted;
@@ -1126,7 +1135,9 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
         CK(cudaMemcpy(sd.slots[cur], slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
     }
     if (c->n_veh) CK(cudaMemcpy(sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(sd.dep_head, head.data(), 4ull * c->n_links, cudaMemcpyHostToDevice));
+    std::vector<uint2> heads(c->n_links);
+    for (uint32_t l = 0; l < c->n_links; ++l) heads[l] = queue_head(c, l, head[l]);
+    CK(cudaMemcpy(sd.dep_head, heads.data(), 8ull * c->n_links, cudaMemcpyHostToDevice));
     st = reset_ctrl(c, in->step, in->arrived, in->inserted, c->stream, n_active, n_buffered, sum_v, hash);
     if (st != TS_OK) return st;
     CK(cudaEventRecord(c->ev, c->stream));

@@ -94,7 +94,7 @@ struct ScenDev {
     const uint32_t *route_links;
     const uint32_t *dep_ids;      // id | last-link flag << 31, queue order
     const uint32_t *dep_steps;
-    uint32_t *dep_head;           // [n_links] absolute queue index
+    uint2 *dep_head;              // [n_links] absolute queue index of the head, its departure step (~0: none left)
     Ctrl *ctrl;                   // nullptr marks an unused table entry
     StatRec *stats;               // [kStatsRing * n_sub]
     uint32_t n_sub;               // sub-records per step (power of two)

@@ -171,21 +171,25 @@ __device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ 
 
 // Departures from parking onto link m after the transfers: the head of m's
 // queue enters the lowest free lane with v = 0 while lanes are free and its
-// departure step has come.  Calls insert(queue entry, lane); returns the new
-// queue head.
+// departure step has come.  The head's departure step is kept beside the
+// head index, so a link with nothing due costs one load.  Calls
+// insert(queue entry, lane).
 template <class F>
-__device__ __forceinline__ uint32_t run_departures(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
-                                                   uint32_t free_mask, F &&insert) {
-    uint32_t h = D.dep_head[m];
-    const uint32_t h0 = h, dep_end = nd.w;
-    while (h < dep_end && free_mask && D.dep_steps[h] <= t) {
+__device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
+                                               uint32_t free_mask, F &&insert) {
+    const uint2 hd = D.dep_head[m];
+    if (hd.y > t || !free_mask) return;  // y = ~0 once the queue is empty
+    const uint32_t dep_end = nd.w;
+    uint32_t h = hd.x, next;
+    do {
         const uint32_t qn = (uint32_t)(__ffs(free_mask) - 1);
         free_mask &= ~(1u << qn);
-        insert(D.dep_ids[h], qn);
+        const uint32_t idw = D.dep_ids[h];
         ++h;
-    }
-    if (h != h0) D.dep_head[m] = h;
-    return h;
+        next = h < dep_end ? D.dep_steps[h] : 0xFFFFFFFFu;
+        insert(idw, qn);
+    } while (next <= t && free_mask);
+    D.dep_head[m] = make_uint2(h, next);
 }
 
 // ------------------------------------------------------------------ link kernel

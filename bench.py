@@ -23,6 +23,7 @@ independent replica of the job; there is no exchange between GPUs.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -478,6 +479,44 @@ def run_empty(args):
     sim.close()
 
 
+def run_relax(args):
+    """Relaxation iterations (Sec. 1) on config 1: each iteration is one full
+    GPU run of 10,800 steps, then 10 % of the travellers are re-planned on
+    the run's link travel times (host Dijkstra)."""
+    import torch
+    from paper_cs_0105004_gb300 import relaxation as R
+    from paper_cs_0105004_gb300.inputs import networks as N
+    torch.cuda.set_device(0)
+    sc = N.config1()
+    if args.job_steps:
+        sc = dataclasses.replace(sc, steps=args.job_steps)
+    stream = torch.cuda.Stream()
+    run = lambda s: R.gpu_run(s, stream)
+    R.relax(sc, 1, run=run)  # warm-up: library load, graph capture
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    last, its = R.relax(sc, args.relax_iters, fraction=0.1, seed=0, run=run)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    sim_s = sum(it.run.seconds for it in its)
+    upd = sum(it.run.vehicle_updates for it in its)
+    line = {"metric": METRIC, "value": upd / sim_s, "unit": METRIC, "n_gpus": 1, "steps": args.relax_iters,
+            "warmup": 1, "ms_per_step": 1000.0 * sim_s / args.relax_iters, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "relaxation iterations on config 1 (20,024 links, 300,000 trips), "
+                                   "10 % re-planned per iteration on measured link travel times",
+                       "steps_per_run": sc.steps, "iterations": args.relax_iters},
+            "wall_seconds_per_iteration": wall / args.relax_iters,
+            "iterations": [{"gpu_s": round(it.run.seconds, 4), "plan_s": round(it.plan_seconds, 3),
+                            "vehicle_updates": it.run.vehicle_updates, "arrived": it.run.arrived,
+                            "mean_link_time": round(it.run.mean_link_time, 3), "replanned": it.replanned}
+                           for it in its],
+            "gpu_launches": args.relax_iters * _launches(sc.steps, "auto"),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_config4(args):
     """Serving: a Poisson stream of simulation jobs admitted by device-memory
     budget into a continuously running batch."""
@@ -536,7 +575,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty", "relax"])
     ap.add_argument("--scenarios", type=int, default=256, help="config3: batch members")
     ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
     ap.add_argument("--seq-sample", type=int, default=256, help="config3: members run one by one for comparison")
@@ -549,6 +588,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=128, help="config4: steps per batch step")
     ap.add_argument("--serve-compare", type=int, default=1, help="config4: also serve the stream one job at a time")
     ap.add_argument("--job-steps", type=int, default=None, help="steps per job (default: the config's)")
+    ap.add_argument("--relax-iters", type=int, default=4, help="relax: iterations")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1800)
@@ -584,6 +624,10 @@ def main():
     if args.workload == "empty":
         if rank == 0:
             run_empty(args)
+        return
+    if args.workload == "relax":
+        if rank == 0:
+            run_relax(args)
         return
     if world > 1:
         import torch

@@ -283,6 +283,20 @@ ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode);
  * the occupancy to the host.  Results do not depend on it. */
 ts_status ts_set_load_balance(ts_ctx *ctx, uint32_t every_steps, uint32_t vehicles_per_tile);
 
+/* Per-link travel times of completed link traversals since the last
+ * ts_load_vehicles / ts_reset / ts_write_state: sum[l] = sum over vehicles
+ * that left link l of (the step at whose end they left it by a node
+ * transfer, or the step in which they arrived, minus the step at whose end
+ * they entered it by a departure or a transfer), count[l] = their number.
+ * Vehicles written by ts_write_state count from the state's step.  These
+ * are the link costs that the re-planning between relaxation iterations
+ * (Sec. 1) feeds back into the routes.  sum and count: host arrays of
+ * n_links entries.  Between resets a link's sum must stay below 2^40 and
+ * its count below 2^24 (the device keeps both in one 64-bit word).  Waits
+ * for the context's queued work (at most timeout_ms; TS_ERR_TIMEOUT after
+ * that). */
+ts_status ts_read_link_times(ts_ctx *ctx, uint64_t *sum, uint64_t *count, uint32_t timeout_ms);
+
 /* Number of kernel launches one time step enqueues in FUSED mode (1: the
  * link kernel, which also completes the node transfers of the step before
  * it; SPLIT mode adds the node kernel: 2).  On top, every chunk of up to 32

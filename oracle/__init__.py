@@ -59,6 +59,7 @@ def lib():
         L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
         L.oracle_vehicle_term.restype = ctypes.c_uint64
         L.oracle_vehicle_term.argtypes = [ctypes.c_uint32] * 5
+        L.oracle_link_times.argtypes = [ctypes.c_void_p, u64p, u64p]
         _lib = L
     return _lib
 
@@ -148,3 +149,10 @@ class Oracle:
                                     _p(a[4], ctypes.c_uint32), _p(a[5], ctypes.c_uint32), _p(sc, ctypes.c_uint64))
         if rc != 0:
             raise ValueError("oracle rejected the state")
+
+    def link_times(self):
+        """Per-link travel-time sums and counts of completed traversals."""
+        tsum = np.zeros(self.n_links, np.uint64)
+        tcnt = np.zeros(self.n_links, np.uint64)
+        lib().oracle_link_times(self.h, _p(tsum, ctypes.c_uint64), _p(tcnt, ctypes.c_uint64))
+        return tsum, tcnt

@@ -37,6 +37,12 @@
  * B = cell<<16 | lane<<8 | v (a vehicle in a link-end buffer has cell =
  * link length); splitmix64 is the finaliser published by Steele, Lea and
  * Flood (OOPSLA 2014) applied to z + 0x9e3779b97f4a7c15.
+ *
+ * Link travel times (the input of the re-planning step of the relaxation
+ * iterations, Sec. 1): a vehicle that enters a link at the end of step t0
+ * (a departure or a node transfer) and leaves it at the end of step t1 (a
+ * node transfer to its next link) or arrives during step t1 adds t1 - t0 to
+ * that link's travel-time sum and 1 to its count.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -74,6 +80,8 @@ typedef struct oracle {
     uint8_t *status;     /* [n_veh] 0 not yet on the network, 1 on a link, 2 arrived */
     uint32_t *dep_head;  /* [n_links] queue entries already inserted */
     uint64_t step, arrived, inserted;
+    uint32_t *t_enter;   /* [n_veh] step at whose end the vehicle entered its current link */
+    uint64_t *lt_sum, *lt_cnt; /* [n_links] travel-time sums and counts of completed traversals */
     /* scratch copies of the cell array */
     int32_t *s_start, *s_lc;
     int32_t *buf_start;
@@ -182,6 +190,7 @@ void oracle_destroy(oracle *o) {
     free(o->lane_base); free(o->lane_link); free(o->cell_base); free(o->in_off); free(o->in_lane);
     free(o->depart); free(o->route_off); free(o->route); free(o->q_off); free(o->q_id);
     free(o->cell); free(o->buf); free(o->vel); free(o->cursor); free(o->status); free(o->dep_head);
+    free(o->t_enter); free(o->lt_sum); free(o->lt_cnt);
     free(o->s_start); free(o->s_lc); free(o->buf_start);
     free(o);
 }
@@ -248,7 +257,10 @@ oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, 
     o->buf = (int32_t *)malloc(4ull * o->n_lanes);
     o->buf_start = (int32_t *)malloc(4ull * o->n_lanes);
     o->dep_head = (uint32_t *)calloc(n_links, 4);
-    if (!o->cell || !o->s_start || !o->s_lc || !o->buf || !o->buf_start || !o->dep_head) goto fail;
+    o->lt_sum = (uint64_t *)calloc(n_links, 8);
+    o->lt_cnt = (uint64_t *)calloc(n_links, 8);
+    if (!o->cell || !o->s_start || !o->s_lc || !o->buf || !o->buf_start || !o->dep_head || !o->lt_sum || !o->lt_cnt)
+        goto fail;
     for (uint64_t i = 0; i < o->n_cells; i++) o->cell[i] = -1;
     for (uint32_t i = 0; i < o->n_lanes; i++) o->buf[i] = -1;
     return o;
@@ -269,10 +281,12 @@ int oracle_load_vehicles(oracle *o, uint32_t n, const uint32_t *depart, const ui
     o->route = (uint32_t *)malloc(4ull * (total ? total : 1));
     o->vel = (int32_t *)calloc(n ? n : 1, 4);
     o->cursor = (uint32_t *)calloc(n ? n : 1, 4);
+    o->t_enter = (uint32_t *)calloc(n ? n : 1, 4);
     o->status = (uint8_t *)calloc(n ? n : 1, 1);
     o->q_off = (uint32_t *)calloc((size_t)o->n_links + 1, 4);
     o->q_id = (uint32_t *)malloc(4ull * (n ? n : 1));
-    if (!o->depart || !o->route_off || !o->route || !o->vel || !o->cursor || !o->status || !o->q_off || !o->q_id)
+    if (!o->depart || !o->route_off || !o->route || !o->vel || !o->cursor || !o->t_enter || !o->status ||
+        !o->q_off || !o->q_id)
         return -1;
     memcpy(o->depart, depart, 4ull * n);
     memcpy(o->route_off, route_off, 4ull * (n + 1));
@@ -387,6 +401,8 @@ static void step_once(oracle *o, oracle_stats *st) {
                 } else if (is_last_link(o, id)) {
                     o->status[id] = 2;                           /* to parking     */
                     o->arrived++;
+                    o->lt_sum[l] += t - o->t_enter[id];
+                    o->lt_cnt[l]++;
                 } else {
                     uint32_t ln = o->lane_base[l] + k;
                     if (o->buf[ln] >= 0) abort();
@@ -421,6 +437,9 @@ static void step_once(oracle *o, oracle_stats *st) {
                     o->buf[ln] = -1;
                     o->cursor[id]++;
                     st->transfers++;
+                    o->lt_sum[l] += t - o->t_enter[id];
+                    o->lt_cnt[l]++;
+                    o->t_enter[id] = (uint32_t)t;
                     break;
                 }
             }
@@ -443,6 +462,7 @@ static void step_once(oracle *o, oracle_stats *st) {
                     o->vel[id] = 0;
                     o->cursor[id] = 0;
                     o->status[id] = 1;
+                    o->t_enter[id] = (uint32_t)t;
                     placed = 1;
                     break;
                 }
@@ -542,5 +562,16 @@ int oracle_set_state(oracle *o, const int32_t *cell_id, const int8_t *cell_v, co
             if (o->status[id] == 0) o->status[id] = 2;
         }
     o->step = scalars[0]; o->arrived = scalars[1]; o->inserted = scalars[2];
+    /* travel times restart: vehicles on the network count from the state's step */
+    for (uint32_t i = 0; i < o->n_veh; i++) o->t_enter[i] = (uint32_t)o->step;
+    memset(o->lt_sum, 0, 8ull * o->n_links);
+    memset(o->lt_cnt, 0, 8ull * o->n_links);
     return 0;
+}
+
+/* Travel-time sums and counts per link since creation or the last
+ * set_state. */
+void oracle_link_times(const oracle *o, uint64_t *sum, uint64_t *cnt) {
+    memcpy(sum, o->lt_sum, 8ull * o->n_links);
+    memcpy(cnt, o->lt_cnt, 8ull * o->n_links);
 }

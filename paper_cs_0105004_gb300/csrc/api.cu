@@ -108,6 +108,7 @@ struct ts_ctx {
     ScenDev sd{};
     uint4 *d_lk_info = nullptr;
     uint2 *d_veh0 = nullptr;           // route starts, for resets
+    unsigned long long *d_lt_tmp = nullptr;  // scratch of ts_read_link_times
     uint2 *d_dep_head0 = nullptr;      // queue starts, for resets
     std::vector<std::pair<void *, size_t>> allocs, veh_allocs;
     World *own = nullptr;
@@ -444,6 +445,7 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
     b += words * (4 + 4 + 4 + 32 + 128) * 2;                  // occupancy, v>0, location, velocity, id (x2)
     b += 16ull * slots * 2 + 8ull * n_vehicles * 2 + 4ull * route_len;  // buffers (x2), vehicles, routes
     b += 8ull * n_vehicles + 8ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
+    b += 4ull * n_vehicles + 16ull * d->n_links;              // link entry steps, link times (+ scratch)
     b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
     return b;
 }
@@ -536,6 +538,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     uint32_t *vid1 = alloc_in<uint32_t>(c.get(), A, (size_t)c->n_words * 32, ok);
     uint4 *slots0 = alloc_in<uint4>(c.get(), A, c->n_slots, ok);
     uint4 *slots1 = alloc_in<uint4>(c.get(), A, c->n_slots, ok);
+    unsigned long long *lt = alloc_in<unsigned long long>(c.get(), A, 2ull * L, ok);  // link times, scratch
     Ctrl *ctrl = alloc_in<Ctrl>(c.get(), A, 1, ok);
     StatRec *stats = alloc_in<StatRec>(c.get(), A, (size_t)kStatsRing * c->n_sub, ok);
     if (!ok) {
@@ -557,6 +560,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.vid[1] = vid1;
     sd.slots[0] = slots0;
     sd.slots[1] = slots1;
+    sd.link_time = lt;
+    c->d_lt_tmp = lt + L;
     sd.ctrl = ctrl;
     sd.stats = stats;
     sd.vmax = params->vmax;
@@ -571,6 +576,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     for (uint32_t *p : {occ0, occ1, mov0, mov1, loc0, loc1}) CK(cudaMemset(p, 0, 4ull * c->n_words));
     CK(cudaMemset(slots0, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(slots1, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
+    CK(cudaMemset(lt, 0, 16ull * L));
     CK(cudaMemset(ctrl, 0, sizeof(Ctrl)));
     CK(cudaMemset(stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub));
     *out = c.release();
@@ -591,6 +597,7 @@ static ts_status upload_vehicles(ts_ctx *c) {
     bool ok = true;
     uint2 *veh = alloc_in<uint2>(c, A, n, ok);
     c->d_veh0 = alloc_in<uint2>(c, A, n, ok);
+    uint32_t *enter = alloc_in<uint32_t>(c, A, n, ok);
     uint32_t *routes = alloc_in<uint32_t>(c, A, total, ok);
     uint32_t *dep_ids = alloc_in<uint32_t>(c, A, n, ok);
     uint32_t *dep_steps = alloc_in<uint32_t>(c, A, n, ok);
@@ -633,6 +640,8 @@ static ts_status upload_vehicles(ts_ctx *c) {
     CK(cudaMemcpy(c->d_dep_head0, heads.data(), 8ull * L, cudaMemcpyHostToDevice));
     ScenDev &sd = c->sd;
     sd.veh = veh;
+    sd.enter_step = enter;
+    if (n) CK(cudaMemset(enter, 0xFF, 4ull * n));  // nobody on the network
     sd.route_links = routes;
     sd.dep_ids = dep_ids;
     sd.dep_steps = dep_steps;
@@ -649,6 +658,8 @@ static ts_status reset_device_state(ts_ctx *c, cudaStream_t s) {
         CK(cudaMemsetAsync(sd.loc[b], 0, 4ull * c->n_words, s));
     }
     for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(sd.slots[b], 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1), s));
+    CK(cudaMemsetAsync(sd.link_time, 0, 8ull * c->n_links, s));
+    if (c->n_veh) CK(cudaMemsetAsync(sd.enter_step, 0xFF, 4ull * c->n_veh, s));  // nobody on the network
     if (c->n_veh) CK(cudaMemcpyAsync(sd.veh, c->d_veh0, 8ull * c->n_veh, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(sd.dep_head, c->d_dep_head0, 8ull * c->n_links, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(sd.ctrl, 0, sizeof(Ctrl), s));
@@ -971,6 +982,27 @@ ts_status ts_read_totals(ts_ctx *c, ts_totals *out, uint32_t timeout_ms) {
     return TS_OK;
 }
 
+ts_status ts_read_link_times(ts_ctx *c, uint64_t *sum, uint64_t *count, uint32_t timeout_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!sum || !count) return fail(TS_ERR_INVALID, "null output");
+    st = wait_ctx(c, timeout_ms);
+    if (st != TS_OK) return st;
+    Ctrl h;
+    st = read_ctrl(c, &h);  // reports device consistency failures
+    if (st != TS_OK) return st;
+    CK(cudaMemcpyAsync(c->d_lt_tmp, c->sd.link_time, 8ull * c->n_links, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->n_veh) launch_link_time_fix(c->sd, c->n_veh, c->d_lt_tmp, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(sum, c->d_lt_tmp, 8ull * c->n_links, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (uint32_t l = 0; l < c->n_links; ++l) {
+        count[l] = sum[l] >> 40;
+        sum[l] &= kLinkTimeOne - 1ull;
+    }
+    return TS_OK;
+}
+
 ts_status ts_state_sizes(const ts_ctx *c, uint64_t *cells, uint32_t *lanes, uint32_t *veh, uint32_t *links) {
     if (!c) return fail(TS_ERR_INVALID, "null context");
     if (cells) *cells = c->n_lane_cells;
@@ -1134,7 +1166,22 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
         CK(cudaMemset(sd.slots[cur ^ 1], 0xFF, 16ull * c->n_slots));
         CK(cudaMemcpy(sd.slots[cur], slots.data(), 16ull * c->n_slots, cudaMemcpyHostToDevice));
     }
-    if (c->n_veh) CK(cudaMemcpy(sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
+    if (c->n_veh) {
+        CK(cudaMemcpy(sd.veh, veh.data(), 8ull * c->n_veh, cudaMemcpyHostToDevice));
+        // travel times restart: vehicles on the network count from the state's
+        // step (entered then: - step on their link's sum)
+        std::vector<uint32_t> enter(c->n_veh, kNotOnLink);
+        std::vector<unsigned long long> lts(c->n_links, 0ull);
+        for (uint32_t i = 0; i < c->n_veh; ++i)
+            if (seen[i]) {
+                enter[i] = (uint32_t)in->step;
+                lts[c->route_links[veh[i].x]] -= in->step;
+            }
+        CK(cudaMemcpy(sd.enter_step, enter.data(), 4ull * c->n_veh, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(sd.link_time, lts.data(), 8ull * c->n_links, cudaMemcpyHostToDevice));
+    } else {
+        CK(cudaMemset(sd.link_time, 0, 8ull * c->n_links));
+    }
     std::vector<uint2> heads(c->n_links);
     for (uint32_t l = 0; l < c->n_links; ++l) heads[l] = queue_head(c, l, head[l]);
     CK(cudaMemcpy(sd.dep_head, heads.data(), 8ull * c->n_links, cudaMemcpyHostToDevice));

@@ -24,7 +24,18 @@
 //     slots[t&1] (which every tile may read to resolve node transfers) and
 //     each tile writes its own links' buffers into slots[(t+1)&1].
 //   * veh[n_vehicles]: {absolute index of the current route entry, end of the
-//     vehicle's route}.
+//     vehicle's route}; enter_step[n_vehicles]: the step at whose end it
+//     entered its current link (departure or node transfer), kNotOnLink
+//     before departure and after arrival.
+//   * link_time[n_links]: per link, in one 64-bit word updated by one
+//     atomic per event, the number of completed traversals times 2^40 plus
+//     the exit steps of completed traversals minus the entry steps of all
+//     traversals begun (mod 2^64); ts_read_link_times adds back the entry
+//     steps of the vehicles still on each link, which leaves count << 40 |
+//     travel-time sum, the input of re-planning between relaxation
+//     iterations.  Neither the entry nor the exit reads any per-vehicle
+//     value.  Between resets a link's sum stays below 2^40 and its count
+//     below 2^24.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -46,6 +57,8 @@ constexpr int kListCap = kTileSmemWords * 32;  // every cell of a tile can hold 
 constexpr uint32_t kStatsRing = 4096;         // steps of statistics kept on the device
 constexpr uint32_t kChunk = 32;               // steps per captured graph
 constexpr uint32_t kNoLink = 0xFFFFFFFFu;
+constexpr uint32_t kNotOnLink = 0xFFFFFFFFu;  // enter_step of a vehicle not (or no longer) on the network
+constexpr unsigned long long kLinkTimeOne = 1ull << 40;  // one completed traversal in link_time
 
 struct Ctrl {
     unsigned long long base;      // steps completed (first step of the next chunk)
@@ -91,6 +104,8 @@ struct ScenDev {
     uint32_t *vid[2];
     uint4 *slots[2];
     uint2 *veh;
+    uint32_t *enter_step;         // [n_vehicles] step at whose end the vehicle entered its current link
+    unsigned long long *link_time;  // [n_links] traversal count << 40 | travel-time sum (before correction)
     const uint32_t *route_links;
     const uint32_t *dep_ids;      // id | last-link flag << 31, queue order
     const uint32_t *dep_steps;
@@ -125,6 +140,8 @@ void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t
                         cudaStream_t s, bool pdl, bool chunk_end);
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
+// adds the entry steps of vehicles on the network to out (a copy of link_time)
+void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s);
 int max_link_blocks();
 int max_node_blocks();
 // Sets the thread-local message returned by ts_last_error.

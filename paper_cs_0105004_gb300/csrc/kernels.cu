@@ -132,18 +132,28 @@ __device__ __forceinline__ uint32_t free_cell0(const uint32_t *__restrict__ occ,
 
 constexpr int kSlotPrefetch = 8;  // buffers of a node loaded together before resolving
 
+// Loads the first kSlotPrefetch buffers of a node's slot group together.
+__device__ __forceinline__ void prefetch_slots(const uint4 *__restrict__ slots, uint32_t slot_lo, uint32_t cnt,
+                                               uint4 (&pre)[kSlotPrefetch]) {
+#pragma unroll
+    for (int s = 0; s < kSlotPrefetch; ++s)
+        pre[s] = (uint32_t)s < cnt ? slots[slot_lo + s] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+}
+
 // Node transfer into link m at the end of a step (Sec. 3): the buffered
 // vehicles at m's upstream node whose next link is m, in slot (priority)
 // order, each take cell 0 of the preferred lane min(k, lanes(m)-1) if it is
-// free, else of the lowest free lane, else stay buffered.  nd = nd_info[m],
+// free, else of the lowest free lane, else stay buffered.  The node's slot
+// group is [slot_lo, slot_lo + cnt), its first buffers prefetched in pre;
 // free_mask from free_cell0 (after the step's moves).  Calls
 // place(slot index, slot, lane) for every placement and returns the lanes
 // still free (for departures).  Any number of threads may evaluate the same
 // m on the same inputs and get the same placements.
 template <class F>
-__device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ slots, const uint4 &nd, uint32_t m,
-                                                      uint32_t free_mask, F &&place) {
-    const uint32_t slot_lo = nd.x, cnt = nd.z & 0xFFu, lanes = (nd.z >> 8) & 0xFFu;
+__device__ __forceinline__ uint32_t resolve_prefetched(const uint4 (&pre)[kSlotPrefetch],
+                                                       const uint4 *__restrict__ slots, uint32_t slot_lo,
+                                                       uint32_t cnt, uint32_t m, uint32_t lanes, uint32_t free_mask,
+                                                       F &&place) {
     auto visit = [&](const uint4 &x, uint32_t si) {
         if (x.x == kSlotEmpty || x.y != m || !free_mask) return;
         const uint32_t ks = (x.w >> 8) & 3u;
@@ -159,14 +169,20 @@ __device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ 
         free_mask &= ~(1u << qn);
         place(si, x, qn);
     };
-    uint4 pre[kSlotPrefetch];
-#pragma unroll
-    for (int s = 0; s < kSlotPrefetch; ++s)
-        pre[s] = (uint32_t)s < cnt ? slots[slot_lo + s] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
 #pragma unroll
     for (int s = 0; s < kSlotPrefetch; ++s) visit(pre[s], slot_lo + (uint32_t)s);
     for (uint32_t s = kSlotPrefetch; s < cnt && free_mask; ++s) visit(slots[slot_lo + s], slot_lo + s);
     return free_mask;
+}
+
+// The same for link m with nd = nd_info[m] (first slot of its upstream node,
+// word of its column 0, slot count | lanes << 8).
+template <class F>
+__device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ slots, const uint4 &nd, uint32_t m,
+                                                      uint32_t free_mask, F &&place) {
+    uint4 pre[kSlotPrefetch];
+    prefetch_slots(slots, nd.x, nd.z & 0xFFu, pre);
+    return resolve_prefetched(pre, slots, nd.x, nd.z & 0xFFu, m, (nd.z >> 8) & 0xFFu, free_mask, place);
 }
 
 // Departures from parking onto link m after the transfers: the head of m's
@@ -314,6 +330,9 @@ __device__ __noinline__ uint32_t link_buffers_phase(LinkSmem &S, const ScenDev &
             vel[pc] = (int8_t)v;
             vid[pc] = x.x;  // id with the last-link flag of l
             atomicAdd(&D.veh[id].x, 1u);
+            atomicAdd(&D.link_time[x.z], kLinkTimeOne + (t - 1u));
+            atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
+            D.enter_step[id] = t - 1u;
             acc2[0] += 1;
             acc2[2] += 1;
             acc2[3] -= 1;
@@ -325,6 +344,8 @@ __device__ __noinline__ uint32_t link_buffers_phase(LinkSmem &S, const ScenDev &
             const size_t pc = (size_t)(nd.y + qn) * 32u;
             vel[pc] = 0;
             vid[pc] = idw;
+            atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
+            D.enter_step[idw & kIdMask] = t - 1u;
             acc2[1] += 1;
             acc2[2] += 1;
             acc2[5] += vehicle_term(idw & kIdMask, l, qn, 0u, 0u);
@@ -736,6 +757,9 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                     } else if (last) {
                         acc[2] += 1;  // leaves to parking
                         acc[3] -= 1;
+                        // travel time: + the exit step here, - the entry step at entry
+                        atomicAdd(&D.link_time[lid], kLinkTimeOne + t);
+                        D.enter_step[id] = kNotOnLink;
                         acc[5] -= v0;
                         acc_hash -= old_term;
                     } else {
@@ -834,6 +858,10 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
         vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
         atomicAdd(&D.veh[id].x, 1u);
         slots[si].x = kSlotEmpty;
+        // travel times: + the exit step on the link left, - the entry step on m
+        atomicAdd(&D.link_time[x.z], kLinkTimeOne + step);
+        atomicAdd(&D.link_time[m], 0ull - step);
+        D.enter_step[id] = (uint32_t)step;
         acc[0] += 1;
         acc[2] += 1;
         acc[3] -= 1;
@@ -845,6 +873,8 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
         occ[w] |= 1u;
         vel[(size_t)w * 32u] = 0;
         vid[(size_t)w * 32u] = idw;
+        atomicAdd(&D.link_time[m], 0ull - step);
+        D.enter_step[idw & kIdMask] = (uint32_t)step;
         acc[1] += 1;
         acc[2] += 1;
         acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
@@ -901,6 +931,27 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
     }
     if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
     span_mark((int)pos * 3 + 1, false);
+}
+
+// ------------------------------------------------------------------ link travel times
+
+// link_time holds, per link, the exit steps of completed traversals minus
+// the entry steps of every traversal begun (plus the count of completed ones
+// times kLinkTimeOne); adding back the entry steps of the vehicles still on
+// each link (in a cell or its buffer) leaves the travel times of the
+// completed ones.  out starts as a copy of link_time.
+__global__ void link_time_fix_kernel(const ScenDev D, uint32_t n_veh, unsigned long long *out) {
+    for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n_veh; id += gridDim.x * blockDim.x) {
+        const uint32_t s = D.enter_step[id];
+        if (s == kNotOnLink) continue;
+        atomicAdd(out + D.route_links[D.veh[id].x], (unsigned long long)s);
+    }
+}
+
+void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s) {
+    const uint32_t blocks = (n_veh + 255u) / 256u;
+    const int grid = blocks == 0u ? 1 : (blocks > 4096u ? 4096 : (int)blocks);
+    link_time_fix_kernel<<<grid, 256, 0, s>>>(sd, n_veh, out);
 }
 
 // ------------------------------------------------------------------ chunk close

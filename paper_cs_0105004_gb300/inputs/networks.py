@@ -267,8 +267,10 @@ def _ptr(a, t):
     return a.ctypes.data_as(ctypes.POINTER(t))
 
 
-def build_routes(net: Network, orig: np.ndarray, dest: np.ndarray, threads: Optional[int] = None):
-    """Shortest path (in cells) from orig[i] to dest[i] as link lists.
+def build_routes(net: Network, orig: np.ndarray, dest: np.ndarray, threads: Optional[int] = None,
+                 weights: Optional[np.ndarray] = None):
+    """Shortest path from orig[i] to dest[i] as link lists, under integer link
+    weights (default: the link length in cells).
 
     Ties between equally short paths go to the predecessor with the
     smaller node id, which makes every route unique."""
@@ -282,7 +284,7 @@ def build_routes(net: Network, orig: np.ndarray, dest: np.ndarray, threads: Opti
     grp_off = np.append(starts, n).astype(np.uint64)
     lf = np.ascontiguousarray(net.link_from, np.uint32)
     lt = np.ascontiguousarray(net.link_to, np.uint32)
-    w = np.ascontiguousarray(net.link_cells, np.uint32)
+    w = np.ascontiguousarray(net.link_cells if weights is None else weights, np.uint32)
     off = np.zeros(n + 1, np.uint64)
     out = ctypes.POINTER(ctypes.c_uint32)()
     if threads is None:

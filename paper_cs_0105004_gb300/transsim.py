@@ -103,6 +103,7 @@ _API = {
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_read_link_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
     "ts_batch_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
     "ts_set_load_balance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
@@ -232,6 +233,14 @@ class Simulation:
 
     def set_tile_words(self, words: int):
         _check(lib().ts_set_tile_words(self.h, words))
+
+    def link_times(self, timeout_ms: int = 600000):
+        """Per-link travel-time sums and counts of completed traversals (uint64 arrays)."""
+        tsum = np.zeros(self.n_links, np.uint64)
+        tcnt = np.zeros(self.n_links, np.uint64)
+        _check(lib().ts_read_link_times(self.h, tsum.ctypes.data_as(ctypes.c_void_p),
+                                        tcnt.ctypes.data_as(ctypes.c_void_p), timeout_ms))
+        return tsum, tcnt
 
     def set_step_mode(self, mode: int):
         """STEP_AUTO, STEP_FUSED or STEP_SPLIT; results do not depend on it."""

@@ -229,3 +229,24 @@ def test_batch_equals_alone(mode):
     full.step(400)
     _cmp_stats(sims[2].stats_range(250, 150), full.stats_range(250, 150), "resumed member")
     b.close()
+
+
+# ------------------------------------------------------------------ link travel times
+
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_link_travel_times_match_oracle(mode):
+    for sc in (N.config0(), N.small_grid_scenario(4, 3, 15, 500, 200, 800, gen_seed=3, seed=22)):
+        sim = T.Simulation(sc)
+        sim.set_step_mode(mode)
+        orc = oracle.Oracle(sc)
+        for n in (500, sc.steps - 500):   # chunk boundaries inside captured chunks
+            sim.step(n)
+            orc.step(n)
+            g, o = sim.link_times(), orc.link_times()
+            assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1]), sc.name
+        sim.reset()
+        sim.step(100)
+        orc2 = oracle.Oracle(sc)
+        orc2.step(100)
+        assert np.array_equal(sim.link_times()[0], orc2.link_times()[0]), "after reset"
+        sim.close()

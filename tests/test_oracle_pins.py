@@ -273,3 +273,33 @@ def test_oracle_matches_naive_restatement_on_rings():
             ci, cv, _, _ = b.state(sc.net)
             st = o.get_state()
             assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
+
+
+# ------------------------------------------------------------------ link travel times
+
+def test_link_travel_times_by_hand():
+    # The two-link trip of the transfer test: it enters link 0 at the end of
+    # step 0 (departure), crosses to link 1 at the end of step 5 and arrives
+    # in step 8: link 0 took 5 steps, link 1 took 3.
+    sc = make_scenario([(0, 1, 12, 1), (1, 2, 12, 1)], 3, [[0, 1]], [0], p=0)
+    o = oracle.Oracle(sc)
+    o.step(10)
+    tsum, tcnt = o.link_times()
+    assert tsum.tolist() == [5, 3] and tcnt.tolist() == [1, 1]
+    # one 12-cell link: cells 0,1,3,6,10 after steps 0..4, arrival in step 5
+    sc = make_scenario([(0, 1, 12, 1)], 2, [[0]], [0], p=0)
+    o = oracle.Oracle(sc)
+    o.step(6)
+    assert [int(x) for x in o.link_times()[0]] == [5]
+
+
+def test_link_travel_time_counts_equal_transfers_plus_arrivals():
+    sc = N.small_grid_scenario(4, 2, 25, n_trips=400, window=200, steps=900, gen_seed=3, seed=5)
+    o = oracle.Oracle(sc)
+    st = o.step(900)
+    tsum, tcnt = o.link_times()
+    assert int(tcnt.sum()) == int(st["transfers"].sum()) + int(st["arrived"][-1])
+    # a traversal lasts at least one step, and the first link of a trip is
+    # entered only at its departure step or later
+    assert np.all(tsum >= tcnt)
+    assert int(tcnt.sum()) > 0

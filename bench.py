@@ -328,6 +328,9 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.e2e_jobs + 1):
             t0 = time.perf_counter()
             s2 = T.Simulation(sc)
+            if args.load_balance:
+                s2.set_load_balance(args.load_balance, args.tile_vehicles)
+            s2.set_step_mode(STEP_MODES[args.step_mode])
             s2.step(steps_per_job)
             t2 = s2.totals()
             s2.close()

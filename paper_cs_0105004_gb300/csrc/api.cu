@@ -103,7 +103,8 @@ struct ts_ctx {
     // vehicles
     bool loaded = false;
     uint32_t n_veh = 0;
-    std::vector<uint32_t> route_off, route_links, depart, depart_sorted, dep_off, dep_ids;
+    std::vector<uint32_t> route_off, depart, depart_sorted, dep_off, dep_ids;
+    std::vector<uint32_t> route_links;  // host copy, fetched from the device when ts_write_state needs it
     // device
     ScenDev sd{};
     uint4 *d_lk_info = nullptr;
@@ -589,7 +590,7 @@ static uint2 queue_head(const ts_ctx *c, uint32_t l, uint32_t h) {
     return make_uint2(h, h < c->dep_off[l + 1] ? c->depart[c->dep_ids[h]] : 0xFFFFFFFFu);
 }
 
-static ts_status upload_vehicles(ts_ctx *c) {
+static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
     free_list(c, c->veh_allocs);
     auto &A = c->veh_allocs;
     const uint32_t n = c->n_veh, L = c->n_links;
@@ -632,7 +633,7 @@ static ts_status upload_vehicles(ts_ctx *c) {
         CK(cudaMemcpy(dep_ids, ids.data(), 4ull * n, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(dep_steps, steps.data(), 4ull * n, cudaMemcpyHostToDevice));
     }
-    if (total) CK(cudaMemcpy(routes, c->route_links.data(), 4ull * total, cudaMemcpyHostToDevice));
+    if (total) CK(cudaMemcpy(routes, links, 4ull * total, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(const_cast<uint4 *>(c->sd.nd_info), nd.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
     std::vector<uint2> heads(L);
     for (uint32_t l = 0; l < L; ++l) heads[l] = queue_head(c, l, c->dep_off[l]);
@@ -687,35 +688,57 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
     if (n && (!dep || !off || !links)) return fail(TS_ERR_INVALID, "null vehicle array");
     std::vector<uint32_t> ro(off, off + n + 1);
     if (ro[0] != 0) return fail(TS_ERR_INVALID, "route offsets must start at 0");
-    for (uint32_t i = 0; i < n; ++i) {
-        const uint32_t a = ro[i], b = ro[i + 1];
-        if (b <= a) return fail(TS_ERR_INVALID, "empty or decreasing route");
-        for (uint32_t j = a; j < b; ++j) {
-            const uint32_t l = links[j];
-            if (l >= c->n_links) return fail(TS_ERR_INVALID, "route link out of range");
-            if (c->ring[l] && b - a != 1) return fail(TS_ERR_INVALID, "a ring link must be the whole route");
-            if (j + 1 < b && c->to[l] != c->from[links[j + 1]]) return fail(TS_ERR_INVALID, "route is not connected");
+    for (uint32_t i = 0; i < n; ++i)
+        if (ro[i + 1] <= ro[i]) return fail(TS_ERR_INVALID, "empty or decreasing route");
+    // every route entry, on host threads: link in range, connected to the
+    // next entry, a ring link only as a whole route
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const uint32_t nt = std::max(1u, std::min(hw ? hw : 1u, 16u));
+        std::vector<int> bad(nt, 0);
+        auto check = [&](uint32_t t) {
+            for (uint32_t i = (uint32_t)((uint64_t)n * t / nt); i < (uint32_t)((uint64_t)n * (t + 1) / nt); ++i) {
+                const uint32_t a = ro[i], b = ro[i + 1];
+                for (uint32_t j = a; j < b; ++j) {
+                    const uint32_t l = links[j];
+                    if (l >= c->n_links) { bad[t] = 1; return; }
+                    if (c->ring[l] && b - a != 1) { bad[t] = 2; return; }
+                    if (j + 1 < b && (links[j + 1] >= c->n_links || c->to[l] != c->from[links[j + 1]])) {
+                        bad[t] = 3;
+                        return;
+                    }
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (uint32_t t = 1; t < nt; ++t) pool.emplace_back(check, t);
+        check(0);
+        for (auto &th : pool) th.join();
+        for (int b : bad) {
+            if (b == 1) return fail(TS_ERR_INVALID, "route link out of range");
+            if (b == 2) return fail(TS_ERR_INVALID, "a ring link must be the whole route");
+            if (b == 3) return fail(TS_ERR_INVALID, "route is not connected");
         }
     }
     c->n_veh = n;
     c->route_off = std::move(ro);
-    c->route_links.assign(links, links + c->route_off[n]);
+    c->route_links.clear();
     c->depart.assign(dep, dep + n);
     c->depart_sorted = c->depart;
     std::sort(c->depart_sorted.begin(), c->depart_sorted.end());
     // departure queues: per first link, ordered by (departure step, id)
     c->dep_off.assign(c->n_links + 1, 0);
-    for (uint32_t i = 0; i < n; ++i) c->dep_off[c->route_links[c->route_off[i]] + 1]++;
+    for (uint32_t i = 0; i < n; ++i) c->dep_off[links[c->route_off[i]] + 1]++;
     for (uint32_t l = 0; l < c->n_links; ++l) c->dep_off[l + 1] += c->dep_off[l];
     c->dep_ids.resize(n);
     {
         std::vector<uint32_t> fill(c->dep_off.begin(), c->dep_off.end() - 1);
-        for (uint32_t i = 0; i < n; ++i) c->dep_ids[fill[c->route_links[c->route_off[i]]]++] = i;
+        for (uint32_t i = 0; i < n; ++i) c->dep_ids[fill[links[c->route_off[i]]]++] = i;
         for (uint32_t l = 0; l < c->n_links; ++l)
             std::stable_sort(c->dep_ids.begin() + c->dep_off[l], c->dep_ids.begin() + c->dep_off[l + 1],
                              [&](uint32_t a, uint32_t b) { return c->depart[a] < c->depart[b]; });
     }
-    st = upload_vehicles(c);
+    st = upload_vehicles(c, links);
     if (st != TS_OK) return st;
     st = reset_device_state(c, c->stream);
     if (st != TS_OK) return st;
@@ -1089,6 +1112,12 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
         return fail(TS_ERR_INVALID, "null state array");
     st = wait_ctx(c, 60000);
     if (st != TS_OK) return st;
+    if (c->route_links.size() != c->route_off[c->n_veh]) {  // host copy of the routes, once
+        c->route_links.resize(c->route_off[c->n_veh]);
+        if (!c->route_links.empty())
+            CK(cudaMemcpy(c->route_links.data(), c->sd.route_links, 4ull * c->route_links.size(),
+                          cudaMemcpyDeviceToHost));
+    }
     const uint32_t vmax = c->params.vmax;
     const size_t nw = c->n_words;
     std::vector<uint32_t> occ(nw, 0), mov(nw, 0), vid(nw * 32, 0);

@@ -250,3 +250,17 @@ def test_link_travel_times_match_oracle(mode):
         orc2.step(100)
         assert np.array_equal(sim.link_times()[0], orc2.link_times()[0]), "after reset"
         sim.close()
+
+
+# ------------------------------------------------------------------ input validation
+
+def test_malformed_routes_are_rejected():
+    links = [(0, 1, 12, 1), (1, 2, 12, 1), (2, 0, 12, 1), (0, 0, 64, 1, 1)]  # the last one is a ring
+    good = make_scenario(links, 3, [[0, 1]], [0])
+    T.Simulation(good).close()
+    for routes in ([[0, 2]],        # link 0 ends at node 1, link 2 starts at node 2
+                   [[0, 7]],        # no link 7
+                   [[3, 3]]):       # a ring link must be the whole route
+        sc = make_scenario(links, 3, routes, [0])
+        with pytest.raises(T.TsError, match="INVALID"):
+            T.Simulation(sc)

@@ -44,7 +44,7 @@ STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
 # an ncu --set full capture (caches flushed) of config 1 at step 5,000
 # (--profile-window 5000:64).  Valid only while link_kernel is unchanged
 # since that capture.
-LINK_TRAFFIC_BYTES = {"config1": 4860160.0 + 2816.0}
+LINK_TRAFFIC_BYTES = {"config1": 4866816.0 + 2560.0}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -366,6 +366,35 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
 
 
+def _oracle_grid_sample(i, steps):
+    """Worker of the all-cores CPU baseline: the oracle, one thread, on the
+    first `steps` steps of batch member i."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_cs_0105004_gb300.inputs import networks as N
+    sc = N.config3_scenario(i)
+    orc = oracle.Oracle(sc)
+    t0 = time.perf_counter()
+    st = orc.step(steps)
+    dt = time.perf_counter() - t0
+    orc.close()
+    return int(st["vehicle_updates"].sum()), dt
+
+
+def _cpu_baseline_grids(n_members, steps):
+    """The oracle as it stands on the host's cores: one process per core, each
+    on one batch member (independent scenarios), processes started by spawn."""
+    import multiprocessing as mp
+    cores = max(1, min(os.cpu_count() or 1, n_members))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_grid_sample, [(i, steps) for i in range(cores)])
+    upd = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": upd / wall, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"config-3 members 0..{cores - 1}, steps 0..{steps - 1} each, one oracle process per core "
+                      f"(spawned), {upd} vehicle updates, slowest process {wall:.1f} s"}
+
+
 def run_config3(args):
     """Batching: 256 independent grid scenarios in one launch set per phase,
     against the same scenarios run one after another."""
@@ -416,6 +445,7 @@ def run_config3(args):
             "sequential": None if seq is None else {"value": seq.updates_per_s, "unit": METRIC,
                                                     "scenarios": args.seq_sample, "seconds": seq.seconds},
             "batched_over_sequential": None if seq is None else value / seq.updates_per_s,
+            "cpu_baseline": None if args.no_cpu_baseline else _cpu_baseline_grids(args.scenarios, 600),
             "gpu_launches": args.steps * (_launches(steps, args.step_mode) - 1 + args.scenarios),
             "clocks": clocks}
     print(json.dumps(line), flush=True)

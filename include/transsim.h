@@ -89,6 +89,15 @@ typedef struct {
     uint32_t n_nodes, n_links;
     const uint32_t *link_from, *link_to, *link_cells, *link_lanes;
     const uint8_t *link_ring;
+    /* Optional (NULL: no signals): [3 * n_links] = per link (cycle, green,
+     * offset), all below 2^16, green <= cycle.  A signal at the end of link l
+     * (Sec. 3: a virtual vehicle of maximum velocity zero at the end of every
+     * lane while the light is red): the lane ends are green at step t iff
+     * (t + offset) mod cycle < green; cycle 0 = no signal.  While red, the
+     * gap to the lane end counts no extra cell and no vehicle reaches the end
+     * (neither the link-end buffer nor parking); a vehicle already in the
+     * buffer crosses the node as usual. */
+    const uint32_t *link_signal;
 } ts_network_desc;
 
 /* Statistics of the state after step `step` (0-based).  active: vehicles

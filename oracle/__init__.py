@@ -40,7 +40,7 @@ def lib():
         P = ctypes.POINTER
         u32p, u64p, i32p, i8p, u8p = P(ctypes.c_uint32), P(ctypes.c_uint64), P(ctypes.c_int32), P(ctypes.c_int8), P(ctypes.c_uint8)
         L.oracle_create.restype = ctypes.c_void_p
-        L.oracle_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, u32p, u32p, u8p,
+        L.oracle_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, u32p, u32p, u8p, u32p,
                                     ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
         L.oracle_load_vehicles.restype = ctypes.c_int
@@ -93,9 +93,12 @@ class Oracle:
         self._keep = [np.ascontiguousarray(a, np.uint32) for a in
                       (net.link_from, net.link_to, net.link_cells, net.link_lanes)]
         ring = np.ascontiguousarray(net.link_ring, np.uint8)
+        sig = getattr(net, "link_signal", None)
+        self._sig = None if sig is None else np.ascontiguousarray(sig, np.uint32).reshape(-1)
         self.h = L.oracle_create(net.n_nodes, net.n_links, *[_p(a, ctypes.c_uint32) for a in self._keep],
-                                 _p(ring, ctypes.c_uint8), scenario.vmax, scenario.p_threshold,
-                                 scenario.seed, scenario.lane_change)
+                                 _p(ring, ctypes.c_uint8),
+                                 _p(self._sig, ctypes.c_uint32) if self._sig is not None else None,
+                                 scenario.vmax, scenario.p_threshold, scenario.seed, scenario.lane_change)
         if not self.h:
             raise ValueError("oracle rejected the network")
         dep = np.ascontiguousarray(dem.depart_step, np.uint32)

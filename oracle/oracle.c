@@ -38,6 +38,12 @@
  * link length); splitmix64 is the finaliser published by Steele, Lea and
  * Flood (OOPSLA 2014) applied to z + 0x9e3779b97f4a7c15.
  *
+ * Traffic signals (Sec. 3): while the light at the end of link l is red, a
+ * virtual vehicle of maximum velocity zero stands at the end of each of
+ * its lanes, so the gap there counts no extra cell and no vehicle reaches
+ * the end; l's lanes are green at step t iff (t + offset) mod cycle < green
+ * (cycle 0: no signal).  A vehicle already in the link-end buffer crosses.
+ *
  * Link travel times (the input of the re-planning step of the relaxation
  * iterations, Sec. 1): a vehicle that enters a link at the end of step t0
  * (a departure or a node transfer) and leaves it at the end of step t1 (a
@@ -61,6 +67,8 @@ typedef struct oracle {
     uint64_t n_cells;
     uint32_t *from, *to, *cells, *lanes;
     uint8_t *ring;
+    uint32_t *sig;        /* [3 * n_links] signal cycle, green, offset (all 0: none) */
+    uint64_t t_now;       /* step being computed (for the signals)        */
     uint32_t *lane_base;  /* first canonical lane of each link            */
     uint32_t *lane_link;  /* link of each canonical lane                  */
     uint64_t *cell_base;  /* first canonical cell of each canonical lane  */
@@ -141,10 +149,17 @@ static int is_last_link(const oracle *o, int32_t id) {
     return o->cursor[id] + 1 == o->route_off[id + 1] - o->route_off[id];
 }
 
+static int is_green(const oracle *o, uint32_t l) {
+    uint32_t cycle = o->sig[3 * l], green = o->sig[3 * l + 1], offset = o->sig[3 * l + 2];
+    if (cycle == 0) return 1;
+    return (o->t_now + offset) % cycle < green;
+}
+
 /* Free cells ahead of (l,k,x) in state S, at most vmax (Sec. 3 rule (ii);
  * Sec. 4: interaction range 5 cells).  There is no look-ahead across a
- * node; at the link end the gap counts one more cell when the lane's
- * link-end buffer is free or this is the vehicle's last link. */
+ * node; at the link end the gap counts one more cell when the light there
+ * is green and the lane's link-end buffer is free or this is the vehicle's
+ * last link. */
 static uint32_t gap_ahead(const oracle *o, const int32_t *S, const int32_t *buf, uint32_t l, uint32_t k,
                           uint32_t x, int32_t id) {
     uint32_t L = o->cells[l];
@@ -154,7 +169,7 @@ static uint32_t gap_ahead(const oracle *o, const int32_t *S, const int32_t *buf,
             if (o->ring[l]) {
                 y -= L;
             } else {
-                uint32_t open = (buf[o->lane_base[l] + k] < 0) || is_last_link(o, id);
+                uint32_t open = is_green(o, l) && ((buf[o->lane_base[l] + k] < 0) || is_last_link(o, id));
                 uint32_t g = i - 1 + open;
                 return g < o->vmax ? g : o->vmax;
             }
@@ -186,7 +201,7 @@ static int room_to_get_in(const oracle *o, const int32_t *S, uint32_t l, uint32_
 /* ------------------------------------------------------------ construction */
 void oracle_destroy(oracle *o) {
     if (!o) return;
-    free(o->from); free(o->to); free(o->cells); free(o->lanes); free(o->ring);
+    free(o->from); free(o->to); free(o->cells); free(o->lanes); free(o->ring); free(o->sig);
     free(o->lane_base); free(o->lane_link); free(o->cell_base); free(o->in_off); free(o->in_lane);
     free(o->depart); free(o->route_off); free(o->route); free(o->q_off); free(o->q_id);
     free(o->cell); free(o->buf); free(o->vel); free(o->cursor); free(o->status); free(o->dep_head);
@@ -197,8 +212,8 @@ void oracle_destroy(oracle *o) {
 
 /* Returns NULL on invalid input or out of memory. */
 oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, const uint32_t *to,
-                      const uint32_t *cells, const uint32_t *lanes, const uint8_t *ring, uint32_t vmax,
-                      uint32_t p_threshold, uint64_t seed, uint32_t lane_change) {
+                      const uint32_t *cells, const uint32_t *lanes, const uint8_t *ring, const uint32_t *signal,
+                      uint32_t vmax, uint32_t p_threshold, uint64_t seed, uint32_t lane_change) {
     if (vmax < 1 || n_links == 0) return NULL;
     oracle *o = (oracle *)calloc(1, sizeof(oracle));
     if (!o) return NULL;
@@ -207,8 +222,14 @@ oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, 
     o->from = (uint32_t *)malloc(4ull * n_links); o->to = (uint32_t *)malloc(4ull * n_links);
     o->cells = (uint32_t *)malloc(4ull * n_links); o->lanes = (uint32_t *)malloc(4ull * n_links);
     o->ring = (uint8_t *)calloc(n_links, 1);
+    o->sig = (uint32_t *)calloc(3ull * n_links, 4);
     o->lane_base = (uint32_t *)malloc(4ull * (n_links + 1));
-    if (!o->from || !o->to || !o->cells || !o->lanes || !o->ring || !o->lane_base) goto fail;
+    if (!o->from || !o->to || !o->cells || !o->lanes || !o->ring || !o->sig || !o->lane_base) goto fail;
+    if (signal) {
+        memcpy(o->sig, signal, 12ull * n_links);
+        for (uint32_t l = 0; l < n_links; l++)
+            if (o->sig[3 * l] && o->sig[3 * l + 1] > o->sig[3 * l]) goto fail;
+    }
     memcpy(o->from, from, 4ull * n_links); memcpy(o->to, to, 4ull * n_links);
     memcpy(o->cells, cells, 4ull * n_links); memcpy(o->lanes, lanes, 4ull * n_links);
     if (ring) memcpy(o->ring, ring, n_links);
@@ -339,6 +360,7 @@ int oracle_load_vehicles(oracle *o, uint32_t n, const uint32_t *depart, const ui
 static void step_once(oracle *o, oracle_stats *st) {
     const uint64_t t = o->step;
     const int d = (t % 2 == 0) ? +1 : -1;
+    o->t_now = t;
     const uint32_t vmax = o->vmax;
     memset(st, 0, sizeof(*st));
 

@@ -396,6 +396,12 @@ ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
         } else if (d->link_from[l] >= d->n_nodes || d->link_to[l] >= d->n_nodes) {
             return fail(TS_ERR_INVALID, "link node id out of range");
         }
+        if (d->link_signal) {
+            const uint32_t cycle = d->link_signal[3 * l], green = d->link_signal[3 * l + 1];
+            const uint32_t offset = d->link_signal[3 * l + 2];
+            if (cycle >= 65536u || green >= 65536u || offset >= 65536u || (cycle && green > cycle))
+                return fail(TS_ERR_INVALID, "signal cycle, green and offset must be below 2^16, green <= cycle");
+        }
     }
     return TS_OK;
 }
@@ -443,6 +449,7 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
     }
     size_t b = 0;
     b += 16ull * d->n_links * 2;                              // lk_info, nd_info
+    if (d->link_signal) b += 8ull * d->n_links;              // signals
     b += words * (4 + 4 + 4 + 32 + 128) * 2;                  // occupancy, v>0, location, velocity, id (x2)
     b += 16ull * slots * 2 + 8ull * n_vehicles * 2 + 4ull * route_len;  // buffers (x2), vehicles, routes
     b += 8ull * n_vehicles + 8ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
@@ -527,6 +534,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     auto &A = c->allocs;
     c->d_lk_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint4 *nd_info = alloc_in<uint4>(c.get(), A, L, ok);
+    uint2 *sig_info = desc->link_signal ? alloc_in<uint2>(c.get(), A, L, ok) : nullptr;
     uint32_t *occ0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
     uint32_t *occ1 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
     uint32_t *mov0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
@@ -549,6 +557,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     ScenDev &sd = c->sd;
     sd.lk_info = c->d_lk_info;
     sd.nd_info = nd_info;
+    sd.sig_info = sig_info;
     sd.occ[0] = occ0;
     sd.occ[1] = occ1;
     sd.mov[0] = mov0;
@@ -575,6 +584,12 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     st = upload_lk_info(c.get());
     if (st != TS_OK) return st;
     for (uint32_t *p : {occ0, occ1, mov0, mov1, loc0, loc1}) CK(cudaMemset(p, 0, 4ull * c->n_words));
+    if (sig_info) {
+        std::vector<uint2> sg(L);
+        for (uint32_t l = 0; l < L; ++l)
+            sg[l] = make_uint2(desc->link_signal[3 * l] | (desc->link_signal[3 * l + 1] << 16), desc->link_signal[3 * l + 2]);
+        CK(cudaMemcpy(sig_info, sg.data(), sizeof(uint2) * L, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemset(slots0, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(slots1, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(lt, 0, 16ull * L));

@@ -97,6 +97,7 @@ static_assert(sizeof(StatRec) == 128, "StatRec is one line");
 struct ScenDev {
     const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8 | column in tile << 16, w slot base
     const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8, w dep end
+    const uint2 *sig_info;        // per link: signal cycle | green << 16, offset (nullptr: no signals)
     uint32_t *occ[2];
     uint32_t *mov[2];
     uint32_t *loc[2];

@@ -232,6 +232,8 @@ struct LinkSmem {
     uint32_t lcells[kTileMaxCols], lid[kTileMaxCols], lbpos[kTileMaxCols];
     uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];  // lexit: lanes whose buffer is empty
     uint8_t lend[kTileMaxCols];       // the link's end (and its buffers) is in this tile
+    uint8_t lgreen[kTileMaxCols];     // the light at the link's end is green in this step (1 without a signal)
+    uint2 lsig[kTileMaxCols];         // its signal: cycle | green << 16, offset
     uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
     uint32_t nlist;                   // vehicles in the list
     uint16_t code[kListCap];          // (local word << 5) | bit
@@ -386,6 +388,11 @@ __device__ __noinline__ uint32_t link_buffers_phase(LinkSmem &S, const ScenDev &
         }
     }
     S.lexit[q] = (uint8_t)open;
+    // the light at the link end (Sec. 3): while red, a virtual vehicle of
+    // maximum velocity zero stands at every lane end
+    const uint2 sg = S.lsig[q];
+    const uint32_t cycle = sg.x & 0xFFFFu, green = sg.x >> 16;
+    S.lgreen[q] = (uint8_t)(cycle == 0u || (t + sg.y) % cycle < green);
     return n_placed;
 }
 
@@ -460,6 +467,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 const uint32_t lanes = li.z & 0xFFu, ring = (li.z >> 8) & 1u;
                 S.lend[q] = (uint8_t)(ring ^ 1u);
                 S.lcw0[q] = ring ? (uint16_t)0xFFFFu : (uint16_t)(li.x - wb);
+                S.lsig[q] = D.sig_info ? D.sig_info[td.a.y + q] : make_uint2(0u, 0u);
                 for (int j = 0; j < ncol; ++j) {
                     const int c = c0 + j;
                     const uint32_t lw = li.x - wb + (uint32_t)j * lanes;
@@ -549,6 +557,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.lbpos[0] = td.b.w;
                 S.lend[0] = (uint8_t)((!ring && j1 == ncol) ? 1u : 0u);
                 S.lcw0[0] = (!ring && j0 == 0) ? (uint16_t)0u : (uint16_t)0xFFFFu;
+                S.lsig[0] = D.sig_info ? D.sig_info[l] : make_uint2(0u, 0u);
                 S.ncols = ncols;
                 S.nwords = ncols * (int)lanes;
                 S.ncore_words = ncore * (int)lanes;
@@ -667,10 +676,11 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 const uint32_t v = (uint32_t)(b1 ? vel1[p] : vel0[p]);
                 const uint32_t last = ((S.cnear[c] >> i) & 1u) ? (b1 ? vid1[p] : vid0[p]) >> 31 : 0u;
                 const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
-                const uint32_t g_own = gap_ahead(S.occ0, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
+                const uint32_t g_own =
+                    gap_ahead(S.occ0, S, c, k, i, dist, (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q], vmax);
                 if (g_own >= want) continue;
                 const uint32_t g_tgt =
-                    gap_ahead(S.occ0, S, c, kt, i, dist, ((S.lexit[q] >> kt) & 1u) | last, vmax);
+                    gap_ahead(S.occ0, S, c, kt, i, dist, (((S.lexit[q] >> kt) & 1u) | last) & S.lgreen[q], vmax);
                 if (g_tgt > g_own && room_behind(S.occ0, S, c, kt, i, vmax)) {
                     atomicOr(&S.mv[S.cw[c] + kt], 1u << i);
                     if (S.ckind[c] == 0) acc[1] += 1;
@@ -742,7 +752,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
                 const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
                 uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;  // (i) accelerate
-                const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, ((S.lexit[q] >> k) & 1u) | last, vmax);
+                const uint32_t g =
+                    gap_ahead(S.occ1, S, c, k, i, dist, (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q], vmax);
                 if (v > g) v = g;                                                 // (ii) gap
                 if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;  // (iii) random
                 const bool core = S.ckind[c] == 0;

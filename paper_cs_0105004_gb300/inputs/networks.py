@@ -15,6 +15,7 @@ Nothing here evaluates the driving rules.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import hashlib
 import os
 from dataclasses import dataclass, field
@@ -36,6 +37,10 @@ class Network:
     link_cells: np.ndarray
     link_lanes: np.ndarray
     link_ring: np.ndarray
+    # traffic signal at each link's end, [n_links, 3] uint32 (cycle, green,
+    # offset): the lanes' ends are green at step t iff (t + offset) mod cycle
+    # < green; cycle 0 = no signal.  None: no signals at all.
+    link_signal: Optional[np.ndarray] = None
 
     @property
     def n_links(self) -> int:
@@ -378,9 +383,25 @@ def _cached(key: str, make):
     return net, dem
 
 
+def grid_signals(net: Network, n_side: int, cycle: int, green: int) -> np.ndarray:
+    """A signal at every link end of a grid_network: links running east-west
+    are green for the first `green` steps of each cycle, links running
+    north-south for the `green` steps that follow (green <= cycle / 2), so
+    crossing streams are never green together."""
+    horizontal = np.abs(net.link_from.astype(np.int64) - net.link_to.astype(np.int64)) == 1
+    sig = np.zeros((net.n_links, 3), np.uint32)
+    sig[:, 0] = cycle
+    sig[:, 1] = green
+    sig[:, 2] = np.where(horizontal, 0, cycle - green)  # (t + offset) mod cycle < green
+    return sig
+
+
 def small_grid_scenario(n_side=3, lanes=2, cells=20, n_trips=60, window=60, steps=200,
-                        gen_seed=0, seed=1, vmax=5, p_threshold=P_THRESHOLD_0_2) -> Scenario:
+                        gen_seed=0, seed=1, vmax=5, p_threshold=P_THRESHOLD_0_2, signal=None) -> Scenario:
+    """signal = (cycle, green): a traffic light at every link end (grid_signals)."""
     net = grid_network(n_side, lanes, cells)
+    if signal is not None:
+        net = dataclasses.replace(net, link_signal=grid_signals(net, n_side, *signal))
     rng = np.random.default_rng(gen_seed)
     o, d, dep = uniform_trips(net, n_trips, window, rng)
     return Scenario(f"grid{n_side}x{n_side}", net, _demand(net, o, d, dep, 1), steps, seed, vmax, p_threshold)

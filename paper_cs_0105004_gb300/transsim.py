@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
 
 class NetworkDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_uint32), ("n_links", ctypes.c_uint32), ("link_from", u32p),
-                ("link_to", u32p), ("link_cells", u32p), ("link_lanes", u32p), ("link_ring", u8p)]
+                ("link_to", u32p), ("link_cells", u32p), ("link_lanes", u32p), ("link_ring", u8p),
+                ("link_signal", u32p)]
 
 
 class Stats(ctypes.Structure):
@@ -158,8 +159,11 @@ class _NetArrays:
         self.lc = np.ascontiguousarray(net.link_cells, np.uint32)
         self.ll = np.ascontiguousarray(net.link_lanes, np.uint32)
         self.lr = np.ascontiguousarray(net.link_ring, np.uint8)
+        sig = getattr(net, "link_signal", None)
+        self.ls = None if sig is None else np.ascontiguousarray(sig, np.uint32).reshape(-1)
         self.desc = NetworkDesc(net.n_nodes, net.n_links, _p(self.lf, ctypes.c_uint32), _p(self.lt, ctypes.c_uint32),
-                                _p(self.lc, ctypes.c_uint32), _p(self.ll, ctypes.c_uint32), _p(self.lr, ctypes.c_uint8))
+                                _p(self.lc, ctypes.c_uint32), _p(self.ll, ctypes.c_uint32), _p(self.lr, ctypes.c_uint8),
+                                _p(self.ls, ctypes.c_uint32) if self.ls is not None else None)
 
 
 def footprint_bytes(scenario) -> int:

@@ -264,3 +264,27 @@ def test_malformed_routes_are_rejected():
         sc = make_scenario(links, 3, routes, [0])
         with pytest.raises(T.TsError, match="INVALID"):
             T.Simulation(sc)
+
+
+# ------------------------------------------------------------------ traffic signals
+
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+@pytest.mark.parametrize("case", [(4, 2, 20, 500, 2, (30, 15)), (5, 3, 45, 1500, 7, (60, 30)),
+                                  (3, 1, 12, 300, 9, (16, 5))])
+def test_signalled_grids_match_oracle(case, mode):
+    side, lanes, cells, trips, seed, signal = case
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 200, 900, gen_seed=seed, seed=seed + 40, signal=signal)
+    run_parity(sc, 900, chunk=300, state_every=300, mode=mode)
+    sim = T.Simulation(sc)
+    orc = oracle.Oracle(sc)
+    sim.step(900)
+    orc.step(900)
+    g, o = sim.link_times(), orc.link_times()
+    assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
+    sim.close()
+
+
+def test_car_waits_at_a_red_light_on_gpu():
+    sc = make_scenario([(0, 1, 20, 1), (1, 2, 20, 1)], 3, [[0, 1]], [0], p=0, steps=30)
+    sc.net.link_signal = np.array([[40, 20, 20], [0, 0, 0]], np.uint32)
+    run_parity(sc, 30, chunk=1)

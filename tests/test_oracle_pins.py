@@ -303,3 +303,46 @@ def test_link_travel_time_counts_equal_transfers_plus_arrivals():
     # entered only at its departure step or later
     assert np.all(tsum >= tcnt)
     assert int(tcnt.sum()) > 0
+
+
+# ------------------------------------------------------------------ traffic signals
+
+def test_car_waits_at_a_red_light_by_hand():
+    # Link 0 (20 cells) ends at a light red for steps 0..19 (cycle 40, green
+    # 20, offset 20: green iff (t + 20) mod 40 < 20).  Cells 1,3,6,10,15
+    # after steps 1..5; in step 6 the virtual vehicle at the end leaves a gap
+    # of 4 cells, so v = 4 and the car stops in cell 19; it stays there with
+    # v = 0 until step 20, when the light is green: v = 1 takes it into the
+    # empty buffer and across to cell 0 of link 1, keeping v = 1.
+    sc = make_scenario([(0, 1, 20, 1), (1, 2, 20, 1)], 3, [[0, 1]], [0], p=0)
+    sc.net.link_signal = np.array([[40, 20, 20], [0, 0, 0]], np.uint32)
+    o = oracle.Oracle(sc)
+    seen = []
+    for _ in range(21):
+        o.step(1)
+        seen.append(positions(o.get_state(), sc.net)[0])
+    assert seen[5] == (0, 0, 15, 5)
+    assert seen[6] == (0, 0, 19, 4)
+    assert all(p == (0, 0, 19, 0) for p in seen[7:20])
+    assert seen[20] == (1, 0, 0, 1)
+    assert o.link_times()[0].tolist() == [20, 0]
+
+
+def test_no_vehicle_reaches_a_red_lane_end():
+    sc = N.small_grid_scenario(4, 2, 20, n_trips=500, window=200, steps=600, gen_seed=2, seed=3, signal=(30, 15))
+    sig = sc.net.link_signal
+    o = oracle.Oracle(sc)
+    before = o.get_state()["buf_id"]
+    lb = sc.net.lane_base()
+    arrived = 0
+    for t in range(600):
+        st = o.step(1)
+        after = o.get_state()["buf_id"]
+        red = (t + sig[:, 2]) % sig[:, 0] >= sig[:, 1]
+        for l in np.nonzero(red)[0]:
+            for ln in range(lb[l], lb[l + 1]):
+                # a buffer of a red link can only keep or lose its vehicle
+                assert after[ln] == -1 or after[ln] == before[ln], (t, l)
+        before = after
+        arrived = int(st["arrived"][0])
+    assert arrived > 0

@@ -288,3 +288,50 @@ def test_car_waits_at_a_red_light_on_gpu():
     sc = make_scenario([(0, 1, 20, 1), (1, 2, 20, 1)], 3, [[0, 1]], [0], p=0, steps=30)
     sc.net.link_signal = np.array([[40, 20, 20], [0, 0, 0]], np.uint32)
     run_parity(sc, 30, chunk=1)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _grid_with(side, lanes, cells, trips, steps, seed, **kw):
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 150, steps, gen_seed=seed, seed=seed + 3)
+    for k, v in kw.items():
+        setattr(sc, k, v)
+    return sc
+
+
+def test_no_travellers_at_all():
+    sc = N.small_grid_scenario(4, 2, 20, 0, 10, 300, gen_seed=1)
+    o = run_parity(sc, 300, chunk=100)
+    assert int(o["active"].max()) == 0 and int(o["state_hash"].max()) == 0
+
+
+def test_four_lane_links():
+    sc = N.small_grid_scenario(4, 4, 40, 1500, 200, 700, gen_seed=17, seed=5)
+    run_parity(sc, 700, chunk=350, state_every=350)
+
+
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_lane_changes_off(mode):
+    sc = _grid_with(4, 3, 25, 900, 600, 19, lane_change=0)
+    o = run_parity(sc, 600, chunk=300, state_every=300, mode=mode)
+    assert int(o["lane_changes"].sum()) == 0
+
+
+def test_slowdown_almost_always():
+    # every draw but 2^32-1 slows a moving vehicle down by one
+    sc = _grid_with(4, 2, 30, 600, 500, 23, p_threshold=0xFFFFFFFF)
+    run_parity(sc, 500, chunk=250, state_every=250)
+
+
+def test_vmax_one_grid():
+    sc = _grid_with(3, 2, 15, 300, 500, 29, vmax=1)
+    run_parity(sc, 500, chunk=250, state_every=250)
+
+
+def test_longest_link_allowed():
+    # cells per link up to 2^22 - 1 (the buffered-vehicle digest packs 22 bits)
+    L = (1 << 22) - 1
+    routes = [[0, 1]] * 6 + [[1]] * 4
+    sc = make_scenario([(0, 1, L, 2), (1, 2, 40, 1)], 3, routes, [0, 0, 1, 2, 3, 4, 0, 1, 2, 5], steps=300,
+                       p=N.P_THRESHOLD_0_2, seed=9)
+    run_parity(sc, 300, chunk=150, state_every=150)

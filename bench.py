@@ -205,7 +205,7 @@ def run_profile_window(args):
         sc, _ = _workload(args.workload)
         sim = T.Simulation(sc, tile_words=args.tile_words)
         if args.load_balance:
-            sim.set_load_balance(args.load_balance, args.tile_vehicles)
+            sim.set_load_balance(args.load_balance, args.tile_vehicles or 6 * sim.tile_words)
         sim.set_step_mode(STEP_MODES[args.step_mode])
         sims = [sim]
         advance = lambda k: sim.step(k, stream)
@@ -235,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sim = T.Simulation(sc, tile_words=args.tile_words)
     if args.load_balance:
-        sim.set_load_balance(args.load_balance, args.tile_vehicles)
+        sim.set_load_balance(args.load_balance, args.tile_vehicles or 6 * sim.tile_words)
     sim.set_step_mode(STEP_MODES[args.step_mode])
     net = sc.net
     C = net.n_lane_cells
@@ -329,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             s2 = T.Simulation(sc)
             if args.load_balance:
-                s2.set_load_balance(args.load_balance, args.tile_vehicles)
+                s2.set_load_balance(args.load_balance, args.tile_vehicles or 6 * s2.tile_words)
             s2.set_step_mode(STEP_MODES[args.step_mode])
             s2.step(steps_per_job)
             t2 = s2.totals()
@@ -356,8 +356,9 @@ def run_ours(args, rank, world, local_rank):
                            "vehicle_updates_per_job": updates, "l2": "flushed (512 MB write) before every job; "
                            "the simulation state stays resident across the steps of a job",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "tile_words": args.tile_words or 128, "step_mode": args.step_mode,
-                           "load_balance": {"every_steps": args.load_balance, "vehicles_per_tile": args.tile_vehicles},
+                           "tile_words": sim.tile_words, "step_mode": args.step_mode,
+                           "load_balance": {"every_steps": args.load_balance,
+                                            "vehicles_per_tile": args.tile_vehicles or 6 * sim.tile_words},
                            "bit_exact_hash": str(tot["last_state_hash"])},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * _launches(steps_per_job, args.step_mode, args.load_balance),
@@ -409,7 +410,7 @@ def run_config3(args):
     if args.tune_sample > 0:
         best, timings = Bt.autotune_tile_words(scs[:args.tune_sample], stream, window=256)
     else:
-        best, timings = (args.tile_words or 128), {}
+        best, timings = (args.tile_words or 256), {}
     sims = Bt.make_members(scs, tile_words=best)
     batch = T.Batch(len(sims))
     batch.set_step_mode(STEP_MODES[args.step_mode])
@@ -626,13 +627,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1800)
     ap.add_argument("--ref-sample-steps", type=int, default=300)
-    ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..128)")
+    ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..256)")
     ap.add_argument("--profile-window", default=None, metavar="S:N",
                     help="step unprofiled to S, then run N steps inside cudaProfilerStart/Stop, and exit")
     ap.add_argument("--step-mode", default="auto", choices=list(STEP_MODES),
                     help="fused: one launch per step; split: link and node kernel per step")
     ap.add_argument("--load-balance", type=int, default=512, help="re-tile from the occupancy every N steps (0 = off)")
-    ap.add_argument("--tile-vehicles", type=int, default=768, help="vehicle budget per tile when re-tiling")
+    ap.add_argument("--tile-vehicles", type=int, default=None,
+                    help="vehicle budget per tile when re-tiling (default: 6 per occupancy word of a tile)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per link_kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

@@ -240,8 +240,11 @@ ts_status ts_ctx_step(ts_ctx *ctx, uint64_t *step);
 void ts_batch_destroy(ts_batch *b);
 
 /* Kernel launch shape: occupancy words (32-cell columns times lanes) per
- * link tile, 8..128 (default 128).  Results do not depend on it. */
+ * link tile, 8..256.  The default is 128, or 256 for a network whose
+ * 128-word tiles outnumber twice the link kernel's resident blocks.
+ * Results do not depend on it.  ts_tile_words returns the current value. */
 ts_status ts_set_tile_words(ts_ctx *ctx, uint32_t words);
+uint32_t ts_tile_words(const ts_ctx *ctx);
 
 /* Advances a periodic ring road held in caller-owned device buffers by
  * n_steps steps, without allocating any device memory.  The paper has no

@@ -48,7 +48,7 @@ def _timed(fn, stream):
     return a.elapsed_time(b) / 1000.0
 
 
-def autotune_tile_words(scenarios, stream, candidates: Sequence[int] = (32, 64, 128), window: int = 256):
+def autotune_tile_words(scenarios, stream, candidates: Sequence[int] = (64, 128, 256), window: int = 256):
     """Times `window` batch steps from the empty network for every candidate
     tile size and returns (best, {candidate: seconds})."""
     timings = {}

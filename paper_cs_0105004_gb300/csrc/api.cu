@@ -68,6 +68,7 @@ struct World {
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1;
+    uint32_t tile_cap = kDefaultTileWords;  // largest tile of the members (picks the link-kernel instance)
     uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
     std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
     bool fused() const;
@@ -93,7 +94,7 @@ struct ts_ctx {
     std::vector<uint32_t> node_in_off;
     uint32_t n_words = 0, n_slots = 0, n_lanes = 0;
     uint64_t n_lane_cells = 0;
-    uint32_t tile_words = kTileWords;
+    uint32_t tile_words = kDefaultTileWords;
     std::vector<LinkTile> link_tiles;
     std::vector<uint4> node_tiles;
     uint32_t n_sub = 1;                // statistics sub-records per step (fixed at creation)
@@ -210,7 +211,14 @@ ts_status World::rebuild() {
     CK(cudaMemcpy(d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
     // persistent grids: at most the resident blocks, and room for the tile
     // count to double through load balancing before blocks loop over tiles
-    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks()));
+    uint32_t cap = kDefaultTileWords;
+    for (ts_ctx *c : members)
+        if (c) cap = std::max(cap, c->tile_words);
+    if (cap != tile_cap) {
+        drop_graphs();
+        tile_cap = cap;
+    }
+    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks(tile_cap)));
     const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
     if (gl > grid_l || gn != grid_n || gl < grid_l / 2) {
         drop_graphs();
@@ -243,7 +251,8 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
-                launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0);
+                launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0,
+                                   tile_cap);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu);
             }
@@ -528,6 +537,12 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
         if (c->node_in_off[n + 1] - c->node_in_off[n] > 255u)
             return fail(TS_ERR_INVALID, "more than 255 lanes end at one node");
     build_tiles(c.get(), nullptr);
+    // a network with many more default tiles than resident blocks runs
+    // throughput-bound: larger tiles spread each tile's fixed cost wider
+    if (c->link_tiles.size() > 2u * (size_t)max_link_blocks(kDefaultTileWords)) {
+        c->tile_words = kTileWords;
+        build_tiles(c.get(), nullptr);
+    }
     c->n_sub = c->link_tiles.size() >= 64 ? 8u : 1u;  // small networks keep one sub-record per step
     // device arrays of the network
     bool ok = true;
@@ -767,7 +782,7 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
 ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
     ts_status st = check_ctx(c);
     if (st != TS_OK) return st;
-    if (words < 8 || words > (uint32_t)kTileWords) return fail(TS_ERR_INVALID, "tile words must be 8..128");
+    if (words < 8 || words > (uint32_t)kTileWords) return fail(TS_ERR_INVALID, "tile words must be 8..256");
     if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
     st = wait_ctx(c, 60000);
     if (st != TS_OK) return st;
@@ -778,6 +793,8 @@ ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
     if (c->own) return ensure_own_world(c);
     return TS_OK;
 }
+
+uint32_t ts_tile_words(const ts_ctx *c) { return c ? c->tile_words : 0u; }
 
 ts_status ts_set_step_mode(ts_ctx *c, uint32_t mode) {
     ts_status st = check_ctx(c);
@@ -905,7 +922,8 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
             for (uint32_t i = 0; i < g; ++i) {
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
-                launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0);
+                launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0,
+                                   w->tile_cap);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu);

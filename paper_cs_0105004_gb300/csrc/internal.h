@@ -48,12 +48,11 @@ constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kLastLinkBit = 0x80000000u;
 constexpr uint32_t kIdMask = 0x7FFFFFFFu;
 constexpr uint32_t kMaxCells = 1u << 22;      // cells per link (buffer digest packs 22 bits)
-constexpr int kTileWords = 128;               // occupancy words per link tile (all lanes)
+constexpr int kTileWords = 256;               // occupancy words per link tile (all lanes), at most
+constexpr int kDefaultTileWords = 128;        // the default tile size
 constexpr int kTileMaxCols = 129;             // columns per tile (one-lane links, plus a merged tail)
-constexpr int kTileSmemWords = kTileWords + 4 + 2 * kMaxLanes;  // core + merged tail + halos
 constexpr int kLinkThreads = 256;
 constexpr int kNodeThreads = 128;
-constexpr int kListCap = kTileSmemWords * 32;  // every cell of a tile can hold a vehicle
 constexpr uint32_t kStatsRing = 4096;         // steps of statistics kept on the device
 constexpr uint32_t kChunk = 32;               // steps per captured graph
 constexpr uint32_t kNoLink = 0xFFFFFFFFu;
@@ -133,8 +132,10 @@ struct LinkTile {
 // xfer: the launch first completes the node transfers and departures of the
 // previous step (the step at position i-1 of the chunk); without it, the
 // previous step must have been completed by node_kernel
+// tile_cap: the largest tile (occupancy words) among the tiles; picks the
+// kernel instance whose shared memory holds it
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer);
+                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap);
 // chunk_end: the pass completes the last step each scenario ran in the
 // chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
@@ -143,7 +144,7 @@ void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cu
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 // adds the entry steps of vehicles on the network to out (a copy of link_time)
 void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s);
-int max_link_blocks();
+int max_link_blocks(uint32_t tile_cap);
 int max_node_blocks();
 // Sets the thread-local message returned by ts_last_error.
 void set_last_error(const char *msg);

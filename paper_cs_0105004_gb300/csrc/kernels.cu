@@ -212,18 +212,23 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
 
 constexpr int kCols = kTileMaxCols + 2;
 
+// Shared memory of one link-kernel block for tiles of at most TW occupancy
+// words (core + a merged tail column + a halo column on each side).
+template <int TW>
 struct LinkSmem {
-    uint32_t occ0[kTileSmemWords];  // step t: occupancy, v > 0, payload buffer
-    uint32_t mov0[kTileSmemWords];
-    uint32_t loc0[kTileSmemWords];
-    uint32_t mv[kTileSmemWords];    // vehicles that changed INTO the word's lane
-    uint32_t occ1[kTileSmemWords];  // after the lane-change sub-step
-    uint32_t mov1[kTileSmemWords];
-    uint32_t oocc[kTileSmemWords];  // step t+1 (core words)
-    uint32_t omov[kTileSmemWords];
-    uint32_t oloc[kTileSmemWords];
-    uint32_t gw[kTileSmemWords];    // global word index of each local word
-    uint8_t wcol[kTileSmemWords], wlane[kTileSmemWords];
+    static constexpr int kWords = TW + 4 + 2 * kMaxLanes;
+    static constexpr int kList = kWords * 32;  // every cell of a tile can hold a vehicle
+    uint32_t occ0[kWords];  // step t: occupancy, v > 0, payload buffer  // step t: occupancy, v > 0, payload buffer
+    uint32_t mov0[kWords];
+    uint32_t loc0[kWords];
+    uint32_t mv[kWords];    // vehicles that changed INTO the word's lane
+    uint32_t occ1[kWords];  // after the lane-change sub-step
+    uint32_t mov1[kWords];
+    uint32_t oocc[kWords];  // step t+1 (core words)
+    uint32_t omov[kWords];
+    uint32_t oloc[kWords];
+    uint32_t gw[kWords];    // global word index of each local word
+    uint8_t wcol[kWords], wlane[kWords];
     uint16_t cw[kCols];             // local word of lane 0 of each column
     uint32_t cx0[kCols];            // first cell of the column within its link
     uint32_t cnear[kCols];          // cells within vmax of a (non-periodic) link end
@@ -236,13 +241,14 @@ struct LinkSmem {
     uint2 lsig[kTileMaxCols];         // its signal: cycle | green << 16, offset
     uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
     uint32_t nlist;                   // vehicles in the list
-    uint16_t code[kListCap];          // (local word << 5) | bit
+    uint16_t code[kList];             // (local word << 5) | bit
     unsigned long long red[kLinkThreads / 32][7];
     unsigned long long xacc[6];       // node-transfer counts of the current previous-step record
     int ncols, nwords, ncore_words, nlinks;
 };
 
-__device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const LinkSmem &S, int c, int k, int i,
+template <class SM>
+__device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const SM &S, int c, int k, int i,
                                               uint32_t dist, uint32_t open, uint32_t vmax) {
     const uint32_t w0 = O[S.cw[c] + k];
     const int r = S.right[c];
@@ -253,7 +259,8 @@ __device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const LinkSmem 
     return g < vmax ? g : vmax;
 }
 
-__device__ __forceinline__ bool room_behind(const uint32_t *O, const LinkSmem &S, int c, int k, int i,
+template <class SM>
+__device__ __forceinline__ bool room_behind(const uint32_t *O, const SM &S, int c, int k, int i,
                                             uint32_t vmax) {
     const int l = S.left[c];
     const unsigned long long back = ((unsigned long long)O[S.cw[c] + k] << 32) | (l >= 0 ? O[S.cw[l] + k] : 0u);
@@ -263,7 +270,8 @@ __device__ __forceinline__ bool room_behind(const uint32_t *O, const LinkSmem &S
 
 // Bit x of the result: cell x+1 of the same lane is occupied (next word's bit
 // 0 for x = 31).
-__device__ __forceinline__ uint32_t ahead_mask(const uint32_t *O, const LinkSmem &S, int c, int k) {
+template <class SM>
+__device__ __forceinline__ uint32_t ahead_mask(const uint32_t *O, const SM &S, int c, int k) {
     const int r = S.right[c];
     return (O[S.cw[c] + k] >> 1) | ((r >= 0 ? O[S.cw[r] + k] : 0u) << 31);
 }
@@ -283,7 +291,8 @@ __device__ __forceinline__ uint32_t move_mask(uint8_t kind, uint32_t vmax) {
 
 // Appends the set bits of m (word w) to the block's vehicle list; one thread
 // per word, one shared-memory reservation per warp.
-__device__ __forceinline__ void list_append(LinkSmem &S, int w, uint32_t m) {
+template <class SM>
+__device__ __forceinline__ void list_append(SM &S, int w, uint32_t m) {
     const int lane = threadIdx.x & 31;
     const uint32_t cnt = (uint32_t)__popc(m);
     uint32_t inc = cnt;
@@ -308,7 +317,8 @@ __device__ __forceinline__ void list_append(LinkSmem &S, int w, uint32_t m) {
 // of step t-1; then sets up q's lane-end buffers for step t (if q ends in this
 // tile).  Returns the vehicles placed on q.  Out of line, so that its
 // registers do not weigh on the rest of the step.
-__device__ __noinline__ uint32_t link_buffers_phase(LinkSmem &S, const ScenDev &D, int q, int cur, uint32_t t,
+template <class SM>
+__device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int q, int cur, uint32_t t,
                                                     bool do_xfer) {
     const int nxt = cur ^ 1;
     uint32_t n_placed = 0u;
@@ -396,13 +406,13 @@ __device__ __noinline__ uint32_t link_buffers_phase(LinkSmem &S, const ScenDev &
     return n_placed;
 }
 
+template <int TW>
 __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__restrict__ table,
                                                             const LinkTile *__restrict__ tiles,
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
                                                             uint32_t xfer) {
-    __shared__ LinkSmem S;
+    __shared__ LinkSmem<TW> S;
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
-    static_assert(kTileSmemWords <= kLinkThreads, "one word per thread");
     // statistics of the block: updates, lane changes, arrivals, and the changes
     // of active, buffered, sum of velocities and digest
     static constexpr int kField[7] = {kUpdates, kLaneChanges, kArrived, kDActive, kDBuffered, kDSumV, kDHash};
@@ -587,7 +597,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         const int cur = (int)(step & 1ull), nxt = cur ^ 1;
         const int d = (t & 1u) ? -1 : 1;
         const int nwords = S.nwords, ncore_words = S.ncore_words;
-        const int w = threadIdx.x;  // one word per thread in the word phases
+        // word phases: one thread per occupancy word, looping when a tile has
+        // more words than the block has threads
 
         // with xfer, memory holds the state after the moves of step t-1 and
         // the node transfers of t-1 are completed here, before step t
@@ -602,7 +613,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
 
         // ---------------- state of step t (occ0/mov0 start at zero: the word
         // loads and the placements of the node transfers are or-ed in)
-        if (w < nwords) {
+        for (int w = threadIdx.x; w < nwords; w += kLinkThreads) {
             const uint32_t g = S.gw[w];
             const uint32_t o = D.occ[cur][g];
             if (o) {
@@ -633,6 +644,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         // Moving vehicles and vehicles near a link end are decided one by one.
         const bool lc_on = D.lane_change != 0u;
         if (lc_on) {
+            for (int wb = 0; wb < nwords; wb += kLinkThreads) {  // uniform per warp (list_append)
+            const int w = wb + (int)threadIdx.x;
             uint32_t listed = 0u;
             if (w < nwords) {
                 const int c = S.wcol[w], k = S.wlane[w], kt = k + d;
@@ -658,6 +671,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 }
             }
             list_append(S, w, listed);
+            }
             __syncthreads();
             const uint32_t total = S.nlist;
             for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
@@ -687,7 +701,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 }
             }
             __syncthreads();
-            if (w < nwords) {
+            for (int w = threadIdx.x; w < nwords; w += kLinkThreads) {
                 const int c = S.wcol[w], k = S.wlane[w];
                 const int lanes = S.llanes[S.clink[c]];
                 const int kf = k + d, kb = k - d;
@@ -698,9 +712,11 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 S.mov1[w] = (S.mov0[w] & ~leaving) | (src_mov & arriving);
             }
             if (threadIdx.x == 0) S.nlist = 0u;
-        } else if (w < nwords) {
-            S.occ1[w] = S.occ0[w];
-            S.mov1[w] = S.mov0[w];
+        } else {
+            for (int w = threadIdx.x; w < nwords; w += kLinkThreads) {
+                S.occ1[w] = S.occ0[w];
+                S.mov1[w] = S.mov0[w];
+            }
         }
         __syncthreads();
         stamp(5, first);
@@ -709,6 +725,8 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         // v = 0, an occupied cell ahead, no lane change and far from the link
         // end keeps v = 0 and its cell: its bits are copied, its payload stays.
         {
+            for (int wb = 0; wb < nwords; wb += kLinkThreads) {  // uniform per warp (list_append)
+            const int w = wb + (int)threadIdx.x;
             uint32_t listed = 0u;
             if (w < nwords) {
                 const int c = S.wcol[w], k = S.wlane[w];
@@ -726,6 +744,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                 }
             }
             list_append(S, w, listed);
+            }
             __syncthreads();
             const uint32_t total = S.nlist;
             int8_t *__restrict__ velw0 = D.vel[0];
@@ -829,7 +848,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         stamp(6, first);
 
         // ---------------- write the state of step t+1 and the buffer states
-        if (w < ncore_words) {
+        for (int w = threadIdx.x; w < ncore_words; w += kLinkThreads) {
             const uint32_t g = S.gw[w];
             D.occ[nxt][g] = S.oocc[w];
             D.mov[nxt][g] = S.omov[w];
@@ -1048,8 +1067,11 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
 }
 
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer) {
-    launch_pdl(link_kernel, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i, xfer ? 1u : 0u);
+                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap) {
+    if (tile_cap <= (uint32_t)kDefaultTileWords)
+        launch_pdl(link_kernel<kDefaultTileWords>, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i, xfer ? 1u : 0u);
+    else
+        launch_pdl(link_kernel<kTileWords>, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i, xfer ? 1u : 0u);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
@@ -1102,7 +1124,17 @@ extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
 }
 #endif
 
-int max_link_blocks() { return resident_blocks((const void *)link_kernel, kLinkThreads); }
+int max_link_blocks(uint32_t tile_cap) {
+    if (tile_cap <= (uint32_t)kDefaultTileWords) return resident_blocks((const void *)link_kernel<kDefaultTileWords>,
+                                                                         kLinkThreads);
+    // the large-tile instance needs more shared memory per block than the
+    // default L1/shared split leaves for four blocks; the largest shared
+    // share measured fastest on GB300 (config 3: 3.3e10 vs 2.4e10
+    // vehicle-updates/s with the default split)
+    const void *fn = (const void *)link_kernel<kTileWords>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return resident_blocks(fn, kLinkThreads);
+}
 int max_node_blocks() { return resident_blocks((const void *)node_kernel, kNodeThreads); }
 
 }  // namespace tsim

@@ -25,8 +25,8 @@ namespace {
 
 constexpr uint32_t kNoAllocMaxCells = 1u << 17;  // cells per lane
 constexpr uint32_t kNoAllocMaxSteps = 1024;      // steps per call
-constexpr uint32_t kNoAllocMaxTiles =  // 4096 columns in runs of kTileWords / lanes columns
-    (kNoAllocMaxCells / 32u + (uint32_t)(kTileWords / kMaxLanes) - 1u) / (uint32_t)(kTileWords / kMaxLanes);
+constexpr uint32_t kNoAllocMaxTiles =  // 4096 columns in runs of kDefaultTileWords / lanes columns
+    (kNoAllocMaxCells / 32u + (uint32_t)(kDefaultTileWords / kMaxLanes) - 1u) / (uint32_t)(kDefaultTileWords / kMaxLanes);
 constexpr uint32_t kNoAllocMaxWords = kNoAllocMaxCells / 32u * (uint32_t)kMaxLanes;
 
 // Byte offsets inside the scratch array.
@@ -186,13 +186,13 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     // halos wrap around the ring
     const uint32_t ncols = cells / 32u, words = ncols * lanes;
     std::vector<LinkTile> tiles;
-    if (words <= (uint32_t)kTileWords) {
+    if (words <= (uint32_t)kDefaultTileWords) {
         LinkTile t;
         t.a = make_uint4(0u, 0u, 1u, 0u);
         t.b = make_uint4(0u, words, 0u, 0u);
         tiles.push_back(t);
     } else {
-        const uint32_t per = (uint32_t)kTileWords / lanes;
+        const uint32_t per = (uint32_t)kDefaultTileWords / lanes;
         for (uint32_t j = 0; j < ncols; j += per) {
             LinkTile t;
             t.a = make_uint4(0u, 0u, kPartial | j, j + per < ncols ? j + per : ncols);
@@ -240,9 +240,9 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
         return bad(TS_ERR_CUDA, "scratch set-up copy failed");
     const uint32_t cur = (uint32_t)(first_step & 1ull), fin = (uint32_t)((first_step + n_steps) & 1ull);
     prep_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, lanes, words, cur);
-    const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks()));
+    const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks(kDefaultTileWords)));
     for (uint32_t i = 0; i < n_steps; ++i)
-        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false, false);
+        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false, false, kDefaultTileWords);
     finish_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, words, fin);
     gather_ring_stats<<<1, kNoAllocMaxSteps, 0, s>>>(d_stats, d_ctrl, first_step, n_steps, dev_stats_out);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");

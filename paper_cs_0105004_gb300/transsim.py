@@ -104,6 +104,7 @@ _API = {
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_tile_words": (ctypes.c_uint32, [ctypes.c_void_p]),
     "ts_read_link_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
     "ts_batch_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
@@ -237,6 +238,10 @@ class Simulation:
 
     def set_tile_words(self, words: int):
         _check(lib().ts_set_tile_words(self.h, words))
+
+    @property
+    def tile_words(self) -> int:
+        return int(lib().ts_tile_words(self.h))
 
     def link_times(self, timeout_ms: int = 600000):
         """Per-link travel-time sums and counts of completed traversals (uint64 arrays)."""

@@ -134,7 +134,7 @@ def test_long_links_partial_tiles():
             routes.append([2 * i + 1 for i in range(b - 1, a - 1, -1)])
         dep.append(int(rng.integers(0, 300)))
     sc = make_scenario(links, n, routes, dep, steps=1500, seed=77, p=N.P_THRESHOLD_0_2)
-    for tc, mode in ((128, T.STEP_FUSED), (8, T.STEP_FUSED), (8, T.STEP_SPLIT)):
+    for tc, mode in ((128, T.STEP_FUSED), (8, T.STEP_FUSED), (8, T.STEP_SPLIT), (256, T.STEP_SPLIT)):
         run_parity(sc, 1500, chunk=500, state_every=500, tile_words=tc, mode=mode)
 
 
@@ -147,7 +147,7 @@ def test_config0_full_run(mode):
 def test_config0_tile_shapes_identical():
     sc = N.config0()
     ref = None
-    for tc in (8, 16, 32, 64, 128):
+    for tc in (8, 16, 32, 64, 128, 256):
         sim = T.Simulation(sc, tile_words=tc)
         sim.step(1200)
         st = sim.stats_range(0, 1200)
@@ -335,3 +335,9 @@ def test_longest_link_allowed():
     sc = make_scenario([(0, 1, L, 2), (1, 2, 40, 1)], 3, routes, [0, 0, 1, 2, 3, 4, 0, 1, 2, 5], steps=300,
                        p=N.P_THRESHOLD_0_2, seed=9)
     run_parity(sc, 300, chunk=150, state_every=150)
+
+
+def test_large_tiles_on_a_loaded_grid():
+    # 256-word tiles: every word phase loops twice per tile
+    sc = N.small_grid_scenario(6, 3, 60, 4000, 300, 900, gen_seed=31, seed=8)
+    run_parity(sc, 900, chunk=300, state_every=300, tile_words=256)

@@ -240,7 +240,7 @@ struct LinkSmem {
     uint8_t lgreen[kTileMaxCols];     // the light at the link's end is green in this step (1 without a signal)
     uint2 lsig[kTileMaxCols];         // its signal: cycle | green << 16, offset
     uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
-    uint32_t nlist;                   // vehicles in the list
+    uint32_t nlist[2];                // vehicles in the lane-change list and in the velocity list
     uint16_t code[kList];             // (local word << 5) | bit
     unsigned long long red[kLinkThreads / 32][7];
     unsigned long long xacc[6];       // node-transfer counts of the current previous-step record
@@ -292,7 +292,7 @@ __device__ __forceinline__ uint32_t move_mask(uint8_t kind, uint32_t vmax) {
 // Appends the set bits of m (word w) to the block's vehicle list; one thread
 // per word, one shared-memory reservation per warp.
 template <class SM>
-__device__ __forceinline__ void list_append(SM &S, int w, uint32_t m) {
+__device__ __forceinline__ void list_append(SM &S, uint32_t &count, int w, uint32_t m) {
     const int lane = threadIdx.x & 31;
     const uint32_t cnt = (uint32_t)__popc(m);
     uint32_t inc = cnt;
@@ -302,7 +302,7 @@ __device__ __forceinline__ void list_append(SM &S, int w, uint32_t m) {
         if (lane >= o) inc += y;
     }
     uint32_t base = 0u;
-    if (lane == 31 && inc) base = atomicAdd(&S.nlist, inc);
+    if (lane == 31 && inc) base = atomicAdd(&count, inc);
     base = __shfl_sync(0xffffffffu, base, 31);
     uint32_t r = base + inc - cnt;
     while (m) {
@@ -579,7 +579,10 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         // they may be read before waiting for the previous kernel.
         const unsigned long long step = D.ctrl->base + pos;
         const bool active = step < D.ctrl->target;
-        if (threadIdx.x == 0) S.nlist = 0u;
+        if (threadIdx.x == 0) {
+            S.nlist[0] = 0u;
+            S.nlist[1] = 0u;
+        }
         __syncthreads();
         stamp(2, first);
         if (!active) continue;
@@ -670,10 +673,10 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                     }
                 }
             }
-            list_append(S, w, listed);
+            list_append(S, S.nlist[0], w, listed);
             }
             __syncthreads();
-            const uint32_t total = S.nlist;
+            const uint32_t total = S.nlist[0];
             for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
                 const uint32_t code = S.code[e];
                 const int ww = code >> 5, i = code & 31;
@@ -700,23 +703,6 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                     if (S.ckind[c] == 0) acc[1] += 1;
                 }
             }
-            __syncthreads();
-            for (int w = threadIdx.x; w < nwords; w += kLinkThreads) {
-                const int c = S.wcol[w], k = S.wlane[w];
-                const int lanes = S.llanes[S.clink[c]];
-                const int kf = k + d, kb = k - d;
-                const uint32_t leaving = (kf >= 0 && kf < lanes) ? S.mv[S.cw[c] + kf] : 0u;
-                const uint32_t arriving = S.mv[w];
-                const uint32_t src_mov = (arriving && kb >= 0 && kb < lanes) ? S.mov0[S.cw[c] + kb] : 0u;
-                S.occ1[w] = (S.occ0[w] & ~leaving) | arriving;
-                S.mov1[w] = (S.mov0[w] & ~leaving) | (src_mov & arriving);
-            }
-            if (threadIdx.x == 0) S.nlist = 0u;
-        } else {
-            for (int w = threadIdx.x; w < nwords; w += kLinkThreads) {
-                S.occ1[w] = S.occ0[w];
-                S.mov1[w] = S.mov0[w];
-            }
         }
         __syncthreads();
         stamp(5, first);
@@ -731,9 +717,24 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
             if (w < nwords) {
                 const int c = S.wcol[w], k = S.wlane[w];
                 const uint8_t kind = S.ckind[c];
-                const uint32_t o1 = S.occ1[w];
-                const uint32_t free_ahead = ~ahead_mask(S.occ1, S, c, k);
-                const uint32_t busy = S.mov1[w] | free_ahead | S.cnear[c] | S.mv[w];
+                // the words after the lane-change sub-step, from the step-t
+                // words and the lane-change marks (mv: vehicles that changed
+                // into a word's lane; those leaving lane k went to k + d)
+                const int lanes = S.llanes[S.clink[c]];
+                const int kf = k + d, kb = k - d;
+                const bool has_f = kf >= 0 && kf < lanes, has_b = kb >= 0 && kb < lanes;
+                const uint32_t arriving = S.mv[w];
+                const uint32_t leaving = has_f ? S.mv[S.cw[c] + kf] : 0u;
+                const uint32_t o1 = (S.occ0[w] & ~leaving) | arriving;
+                const uint32_t src_mov = (arriving && has_b) ? S.mov0[S.cw[c] + kb] : 0u;
+                const uint32_t m1 = (S.mov0[w] & ~leaving) | (src_mov & arriving);
+                S.occ1[w] = o1;
+                S.mov1[w] = m1;
+                const int r = S.right[c];
+                const uint32_t o1r =
+                    r >= 0 ? (S.occ0[S.cw[r] + k] & ~(has_f ? S.mv[S.cw[r] + kf] : 0u)) | S.mv[S.cw[r] + k] : 0u;
+                const uint32_t free_ahead = ~((o1 >> 1) | (o1r << 31));
+                const uint32_t busy = m1 | free_ahead | S.cnear[c] | arriving;
                 listed = o1 & busy & move_mask(kind, vmax);
                 if (kind == 0) {
                     const uint32_t inert = o1 & ~busy;
@@ -743,10 +744,10 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
                     }
                 }
             }
-            list_append(S, w, listed);
+            list_append(S, S.nlist[1], w, listed);
             }
             __syncthreads();
-            const uint32_t total = S.nlist;
+            const uint32_t total = S.nlist[1];
             int8_t *__restrict__ velw0 = D.vel[0];
             int8_t *__restrict__ velw1 = D.vel[1];
             uint32_t *__restrict__ vidw0 = D.vid[0];

@@ -4,27 +4,30 @@
 //
 //   link_kernel  lane change (sub-step 1), velocity update and move
 //                (sub-step 2) of every vehicle on every lane.  It reads the
-//                state of step t (buffer t&1) and writes the cells of step
-//                t+1 (buffer (t+1)&1); a vehicle reaching its link end enters
-//                the lane's link-end buffer, or leaves on its last link.
+//                state of step t (set t&1) and writes the cells of step t+1
+//                (set (t+1)&1); a vehicle reaching its link end enters the
+//                lane's link-end buffer, or leaves on its last link.
 //   node_kernel  node transfer: for every link m, the buffered vehicles at
 //                m's upstream node whose next link is m, in fixed priority
 //                order (incoming link id, then lane), move to cell 0 of m;
 //                then departures from parking enter m.
-// Once per captured chunk of steps, advance_kernel closes the chunk's
-// statistics and moves the step counter; inside a chunk the step index of a
-// launch is the chunk base plus the launch's position.
+// (Fused steps fold the node transfer of step t-1 into the link kernel of
+// step t and run the node kernel once per chunk.)  Once per captured chunk
+// of steps, advance_kernel closes the chunk's statistics and moves the step
+// counter; inside a chunk the step index of a launch is the chunk base plus
+// the launch's position.
 //
 // The paper's split-link boundary exchange (Sec. 4: each CPU sends the
 // first five cells of its half of a split link to the other) becomes a
 // one-column halo here: a block owns a tile of 32-cell columns and
 // re-computes the lane-change decisions of the vehicles in the neighbouring
-// column that can influence its own cells instead of exchanging them.  Work
-// inside a tile is one thread per vehicle: occupancy words are staged in
-// shared memory, the vehicles are compacted into a list with their
-// velocity and id loaded once, so the cost follows the number of vehicles
-// and not the number of cells.  Gaps come from a 64-bit funnel of two
-// occupancy words and one find-first-set.
+// column that can influence its own cells instead of exchanging them.
+// Inside a tile, occupancy, moving and location words are staged in shared
+// memory.  Stopped vehicles whose next cell stays occupied are handled 32 at
+// a time with bit operations and never touch their payload; the others are
+// compacted into a list, one thread per vehicle, so the cost follows the
+// number of vehicles that move or may move.  Gaps come from a 64-bit window
+// of two occupancy words and one find-first-set.
 #include "internal.h"
 
 namespace tsim {

@@ -220,6 +220,18 @@ def run_profile_window(args):
                                          "vehicle_updates_to_end": upd}}), flush=True)
 
 
+def aggregate_over_ranks(t_region, work, dist, device):
+    """Replicas (one independent job stream per GPU, no data exchange): the
+    job's time is the slowest rank's timed region, its work the sum of the
+    ranks' work."""
+    import torch
+    tt = torch.tensor([t_region], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ww = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ww.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_cs_0105004_gb300 import transsim as T
@@ -284,11 +296,7 @@ def run_ours(args, rank, world, local_rank):
     t_region = sum(times_ms) / 1000.0
     work = float(updates) * args.steps
     if dist:
-        tt = torch.tensor([t_region], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ww = torch.tensor([work], dtype=torch.float64, device=dev)
-        dist.all_reduce(ww, op=dist.ReduceOp.SUM)
-        t_region, work = float(tt.item()), float(ww.item())
+        t_region, work = aggregate_over_ranks(t_region, work, dist, dev)
     value = work / t_region
 
     # per-kernel durations with CUDA events on the launching stream (one extra job)

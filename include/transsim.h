@@ -207,6 +207,15 @@ ts_status ts_read_state(ts_ctx *ctx, ts_state *out, uint32_t timeout_ms);
  * cursor does not name, or a velocity is outside 0..vmax. */
 ts_status ts_write_state(ts_ctx *ctx, const ts_state *in);
 
+/* Checkpoints as one byte buffer: the canonical state (ts_state) behind a
+ * 64-byte header (magic "TSCK", format 1, the four sizes, step, arrived,
+ * inserted).  ts_save_state with host == NULL sets *bytes to the size
+ * needed; otherwise it fills host (*bytes must be at least that size) after
+ * a bounded wait.  ts_load_state replaces the state like ts_write_state and
+ * returns TS_ERR_INVALID for a buffer of another format or network. */
+ts_status ts_save_state(ts_ctx *ctx, void *host, size_t *bytes, uint32_t timeout_ms);
+ts_status ts_load_state(ts_ctx *ctx, const void *host, size_t bytes);
+
 /* Device bytes a context would hold for a network of this shape with
  * n_vehicles travellers and route_len route entries in total (admission
  * control for the job server). */

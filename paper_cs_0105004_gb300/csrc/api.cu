@@ -1253,6 +1253,84 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
     return TS_OK;
 }
 
+namespace {
+struct CkptHeader {
+    char magic[4];
+    uint32_t format;
+    uint64_t n_lane_cells;
+    uint32_t n_lanes, n_veh, n_links, pad;
+    uint64_t step, arrived, inserted;
+    uint64_t reserved;
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+size_t ckpt_bytes(const ts_ctx *c) {
+    return sizeof(CkptHeader) + 4ull * c->n_lane_cells + 4ull * c->n_lanes + 4ull * c->n_veh +
+           4ull * c->n_links + c->n_lane_cells + c->n_lanes;
+}
+
+// The arrays behind the header: the 4-byte ones first, then the 1-byte ones.
+ts_state ckpt_view(const ts_ctx *c, unsigned char *base) {
+    ts_state s{};
+    unsigned char *p = base + sizeof(CkptHeader);
+    s.cell_id = reinterpret_cast<int32_t *>(p);
+    p += 4ull * c->n_lane_cells;
+    s.buf_id = reinterpret_cast<int32_t *>(p);
+    p += 4ull * c->n_lanes;
+    s.cursor = reinterpret_cast<uint32_t *>(p);
+    p += 4ull * c->n_veh;
+    s.dep_head = reinterpret_cast<uint32_t *>(p);
+    p += 4ull * c->n_links;
+    s.cell_v = reinterpret_cast<int8_t *>(p);
+    p += c->n_lane_cells;
+    s.buf_v = reinterpret_cast<int8_t *>(p);
+    return s;
+}
+}  // namespace
+
+ts_status ts_save_state(ts_ctx *c, void *host, size_t *bytes, uint32_t timeout_ms) {
+    if (!c || !bytes) return fail(TS_ERR_INVALID, "null argument");
+    const size_t need = ckpt_bytes(c);
+    if (!host) {
+        *bytes = need;
+        return TS_OK;
+    }
+    if (*bytes < need) return fail(TS_ERR_INVALID, "checkpoint buffer too small");
+    unsigned char *base = static_cast<unsigned char *>(host);
+    ts_state s = ckpt_view(c, base);
+    const ts_status st = ts_read_state(c, &s, timeout_ms);
+    if (st != TS_OK) return st;
+    CkptHeader h{};
+    memcpy(h.magic, "TSCK", 4);
+    h.format = 1;
+    h.n_lane_cells = c->n_lane_cells;
+    h.n_lanes = c->n_lanes;
+    h.n_veh = c->n_veh;
+    h.n_links = c->n_links;
+    h.step = s.step;
+    h.arrived = s.arrived;
+    h.inserted = s.inserted;
+    memcpy(base, &h, sizeof(h));
+    *bytes = need;
+    return TS_OK;
+}
+
+ts_status ts_load_state(ts_ctx *c, const void *host, size_t bytes) {
+    if (!c || !host) return fail(TS_ERR_INVALID, "null argument");
+    CkptHeader h;
+    if (bytes < sizeof(h)) return fail(TS_ERR_INVALID, "checkpoint too short");
+    memcpy(&h, host, sizeof(h));
+    if (memcmp(h.magic, "TSCK", 4) != 0 || h.format != 1) return fail(TS_ERR_INVALID, "not a checkpoint of format 1");
+    if (h.n_lane_cells != c->n_lane_cells || h.n_lanes != c->n_lanes || h.n_veh != c->n_veh ||
+        h.n_links != c->n_links || bytes < ckpt_bytes(c))
+        return fail(TS_ERR_INVALID, "checkpoint of another network or vehicle set");
+    ts_state s = ckpt_view(c, const_cast<unsigned char *>(static_cast<const unsigned char *>(host)));
+    s.step = h.step;
+    s.arrived = h.arrived;
+    s.inserted = h.inserted;
+    return ts_write_state(c, &s);
+}
+
 void ts_destroy(ts_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);

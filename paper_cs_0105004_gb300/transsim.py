@@ -104,6 +104,9 @@ _API = {
     "ts_batch_destroy": (None, [ctypes.c_void_p]),
     "ts_set_tile_words": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.c_uint32]),
+    "ts_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ts_tile_words": (ctypes.c_uint32, [ctypes.c_void_p]),
     "ts_read_link_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
     "ts_batch_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
@@ -242,6 +245,18 @@ class Simulation:
     @property
     def tile_words(self) -> int:
         return int(lib().ts_tile_words(self.h))
+
+    def save(self, timeout_ms: int = 600000) -> bytes:
+        """A checkpoint of the current state (ts_save_state)."""
+        n = ctypes.c_size_t(0)
+        _check(lib().ts_save_state(self.h, None, ctypes.byref(n), timeout_ms))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().ts_save_state(self.h, buf, ctypes.byref(n), timeout_ms))
+        return buf.raw[:n.value]
+
+    def load(self, checkpoint: bytes):
+        """Replaces the state by a checkpoint from save() (ts_load_state)."""
+        _check(lib().ts_load_state(self.h, ctypes.c_char_p(checkpoint), len(checkpoint)))
 
     def link_times(self, timeout_ms: int = 600000):
         """Per-link travel-time sums and counts of completed traversals (uint64 arrays)."""

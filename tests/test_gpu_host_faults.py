@@ -68,3 +68,26 @@ def test_checkpoint_resume_equals_the_uninterrupted_run():
         assert np.array_equal(got_state[k], want_state[k]), k
     full.close()
     resumed.close()
+
+
+def test_checkpoint_bytes_round_trip():
+    sc = N.small_grid_scenario(4, 2, 30, 800, 300, 1200, gen_seed=14, seed=32)
+    full = T.Simulation(sc)
+    full.step(1200)
+    part = T.Simulation(sc)
+    part.step(500)
+    ck = part.save()
+    assert ck[:4] == b"TSCK"
+    part.close()
+    resumed = T.Simulation(sc)
+    resumed.load(ck)
+    resumed.step(700)
+    a, b = full.stats_range(500, 700), resumed.stats_range(500, 700)
+    for f in T.STATS_FIELDS:
+        assert np.array_equal(a[f], b[f]), f
+    # a checkpoint of another network is refused
+    other = T.Simulation(N.small_grid_scenario(3, 1, 20, 50, 50, 100, gen_seed=1))
+    with pytest.raises(T.TsError, match="INVALID"):
+        other.load(ck)
+    for s in (full, resumed, other):
+        s.close()

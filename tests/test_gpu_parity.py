@@ -341,3 +341,22 @@ def test_large_tiles_on_a_loaded_grid():
     # 256-word tiles: every word phase loops twice per tile
     sc = N.small_grid_scenario(6, 3, 60, 4000, 300, 900, gen_seed=31, seed=8)
     run_parity(sc, 900, chunk=300, state_every=300, tile_words=256)
+
+
+def test_config1_busy_window_from_the_oracle_state():
+    # full-size config 1 started from the oracle's own state at step 2,400
+    # (congestion building up), then 300 steps on both sides, with the
+    # bench's load balancing
+    sc = N.config1()
+    orc = oracle.Oracle(sc)
+    orc.step(2400)
+    s = orc.get_state()
+    init = N.InitialState(**{k: s[k] for k in ("cell_id", "cell_v", "buf_id", "buf_v", "cursor", "dep_head")},
+                          step=s["step"], arrived=s["arrived"], inserted=s["inserted"])
+    sim = T.Simulation(sc)
+    sim.set_load_balance(64, 768)
+    sim.write_state(init)
+    sim.step(300)
+    _cmp_stats(sim.stats_range(2400, 300), orc.step(300), "config1 from step 2400")
+    _cmp_state(sim.read_state(), orc.get_state(), "config1 after step 2699")
+    sim.close()

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -620,6 +621,59 @@ static uint2 queue_head(const ts_ctx *c, uint32_t l, uint32_t h) {
     return make_uint2(h, h < c->dep_off[l + 1] ? c->depart[c->dep_ids[h]] : 0xFFFFFFFFu);
 }
 
+// Host-to-device copy of a large pageable buffer: host threads fill two
+// pinned staging buffers in turn while the copy engine drains the other, so
+// the transfer is not limited by one thread's pageable staging.  The staging
+// buffers are allocated on first use and kept for the process; without
+// them (allocation refused) the copy is a plain cudaMemcpy.
+static ts_status upload_large(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    constexpr size_t kStage = 128ull << 20;
+    static std::mutex mu;
+    static void *stage[2] = {nullptr, nullptr};
+    if (bytes < 2 * kStage) {
+        CK(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+        return TS_OK;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < 2; ++i)
+        if (!stage[i] && cudaHostAlloc(&stage[i], kStage, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            stage[i] = nullptr;
+        }
+    if (!stage[0] || !stage[1]) {
+        CK(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+        return TS_OK;
+    }
+    cudaEvent_t done[2];
+    CK(cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&done[1], cudaEventDisableTiming));
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t nt = std::max<size_t>(1, std::min<size_t>(hw ? hw : 1u, 16u));
+    const char *from = static_cast<const char *>(src);
+    char *to = static_cast<char *>(dst);
+    cudaError_t e = cudaSuccess;
+    int buf = 0;
+    for (size_t off = 0; off < bytes && e == cudaSuccess; off += kStage, buf ^= 1) {
+        const size_t n = std::min(kStage, bytes - off);
+        if (off >= 2 * kStage) e = cudaEventSynchronize(done[buf]);  // this buffer's previous copy
+        if (e != cudaSuccess) break;
+        char *st = static_cast<char *>(stage[buf]);
+        std::vector<std::thread> pool;
+        for (size_t t = 1; t < nt; ++t)
+            pool.emplace_back([=] { memcpy(st + n * t / nt, from + off + n * t / nt, n * (t + 1) / nt - n * t / nt); });
+        memcpy(st, from + off, n / nt);
+        for (auto &th : pool) th.join();
+        e = cudaMemcpyAsync(to + off, st, n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(done[buf], s);
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaEventDestroy(done[0]);
+    cudaEventDestroy(done[1]);
+    if (e != cudaSuccess) return cuda_fail(e, "route upload");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "route upload");
+    return TS_OK;
+}
+
 static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
     free_list(c, c->veh_allocs);
     auto &A = c->veh_allocs;
@@ -663,7 +717,10 @@ static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
         CK(cudaMemcpy(dep_ids, ids.data(), 4ull * n, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(dep_steps, steps.data(), 4ull * n, cudaMemcpyHostToDevice));
     }
-    if (total) CK(cudaMemcpy(routes, links, 4ull * total, cudaMemcpyHostToDevice));
+    if (total) {
+        const ts_status su = upload_large(routes, links, 4ull * total, c->stream);
+        if (su != TS_OK) return su;
+    }
     CK(cudaMemcpy(const_cast<uint4 *>(c->sd.nd_info), nd.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
     std::vector<uint2> heads(L);
     for (uint32_t l = 0; l < L; ++l) heads[l] = queue_head(c, l, c->dep_off[l]);

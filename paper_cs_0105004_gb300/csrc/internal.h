@@ -51,7 +51,8 @@ constexpr uint32_t kMaxCells = 1u << 22;      // cells per link (buffer digest p
 constexpr int kTileWords = 256;               // occupancy words per link tile (all lanes), at most
 constexpr int kDefaultTileWords = 128;        // the default tile size
 constexpr int kTileMaxCols = 129;             // columns per tile (one-lane links, plus a merged tail)
-constexpr int kLinkThreads = 256;
+constexpr int kLinkThreads = 256;       // link-kernel block for large tiles (and the most threads of any)
+constexpr int kSmallTileThreads = 192;  // for default tiles: 140 words with halos, 5 blocks per SM
 constexpr int kNodeThreads = 128;
 constexpr uint32_t kStatsRing = 4096;         // steps of statistics kept on the device
 constexpr uint32_t kChunk = 32;               // steps per captured graph

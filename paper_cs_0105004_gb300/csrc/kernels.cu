@@ -245,7 +245,7 @@ struct LinkSmem {
     uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
     uint32_t nlist[2];                // vehicles in the lane-change list and in the velocity list
     uint16_t code[kList];             // (local word << 5) | bit
-    unsigned long long red[kLinkThreads / 32][7];
+    unsigned long long red[kLinkThreads / 32][7];  // per warp (at most kLinkThreads threads)
     unsigned long long xacc[6];       // node-transfer counts of the current previous-step record
     int ncols, nwords, ncore_words, nlinks;
 };
@@ -409,8 +409,18 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
     return n_placed;
 }
 
+// Threads of a link-kernel block for tiles of at most TW words: one per word
+// of the default tile (halos included), or 256 for the large tiles; as many
+// blocks per SM as 64 registers per thread allow.
 template <int TW>
-__global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__restrict__ table,
+struct LinkLaunch {
+    static constexpr int kThreads = TW <= kDefaultTileWords ? kSmallTileThreads : kLinkThreads;
+    static constexpr int kMinBlocks = 65536 / (kThreads * 64);
+};
+
+template <int TW>
+__global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
+    link_kernel(const ScenDev *__restrict__ table,
                                                             const LinkTile *__restrict__ tiles,
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
                                                             uint32_t xfer) {
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         unsigned long long v[7] = {acc[0], acc[1], acc[2], (unsigned long long)(long long)(int)acc[3],
                                    (unsigned long long)(long long)(int)acc[4],
                                    (unsigned long long)(long long)(int)acc[5], acc_hash};
-        block_flush<7, kLinkThreads>(v, rec, kField, S.red);
+        block_flush<7, LinkLaunch<TW>::kThreads>(v, rec, kField, S.red);
 #pragma unroll
         for (int f = 0; f < 6; ++f) acc[f] = 0u;
         acc_hash = 0ull;
@@ -619,7 +629,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
 
         // ---------------- state of step t (occ0/mov0 start at zero: the word
         // loads and the placements of the node transfers are or-ed in)
-        for (int w = threadIdx.x; w < nwords; w += kLinkThreads) {
+        for (int w = threadIdx.x; w < nwords; w += LinkLaunch<TW>::kThreads) {
             const uint32_t g = S.gw[w];
             const uint32_t o = D.occ[cur][g];
             if (o) {
@@ -631,7 +641,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         }
         {
             // link threads, counted down from the last thread
-            const int q = kLinkThreads - 1 - (int)threadIdx.x;
+            const int q = LinkLaunch<TW>::kThreads - 1 - (int)threadIdx.x;
             if (q < S.nlinks) acc[0] += link_buffers_phase(S, D, q, cur, t, do_xfer);
         }
         __syncthreads();
@@ -650,7 +660,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         // Moving vehicles and vehicles near a link end are decided one by one.
         const bool lc_on = D.lane_change != 0u;
         if (lc_on) {
-            for (int wb = 0; wb < nwords; wb += kLinkThreads) {  // uniform per warp (list_append)
+            for (int wb = 0; wb < nwords; wb += LinkLaunch<TW>::kThreads) {  // uniform per warp (list_append)
             const int w = wb + (int)threadIdx.x;
             uint32_t listed = 0u;
             if (w < nwords) {
@@ -714,7 +724,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         // v = 0, an occupied cell ahead, no lane change and far from the link
         // end keeps v = 0 and its cell: its bits are copied, its payload stays.
         {
-            for (int wb = 0; wb < nwords; wb += kLinkThreads) {  // uniform per warp (list_append)
+            for (int wb = 0; wb < nwords; wb += LinkLaunch<TW>::kThreads) {  // uniform per warp (list_append)
             const int w = wb + (int)threadIdx.x;
             uint32_t listed = 0u;
             if (w < nwords) {
@@ -852,7 +862,7 @@ __global__ void __launch_bounds__(kLinkThreads, 4) link_kernel(const ScenDev *__
         stamp(6, first);
 
         // ---------------- write the state of step t+1 and the buffer states
-        for (int w = threadIdx.x; w < ncore_words; w += kLinkThreads) {
+        for (int w = threadIdx.x; w < ncore_words; w += LinkLaunch<TW>::kThreads) {
             const uint32_t g = S.gw[w];
             D.occ[nxt][g] = S.oocc[w];
             D.mov[nxt][g] = S.omov[w];
@@ -1073,9 +1083,11 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap) {
     if (tile_cap <= (uint32_t)kDefaultTileWords)
-        launch_pdl(link_kernel<kDefaultTileWords>, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i, xfer ? 1u : 0u);
+        launch_pdl(link_kernel<kDefaultTileWords>, grid, LinkLaunch<kDefaultTileWords>::kThreads, pdl, s, table, tiles,
+                   n_tiles, i, xfer ? 1u : 0u);
     else
-        launch_pdl(link_kernel<kTileWords>, grid, kLinkThreads, pdl, s, table, tiles, n_tiles, i, xfer ? 1u : 0u);
+        launch_pdl(link_kernel<kTileWords>, grid, LinkLaunch<kTileWords>::kThreads, pdl, s, table, tiles, n_tiles, i,
+                   xfer ? 1u : 0u);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
@@ -1129,15 +1141,20 @@ extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
 #endif
 
 int max_link_blocks(uint32_t tile_cap) {
-    if (tile_cap <= (uint32_t)kDefaultTileWords) return resident_blocks((const void *)link_kernel<kDefaultTileWords>,
-                                                                         kLinkThreads);
+    if (tile_cap <= (uint32_t)kDefaultTileWords) {
+        // five blocks of the default instance need more shared memory than
+        // the smallest L1/shared splits give
+        const void *fn = (const void *)link_kernel<kDefaultTileWords>;
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+        return resident_blocks(fn, LinkLaunch<kDefaultTileWords>::kThreads);
+    }
     // the large-tile instance needs more shared memory per block than the
     // default L1/shared split leaves for four blocks; the largest shared
     // share measured fastest on GB300 (config 3: 3.3e10 vs 2.4e10
     // vehicle-updates/s with the default split)
     const void *fn = (const void *)link_kernel<kTileWords>;
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    return resident_blocks(fn, kLinkThreads);
+    return resident_blocks(fn, LinkLaunch<kTileWords>::kThreads);
 }
 int max_node_blocks() { return resident_blocks((const void *)node_kernel, kNodeThreads); }
 

@@ -44,7 +44,7 @@ STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
 # an ncu --set full capture (caches flushed) of config 1 at step 5,000
 # (--profile-window 5000:64).  Valid only while link_kernel is unchanged
 # since that capture.
-LINK_TRAFFIC_BYTES = {"config1": 4867072.0 + 1024.0}
+LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

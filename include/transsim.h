@@ -249,9 +249,9 @@ ts_status ts_ctx_step(ts_ctx *ctx, uint64_t *step);
 void ts_batch_destroy(ts_batch *b);
 
 /* Kernel launch shape: occupancy words (32-cell columns times lanes) per
- * link tile, 8..256.  The default is 128, or 256 for a network whose
- * 128-word tiles outnumber twice the link kernel's resident blocks.
- * Results do not depend on it.  ts_tile_words returns the current value. */
+ * link tile, 8..256 (default 128; tiles above 128 words run in a kernel
+ * instance with larger blocks).  Results do not depend on it.
+ * ts_tile_words returns the current value. */
 ts_status ts_set_tile_words(ts_ctx *ctx, uint32_t words);
 uint32_t ts_tile_words(const ts_ctx *ctx);
 

@@ -538,12 +538,6 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
         if (c->node_in_off[n + 1] - c->node_in_off[n] > 255u)
             return fail(TS_ERR_INVALID, "more than 255 lanes end at one node");
     build_tiles(c.get(), nullptr);
-    // a network with many more default tiles than resident blocks runs
-    // throughput-bound: larger tiles spread each tile's fixed cost wider
-    if (c->link_tiles.size() > 2u * (size_t)max_link_blocks(kDefaultTileWords)) {
-        c->tile_words = kTileWords;
-        build_tiles(c.get(), nullptr);
-    }
     c->n_sub = c->link_tiles.size() >= 64 ? 8u : 1u;  // small networks keep one sub-record per step
     // device arrays of the network
     bool ok = true;

@@ -217,8 +217,13 @@ class Simulation:
         dep = np.ascontiguousarray(dem.depart_step, np.uint32)
         off = np.ascontiguousarray(dem.route_offsets, np.uint32)
         links = np.ascontiguousarray(dem.route_links, np.uint32)
-        _check(L.ts_load_vehicles(self.h, dem.n, _p(dep, ctypes.c_uint32), _p(off, ctypes.c_uint32),
-                                  _p(links, ctypes.c_uint32)))
+        rc = L.ts_load_vehicles(self.h, dem.n, _p(dep, ctypes.c_uint32), _p(off, ctypes.c_uint32),
+                                _p(links, ctypes.c_uint32))
+        if rc != TS_OK:
+            msg = L.ts_last_error().decode(errors="replace")
+            L.ts_destroy(self.h)
+            self.h = None
+            raise TsError(rc, msg)
         cells, lanes, veh, nl = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         _check(L.ts_state_sizes(self.h, ctypes.byref(cells), ctypes.byref(lanes), ctypes.byref(veh), ctypes.byref(nl)))
         self.n_lane_cells, self.n_lanes, self.n_veh, self.n_links = cells.value, lanes.value, veh.value, nl.value

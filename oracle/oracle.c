@@ -44,6 +44,21 @@
  * the end; l's lanes are green at step t iff (t + offset) mod cycle < green
  * (cycle 0: no signal).  A vehicle already in the link-end buffer crosses.
  *
+ * Lane changing for plan following (Sec. 3: a driver who must turn at the
+ * end of the link needs the right lane for it, and the gap such a driver
+ * accepts shrinks as the intersection comes closer).  An optional turn
+ * table lists, for every link l and every link m leaving l's end node
+ * (ascending link id), the lanes of l from which a vehicle may continue
+ * onto m (bit k = lane k).  A vehicle's allowed lanes are those of the turn
+ * to the next link of its route (all lanes on its last link, or without a
+ * table).  Readings: the extra cell at the link end is open only from an
+ * allowed lane (from any other lane the end is closed, as at a red light);
+ * a vehicle outside its allowed lanes has a reason to change when an
+ * allowed lane lies on the side the step's direction points to, and then
+ * needs the target cell and only the min(vmax, dist) cells behind it
+ * empty, dist = cells between it and the link's last cell; the speed reason
+ * applies only into an allowed lane.
+ *
  * Link travel times (the input of the re-planning step of the relaxation
  * iterations, Sec. 1): a vehicle that enters a link at the end of step t0
  * (a departure or a node transfer) and leaves it at the end of step t1 (a
@@ -68,6 +83,9 @@ typedef struct oracle {
     uint32_t *from, *to, *cells, *lanes;
     uint8_t *ring;
     uint32_t *sig;        /* [3 * n_links] signal cycle, green, offset (all 0: none) */
+    uint8_t *turn;        /* turn table (NULL: every lane for every turn)  */
+    uint32_t *turn_off;   /* first turn-table entry of each link          */
+    uint32_t *out_off, *out_link; /* per node: outgoing links, ascending id */
     uint64_t t_now;       /* step being computed (for the signals)        */
     uint32_t *lane_base;  /* first canonical lane of each link            */
     uint32_t *lane_link;  /* link of each canonical lane                  */
@@ -149,6 +167,19 @@ static int is_last_link(const oracle *o, int32_t id) {
     return o->cursor[id] + 1 == o->route_off[id + 1] - o->route_off[id];
 }
 
+/* Lanes of the vehicle's current link from which it may continue onto the
+ * next link of its route: bit k = lane k. */
+static uint32_t allowed_lanes(const oracle *o, int32_t id) {
+    uint32_t l = o->route[o->route_off[id] + o->cursor[id]];
+    uint32_t all = (1u << o->lanes[l]) - 1u;
+    if (!o->turn || is_last_link(o, id)) return all;
+    uint32_t m = o->route[o->route_off[id] + o->cursor[id] + 1];
+    uint32_t n = o->to[l];
+    for (uint32_t j = o->out_off[n]; j < o->out_off[n + 1]; j++)
+        if (o->out_link[j] == m) return o->turn[o->turn_off[l] + (j - o->out_off[n])];
+    abort(); /* the route is not connected: rejected when loaded */
+}
+
 static int is_green(const oracle *o, uint32_t l) {
     uint32_t cycle = o->sig[3 * l], green = o->sig[3 * l + 1], offset = o->sig[3 * l + 2];
     if (cycle == 0) return 1;
@@ -158,8 +189,8 @@ static int is_green(const oracle *o, uint32_t l) {
 /* Free cells ahead of (l,k,x) in state S, at most vmax (Sec. 3 rule (ii);
  * Sec. 4: interaction range 5 cells).  There is no look-ahead across a
  * node; at the link end the gap counts one more cell when the light there
- * is green and the lane's link-end buffer is free or this is the vehicle's
- * last link. */
+ * is green, the lane's link-end buffer is free or this is the vehicle's
+ * last link, and the lane is one of the vehicle's allowed lanes. */
 static uint32_t gap_ahead(const oracle *o, const int32_t *S, const int32_t *buf, uint32_t l, uint32_t k,
                           uint32_t x, int32_t id) {
     uint32_t L = o->cells[l];
@@ -169,7 +200,8 @@ static uint32_t gap_ahead(const oracle *o, const int32_t *S, const int32_t *buf,
             if (o->ring[l]) {
                 y -= L;
             } else {
-                uint32_t open = is_green(o, l) && ((buf[o->lane_base[l] + k] < 0) || is_last_link(o, id));
+                uint32_t open = is_green(o, l) && ((buf[o->lane_base[l] + k] < 0) || is_last_link(o, id)) &&
+                                ((allowed_lanes(o, id) >> k) & 1u);
                 uint32_t g = i - 1 + open;
                 return g < o->vmax ? g : o->vmax;
             }
@@ -179,13 +211,13 @@ static uint32_t gap_ahead(const oracle *o, const int32_t *S, const int32_t *buf,
     return o->vmax;
 }
 
-/* Safety check of a lane change into (l,k,x): the target cell and the vmax
- * cells behind it must be empty (on a non-periodic link only the cells that
- * exist behind x). */
-static int room_to_get_in(const oracle *o, const int32_t *S, uint32_t l, uint32_t k, uint32_t x) {
+/* Safety check of a lane change into (l,k,x): the target cell and the
+ * `back` cells behind it must be empty (on a non-periodic link only the
+ * cells that exist behind x). */
+static int room_to_get_in(const oracle *o, const int32_t *S, uint32_t l, uint32_t k, uint32_t x, uint32_t back) {
     uint32_t L = o->cells[l];
     if (S[cell_index(o, l, k, x)] >= 0) return 0;
-    for (uint32_t i = 1; i <= o->vmax; i++) {
+    for (uint32_t i = 1; i <= back; i++) {
         uint32_t y;
         if (i > x) {
             if (!o->ring[l]) break;
@@ -202,6 +234,7 @@ static int room_to_get_in(const oracle *o, const int32_t *S, uint32_t l, uint32_
 void oracle_destroy(oracle *o) {
     if (!o) return;
     free(o->from); free(o->to); free(o->cells); free(o->lanes); free(o->ring); free(o->sig);
+    free(o->turn); free(o->turn_off); free(o->out_off); free(o->out_link);
     free(o->lane_base); free(o->lane_link); free(o->cell_base); free(o->in_off); free(o->in_lane);
     free(o->depart); free(o->route_off); free(o->route); free(o->q_off); free(o->q_id);
     free(o->cell); free(o->buf); free(o->vel); free(o->cursor); free(o->status); free(o->dep_head);
@@ -213,7 +246,8 @@ void oracle_destroy(oracle *o) {
 /* Returns NULL on invalid input or out of memory. */
 oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, const uint32_t *to,
                       const uint32_t *cells, const uint32_t *lanes, const uint8_t *ring, const uint32_t *signal,
-                      uint32_t vmax, uint32_t p_threshold, uint64_t seed, uint32_t lane_change) {
+                      const uint8_t *turn, uint32_t vmax, uint32_t p_threshold, uint64_t seed,
+                      uint32_t lane_change) {
     if (vmax < 1 || n_links == 0) return NULL;
     oracle *o = (oracle *)calloc(1, sizeof(oracle));
     if (!o) return NULL;
@@ -271,6 +305,33 @@ oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, 
             if (!o->ring[l])
                 for (uint32_t k = 0; k < lanes[l]; k++) o->in_lane[fill[to[l]]++] = o->lane_base[l] + k;
         free(fill);
+    }
+    /* outgoing links of every node, ascending id, and the turn table */
+    o->out_off = (uint32_t *)calloc((size_t)n_nodes + 1, 4);
+    o->out_link = (uint32_t *)malloc(4ull * n_links);
+    o->turn_off = (uint32_t *)malloc(4ull * (n_links + 1));
+    if (!o->out_off || !o->out_link || !o->turn_off) goto fail;
+    for (uint32_t l = 0; l < n_links; l++)
+        if (!o->ring[l]) o->out_off[from[l] + 1]++;
+    for (uint32_t n = 0; n < n_nodes; n++) o->out_off[n + 1] += o->out_off[n];
+    {
+        uint32_t *fill = (uint32_t *)malloc(4ull * (n_nodes + 1));
+        if (!fill) goto fail;
+        memcpy(fill, o->out_off, 4ull * (n_nodes + 1));
+        for (uint32_t l = 0; l < n_links; l++)
+            if (!o->ring[l]) o->out_link[fill[from[l]]++] = l;
+        free(fill);
+    }
+    o->turn_off[0] = 0;
+    for (uint32_t l = 0; l < n_links; l++)
+        o->turn_off[l + 1] = o->turn_off[l] + (o->ring[l] ? 0 : o->out_off[to[l] + 1] - o->out_off[to[l]]);
+    if (turn) {
+        o->turn = (uint8_t *)malloc(o->turn_off[n_links] ? o->turn_off[n_links] : 1);
+        if (!o->turn) goto fail;
+        memcpy(o->turn, turn, o->turn_off[n_links]);
+        for (uint32_t l = 0; l < n_links; l++)
+            for (uint32_t j = o->turn_off[l]; j < o->turn_off[l + 1]; j++)
+                if (o->turn[j] == 0 || o->turn[j] >> lanes[l]) goto fail; /* no lane, or a lane l lacks */
     }
     o->cell = (int32_t *)malloc(4ull * o->n_cells);
     o->s_start = (int32_t *)malloc(4ull * o->n_cells);
@@ -382,8 +443,20 @@ static void step_once(oracle *o, oracle_stats *st) {
                     uint32_t g_own = gap_ahead(o, o->s_start, o->buf_start, l, k, x, id);
                     uint32_t g_tgt = gap_ahead(o, o->s_start, o->buf_start, l, (uint32_t)kt, x, id);
                     uint32_t want_v = v + 1 < vmax ? v + 1 : vmax;
-                    int reason = g_own < want_v && g_tgt > g_own;
-                    if (reason && room_to_get_in(o, o->s_start, l, (uint32_t)kt, x)) {
+                    /* plan following: outside the allowed lanes, with one of
+                     * them on the side d points to */
+                    uint32_t allowed = allowed_lanes(o, id);
+                    int toward = 0;
+                    for (uint32_t j = 0; j < o->lanes[l]; j++)
+                        if (((allowed >> j) & 1u) && ((int)j - (int)k) * d > 0) toward = 1;
+                    int plan = !((allowed >> k) & 1u) && toward;
+                    /* the faster lane, if it is an allowed one */
+                    int faster = g_own < want_v && g_tgt > g_own && ((allowed >> kt) & 1u);
+                    /* the gap accepted behind: vmax cells, shrinking to 0 over
+                     * the last vmax cells for a plan-following change */
+                    uint32_t back = vmax;
+                    if (plan && !o->ring[l] && o->cells[l] - 1 - x < back) back = o->cells[l] - 1 - x;
+                    if ((plan || faster) && room_to_get_in(o, o->s_start, l, (uint32_t)kt, x, back)) {
                         o->s_lc[cell_index(o, l, k, x)] = -1;
                         o->s_lc[cell_index(o, l, (uint32_t)kt, x)] = id;
                         st->lane_changes++;

@@ -41,6 +41,11 @@ class Network:
     # offset): the lanes' ends are green at step t iff (t + offset) mod cycle
     # < green; cycle 0 = no signal.  None: no signals at all.
     link_signal: Optional[np.ndarray] = None
+    # turn lanes (plan-following lane changes): for every non-ring link l and
+    # every non-ring link m leaving l's end node (ascending link id), in that
+    # order, one uint8 whose bit k says that lane k of l may be used to
+    # continue onto m.  None: every lane for every turn.
+    turn_lanes: Optional[np.ndarray] = None
 
     @property
     def n_links(self) -> int:
@@ -396,12 +401,52 @@ def grid_signals(net: Network, n_side: int, cycle: int, green: int) -> np.ndarra
     return sig
 
 
+def turn_table_offsets(net: Network) -> np.ndarray:
+    """First turn-table entry of every link (n_links + 1 entries): a non-ring
+    link has one entry per non-ring link leaving its end node."""
+    ring = np.asarray(net.link_ring, bool)
+    outdeg = np.bincount(np.asarray(net.link_from, np.int64)[~ring], minlength=net.n_nodes)
+    per = np.where(ring, 0, outdeg[np.where(ring, 0, np.asarray(net.link_to, np.int64))])
+    off = np.zeros(net.n_links + 1, np.int64)
+    np.cumsum(per, out=off[1:])
+    return off
+
+
+def turn_lanes_by_rank(net: Network) -> np.ndarray:
+    """Synthetic turn lanes: the n links leaving a link's end node, in
+    ascending id, share the link's L lanes in order, lane k serving turns
+    [k n / L, (k+1) n / L): turn j may use lane k iff those ranges overlap
+    (j L < (k+1) n and k n < (j+1) L).  Every turn gets at least one lane and
+    every lane at least one turn; a one-lane link serves every turn."""
+    off = turn_table_offsets(net)
+    out = np.zeros(int(off[-1]), np.uint8)
+    lanes = np.asarray(net.link_lanes, np.int64)
+    for l in range(net.n_links):
+        n = int(off[l + 1] - off[l])
+        L = int(lanes[l])
+        for j in range(n):
+            m = 0
+            for k in range(L):
+                if j * L < (k + 1) * n and k * n < (j + 1) * L:
+                    m |= 1 << k
+            out[off[l] + j] = m
+    return out
+
+
 def small_grid_scenario(n_side=3, lanes=2, cells=20, n_trips=60, window=60, steps=200,
-                        gen_seed=0, seed=1, vmax=5, p_threshold=P_THRESHOLD_0_2, signal=None) -> Scenario:
-    """signal = (cycle, green): a traffic light at every link end (grid_signals)."""
+                        gen_seed=0, seed=1, vmax=5, p_threshold=P_THRESHOLD_0_2, signal=None,
+                        turns=False, lane_seed=None) -> Scenario:
+    """signal = (cycle, green): a traffic light at every link end (grid_signals).
+    turns: turn lanes by rank (turn_lanes_by_rank).  lane_seed: lanes per
+    undirected edge ~ U{1..lanes} from that seed instead of `lanes` everywhere."""
     net = grid_network(n_side, lanes, cells)
+    if lane_seed is not None:
+        per_edge = np.random.default_rng(lane_seed).integers(1, lanes + 1, net.n_links // 2)
+        net = dataclasses.replace(net, link_lanes=np.repeat(per_edge, 2).astype(np.uint32))
     if signal is not None:
         net = dataclasses.replace(net, link_signal=grid_signals(net, n_side, *signal))
+    if turns:
+        net = dataclasses.replace(net, turn_lanes=turn_lanes_by_rank(net))
     rng = np.random.default_rng(gen_seed)
     o, d, dep = uniform_trips(net, n_trips, window, rng)
     return Scenario(f"grid{n_side}x{n_side}", net, _demand(net, o, d, dep, 1), steps, seed, vmax, p_threshold)

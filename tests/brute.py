@@ -35,6 +35,18 @@ class Brute:
         self.frm = [int(c) for c in net.link_from]
         self.to = [int(c) for c in net.link_to]
         self.n_nodes = net.n_nodes
+        # turn lanes: (link, next link) -> set of lanes; the table lists, per
+        # link, the links leaving its end node in ascending id
+        self.turn = None
+        if getattr(net, "turn_lanes", None) is not None:
+            self.turn = {}
+            j = 0
+            for l in range(len(self.cells)):
+                if self.ring[l]:
+                    continue
+                for m in sorted(m for m in range(len(self.cells)) if self.frm[m] == self.to[l] and not self.ring[m]):
+                    self.turn[(l, m)] = {k for k in range(self.lanes[l]) if int(net.turn_lanes[j]) >> k & 1}
+                    j += 1
         off = [int(c) for c in dem.route_offsets]
         self.routes = [[int(x) for x in dem.route_links[off[i]:off[i + 1]]] for i in range(dem.n)]
         self.depart = [int(x) for x in dem.depart_step]
@@ -75,13 +87,18 @@ class Brute:
     def last(self, i):
         return self.cur[i] == len(self.routes[i]) - 1
 
+    def allowed(self, i, l):
+        if self.turn is None or self.last(i):
+            return set(range(self.lanes[l]))
+        return self.turn[(l, self.routes[i][self.cur[i] + 1])]
+
     def gap(self, occ, buf, l, k, x, i):
         L = self.cells[l]
         g = 0
         while g < self.vmax:
             y = x + g + 1
             if y >= L and not self.ring[l]:
-                if (l, k) not in buf or self.last(i):
+                if ((l, k) not in buf or self.last(i)) and k in self.allowed(i, l):
                     g += 1
                 return min(g, self.vmax)
             if (l, k, y % L) in occ:
@@ -104,10 +121,16 @@ class Brute:
                     continue
                 go = self.gap(old, buf0, l, k, x, i)
                 gt = self.gap(old, buf0, l, kt, x, i)
-                if not (go < min(self.v[i] + 1, vmax) and gt > go):
+                ok = self.allowed(i, l)
+                need_lane = k not in ok and any((j - k) * d > 0 for j in ok)
+                faster = go < min(self.v[i] + 1, vmax) and gt > go and kt in ok
+                if not (need_lane or faster):
                     continue
                 L = self.cells[l]
-                behind = range(x - vmax, x + 1) if self.ring[l] else range(max(0, x - vmax), x + 1)
+                back = vmax
+                if need_lane and not self.ring[l]:
+                    back = min(vmax, L - 1 - x)
+                behind = range(x - back, x + 1) if self.ring[l] else range(max(0, x - back), x + 1)
                 if any((l, kt, y % L) in old for y in behind):
                     continue
                 moves.append(((l, k, x), (l, kt, x), i))

@@ -346,3 +346,153 @@ def test_no_vehicle_reaches_a_red_lane_end():
         before = after
         arrived = int(st["arrived"][0])
     assert arrived > 0
+
+
+# ------------------------------------------------------------------ plan-following lane changes
+
+def _fork(placed, routes, lane_change=1, start_step=0, turns=(0b01, 0b10)):
+    # link 0 (2 lanes, 20 cells) ends at node 1, which links 1 and 2 leave;
+    # the turn onto link 1 is taken from lane 0 only, onto link 2 from lane 1
+    sc = make_scenario([(0, 1, 20, 2), (1, 2, 10, 1), (1, 3, 10, 1)], 4, routes, [0] * len(routes), p=0,
+                       lane_change=lane_change, placed=placed, start_step=start_step)
+    if turns is not None:
+        sc.net.turn_lanes = np.array(turns, np.uint8)
+    return sc
+
+
+def test_turn_table_generator_covers_every_turn_and_lane():
+    net = N.small_grid_scenario(4, 4, 20, lane_seed=5, turns=True).net
+    off = N.turn_table_offsets(net)
+    for l in range(net.n_links):
+        masks = net.turn_lanes[off[l]:off[l + 1]].astype(int)
+        assert len(masks) == int((net.link_from == net.link_to[l]).sum())
+        full = (1 << int(net.link_lanes[l])) - 1
+        assert all(0 < m <= full for m in masks)
+        assert np.bitwise_or.reduce(masks) == full
+    # three lanes, three turns: one lane each, in order
+    assert N.turn_lanes_by_rank(N.Network(4, np.array([0, 1, 1, 1], np.uint32), np.array([1, 2, 3, 0], np.uint32),
+                                          np.full(4, 10, np.uint32), np.array([3, 1, 1, 1], np.uint32),
+                                          np.zeros(4, np.uint8)))[:3].tolist() == [1, 2, 4]
+
+
+def test_wrong_lane_changes_towards_its_turn_on_the_next_odd_step():
+    # vehicle 0 in lane 1 must take the turn onto link 1 (lane 0 only).  Step
+    # 0 points to lane 2, which does not exist: it only drives (v 1, cell 1).
+    # Step 1 points to lane 0: it changes there and accelerates to cell 3.
+    sc = _fork([(0, 0, 1, 0, 0)], [[0, 1]])
+    o = oracle.Oracle(sc)
+    st = o.step(2)
+    assert positions(o.get_state(), sc.net)[0] == (0, 0, 3, 2)
+    assert [int(s["lane_changes"]) for s in st] == [0, 1]
+    # without a turn table there is no reason to change
+    sc = _fork([(0, 0, 1, 0, 0)], [[0, 1]], turns=None)
+    o = oracle.Oracle(sc)
+    assert [int(s["lane_changes"]) for s in o.step(2)] == [0, 0]
+
+
+def test_accepted_gap_shrinks_near_the_intersection():
+    # vehicle 0 (wrong lane 1) with vehicle 1 stopped two cells behind it in
+    # lane 0, at step 1 (d = -1).  Far from the link end the change needs the
+    # 5 cells behind the target cell empty: no change.  On cell 18 (one cell
+    # before the last) it needs only one: it changes.
+    far = _fork([(0, 0, 1, 10, 0), (1, 0, 0, 8, 0)], [[0, 1], [0, 1]], start_step=1)
+    o = oracle.Oracle(far)
+    assert int(o.step(1)[0]["lane_changes"]) == 0
+    near = _fork([(0, 0, 1, 18, 0), (1, 0, 0, 16, 0)], [[0, 1], [0, 1]], start_step=1)
+    o = oracle.Oracle(near)
+    assert int(o.step(1)[0]["lane_changes"]) == 1
+    assert positions(o.get_state(), near.net)[0][:2] == (0, 0)
+    # in the last cell it needs only the target cell: a vehicle right behind
+    # that cell does not stop it, one in it does
+    last = _fork([(0, 0, 1, 19, 0), (1, 0, 0, 18, 0)], [[0, 1], [0, 1]], start_step=1)
+    o = oracle.Oracle(last)
+    assert int(o.step(1)[0]["lane_changes"]) == 1
+    taken = _fork([(0, 0, 1, 19, 0), (1, 0, 0, 19, 0)], [[0, 1], [0, 1]], start_step=1)
+    o = oracle.Oracle(taken)
+    assert int(o.step(1)[0]["lane_changes"]) == 0
+
+
+def test_wrong_lane_stops_at_the_link_end():
+    # lane changes off: vehicle 0 in lane 1 needs lane 0 for its turn.  It
+    # runs cells 1,3,6,10,15 and stops in the last cell (19) with v 4 then 0,
+    # never entering the buffer; the same vehicle heading for link 2 (lane 1
+    # allowed) crosses.
+    sc = _fork([(0, 0, 1, 0, 0)], [[0, 1]], lane_change=0)
+    o = oracle.Oracle(sc)
+    seen = []
+    for _ in range(12):
+        o.step(1)
+        seen.append(positions(o.get_state(), sc.net)[0])
+    assert seen[4] == (0, 1, 15, 5) and seen[5] == (0, 1, 19, 4)
+    assert all(p == (0, 1, 19, 0) for p in seen[6:])
+    sc = _fork([(0, 0, 1, 0, 0)], [[0, 2]], lane_change=0)
+    o = oracle.Oracle(sc)
+    o.step(6)
+    assert positions(o.get_state(), sc.net)[0] == (2, 0, 0, 5)
+
+
+def test_speed_change_only_into_an_allowed_lane():
+    # vehicle 0 (lane 0, v 3) closes on vehicle 1 stopped two cells ahead at
+    # step 0 (d = +1).  Without a table it overtakes by changing to lane 1; when
+    # its turn allows lane 0 only, it stays behind.
+    placed = [(0, 0, 0, 5, 3), (1, 0, 0, 7, 0)]
+    o = oracle.Oracle(_fork(placed, [[0, 1], [0, 1]], turns=None))
+    assert int(o.step(1)[0]["lane_changes"]) == 1
+    sc = _fork(placed, [[0, 1], [0, 1]])
+    o = oracle.Oracle(sc)
+    assert int(o.step(1)[0]["lane_changes"]) == 0
+    assert positions(o.get_state(), sc.net)[0] == (0, 0, 6, 1)
+
+
+def test_every_lane_allowed_equals_no_table():
+    sc = N.small_grid_scenario(4, 3, 20, n_trips=500, window=200, steps=500, gen_seed=7, seed=8, lane_seed=3)
+    a = oracle.Oracle(sc).step(500)
+    off = N.turn_table_offsets(sc.net)
+    full = np.repeat((1 << sc.net.link_lanes.astype(np.int64)) - 1, np.diff(off)).astype(np.uint8)
+    sc.net.turn_lanes = full
+    b = oracle.Oracle(sc).step(500)
+    assert np.array_equal(a, b)
+
+
+def test_vehicles_leave_links_only_from_allowed_lanes():
+    sc = N.small_grid_scenario(4, 4, 20, n_trips=600, window=200, steps=700, gen_seed=9, seed=10, lane_seed=4,
+                               turns=True)
+    net, dem = sc.net, sc.demand
+    off = N.turn_table_offsets(net)
+    outs = {n: sorted(np.nonzero(net.link_from == n)[0].tolist()) for n in range(net.n_nodes)}
+    lb = net.lane_base()
+    lane_link = np.repeat(np.arange(net.n_links), net.link_lanes.astype(np.int64))
+    o = oracle.Oracle(sc)
+    prev = None
+    for _ in range(700):
+        row = o.step(1)[0]
+        s = o.get_state()
+        prev = check_invariants(sc, s, row, prev)
+        for ln in np.nonzero(s["buf_id"] >= 0)[0]:
+            i = int(s["buf_id"][ln])
+            l = int(lane_link[ln])
+            m = int(dem.route_links[dem.route_offsets[i] + s["cursor"][i] + 1])
+            mask = int(net.turn_lanes[off[l] + outs[int(net.link_to[l])].index(m)])
+            assert mask >> (ln - lb[l]) & 1, (int(row["step"]), i)
+    assert int(row["arrived"]) > 300 and int(o.step(1)[0]["lane_changes"]) >= 0
+
+
+@pytest.mark.parametrize("case", [(3, 2, 15, 120, 0, 5, None), (3, 3, 12, 150, 1, 5, 2), (3, 4, 15, 200, 2, 7, 3),
+                                  (2, 4, 10, 60, 3, 3, 4)])
+def test_plan_following_matches_naive_restatement(case):
+    side, lanes, cells, trips, seed, vmax, lane_seed = case
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 60, 250, gen_seed=seed, seed=seed + 21, vmax=vmax,
+                               turns=True, lane_seed=lane_seed)
+    o, b = oracle.Oracle(sc), Brute(sc)
+    changes = 0
+    for t in range(250):
+        so = o.step(1)[0]
+        sb = b.step()
+        for k, v in sb.items():
+            assert int(so[k]) == v, (t, k)
+        changes += sb["lane_changes"]
+        st = o.get_state()
+        ci, cv, bi, bv = b.state(sc.net)
+        assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
+        assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
+    assert changes > 0

@@ -98,6 +98,23 @@ typedef struct {
      * (neither the link-end buffer nor parking); a vehicle already in the
      * buffer crosses the node as usual. */
     const uint32_t *link_signal;
+    /* Optional (NULL: any lane serves every turn): turn lanes for
+     * plan-following lane changes (Sec. 3: a driver who turns at the end of
+     * the link needs the right lane, and accepts a smaller gap to get there
+     * the closer the intersection is).  For every non-ring link l in id
+     * order, one byte per non-ring link m leaving node link_to[l], in
+     * ascending id of m: bit k set = lane k of l may be used to continue
+     * onto m.  Each byte must be non-zero and name only lanes l has
+     * (TS_ERR_INVALID otherwise).  A vehicle's allowed lanes are those of
+     * the turn onto the next link of its route (every lane on its last
+     * link).  With a table: the extra cell at the link end is open only
+     * from an allowed lane (from any other lane the end is closed, as at a
+     * red light); a vehicle outside its allowed lanes has a reason to
+     * change lanes when an allowed lane lies on the side the step's
+     * direction points to, and then needs the target cell and the
+     * min(vmax, cells left to the link's last cell) cells behind it empty;
+     * the faster-lane reason applies only into an allowed lane. */
+    const uint8_t *turn_lanes;
 } ts_network_desc;
 
 /* Statistics of the state after step `step` (0-based).  active: vehicles

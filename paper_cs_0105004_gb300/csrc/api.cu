@@ -70,6 +70,7 @@ struct World {
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1;
     uint32_t tile_cap = kDefaultTileWords;  // largest tile of the members (picks the link-kernel instance)
+    bool plan = false;  // some member has a turn table (picks the plan-following instances)
     uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
     std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
     bool fused() const;
@@ -93,6 +94,11 @@ struct ts_ctx {
     std::vector<uint8_t> ring;
     std::vector<uint64_t> cell_base;
     std::vector<uint32_t> node_in_off;
+    // turn table (plan-following lane changes): per link, entries for the
+    // links leaving its end node (out_link[out_off[n]..], ascending id)
+    bool has_turn = false;
+    std::vector<uint8_t> turn;
+    std::vector<uint32_t> turn_off, out_off, out_link;
     uint32_t n_words = 0, n_slots = 0, n_lanes = 0;
     uint64_t n_lane_cells = 0;
     uint32_t tile_words = kDefaultTileWords;
@@ -107,6 +113,7 @@ struct ts_ctx {
     uint32_t n_veh = 0;
     std::vector<uint32_t> route_off, depart, depart_sorted, dep_off, dep_ids;
     std::vector<uint32_t> route_links;  // host copy, fetched from the device when ts_write_state needs it
+    std::vector<uint8_t> route_turn;    // allowed lanes of the turn after each route entry (with a turn table)
     // device
     ScenDev sd{};
     uint4 *d_lk_info = nullptr;
@@ -213,14 +220,19 @@ ts_status World::rebuild() {
     // persistent grids: at most the resident blocks, and room for the tile
     // count to double through load balancing before blocks loop over tiles
     uint32_t cap = kDefaultTileWords;
+    bool pl = false;
     for (ts_ctx *c : members)
-        if (c) cap = std::max(cap, c->tile_words);
-    if (cap != tile_cap) {
+        if (c) {
+            cap = std::max(cap, c->tile_words);
+            pl = pl || c->sd.route_turn != nullptr;
+        }
+    if (cap != tile_cap || pl != plan) {
         drop_graphs();
         tile_cap = cap;
+        plan = pl;
     }
-    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks(tile_cap)));
-    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks()));
+    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks(tile_cap, plan)));
+    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks(plan)));
     if (gl > grid_l || gn != grid_n || gl < grid_l / 2) {
         drop_graphs();
         grid_l = gl;
@@ -253,9 +265,9 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
                 launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0,
-                                   tile_cap);
+                                   tile_cap, plan);
                 if (!fu || i + 1 == g)
-                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu);
+                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, plan);
             }
             launch_advance_kernel(d_table, capacity, g, cap_stream, true);
             CK(cudaStreamEndCapture(cap_stream, &graph));
@@ -465,6 +477,7 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
     b += 8ull * n_vehicles + 8ull * d->n_links * 2;           // departure queue, heads (+ reset copy)
     b += 4ull * n_vehicles + 16ull * d->n_links;              // link entry steps, link times (+ scratch)
     b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
+    if (d->turn_lanes) b += route_len + n_vehicles;             // allowed lanes per route entry and departure
     return b;
 }
 
@@ -537,6 +550,28 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     for (uint32_t n = 0; n < c->n_nodes; ++n)
         if (c->node_in_off[n + 1] - c->node_in_off[n] > 255u)
             return fail(TS_ERR_INVALID, "more than 255 lanes end at one node");
+    // links leaving every node (ascending id) and the turn table
+    c->out_off.assign(c->n_nodes + 1, 0);
+    for (uint32_t l = 0; l < L; ++l)
+        if (!c->ring[l]) c->out_off[c->from[l] + 1]++;
+    for (uint32_t n = 0; n < c->n_nodes; ++n) c->out_off[n + 1] += c->out_off[n];
+    c->out_link.resize(c->out_off[c->n_nodes]);
+    {
+        std::vector<uint32_t> fill(c->out_off.begin(), c->out_off.end() - 1);
+        for (uint32_t l = 0; l < L; ++l)
+            if (!c->ring[l]) c->out_link[fill[c->from[l]]++] = l;
+    }
+    c->turn_off.assign(L + 1, 0);
+    for (uint32_t l = 0; l < L; ++l)
+        c->turn_off[l + 1] = c->turn_off[l] + (c->ring[l] ? 0u : c->out_off[c->to[l] + 1] - c->out_off[c->to[l]]);
+    if (desc->turn_lanes) {
+        c->has_turn = true;
+        c->turn.assign(desc->turn_lanes, desc->turn_lanes + c->turn_off[L]);
+        for (uint32_t l = 0; l < L; ++l)
+            for (uint32_t j = c->turn_off[l]; j < c->turn_off[l + 1]; ++j)
+                if (c->turn[j] == 0 || (c->turn[j] >> c->lanes[l]) != 0)
+                    return fail(TS_ERR_INVALID, "a turn needs at least one lane of its link, and only lanes it has");
+    }
     build_tiles(c.get(), nullptr);
     c->n_sub = c->link_tiles.size() >= 64 ? 8u : 1u;  // small networks keep one sub-record per step
     // device arrays of the network
@@ -668,6 +703,20 @@ static ts_status upload_large(void *dst, const void *src, size_t bytes, cudaStre
     return TS_OK;
 }
 
+// Allowed lanes of the turn after route entry j (of a route ending before
+// entry b): the turn-table entry of (links[j], links[j + 1]); 0 (any lane)
+// on the last entry and where every lane of the link serves the turn.
+static uint8_t turn_after(const ts_ctx *c, const uint32_t *links, uint32_t j, uint32_t b) {
+    if (j + 1 >= b) return 0;
+    const uint32_t l = links[j], m = links[j + 1], n = c->to[l];
+    for (uint32_t r = c->out_off[n]; r < c->out_off[n + 1]; ++r)
+        if (c->out_link[r] == m) {
+            const uint8_t a = c->turn[c->turn_off[l] + (r - c->out_off[n])];
+            return a == (uint8_t)((1u << c->lanes[l]) - 1u) ? (uint8_t)0 : a;
+        }
+    return 0;  // not reached for a connected route
+}
+
 static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
     free_list(c, c->veh_allocs);
     auto &A = c->veh_allocs;
@@ -682,6 +731,8 @@ static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
     uint32_t *dep_steps = alloc_in<uint32_t>(c, A, n, ok);
     uint2 *dep_head = alloc_in<uint2>(c, A, L, ok);
     c->d_dep_head0 = alloc_in<uint2>(c, A, L, ok);
+    uint8_t *route_turn = c->has_turn ? alloc_in<uint8_t>(c, A, total, ok) : nullptr;
+    uint8_t *dep_turn = c->has_turn ? alloc_in<uint8_t>(c, A, n, ok) : nullptr;
     if (!ok) {
         free_list(c, A);
         return fail(TS_ERR_OOM, "device allocation failed");
@@ -715,6 +766,13 @@ static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
         const ts_status su = upload_large(routes, links, 4ull * total, c->stream);
         if (su != TS_OK) return su;
     }
+    if (c->has_turn && total) {
+        const ts_status su = upload_large(route_turn, c->route_turn.data(), total, c->stream);
+        if (su != TS_OK) return su;
+        std::vector<uint8_t> dt(n);
+        for (uint32_t q = 0; q < n; ++q) dt[q] = c->route_turn[c->route_off[c->dep_ids[q]]];
+        if (n) CK(cudaMemcpy(dep_turn, dt.data(), n, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(const_cast<uint4 *>(c->sd.nd_info), nd.data(), sizeof(uint4) * L, cudaMemcpyHostToDevice));
     std::vector<uint2> heads(L);
     for (uint32_t l = 0; l < L; ++l) heads[l] = queue_head(c, l, c->dep_off[l]);
@@ -728,6 +786,8 @@ static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
     sd.dep_ids = dep_ids;
     sd.dep_steps = dep_steps;
     sd.dep_head = dep_head;
+    sd.route_turn = route_turn;
+    sd.dep_turn = dep_turn;
     return TS_OK;
 }
 
@@ -804,6 +864,22 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
     c->n_veh = n;
     c->route_off = std::move(ro);
     c->route_links.clear();
+    c->route_turn.clear();
+    if (c->has_turn) {
+        // the allowed lanes of every route entry's turn, on host threads
+        c->route_turn.resize(c->route_off[n]);
+        const unsigned hw = std::thread::hardware_concurrency();
+        const uint32_t nt = std::max(1u, std::min(hw ? hw : 1u, 16u));
+        auto fill = [&](uint32_t t) {
+            for (uint32_t i = (uint32_t)((uint64_t)n * t / nt); i < (uint32_t)((uint64_t)n * (t + 1) / nt); ++i)
+                for (uint32_t j = c->route_off[i]; j < c->route_off[i + 1]; ++j)
+                    c->route_turn[j] = turn_after(c, links, j, c->route_off[i + 1]);
+        };
+        std::vector<std::thread> pool;
+        for (uint32_t t = 1; t < nt; ++t) pool.emplace_back(fill, t);
+        fill(0);
+        for (auto &th : pool) th.join();
+    }
     c->depart.assign(dep, dep + n);
     c->depart_sorted = c->depart;
     std::sort(c->depart_sorted.begin(), c->depart_sorted.end());
@@ -974,10 +1050,11 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
                 launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0,
-                                   w->tile_cap);
+                                   w->tile_cap, w->plan);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
-                    launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu);
+                    launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu,
+                                       w->plan);
                 cudaEventRecord(ev[e + 2], s);
             }
             launch_advance_kernel(w->d_table, w->capacity, g, s, false);
@@ -1168,7 +1245,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
                     const uint64_t ci = c->cell_base[c->lane_base[l] + k] + x;
                     const bool b1 = (loc[w] >> b) & 1u;
                     o->cell_id[ci] = (int32_t)((b1 ? vid1 : vid0)[w * 32 + b] & kIdMask);
-                    o->cell_v[ci] = (b1 ? vel1 : vel0)[w * 32 + b];
+                    o->cell_v[ci] = (int8_t)((b1 ? vel1 : vel0)[w * 32 + b] & 0x0F);  // v (not the allowed lanes)
                 }
             }
         if (!c->ring[l])
@@ -1176,7 +1253,7 @@ ts_status ts_read_state(ts_ctx *c, ts_state *o, uint32_t timeout_ms) {
                 const uint4 s = slots[c->bpos[l] + k];
                 if (s.x == kSlotEmpty) continue;
                 o->buf_id[c->lane_base[l] + k] = (int32_t)(s.x & kIdMask);
-                o->buf_v[c->lane_base[l] + k] = (int8_t)(s.w & 0xFFu);
+                o->buf_v[c->lane_base[l] + k] = (int8_t)(s.w & 0x0Fu);
             }
     }
     for (uint32_t i = 0; i < c->n_veh; ++i) o->cursor[i] = veh[i].x - c->route_off[i];
@@ -1228,7 +1305,8 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
                 const size_t w = (size_t)c->wbase[l] + (size_t)(x / 32) * nl + k;
                 occ[w] |= 1u << (x % 32);
                 if (v) mov[w] |= 1u << (x % 32);
-                vel[w * 32 + x % 32] = v;
+                const uint32_t al = c->has_turn ? c->route_turn[c->route_off[id] + in->cursor[id]] : 0u;
+                vel[w * 32 + x % 32] = (int8_t)((uint32_t)v | (al << 4));
                 const bool last = in->cursor[id] + 1 == c->route_off[id + 1] - c->route_off[id];
                 vid[w * 32 + x % 32] = (uint32_t)id | (last ? kLastLinkBit : 0u);
                 ++n_active;
@@ -1247,8 +1325,9 @@ ts_status ts_write_state(ts_ctx *c, const ts_state *in) {
                 seen[b] = 1;
                 const uint32_t p = c->route_off[b] + in->cursor[b];
                 const uint32_t fl = (in->cursor[b] + 2 == len) ? kLastLinkBit : 0u;
-                slots[c->bpos[l] + k] =
-                    make_uint4((uint32_t)b | fl, c->route_links[p + 1], l, (uint32_t)v | (k << 8) | (c->cells[l] << 10));
+                const uint32_t al = c->has_turn ? c->route_turn[p + 1] : 0u;
+                slots[c->bpos[l] + k] = make_uint4((uint32_t)b | fl, c->route_links[p + 1], l,
+                                                   (uint32_t)v | (al << 4) | (k << 8) | (c->cells[l] << 10));
                 ++n_buffered;
                 hash += vehicle_term((uint32_t)b, l, k, c->cells[l], (uint32_t)v);
             }

@@ -15,11 +15,15 @@
 //     A vehicle that stays where it is with v = 0 keeps its payload where it
 //     is; a vehicle that moves or changes speed writes the buffer that no
 //     reader of the step can be using (the other one than the cell's current
-//     occupant's).  Payload of empty cells is never read.
+//     occupant's).  Payload of empty cells is never read.  With a turn table
+//     (plan-following lane changes) the velocity byte is v | A << 4, A the
+//     lanes of the current link from which the vehicle may take its next
+//     turn (0: any lane).
 //   * slots[2][n_slots]: one link-end buffer per lane, grouped by the node
 //     the link ends at, in intersection priority order (link id, then lane):
 //     x = id | next-link-is-last << 31 (0xffffffff = empty), y = next link,
-//     z = current link, w = v | lane << 8 | current link cells << 10.
+//     z = current link, w = v | A << 4 | lane << 8 | current link cells << 10
+//     (A: the allowed lanes on the next link, as in the velocity byte).
 //     Double-buffered by step parity like the cells: a step reads
 //     slots[t&1] (which every tile may read to resolve node transfers) and
 //     each tile writes its own links' buffers into slots[(t+1)&1].
@@ -116,6 +120,12 @@ struct ScenDev {
     uint32_t n_sub;               // sub-records per step (power of two)
     uint32_t vmax, p_threshold, seed_lo, seed_hi, lane_change;
     uint32_t n_links;
+    // turn table (nullptr: none): per route entry, the lanes of that link from
+    // which the turn onto the route's next link may be taken (bit k = lane k;
+    // 0 = any lane, and on the route's last entry); per departure-queue entry,
+    // the same for the traveller's first link
+    const uint8_t *route_turn;
+    const uint8_t *dep_turn;
 };
 
 // link tile, two uint4: whole links  {scen, l0, nl, 0}            {w_begin, w_end, 0, 0}
@@ -135,18 +145,20 @@ struct LinkTile {
 // previous step must have been completed by node_kernel
 // tile_cap: the largest tile (occupancy words) among the tiles; picks the
 // kernel instance whose shared memory holds it
+// plan: some scenario of the table has a turn table (plan-following lane
+// changes); picks the instances that read the allowed lanes
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap);
+                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool plan);
 // chunk_end: the pass completes the last step each scenario ran in the
 // chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool chunk_end);
+                        cudaStream_t s, bool pdl, bool chunk_end, bool plan);
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 // adds the entry steps of vehicles on the network to out (a copy of link_time)
 void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s);
-int max_link_blocks(uint32_t tile_cap);
-int max_node_blocks();
+int max_link_blocks(uint32_t tile_cap, bool plan);
+int max_node_blocks(bool plan);
 // Sets the thread-local message returned by ts_last_error.
 void set_last_error(const char *msg);
 

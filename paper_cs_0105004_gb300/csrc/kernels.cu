@@ -192,7 +192,7 @@ __device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ 
 // queue enters the lowest free lane with v = 0 while lanes are free and its
 // departure step has come.  The head's departure step is kept beside the
 // head index, so a link with nothing due costs one load.  Calls
-// insert(queue entry, lane).
+// insert(queue entry, lane, queue index).
 template <class F>
 __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
                                                uint32_t free_mask, F &&insert) {
@@ -204,9 +204,10 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
         const uint32_t qn = (uint32_t)(__ffs(free_mask) - 1);
         free_mask &= ~(1u << qn);
         const uint32_t idw = D.dep_ids[h];
+        const uint32_t qi = h;
         ++h;
         next = h < dep_end ? D.dep_steps[h] : 0xFFFFFFFFu;
-        insert(idw, qn);
+        insert(idw, qn, qi);
     } while (next <= t && free_mask);
     D.dep_head[m] = make_uint2(h, next);
 }
@@ -319,8 +320,9 @@ __device__ __forceinline__ void list_append(SM &S, uint32_t &count, int w, uint3
 // node transfers and departures into q (if q starts in this tile) at the end
 // of step t-1; then sets up q's lane-end buffers for step t (if q ends in this
 // tile).  Returns the vehicles placed on q.  Out of line, so that its
-// registers do not weigh on the rest of the step.
-template <class SM>
+// registers do not weigh on the rest of the step.  PLAN: velocity bytes and
+// buffer words carry the allowed lanes of the next turn.
+template <bool PLAN, class SM>
 __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int q, int cur, uint32_t t,
                                                     bool do_xfer) {
     const int nxt = cur ^ 1;
@@ -338,11 +340,11 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
         uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
         uint32_t fr = resolve_transfers(sc, nd, l, free_cell0(oc, nd), [&](uint32_t, const uint4 &x,
                                                                           uint32_t qn) {
-            const uint32_t id = x.x & kIdMask, v = x.w & 0xFFu, ks = (x.w >> 8) & 3u;
+            const uint32_t id = x.x & kIdMask, v = x.w & (PLAN ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
             placed |= 1u << qn;
             if (v) moving |= 1u << qn;
             const size_t pc = (size_t)(nd.y + qn) * 32u;
-            vel[pc] = (int8_t)v;
+            vel[pc] = (int8_t)(PLAN ? (x.w & 0xFFu) : v);
             vid[pc] = x.x;  // id with the last-link flag of l
             atomicAdd(&D.veh[id].x, 1u);
             atomicAdd(&D.link_time[x.z], kLinkTimeOne + (t - 1u));
@@ -354,10 +356,10 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
             acc2[4] += v;
             acc2[5] += vehicle_term(id, l, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
         });
-        run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn) {
+        run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
             placed |= 1u << qn;
             const size_t pc = (size_t)(nd.y + qn) * 32u;
-            vel[pc] = 0;
+            vel[pc] = (PLAN && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
             vid[pc] = idw;
             atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
             D.enter_step[idw & kIdMask] = t - 1u;
@@ -418,13 +420,13 @@ struct LinkLaunch {
     static constexpr int kMinBlocks = 65536 / (kThreads * 64);
 };
 
-template <int TW>
-__global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
-    link_kernel(const ScenDev *__restrict__ table,
-                                                            const LinkTile *__restrict__ tiles,
-                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
-                                                            uint32_t xfer) {
-    __shared__ LinkSmem<TW> S;
+// One launch of the link kernel (body of link_kernel and plan_link_kernel).
+// PLAN: plan-following lane changes (Sec. 3): every velocity byte carries
+// the lanes A of its link from which the vehicle may take its next turn.
+template <int TW, bool PLAN>
+__device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__restrict__ table,
+                                          const LinkTile *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
+                                          uint32_t pos, uint32_t xfer) {
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
     // statistics of the block: updates, lane changes, arrivals, and the changes
     // of active, buffered, sum of velocities and digest
@@ -642,7 +644,7 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
         {
             // link threads, counted down from the last thread
             const int q = LinkLaunch<TW>::kThreads - 1 - (int)threadIdx.x;
-            if (q < S.nlinks) acc[0] += link_buffers_phase(S, D, q, cur, t, do_xfer);
+            if (q < S.nlinks) acc[0] += link_buffers_phase<PLAN>(S, D, q, cur, t, do_xfer);
         }
         __syncthreads();
         stamp(4, first);
@@ -668,7 +670,11 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
                 const int q = S.clink[c];
                 if (kt >= 0 && kt < (int)S.llanes[q]) {
                     const uint32_t o = S.occ0[w] & lc_mask(S.ckind[c], vmax);
-                    if (o) {
+                    if (PLAN && o) {
+                        // the allowed lanes are in the payload: every vehicle
+                        // whose target cell is free is decided one by one
+                        listed = o & ~S.occ0[S.cw[c] + kt];
+                    } else if (o) {
                         const uint32_t near = S.cnear[c];
                         const uint32_t tw = S.occ0[S.cw[c] + kt];
                         const int lf = S.left[c];
@@ -703,7 +709,33 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
                 // vmax cells of the link end
                 const size_t p = (size_t)S.gw[ww] * 32u + (uint32_t)i;
                 const bool b1 = (S.loc0[ww] >> i) & 1u;
-                const uint32_t v = (uint32_t)(b1 ? vel1[p] : vel0[p]);
+                uint32_t v;
+                uint32_t al = 0xFu;  // lanes it may leave the link from
+                if constexpr (PLAN) {
+                    const uint32_t byte = (uint32_t)(uint8_t)(b1 ? vel1[p] : vel0[p]);
+                    v = byte & 0xFu;
+                    if (byte >> 4) al = byte >> 4;
+                } else {
+                    v = (uint32_t)(b1 ? vel1[p] : vel0[p]);
+                }
+                if constexpr (PLAN) {
+                    if (!((al >> k) & 1u)) {
+                        // outside its allowed lanes: a reason to change when
+                        // one of them lies on the side d points to; the gap
+                        // accepted behind the target cell shrinks from vmax to
+                        // 0 over the link's last vmax cells
+                        const uint32_t side = d > 0 ? al & ~((2u << k) - 1u) : al & ((1u << k) - 1u);
+                        if (side && room_behind(S.occ0, S, c, kt, i, dist < vmax ? dist : vmax)) {
+                            atomicOr(&S.mv[S.cw[c] + kt], 1u << i);
+                            if (S.ckind[c] == 0) acc[1] += 1;
+                        }
+                        continue;
+                    }
+                    // the speed reason applies only into an allowed lane (and
+                    // then both lanes are allowed: the gaps below need no
+                    // closed link end)
+                    if (!((al >> kt) & 1u)) continue;
+                }
                 const uint32_t last = ((S.cnear[c] >> i) & 1u) ? (b1 ? vid1[p] : vid0[p]) >> 31 : 0u;
                 const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
                 const uint32_t g_own =
@@ -778,15 +810,25 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
                 const size_t ps = (size_t)S.gw[sw] * 32u + (uint32_t)i;
                 const bool sb1 = (S.loc0[sw] >> i) & 1u;
                 const uint32_t idw = sb1 ? vid1[ps] : vid0[ps];
-                const uint32_t v0 = (uint32_t)(sb1 ? vel1[ps] : vel0[ps]);
+                uint32_t v0, al = 0u;  // al: allowed lanes of the next turn (0: any)
+                if constexpr (PLAN) {
+                    const uint32_t byte = (uint32_t)(uint8_t)(sb1 ? vel1[ps] : vel0[ps]);
+                    v0 = byte & 0xFu;
+                    al = byte >> 4;
+                } else {
+                    v0 = (uint32_t)(sb1 ? vel1[ps] : vel0[ps]);
+                }
                 const int q = S.clink[c];
                 const uint32_t id = idw & kIdMask, last = idw >> 31;
                 const uint32_t ring = S.lring[q];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
                 const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
                 uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;  // (i) accelerate
-                const uint32_t g =
-                    gap_ahead(S.occ1, S, c, k, i, dist, (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q], vmax);
+                uint32_t open = (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q];
+                if constexpr (PLAN) {
+                    if (al && !((al >> k) & 1u)) open = 0u;  // the next turn is not taken from lane k
+                }
+                const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, open, vmax);
                 if (v > g) v = g;                                                 // (ii) gap
                 if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;  // (iii) random
                 const bool core = S.ckind[c] == 0;
@@ -814,8 +856,12 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
                             const uint32_t m = D.route_links[ve.x + 1u];
                             const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
                             if (!((S.lexit[q] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
+                            uint32_t vb = v;  // with the allowed lanes of the turn after m
+                            if constexpr (PLAN) {
+                                if (D.route_turn) vb |= (uint32_t)D.route_turn[ve.x + 1u] << 4;
+                            }
                             D.slots[nxt][S.lbpos[q] + (uint32_t)k] =
-                                make_uint4(id | fl, m, lid, v | ((uint32_t)k << 8) | (S.lcells[q] << 10));
+                                make_uint4(id | fl, m, lid, vb | ((uint32_t)k << 8) | (S.lcells[q] << 10));
                             acc[3] -= 1;
                             acc[4] += 1;
                             acc[5] -= v0;
@@ -842,12 +888,13 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
                             // write the payload buffer that no reader of this step uses
                             const bool b1 = (S.occ0[dw] & bit) ? !(S.loc0[dw] & bit) : false;
                             const size_t pd = (size_t)S.gw[dw] * 32u + (uint32_t)ni;
+                            const int8_t vb = (int8_t)(PLAN ? (v | (al << 4)) : v);
                             if (b1) {
-                                velw1[pd] = (int8_t)v;
+                                velw1[pd] = vb;
                                 vidw1[pd] = idw;
                                 atomicOr(&S.oloc[dw], bit);
                             } else {
-                                velw0[pd] = (int8_t)v;
+                                velw0[pd] = vb;
                                 vidw0[pd] = idw;
                             }
                             const uint32_t old = atomicOr(&S.oocc[dw], bit);
@@ -878,11 +925,31 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
     span_mark((int)pos * 3, false);
 }
 
+template <int TW>
+__global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
+    link_kernel(const ScenDev *__restrict__ table, const LinkTile *__restrict__ tiles,
+                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer) {
+    __shared__ LinkSmem<TW> S;
+    link_step<TW, false>(S, table, tiles, n_tiles_p, pos, xfer);
+}
+
+// The same with plan-following lane changes (scenarios with a turn table).
+template <int TW>
+__global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
+    plan_link_kernel(const ScenDev *__restrict__ table, const LinkTile *__restrict__ tiles,
+                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer) {
+    __shared__ LinkSmem<TW> S;
+    link_step<TW, true>(S, table, tiles, n_tiles_p, pos, xfer);
+}
+
 // ------------------------------------------------------------------ node kernel
 
 // Node transfers and departures into link m (nd = nd_info[m]) at the end of
 // step `step`, on the state after that step's moves; acc gets the transfers,
 // insertions and the changes of active, buffered, sum of velocities, digest.
+// PLAN: velocity bytes and buffer words carry the allowed lanes of the next
+// turn.
+template <bool PLAN>
 __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const uint4 &nd, unsigned long long step,
                                           unsigned long long (&acc)[6]) {
     const int nxt = (int)((step + 1ull) & 1ull);
@@ -894,11 +961,11 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
     // slots with next link m, and the cells 0 of m, are written by this thread only
     const uint32_t fr = resolve_transfers(slots, nd, m, free_cell0(occ, nd), [&](uint32_t si, const uint4 &x,
                                                                                   uint32_t qn) {
-        const uint32_t id = x.x & kIdMask, v = x.w & 0xFFu, ks = (x.w >> 8) & 3u;
+        const uint32_t id = x.x & kIdMask, v = x.w & (PLAN ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
         const uint32_t w = nd.y + qn;  // column 0 of lane qn
         occ[w] |= 1u;
         if (v) mov[w] |= 1u;
-        vel[(size_t)w * 32u] = (int8_t)v;
+        vel[(size_t)w * 32u] = (int8_t)(PLAN ? (x.w & 0xFFu) : v);
         vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
         atomicAdd(&D.veh[id].x, 1u);
         slots[si].x = kSlotEmpty;
@@ -912,10 +979,10 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
         acc[4] += v;
         acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
     });
-    run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn) {
+    run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
         const uint32_t w = nd.y + qn;
         occ[w] |= 1u;
-        vel[(size_t)w * 32u] = 0;
+        vel[(size_t)w * 32u] = (PLAN && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
         vid[(size_t)w * 32u] = idw;
         atomicAdd(&D.link_time[m], 0ull - step);
         D.enter_step[idw & kIdMask] = (uint32_t)step;
@@ -939,12 +1006,12 @@ __device__ __forceinline__ bool node_step(const ScenDev &D, uint32_t pos, bool c
     return true;
 }
 
-// One thread per link m.
-__global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
-                                                            const uint4 *__restrict__ tiles,
-                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
-                                                            uint32_t chunk_end) {
-    __shared__ unsigned long long red[kNodeThreads / 32][6];
+// One node pass, one thread per link m (body of node_kernel and
+// plan_node_kernel).
+template <bool PLAN>
+__device__ __forceinline__ void node_pass(unsigned long long (*red)[6], const ScenDev *__restrict__ table,
+                                          const uint4 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
+                                          uint32_t pos, uint32_t chunk_end) {
     const uint32_t n_tiles = *n_tiles_p;
     // transfers, insertions and the changes of active, buffered, sum of velocities, digest
     static constexpr int kField[6] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash};
@@ -971,10 +1038,27 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
             if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
             cur_rec = rec;
         }
-        if (m < td.z) node_link(D, m, nd, step, acc);
+        if (m < td.z) node_link<PLAN>(D, m, nd, step, acc);
     }
     if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
     span_mark((int)pos * 3 + 1, false);
+}
+
+__global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
+                                                            const uint4 *__restrict__ tiles,
+                                                            const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
+                                                            uint32_t chunk_end) {
+    __shared__ unsigned long long red[kNodeThreads / 32][6];
+    node_pass<false>(red, table, tiles, n_tiles_p, pos, chunk_end);
+}
+
+// The same for scenarios with a turn table.
+__global__ void __launch_bounds__(kNodeThreads) plan_node_kernel(const ScenDev *__restrict__ table,
+                                                                 const uint4 *__restrict__ tiles,
+                                                                 const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
+                                                                 uint32_t chunk_end) {
+    __shared__ unsigned long long red[kNodeThreads / 32][6];
+    node_pass<true>(red, table, tiles, n_tiles_p, pos, chunk_end);
 }
 
 // ------------------------------------------------------------------ link travel times
@@ -1080,19 +1164,25 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+template <int TW>
+static void (*link_instance(bool plan))(const ScenDev *, const LinkTile *, const uint32_t *, uint32_t, uint32_t) {
+    return plan ? plan_link_kernel<TW> : link_kernel<TW>;
+}
+
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap) {
+                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool plan) {
     if (tile_cap <= (uint32_t)kDefaultTileWords)
-        launch_pdl(link_kernel<kDefaultTileWords>, grid, LinkLaunch<kDefaultTileWords>::kThreads, pdl, s, table, tiles,
-                   n_tiles, i, xfer ? 1u : 0u);
+        launch_pdl(link_instance<kDefaultTileWords>(plan), grid, LinkLaunch<kDefaultTileWords>::kThreads, pdl, s,
+                   table, tiles, n_tiles, i, xfer ? 1u : 0u);
     else
-        launch_pdl(link_kernel<kTileWords>, grid, LinkLaunch<kTileWords>::kThreads, pdl, s, table, tiles, n_tiles, i,
-                   xfer ? 1u : 0u);
+        launch_pdl(link_instance<kTileWords>(plan), grid, LinkLaunch<kTileWords>::kThreads, pdl, s, table, tiles,
+                   n_tiles, i, xfer ? 1u : 0u);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool chunk_end) {
-    launch_pdl(node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i, chunk_end ? 1u : 0u);
+                        cudaStream_t s, bool pdl, bool chunk_end, bool plan) {
+    launch_pdl(plan ? plan_node_kernel : node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i,
+               chunk_end ? 1u : 0u);
 }
 
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl) {
@@ -1140,11 +1230,11 @@ extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
 }
 #endif
 
-int max_link_blocks(uint32_t tile_cap) {
+int max_link_blocks(uint32_t tile_cap, bool plan) {
     if (tile_cap <= (uint32_t)kDefaultTileWords) {
         // five blocks of the default instance need more shared memory than
         // the smallest L1/shared splits give
-        const void *fn = (const void *)link_kernel<kDefaultTileWords>;
+        const void *fn = (const void *)link_instance<kDefaultTileWords>(plan);
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
         return resident_blocks(fn, LinkLaunch<kDefaultTileWords>::kThreads);
     }
@@ -1152,10 +1242,12 @@ int max_link_blocks(uint32_t tile_cap) {
     // default L1/shared split leaves for four blocks; the largest shared
     // share measured fastest on GB300 (config 3: 3.3e10 vs 2.4e10
     // vehicle-updates/s with the default split)
-    const void *fn = (const void *)link_kernel<kTileWords>;
+    const void *fn = (const void *)link_instance<kTileWords>(plan);
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     return resident_blocks(fn, LinkLaunch<kTileWords>::kThreads);
 }
-int max_node_blocks() { return resident_blocks((const void *)node_kernel, kNodeThreads); }
+int max_node_blocks(bool plan) {
+    return resident_blocks(plan ? (const void *)plan_node_kernel : (const void *)node_kernel, kNodeThreads);
+}
 
 }  // namespace tsim

@@ -240,9 +240,9 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
         return bad(TS_ERR_CUDA, "scratch set-up copy failed");
     const uint32_t cur = (uint32_t)(first_step & 1ull), fin = (uint32_t)((first_step + n_steps) & 1ull);
     prep_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, lanes, words, cur);
-    const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks(kDefaultTileWords)));
+    const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks(kDefaultTileWords, false)));
     for (uint32_t i = 0; i < n_steps; ++i)
-        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false, false, kDefaultTileWords);
+        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false, false, kDefaultTileWords, false);
     finish_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, words, fin);
     gather_ring_stats<<<1, kNoAllocMaxSteps, 0, s>>>(d_stats, d_ctrl, first_step, n_steps, dev_stats_out);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");

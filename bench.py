@@ -40,11 +40,11 @@ sys.path.insert(0, ROOT)
 METRIC = "vehicle-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
-# dram__bytes_read.sum + dram__bytes_write.sum of one link_kernel launch from
-# an ncu --set full capture (caches flushed) of config 1 at step 5,000
-# (--profile-window 5000:64).  Valid only while link_kernel is unchanged
-# since that capture.
-LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0}
+# dram__bytes_read.sum + dram__bytes_write.sum of one link_kernel launch
+# (plan_link_kernel for plan1) from an ncu --set full capture (caches
+# flushed) at step 5,000 (--profile-window 5000:64).  Valid only while the
+# kernel is unchanged since that capture.
+LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0, "plan1": 4796416.0 + 2816.0}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -77,7 +77,6 @@ def _node_launch_ms(node_ms, mode):
 
 
 def _workload(name):
-    import dataclasses
     from paper_cs_0105004_gb300.inputs import networks as N
     sc = {"config1": N.config1, "config2": N.config2, "config0": N.config0, "plan1": N.config1}[name]()
     if name == "plan1":

@@ -40,7 +40,7 @@ def lib():
         P = ctypes.POINTER
         u32p, u64p, i32p, i8p, u8p = P(ctypes.c_uint32), P(ctypes.c_uint64), P(ctypes.c_int32), P(ctypes.c_int8), P(ctypes.c_uint8)
         L.oracle_create.restype = ctypes.c_void_p
-        L.oracle_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, u32p, u32p, u8p, u32p, u8p,
+        L.oracle_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, u32p, u32p, u8p, u32p, u8p, u8p,
                                     ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
         L.oracle_load_vehicles.restype = ctypes.c_int
@@ -97,10 +97,13 @@ class Oracle:
         self._sig = None if sig is None else np.ascontiguousarray(sig, np.uint32).reshape(-1)
         turn = getattr(net, "turn_lanes", None)
         self._turn = None if turn is None else np.ascontiguousarray(turn, np.uint8).reshape(-1)
+        ga = getattr(net, "link_yield", None)
+        self._yield = None if ga is None else np.ascontiguousarray(ga, np.uint8).reshape(-1)
         self.h = L.oracle_create(net.n_nodes, net.n_links, *[_p(a, ctypes.c_uint32) for a in self._keep],
                                  _p(ring, ctypes.c_uint8),
                                  _p(self._sig, ctypes.c_uint32) if self._sig is not None else None,
                                  _p(self._turn, ctypes.c_uint8) if self._turn is not None else None,
+                                 _p(self._yield, ctypes.c_uint8) if self._yield is not None else None,
                                  scenario.vmax, scenario.p_threshold, scenario.seed, scenario.lane_change)
         if not self.h:
             raise ValueError("oracle rejected the network")

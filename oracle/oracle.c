@@ -59,6 +59,16 @@
  * empty, dist = cells between it and the link's last cell; the speed reason
  * applies only into an allowed lane.
  *
+ * Gap acceptance at unprotected turns (Sec. 3: a car from the non-priority
+ * street needs a large enough gap on the priority street).  An optional
+ * per-link acceptance gap G (0: a priority approach, 1..31: a yield
+ * approach): a vehicle in the link-end buffer of a yield approach crosses
+ * only while every priority approach of the same node has no vehicle in
+ * its last G cells (not counting its cell 0) on any lane, in the state
+ * after the step's moves and before any transfer; it still needs a free
+ * cell 0.  A node serves its priority approaches first, then its yield
+ * approaches, each in ascending link id and lane.
+ *
  * Link travel times (the input of the re-planning step of the relaxation
  * iterations, Sec. 1): a vehicle that enters a link at the end of step t0
  * (a departure or a node transfer) and leaves it at the end of step t1 (a
@@ -86,6 +96,7 @@ typedef struct oracle {
     uint8_t *turn;        /* turn table (NULL: every lane for every turn)  */
     uint32_t *turn_off;   /* first turn-table entry of each link          */
     uint32_t *out_off, *out_link; /* per node: outgoing links, ascending id */
+    uint8_t *gap_accept;  /* [n_links] acceptance gap G of a yield approach, 0: priority */
     uint64_t t_now;       /* step being computed (for the signals)        */
     uint32_t *lane_base;  /* first canonical lane of each link            */
     uint32_t *lane_link;  /* link of each canonical lane                  */
@@ -234,7 +245,7 @@ static int room_to_get_in(const oracle *o, const int32_t *S, uint32_t l, uint32_
 void oracle_destroy(oracle *o) {
     if (!o) return;
     free(o->from); free(o->to); free(o->cells); free(o->lanes); free(o->ring); free(o->sig);
-    free(o->turn); free(o->turn_off); free(o->out_off); free(o->out_link);
+    free(o->turn); free(o->turn_off); free(o->out_off); free(o->out_link); free(o->gap_accept);
     free(o->lane_base); free(o->lane_link); free(o->cell_base); free(o->in_off); free(o->in_lane);
     free(o->depart); free(o->route_off); free(o->route); free(o->q_off); free(o->q_id);
     free(o->cell); free(o->buf); free(o->vel); free(o->cursor); free(o->status); free(o->dep_head);
@@ -246,8 +257,8 @@ void oracle_destroy(oracle *o) {
 /* Returns NULL on invalid input or out of memory. */
 oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, const uint32_t *to,
                       const uint32_t *cells, const uint32_t *lanes, const uint8_t *ring, const uint32_t *signal,
-                      const uint8_t *turn, uint32_t vmax, uint32_t p_threshold, uint64_t seed,
-                      uint32_t lane_change) {
+                      const uint8_t *turn, const uint8_t *gap_accept, uint32_t vmax, uint32_t p_threshold,
+                      uint64_t seed, uint32_t lane_change) {
     if (vmax < 1 || n_links == 0) return NULL;
     oracle *o = (oracle *)calloc(1, sizeof(oracle));
     if (!o) return NULL;
@@ -257,8 +268,15 @@ oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, 
     o->cells = (uint32_t *)malloc(4ull * n_links); o->lanes = (uint32_t *)malloc(4ull * n_links);
     o->ring = (uint8_t *)calloc(n_links, 1);
     o->sig = (uint32_t *)calloc(3ull * n_links, 4);
+    o->gap_accept = (uint8_t *)calloc(n_links, 1);
     o->lane_base = (uint32_t *)malloc(4ull * (n_links + 1));
-    if (!o->from || !o->to || !o->cells || !o->lanes || !o->ring || !o->sig || !o->lane_base) goto fail;
+    if (!o->from || !o->to || !o->cells || !o->lanes || !o->ring || !o->sig || !o->gap_accept || !o->lane_base)
+        goto fail;
+    if (gap_accept) {
+        memcpy(o->gap_accept, gap_accept, n_links);
+        for (uint32_t l = 0; l < n_links; l++)
+            if (o->gap_accept[l] > 31) goto fail;
+    }
     if (signal) {
         memcpy(o->sig, signal, 12ull * n_links);
         for (uint32_t l = 0; l < n_links; l++)
@@ -290,7 +308,8 @@ oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, 
             o->cell_base[ln + 1] = o->cell_base[ln] + cells[l];
         }
     o->n_cells = o->cell_base[o->n_lanes];
-    /* incoming lanes of every node: links in ascending id, lanes ascending */
+    /* incoming lanes of every node: priority approaches, then yield
+     * approaches, each in ascending link id, lanes ascending */
     o->in_off = (uint32_t *)calloc((size_t)n_nodes + 1, 4);
     o->in_lane = (uint32_t *)malloc(4ull * (o->n_lanes ? o->n_lanes : 1));
     if (!o->in_off || !o->in_lane) goto fail;
@@ -301,9 +320,10 @@ oracle *oracle_create(uint32_t n_nodes, uint32_t n_links, const uint32_t *from, 
         uint32_t *fill = (uint32_t *)malloc(4ull * (n_nodes + 1));
         if (!fill) goto fail;
         memcpy(fill, o->in_off, 4ull * (n_nodes + 1));
-        for (uint32_t l = 0; l < n_links; l++)
-            if (!o->ring[l])
-                for (uint32_t k = 0; k < lanes[l]; k++) o->in_lane[fill[to[l]]++] = o->lane_base[l] + k;
+        for (int yield = 0; yield < 2; yield++)
+            for (uint32_t l = 0; l < n_links; l++)
+                if (!o->ring[l] && (o->gap_accept[l] > 0) == yield)
+                    for (uint32_t k = 0; k < lanes[l]; k++) o->in_lane[fill[to[l]]++] = o->lane_base[l] + k;
         free(fill);
     }
     /* outgoing links of every node, ascending id, and the turn table */
@@ -417,6 +437,22 @@ int oracle_load_vehicles(oracle *o, uint32_t n, const uint32_t *depart, const ui
     return 0;
 }
 
+/* Gap acceptance: may a vehicle leave yield approach l (gap G) at node n?
+ * Every priority approach p of n must have its cells max(1, L_p - G) ..
+ * L_p - 1 empty on every lane in the cell state S. */
+static int priority_gap_clear(const oracle *o, const int32_t *S, uint32_t n, uint32_t l) {
+    uint32_t G = o->gap_accept[l];
+    for (uint32_t p = 0; p < o->n_links; p++) {
+        if (o->ring[p] || o->to[p] != n || o->gap_accept[p] != 0) continue;
+        uint32_t L = o->cells[p];
+        uint32_t lo = L > G ? L - G : 1;
+        for (uint32_t k = 0; k < o->lanes[p]; k++)
+            for (uint32_t x = lo; x < L; x++)
+                if (S[cell_index(o, p, k, x)] >= 0) return 0;
+    }
+    return 1;
+}
+
 /* ------------------------------------------------------------ one time step */
 static void step_once(oracle *o, oracle_stats *st) {
     const uint64_t t = o->step;
@@ -508,10 +544,13 @@ static void step_once(oracle *o, oracle_stats *st) {
     }
 
     /* Node transfer: at every node, buffered vehicles in priority order
-     * (incoming link id ascending, then lane) move to cell 0 of their next
-     * link, trying the lane with the same index (or the highest one) first,
-     * then the other lanes ascending.  A vehicle keeps its velocity; one that
-     * finds no free cell 0 stays in its buffer. */
+     * (priority approaches before yield approaches, then incoming link id
+     * ascending, then lane) move to cell 0 of their next link, trying the
+     * lane with the same index (or the highest one) first, then the other
+     * lanes ascending.  A vehicle keeps its velocity; one that finds no free
+     * cell 0, or leaves a yield approach while the priority approaches lack
+     * the gap, stays in its buffer.  (The gap is judged on cells 1 and up,
+     * which transfers never write: it is the state after the moves.) */
     for (uint32_t n = 0; n < o->n_nodes; n++) {
         for (uint32_t s = o->in_off[n]; s < o->in_off[n + 1]; s++) {
             uint32_t ln = o->in_lane[s];
@@ -519,6 +558,7 @@ static void step_once(oracle *o, oracle_stats *st) {
             if (id < 0) continue;
             uint32_t l = o->lane_link[ln];
             uint32_t k = ln - o->lane_base[l];
+            if (o->gap_accept[l] && !priority_gap_clear(o, o->cell, n, l)) continue;
             uint32_t m = o->route[o->route_off[id] + o->cursor[id] + 1];
             uint32_t nl = o->lanes[m];
             uint32_t pref = k < nl - 1 ? k : nl - 1;

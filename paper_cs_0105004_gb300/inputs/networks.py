@@ -46,6 +46,11 @@ class Network:
     # order, one uint8 whose bit k says that lane k of l may be used to
     # continue onto m.  None: every lane for every turn.
     turn_lanes: Optional[np.ndarray] = None
+    # gap acceptance at unprotected turns, uint8 [n_links]: 0 = a priority
+    # approach, G in 1..31 = a yield approach whose vehicles cross only while
+    # the priority approaches of the node have no vehicle in their last G
+    # cells.  None: every approach has priority.
+    link_yield: Optional[np.ndarray] = None
 
     @property
     def n_links(self) -> int:
@@ -433,12 +438,33 @@ def turn_lanes_by_rank(net: Network) -> np.ndarray:
     return out
 
 
+def grid_yield(net: Network, gap: int) -> np.ndarray:
+    """Unprotected turns on a grid_network: links running north-south yield
+    (acceptance gap `gap` cells) to links running east-west."""
+    horizontal = np.abs(net.link_from.astype(np.int64) - net.link_to.astype(np.int64)) == 1
+    return np.where(horizontal, 0, gap).astype(np.uint8)
+
+
+def yield_by_lanes(net: Network, gap: int) -> np.ndarray:
+    """Unprotected turns on any network: at every node, the approaches with
+    fewer lanes than the node's widest approach yield (acceptance gap `gap`
+    cells); a node whose approaches are all equally wide has no yield."""
+    ring = np.asarray(net.link_ring, bool)
+    to = np.where(ring, 0, np.asarray(net.link_to, np.int64))
+    lanes = np.asarray(net.link_lanes, np.int64)
+    widest = np.zeros(net.n_nodes, np.int64)
+    np.maximum.at(widest, to[~ring], lanes[~ring])
+    return np.where(~ring & (lanes < widest[to]), gap, 0).astype(np.uint8)
+
+
 def small_grid_scenario(n_side=3, lanes=2, cells=20, n_trips=60, window=60, steps=200,
                         gen_seed=0, seed=1, vmax=5, p_threshold=P_THRESHOLD_0_2, signal=None,
-                        turns=False, lane_seed=None) -> Scenario:
+                        turns=False, lane_seed=None, yield_gap=None) -> Scenario:
     """signal = (cycle, green): a traffic light at every link end (grid_signals).
     turns: turn lanes by rank (turn_lanes_by_rank).  lane_seed: lanes per
-    undirected edge ~ U{1..lanes} from that seed instead of `lanes` everywhere."""
+    undirected edge ~ U{1..lanes} from that seed instead of `lanes` everywhere.
+    yield_gap: north-south links yield to east-west links with that
+    acceptance gap (grid_yield)."""
     net = grid_network(n_side, lanes, cells)
     if lane_seed is not None:
         per_edge = np.random.default_rng(lane_seed).integers(1, lanes + 1, net.n_links // 2)
@@ -447,6 +473,8 @@ def small_grid_scenario(n_side=3, lanes=2, cells=20, n_trips=60, window=60, step
         net = dataclasses.replace(net, link_signal=grid_signals(net, n_side, *signal))
     if turns:
         net = dataclasses.replace(net, turn_lanes=turn_lanes_by_rank(net))
+    if yield_gap is not None:
+        net = dataclasses.replace(net, link_yield=grid_yield(net, yield_gap))
     rng = np.random.default_rng(gen_seed)
     o, d, dep = uniform_trips(net, n_trips, window, rng)
     return Scenario(f"grid{n_side}x{n_side}", net, _demand(net, o, d, dep, 1), steps, seed, vmax, p_threshold)

@@ -3,9 +3,10 @@
 It exists to pin the C oracle on tiny inputs: a slip in either (a dropped
 term, a wrong index or sign) shows up as a state mismatch.  It keeps the
 state as dictionaries keyed by position and re-derives everything from the
-rules of Sec. 3 (car following, lane changing) and Sec. 4 (sub-step order,
-entry from parking), with the same readings of the points the paper leaves
-open as the oracle documents.  It has its own Philox-4x32-10.
+rules of Sec. 3 (car following, lane changing, signals, lane changing for
+plan following, gap acceptance at unprotected turns) and Sec. 4 (sub-step
+order, entry from parking), with the same readings of the points the paper
+leaves open as the oracle documents.  It has its own Philox-4x32-10.
 """
 from __future__ import annotations
 
@@ -47,6 +48,10 @@ class Brute:
                 for m in sorted(m for m in range(len(self.cells)) if self.frm[m] == self.to[l] and not self.ring[m]):
                     self.turn[(l, m)] = {k for k in range(self.lanes[l]) if int(net.turn_lanes[j]) >> k & 1}
                     j += 1
+        sig = getattr(net, "link_signal", None)
+        self.sig = None if sig is None else [tuple(int(x) for x in row) for row in sig]
+        ga = getattr(net, "link_yield", None)
+        self.gap_accept = [0] * len(self.cells) if ga is None else [int(g) for g in ga]
         off = [int(c) for c in dem.route_offsets]
         self.routes = [[int(x) for x in dem.route_links[off[i]:off[i + 1]]] for i in range(dem.n)]
         self.depart = [int(x) for x in dem.depart_step]
@@ -92,13 +97,19 @@ class Brute:
             return set(range(self.lanes[l]))
         return self.turn[(l, self.routes[i][self.cur[i] + 1])]
 
+    def green(self, l):
+        if self.sig is None or self.sig[l][0] == 0:
+            return True
+        cycle, green, offset = self.sig[l]
+        return (self.t + offset) % cycle < green
+
     def gap(self, occ, buf, l, k, x, i):
         L = self.cells[l]
         g = 0
         while g < self.vmax:
             y = x + g + 1
             if y >= L and not self.ring[l]:
-                if ((l, k) not in buf or self.last(i)) and k in self.allowed(i, l):
+                if ((l, k) not in buf or self.last(i)) and k in self.allowed(i, l) and self.green(l):
                     g += 1
                 return min(g, self.vmax)
             if (l, k, y % L) in occ:
@@ -163,10 +174,21 @@ class Brute:
                 self.buf[(l, k)] = i
         transfers = 0
         for n in range(self.n_nodes):
-            inc = sorted(l for l in range(len(self.cells)) if self.to[l] == n and not self.ring[l])
+            inc = sorted((l for l in range(len(self.cells)) if self.to[l] == n and not self.ring[l]),
+                         key=lambda l: (self.gap_accept[l] > 0, l))
+            # the gap on the priority approaches, judged after the moves
+            def clear(G):
+                for p in inc:
+                    if self.gap_accept[p] == 0:
+                        L = self.cells[p]
+                        if any((p, k, x) in new for k in range(self.lanes[p]) for x in range(max(1, L - G), L)):
+                            return False
+                return True
             for l in inc:
                 for k in range(self.lanes[l]):
                     if (l, k) not in self.buf:
+                        continue
+                    if self.gap_accept[l] and not clear(self.gap_accept[l]):
                         continue
                     i = self.buf[(l, k)]
                     m = self.routes[i][self.cur[i] + 1]

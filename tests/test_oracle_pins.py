@@ -496,3 +496,96 @@ def test_plan_following_matches_naive_restatement(case):
         assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
         assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
     assert changes > 0
+
+
+# ------------------------------------------------------------------ gap acceptance at unprotected turns
+
+def _tee(placed, bufs, gap=5, p_cells=20, p=0):
+    # node 1: link 0 from node 2 (a yield approach with acceptance gap `gap`)
+    # and link 1 from node 0 (priority) both lead to link 2 (one lane)
+    sc = make_scenario([(2, 1, 20, 1), (0, 1, p_cells, 1), (1, 3, 20, 1)], 4, [[0, 2], [1, 2]], [0, 0], p=p,
+                       placed=placed, bufs=bufs)
+    if gap is not None:
+        sc.net.link_yield = np.array([gap, 0, 0], np.uint8)
+    return sc
+
+
+def test_yield_waits_for_the_gap_on_the_priority_street_by_hand():
+    # vehicle 0 waits in link 0's buffer (v 2).  Vehicle 1 drives link 1 at
+    # v 5 from cell 10: after step 0 it is in cell 15, inside the last 5
+    # cells, so vehicle 0 may not go; in step 1 it reaches the end and, from
+    # the priority approach, takes link 2's cell 0 first; in step 2 it moves
+    # on to cell 5 and vehicle 0 crosses into cell 0.
+    sc = _tee([(1, 1, 0, 10, 5)], [(0, 0, 0, 2)])
+    o = oracle.Oracle(sc)
+    seen = []
+    for _ in range(3):
+        o.step(1)
+        seen.append(positions(o.get_state(), sc.net))
+    assert seen[0][0] == (0, 0, 20, 2) and seen[0][1] == (1, 0, 15, 5)
+    assert seen[1][0] == (0, 0, 20, 2) and seen[1][1] == (2, 0, 0, 5)
+    assert seen[2][0] == (2, 0, 0, 2) and seen[2][1] == (2, 0, 5, 5)
+    # without gap acceptance the lower link id goes first, in step 0
+    sc = _tee([(1, 1, 0, 10, 5)], [(0, 0, 0, 2)], gap=None)
+    o = oracle.Oracle(sc)
+    o.step(1)
+    assert positions(o.get_state(), sc.net)[0] == (2, 0, 0, 2)
+
+
+def test_yield_crosses_when_the_priority_vehicle_is_far():
+    # vehicle 1 starts at cell 5 with v 0 and is in cell 6 after step 0: the
+    # last 5 cells of link 1 are empty and vehicle 0 crosses at once
+    sc = _tee([(1, 1, 0, 5, 0)], [(0, 0, 0, 2)])
+    o = oracle.Oracle(sc)
+    o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (2, 0, 0, 2) and pos[1] == (1, 0, 6, 1)
+
+
+def test_yield_gap_never_counts_cell_zero():
+    # every draw slows a vehicle down (threshold 2^32 - 1), so vehicle 1 never
+    # leaves its cell.  With a 4-cell priority link and a gap of 31 only cells
+    # 1..3 count: vehicle 1 in cell 0 does not hold vehicle 0 back, in cell 1
+    # it does.
+    sc = _tee([(1, 1, 0, 0, 0)], [(0, 0, 0, 2)], gap=31, p_cells=4, p=0xFFFFFFFF)
+    o = oracle.Oracle(sc)
+    o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (2, 0, 0, 2) and pos[1] == (1, 0, 0, 0)
+    sc = _tee([(1, 1, 0, 1, 0)], [(0, 0, 0, 2)], gap=31, p_cells=4, p=0xFFFFFFFF)
+    o = oracle.Oracle(sc)
+    o.step(3)
+    pos = positions(o.get_state(), sc.net)
+    assert pos[0] == (0, 0, 20, 2) and pos[1] == (1, 0, 1, 0)
+
+
+def test_generated_yield_tables():
+    net = N.grid_network(4, 2, 20)
+    g = N.grid_yield(net, 7)
+    horizontal = np.abs(net.link_from.astype(int) - net.link_to.astype(int)) == 1
+    assert set(g[horizontal].tolist()) == {0} and set(g[~horizontal].tolist()) == {7}
+    net = N.small_grid_scenario(4, 3, 20, lane_seed=2).net
+    y = N.yield_by_lanes(net, 4)
+    for n in range(net.n_nodes):
+        inc = np.nonzero(net.link_to == n)[0]
+        wide = net.link_lanes[inc].max()
+        assert all((y[l] == 4) == (net.link_lanes[l] < wide) for l in inc)
+
+
+@pytest.mark.parametrize("case", [(3, 2, 15, 200, 0, 5, None, False, None), (3, 3, 12, 200, 1, 5, 2, True, None),
+                                  (3, 2, 15, 250, 2, 7, None, False, (20, 10)), (2, 4, 10, 80, 3, 3, 4, True, None)])
+def test_gap_acceptance_matches_naive_restatement(case):
+    side, lanes, cells, trips, seed, vmax, lane_seed, turns, signal = case
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 60, 250, gen_seed=seed, seed=seed + 31, vmax=vmax,
+                               turns=turns, lane_seed=lane_seed, signal=signal, yield_gap=3 + seed)
+    o, b = oracle.Oracle(sc), Brute(sc)
+    for t in range(250):
+        so = o.step(1)[0]
+        sb = b.step()
+        for k, v in sb.items():
+            assert int(so[k]) == v, (t, k)
+        st = o.get_state()
+        ci, cv, bi, bv = b.state(sc.net)
+        assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
+        assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
+    assert int(so["arrived"]) > 0

@@ -44,7 +44,7 @@ STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
 # (plan_link_kernel for plan1) from an ncu --set full capture (caches
 # flushed) at step 5,000 (--profile-window 5000:64).  Valid only while the
 # kernel is unchanged since that capture.
-LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0, "plan1": 4796416.0 + 2816.0}
+LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -78,15 +78,21 @@ def _node_launch_ms(node_ms, mode):
 
 def _workload(name):
     from paper_cs_0105004_gb300.inputs import networks as N
-    sc = {"config1": N.config1, "config2": N.config2, "config0": N.config0, "plan1": N.config1}[name]()
-    if name == "plan1":
+    sc = {"config1": N.config1, "config2": N.config2, "config0": N.config0, "plan1": N.config1,
+          "yield1": N.config1}[name]()
+    if name in ("plan1", "yield1"):
         sc = dataclasses.replace(sc, name="config1-turn-lanes",
                                  net=dataclasses.replace(sc.net, turn_lanes=N.turn_lanes_by_rank(sc.net)))
+    if name == "yield1":
+        sc = dataclasses.replace(sc, name="config1-turn-lanes-yield",
+                                 net=dataclasses.replace(sc.net, link_yield=N.yield_by_lanes(sc.net, 8)))
     desc = {
         "config0": "5x5 grid, 80 links of 2 lanes x 60 cells, 2,000 trips",
         "config1": "Portland-shaped planar network, 20,024 links, 8,500 nodes, 300,000 trips",
         "config2": "scale-up planar network, 200,000 links, 85,000 nodes, 2,000,000 trips",
         "plan1": "config 1 (20,024 links, 300,000 trips) with turn lanes: plan-following lane changes",
+        "yield1": "config 1 (20,024 links, 300,000 trips) with turn lanes and gap acceptance (narrower "
+                  "approaches yield, 8-cell gap)",
     }[name]
     return sc, desc
 
@@ -319,7 +325,8 @@ def run_ours(args, rank, world, local_rank):
     node_s = float(node_launch_ms.sum()) / 1000.0
     peak, peak_kind = _peaks()
     achieved = link_bytes / link_s / 1e9
-    kernel = "plan_link_kernel" if getattr(net, "turn_lanes", None) is not None else "link_kernel"
+    turns = getattr(net, "turn_lanes", None) is not None or getattr(net, "link_yield", None) is not None
+    kernel = "turn_link_kernel" if turns else "link_kernel"
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": args.traffic if args.traffic is not None else LINK_TRAFFIC_BYTES.get(args.workload),
@@ -336,7 +343,8 @@ def run_ours(args, rank, world, local_rank):
         dem = sc.demand
         h2d = (net.link_from.nbytes + net.link_to.nbytes + net.link_cells.nbytes + net.link_lanes.nbytes
                + net.link_ring.nbytes + dem.depart_step.nbytes + dem.route_offsets.nbytes + dem.route_links.nbytes
-               + (net.turn_lanes.nbytes if getattr(net, "turn_lanes", None) is not None else 0))
+               + sum(a.nbytes for a in (getattr(net, "turn_lanes", None), getattr(net, "link_yield", None))
+                     if a is not None))
         d2h = 7 * 8
         times = []
         for k in range(args.e2e_jobs + 1):
@@ -623,7 +631,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty", "relax", "plan1"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty", "relax", "plan1",
+                                                  "yield1"])
     ap.add_argument("--scenarios", type=int, default=256, help="config3: batch members")
     ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
     ap.add_argument("--seq-sample", type=int, default=256, help="config3: members run one by one for comparison")

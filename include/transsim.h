@@ -80,7 +80,7 @@ typedef struct {
 
 /* Road network: directed links between nodes.  Link l runs from node
  * link_from[l] to node link_to[l], has link_cells[l] cells of 7.5 m
- * (1 .. 2^24) and link_lanes[l] lanes (1..4).  link_ring may be NULL; a
+ * (1 .. 2^22 - 1) and link_lanes[l] lanes (1..4).  link_ring may be NULL; a
  * link with link_ring[l] = 1 is a periodic circle road (Sec. 5) with no
  * nodes: its from/to are ignored, it must not appear in a multi-link route,
  * and its cell count must be a multiple of 32.  Intersection priority is
@@ -115,6 +115,18 @@ typedef struct {
      * min(vmax, cells left to the link's last cell) cells behind it empty;
      * the faster-lane reason applies only into an allowed lane. */
     const uint8_t *turn_lanes;
+    /* Optional (NULL: every approach has priority): gap acceptance at
+     * unprotected turns (Sec. 3: the car from the non-priority street needs
+     * a large enough gap on the priority street).  [n_links] acceptance gap
+     * G in cells, 0..31 (TS_ERR_INVALID above): 0 = link l's end is a
+     * priority approach, G > 0 = a yield approach.  A vehicle in a link-end
+     * buffer of a yield approach crosses only while every priority approach
+     * of the same node has no vehicle in its last G cells on any lane
+     * (cells max(1, cells - G) .. cells - 1, judged after the step's moves
+     * and before any transfer); it still needs a free cell 0.  A node serves
+     * its priority approaches first, then its yield approaches, each in
+     * ascending link id and lane. */
+    const uint8_t *link_yield;
 } ts_network_desc;
 
 /* Statistics of the state after step `step` (0-based).  active: vehicles

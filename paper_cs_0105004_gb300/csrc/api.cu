@@ -70,7 +70,7 @@ struct World {
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1;
     uint32_t tile_cap = kDefaultTileWords;  // largest tile of the members (picks the link-kernel instance)
-    bool plan = false;  // some member has a turn table (picks the plan-following instances)
+    bool turns = false;  // some member has turn lanes or yield approaches (picks the turn instances)
     uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
     std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
     bool fused() const;
@@ -98,6 +98,8 @@ struct ts_ctx {
     // links leaving its end node (out_link[out_off[n]..], ascending id)
     bool has_turn = false;
     std::vector<uint8_t> turn;
+    std::vector<uint8_t> gap_accept;       // acceptance gap per link (empty: every approach has priority)
+    std::vector<uint32_t> node_prio;       // per node: slots of its priority approaches (they come first)
     std::vector<uint32_t> turn_off, out_off, out_link;
     uint32_t n_words = 0, n_slots = 0, n_lanes = 0;
     uint64_t n_lane_cells = 0;
@@ -224,15 +226,15 @@ ts_status World::rebuild() {
     for (ts_ctx *c : members)
         if (c) {
             cap = std::max(cap, c->tile_words);
-            pl = pl || c->sd.route_turn != nullptr;
+            pl = pl || c->sd.route_turn != nullptr || c->sd.slot_gap != nullptr;
         }
-    if (cap != tile_cap || pl != plan) {
+    if (cap != tile_cap || pl != turns) {
         drop_graphs();
         tile_cap = cap;
-        plan = pl;
+        turns = pl;
     }
-    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks(tile_cap, plan)));
-    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks(plan)));
+    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks(tile_cap, turns)));
+    const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks(turns)));
     if (gl > grid_l || gn != grid_n || gl < grid_l / 2) {
         drop_graphs();
         grid_l = gl;
@@ -265,9 +267,9 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
             for (uint32_t i = 0; i < g; ++i) {
                 launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0,
-                                   tile_cap, plan);
+                                   tile_cap, turns);
                 if (!fu || i + 1 == g)
-                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, plan);
+                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, turns);
             }
             launch_advance_kernel(d_table, capacity, g, cap_stream, true);
             CK(cudaStreamEndCapture(cap_stream, &graph));
@@ -418,6 +420,8 @@ ts_status validate_desc(const ts_network_desc *d, const ts_params *p) {
         } else if (d->link_from[l] >= d->n_nodes || d->link_to[l] >= d->n_nodes) {
             return fail(TS_ERR_INVALID, "link node id out of range");
         }
+        if (d->link_yield && d->link_yield[l] > 31u)
+            return fail(TS_ERR_INVALID, "an acceptance gap must be 0..31 cells");
         if (d->link_signal) {
             const uint32_t cycle = d->link_signal[3 * l], green = d->link_signal[3 * l + 1];
             const uint32_t offset = d->link_signal[3 * l + 2];
@@ -478,6 +482,7 @@ size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_
     b += 4ull * n_vehicles + 16ull * d->n_links;              // link entry steps, link times (+ scratch)
     b += sizeof(Ctrl) + sizeof(StatRec) * kStatsRing * 8;
     if (d->turn_lanes) b += route_len + n_vehicles;             // allowed lanes per route entry and departure
+    if (d->link_yield) b += 9ull * slots;                       // acceptance gap and lane tail per buffer
     return b;
 }
 
@@ -538,14 +543,21 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
         if (!c->ring[l]) c->node_in_off[c->to[l] + 1] += c->lanes[l];
     for (uint32_t n = 0; n < c->n_nodes; ++n) c->node_in_off[n + 1] += c->node_in_off[n];
     c->n_slots = c->node_in_off[c->n_nodes];
+    if (desc->link_yield) c->gap_accept.assign(desc->link_yield, desc->link_yield + L);
+    auto yields = [&](uint32_t l) { return !c->gap_accept.empty() && c->gap_accept[l] > 0; };
+    // a node's buffers: its priority approaches, then its yield approaches,
+    // each in ascending link id
     c->bpos.assign(L, 0);
+    c->node_prio.assign(c->n_nodes, 0);
     {
         std::vector<uint32_t> fill(c->node_in_off.begin(), c->node_in_off.end() - 1);
-        for (uint32_t l = 0; l < L; ++l)
-            if (!c->ring[l]) {
-                c->bpos[l] = fill[c->to[l]];
-                fill[c->to[l]] += c->lanes[l];
-            }
+        for (int pass = 0; pass < 2; ++pass)
+            for (uint32_t l = 0; l < L; ++l)
+                if (!c->ring[l] && yields(l) == (pass == 1)) {
+                    c->bpos[l] = fill[c->to[l]];
+                    fill[c->to[l]] += c->lanes[l];
+                    if (pass == 0) c->node_prio[c->to[l]] += c->lanes[l];
+                }
     }
     for (uint32_t n = 0; n < c->n_nodes; ++n)
         if (c->node_in_off[n + 1] - c->node_in_off[n] > 255u)
@@ -580,6 +592,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     c->d_lk_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint4 *nd_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint2 *sig_info = desc->link_signal ? alloc_in<uint2>(c.get(), A, L, ok) : nullptr;
+    uint8_t *slot_gap = desc->link_yield ? alloc_in<uint8_t>(c.get(), A, c->n_slots, ok) : nullptr;
+    uint2 *slot_tail = desc->link_yield ? alloc_in<uint2>(c.get(), A, c->n_slots, ok) : nullptr;
     uint32_t *occ0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
     uint32_t *occ1 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
     uint32_t *mov0 = alloc_in<uint32_t>(c.get(), A, c->n_words, ok);
@@ -603,6 +617,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.lk_info = c->d_lk_info;
     sd.nd_info = nd_info;
     sd.sig_info = sig_info;
+    sd.slot_gap = slot_gap;
+    sd.slot_tail = slot_tail;
     sd.occ[0] = occ0;
     sd.occ[1] = occ1;
     sd.mov[0] = mov0;
@@ -634,6 +650,20 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
         for (uint32_t l = 0; l < L; ++l)
             sg[l] = make_uint2(desc->link_signal[3 * l] | (desc->link_signal[3 * l + 1] << 16), desc->link_signal[3 * l + 2]);
         CK(cudaMemcpy(sig_info, sg.data(), sizeof(uint2) * L, cudaMemcpyHostToDevice));
+    }
+    if (slot_gap && c->n_slots) {
+        // per buffer: its link's acceptance gap, and its lane's last column
+        std::vector<uint8_t> sg(c->n_slots);
+        std::vector<uint2> tl(c->n_slots);
+        for (uint32_t l = 0; l < L; ++l)
+            if (!c->ring[l])
+                for (uint32_t k = 0; k < c->lanes[l]; ++k) {
+                    sg[c->bpos[l] + k] = c->gap_accept[l];
+                    tl[c->bpos[l] + k] = make_uint2(c->wbase[l] + (c->ncols[l] - 1u) * c->lanes[l] + k,
+                                                    c->cells[l] | (c->lanes[l] << 24));
+                }
+        CK(cudaMemcpy(slot_gap, sg.data(), c->n_slots, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(slot_tail, tl.data(), sizeof(uint2) * c->n_slots, cudaMemcpyHostToDevice));
     }
     CK(cudaMemset(slots0, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
     CK(cudaMemset(slots1, 0xFF, 16ull * std::max<uint32_t>(c->n_slots, 1)));
@@ -749,12 +779,13 @@ static ts_status upload_vehicles(ts_ctx *c, const uint32_t *links) {
     // count, lanes and end of its departure queue
     std::vector<uint4> nd(L);
     for (uint32_t m = 0; m < L; ++m) {
-        uint32_t lo = 0, cnt = 0;
+        uint32_t lo = 0, cnt = 0, prio = 0;
         if (!c->ring[m]) {
             lo = c->node_in_off[c->from[m]];
             cnt = c->node_in_off[c->from[m] + 1] - lo;
+            prio = c->node_prio[c->from[m]];
         }
-        nd[m] = make_uint4(lo, c->wbase[m], cnt | (c->lanes[m] << 8), c->dep_off[m + 1]);
+        nd[m] = make_uint4(lo, c->wbase[m], cnt | (c->lanes[m] << 8) | (prio << 16), c->dep_off[m + 1]);
     }
     if (n) {
         CK(cudaMemcpy(veh, hv.data(), 8ull * n, cudaMemcpyHostToDevice));
@@ -1050,11 +1081,11 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
                 launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0,
-                                   w->tile_cap, w->plan);
+                                   w->tile_cap, w->turns);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu,
-                                       w->plan);
+                                       w->turns);
                 cudaEventRecord(ev[e + 2], s);
             }
             launch_advance_kernel(w->d_table, w->capacity, g, s, false);

@@ -20,7 +20,8 @@
 //     lanes of the current link from which the vehicle may take its next
 //     turn (0: any lane).
 //   * slots[2][n_slots]: one link-end buffer per lane, grouped by the node
-//     the link ends at, in intersection priority order (link id, then lane):
+//     the link ends at, in intersection priority order (priority approaches
+//     before yield approaches, then link id, then lane):
 //     x = id | next-link-is-last << 31 (0xffffffff = empty), y = next link,
 //     z = current link, w = v | A << 4 | lane << 8 | current link cells << 10
 //     (A: the allowed lanes on the next link, as in the velocity byte).
@@ -100,7 +101,8 @@ static_assert(sizeof(StatRec) == 128, "StatRec is one line");
 
 struct ScenDev {
     const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8 | column in tile << 16, w slot base
-    const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8, w dep end
+    const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8 |
+                                  // priority slots << 16, w dep end
     const uint2 *sig_info;        // per link: signal cycle | green << 16, offset (nullptr: no signals)
     uint32_t *occ[2];
     uint32_t *mov[2];
@@ -126,6 +128,12 @@ struct ScenDev {
     // the same for the traveller's first link
     const uint8_t *route_turn;
     const uint8_t *dep_turn;
+    // gap acceptance (nullptr: none): per slot the acceptance gap G of its
+    // link (0: a priority approach), and {word of the lane's last column,
+    // link cells | lanes << 24}; a node's priority slots come first, their
+    // count in nd_info z bits 16..23
+    const uint8_t *slot_gap;
+    const uint2 *slot_tail;
 };
 
 // link tile, two uint4: whole links  {scen, l0, nl, 0}            {w_begin, w_end, 0, 0}
@@ -145,20 +153,21 @@ struct LinkTile {
 // previous step must have been completed by node_kernel
 // tile_cap: the largest tile (occupancy words) among the tiles; picks the
 // kernel instance whose shared memory holds it
-// plan: some scenario of the table has a turn table (plan-following lane
-// changes); picks the instances that read the allowed lanes
+// turns: some scenario of the table has turn lanes (plan-following lane
+// changes) or yield approaches (gap acceptance); picks the instances that
+// apply those rules
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool plan);
+                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool turns);
 // chunk_end: the pass completes the last step each scenario ran in the
 // chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool chunk_end, bool plan);
+                        cudaStream_t s, bool pdl, bool chunk_end, bool turns);
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 // adds the entry steps of vehicles on the network to out (a copy of link_time)
 void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s);
-int max_link_blocks(uint32_t tile_cap, bool plan);
-int max_node_blocks(bool plan);
+int max_link_blocks(uint32_t tile_cap, bool turns);
+int max_node_blocks(bool turns);
 // Sets the thread-local message returned by ts_last_error.
 void set_last_error(const char *msg);
 

@@ -143,6 +143,29 @@ __device__ __forceinline__ void prefetch_slots(const uint4 *__restrict__ slots, 
         pre[s] = (uint32_t)s < cnt ? slots[slot_lo + s] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
 }
 
+// Gap acceptance at unprotected turns (Sec. 3): true iff none of the
+// node's first `prio` slots (the lanes of its priority approaches, from
+// slot_lo) has a vehicle in cells max(1, cells - G) .. cells - 1 of its lane
+// in occ (the state after the step's moves; cell 0, which transfers write,
+// never counts).  G <= 31: at most the last two columns of a lane.
+__device__ __forceinline__ bool priority_gap_clear(const ScenDev &D, const uint32_t *__restrict__ occ,
+                                                   uint32_t slot_lo, uint32_t prio, uint32_t G) {
+    for (uint32_t s = 0; s < prio; ++s) {
+        const uint2 tl = D.slot_tail[slot_lo + s];
+        const uint32_t L = tl.y & 0xFFFFFFu, lanes = tl.y >> 24;
+        const uint32_t lo = L > G ? L - G : 1u;
+        if (lo >= L) continue;
+        const uint32_t jl = (L - 1u) >> 5, jf = lo >> 5;
+        for (uint32_t j = jf; j <= jl; ++j) {
+            const uint32_t a = j == jf ? (lo & 31u) : 0u;
+            const uint32_t b = j == jl ? ((L - 1u) & 31u) : 31u;
+            const uint32_t mask = (0xFFFFFFFFu >> (31u - b)) & (0xFFFFFFFFu << a);
+            if (occ[tl.x - (jl - j) * lanes] & mask) return false;
+        }
+    }
+    return true;
+}
+
 // Node transfer into link m at the end of a step (Sec. 3): the buffered
 // vehicles at m's upstream node whose next link is m, in slot (priority)
 // order, each take cell 0 of the preferred lane min(k, lanes(m)-1) if it is
@@ -151,14 +174,23 @@ __device__ __forceinline__ void prefetch_slots(const uint4 *__restrict__ slots, 
 // free_mask from free_cell0 (after the step's moves).  Calls
 // place(slot index, slot, lane) for every placement and returns the lanes
 // still free (for departures).  Any number of threads may evaluate the same
-// m on the same inputs and get the same placements.
-template <class F>
+// m on the same inputs and get the same placements.  TURNS: a vehicle of a
+// yield approach also needs the gap on the node's `prio` priority slots in
+// occ (priority_gap_clear).
+template <bool TURNS, class F>
 __device__ __forceinline__ uint32_t resolve_prefetched(const uint4 (&pre)[kSlotPrefetch],
                                                        const uint4 *__restrict__ slots, uint32_t slot_lo,
                                                        uint32_t cnt, uint32_t m, uint32_t lanes, uint32_t free_mask,
-                                                       F &&place) {
+                                                       const ScenDev &D, const uint32_t *__restrict__ occ,
+                                                       uint32_t prio, F &&place) {
     auto visit = [&](const uint4 &x, uint32_t si) {
         if (x.x == kSlotEmpty || x.y != m || !free_mask) return;
+        if constexpr (TURNS) {
+            if (D.slot_gap) {
+                const uint32_t G = D.slot_gap[si];
+                if (G && !priority_gap_clear(D, occ, slot_lo, prio, G)) return;
+            }
+        }
         const uint32_t ks = (x.w >> 8) & 3u;
         const uint32_t pref = ks < lanes - 1u ? ks : lanes - 1u;
         uint32_t qn;
@@ -179,13 +211,15 @@ __device__ __forceinline__ uint32_t resolve_prefetched(const uint4 (&pre)[kSlotP
 }
 
 // The same for link m with nd = nd_info[m] (first slot of its upstream node,
-// word of its column 0, slot count | lanes << 8).
-template <class F>
+// word of its column 0, slot count | lanes << 8 | priority slots << 16).
+template <bool TURNS, class F>
 __device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ slots, const uint4 &nd, uint32_t m,
-                                                      uint32_t free_mask, F &&place) {
+                                                      uint32_t free_mask, const ScenDev &D,
+                                                      const uint32_t *__restrict__ occ, F &&place) {
     uint4 pre[kSlotPrefetch];
     prefetch_slots(slots, nd.x, nd.z & 0xFFu, pre);
-    return resolve_prefetched(pre, slots, nd.x, nd.z & 0xFFu, m, (nd.z >> 8) & 0xFFu, free_mask, place);
+    return resolve_prefetched<TURNS>(pre, slots, nd.x, nd.z & 0xFFu, m, (nd.z >> 8) & 0xFFu, free_mask, D, occ,
+                                     (nd.z >> 16) & 0xFFu, place);
 }
 
 // Departures from parking onto link m after the transfers: the head of m's
@@ -320,9 +354,10 @@ __device__ __forceinline__ void list_append(SM &S, uint32_t &count, int w, uint3
 // node transfers and departures into q (if q starts in this tile) at the end
 // of step t-1; then sets up q's lane-end buffers for step t (if q ends in this
 // tile).  Returns the vehicles placed on q.  Out of line, so that its
-// registers do not weigh on the rest of the step.  PLAN: velocity bytes and
-// buffer words carry the allowed lanes of the next turn.
-template <bool PLAN, class SM>
+// registers do not weigh on the rest of the step.  TURNS: velocity bytes and
+// buffer words carry the allowed lanes of the next turn, and transfers from
+// yield approaches wait for the gap.
+template <bool TURNS, class SM>
 __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int q, int cur, uint32_t t,
                                                     bool do_xfer) {
     const int nxt = cur ^ 1;
@@ -338,13 +373,13 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
         unsigned long long acc2[6] = {0, 0, 0, 0, 0, 0};
         int8_t *vel = D.vel[0];  // cell 0 was empty: its payload goes
         uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
-        uint32_t fr = resolve_transfers(sc, nd, l, free_cell0(oc, nd), [&](uint32_t, const uint4 &x,
-                                                                          uint32_t qn) {
-            const uint32_t id = x.x & kIdMask, v = x.w & (PLAN ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
+        uint32_t fr = resolve_transfers<TURNS>(sc, nd, l, free_cell0(oc, nd), D, oc, [&](uint32_t, const uint4 &x,
+                                                                                        uint32_t qn) {
+            const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
             placed |= 1u << qn;
             if (v) moving |= 1u << qn;
             const size_t pc = (size_t)(nd.y + qn) * 32u;
-            vel[pc] = (int8_t)(PLAN ? (x.w & 0xFFu) : v);
+            vel[pc] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
             vid[pc] = x.x;  // id with the last-link flag of l
             atomicAdd(&D.veh[id].x, 1u);
             atomicAdd(&D.link_time[x.z], kLinkTimeOne + (t - 1u));
@@ -359,7 +394,7 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
         run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
             placed |= 1u << qn;
             const size_t pc = (size_t)(nd.y + qn) * 32u;
-            vel[pc] = (PLAN && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
+            vel[pc] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
             vid[pc] = idw;
             atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
             D.enter_step[idw & kIdMask] = t - 1u;
@@ -395,8 +430,8 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
             bool empty = x.x == kSlotEmpty;
             if (!empty && do_xfer) {
                 const uint4 nd = D.nd_info[x.y];
-                resolve_transfers(sc, nd, x.y, free_cell0(oc, nd),
-                                  [&](uint32_t si, const uint4 &, uint32_t) { empty |= si == idx; });
+                resolve_transfers<TURNS>(sc, nd, x.y, free_cell0(oc, nd), D, oc,
+                                         [&](uint32_t si, const uint4 &, uint32_t) { empty |= si == idx; });
             }
             if (empty) open |= 1u << k;
             sn[idx] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : x;
@@ -420,10 +455,12 @@ struct LinkLaunch {
     static constexpr int kMinBlocks = 65536 / (kThreads * 64);
 };
 
-// One launch of the link kernel (body of link_kernel and plan_link_kernel).
-// PLAN: plan-following lane changes (Sec. 3): every velocity byte carries
-// the lanes A of its link from which the vehicle may take its next turn.
-template <int TW, bool PLAN>
+// One launch of the link kernel (body of link_kernel and turn_link_kernel).
+// TURNS: the intersection rules of Sec. 3 a network may carry: plan-following
+// lane changes (every velocity byte carries the lanes A of its link from
+// which the vehicle may take its next turn) and gap acceptance at
+// unprotected turns (in the node transfers).
+template <int TW, bool TURNS>
 __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__restrict__ table,
                                           const LinkTile *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
                                           uint32_t pos, uint32_t xfer) {
@@ -644,7 +681,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
         {
             // link threads, counted down from the last thread
             const int q = LinkLaunch<TW>::kThreads - 1 - (int)threadIdx.x;
-            if (q < S.nlinks) acc[0] += link_buffers_phase<PLAN>(S, D, q, cur, t, do_xfer);
+            if (q < S.nlinks) acc[0] += link_buffers_phase<TURNS>(S, D, q, cur, t, do_xfer);
         }
         __syncthreads();
         stamp(4, first);
@@ -670,7 +707,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                 const int q = S.clink[c];
                 if (kt >= 0 && kt < (int)S.llanes[q]) {
                     const uint32_t o = S.occ0[w] & lc_mask(S.ckind[c], vmax);
-                    if (PLAN && o) {
+                    if (TURNS && o) {
                         // the allowed lanes are in the payload: every vehicle
                         // whose target cell is free is decided one by one
                         listed = o & ~S.occ0[S.cw[c] + kt];
@@ -711,14 +748,14 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                 const bool b1 = (S.loc0[ww] >> i) & 1u;
                 uint32_t v;
                 uint32_t al = 0xFu;  // lanes it may leave the link from
-                if constexpr (PLAN) {
+                if constexpr (TURNS) {
                     const uint32_t byte = (uint32_t)(uint8_t)(b1 ? vel1[p] : vel0[p]);
                     v = byte & 0xFu;
                     if (byte >> 4) al = byte >> 4;
                 } else {
                     v = (uint32_t)(b1 ? vel1[p] : vel0[p]);
                 }
-                if constexpr (PLAN) {
+                if constexpr (TURNS) {
                     if (!((al >> k) & 1u)) {
                         // outside its allowed lanes: a reason to change when
                         // one of them lies on the side d points to; the gap
@@ -811,7 +848,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                 const bool sb1 = (S.loc0[sw] >> i) & 1u;
                 const uint32_t idw = sb1 ? vid1[ps] : vid0[ps];
                 uint32_t v0, al = 0u;  // al: allowed lanes of the next turn (0: any)
-                if constexpr (PLAN) {
+                if constexpr (TURNS) {
                     const uint32_t byte = (uint32_t)(uint8_t)(sb1 ? vel1[ps] : vel0[ps]);
                     v0 = byte & 0xFu;
                     al = byte >> 4;
@@ -825,7 +862,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                 const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
                 uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;  // (i) accelerate
                 uint32_t open = (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q];
-                if constexpr (PLAN) {
+                if constexpr (TURNS) {
                     if (al && !((al >> k) & 1u)) open = 0u;  // the next turn is not taken from lane k
                 }
                 const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, open, vmax);
@@ -857,7 +894,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                             const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
                             if (!((S.lexit[q] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
                             uint32_t vb = v;  // with the allowed lanes of the turn after m
-                            if constexpr (PLAN) {
+                            if constexpr (TURNS) {
                                 if (D.route_turn) vb |= (uint32_t)D.route_turn[ve.x + 1u] << 4;
                             }
                             D.slots[nxt][S.lbpos[q] + (uint32_t)k] =
@@ -888,7 +925,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                             // write the payload buffer that no reader of this step uses
                             const bool b1 = (S.occ0[dw] & bit) ? !(S.loc0[dw] & bit) : false;
                             const size_t pd = (size_t)S.gw[dw] * 32u + (uint32_t)ni;
-                            const int8_t vb = (int8_t)(PLAN ? (v | (al << 4)) : v);
+                            const int8_t vb = (int8_t)(TURNS ? (v | (al << 4)) : v);
                             if (b1) {
                                 velw1[pd] = vb;
                                 vidw1[pd] = idw;
@@ -933,10 +970,11 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
     link_step<TW, false>(S, table, tiles, n_tiles_p, pos, xfer);
 }
 
-// The same with plan-following lane changes (scenarios with a turn table).
+// The same with the intersection rules (scenarios with turn lanes or yield
+// approaches).
 template <int TW>
 __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
-    plan_link_kernel(const ScenDev *__restrict__ table, const LinkTile *__restrict__ tiles,
+    turn_link_kernel(const ScenDev *__restrict__ table, const LinkTile *__restrict__ tiles,
                      const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer) {
     __shared__ LinkSmem<TW> S;
     link_step<TW, true>(S, table, tiles, n_tiles_p, pos, xfer);
@@ -947,9 +985,9 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
 // Node transfers and departures into link m (nd = nd_info[m]) at the end of
 // step `step`, on the state after that step's moves; acc gets the transfers,
 // insertions and the changes of active, buffered, sum of velocities, digest.
-// PLAN: velocity bytes and buffer words carry the allowed lanes of the next
-// turn.
-template <bool PLAN>
+// TURNS: velocity bytes and buffer words carry the allowed lanes of the next
+// turn, and transfers from yield approaches wait for the gap.
+template <bool TURNS>
 __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const uint4 &nd, unsigned long long step,
                                           unsigned long long (&acc)[6]) {
     const int nxt = (int)((step + 1ull) & 1ull);
@@ -959,13 +997,13 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
     int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
     uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
     // slots with next link m, and the cells 0 of m, are written by this thread only
-    const uint32_t fr = resolve_transfers(slots, nd, m, free_cell0(occ, nd), [&](uint32_t si, const uint4 &x,
-                                                                                  uint32_t qn) {
-        const uint32_t id = x.x & kIdMask, v = x.w & (PLAN ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
+    const uint32_t fr = resolve_transfers<TURNS>(slots, nd, m, free_cell0(occ, nd), D, occ,
+                                                 [&](uint32_t si, const uint4 &x, uint32_t qn) {
+        const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
         const uint32_t w = nd.y + qn;  // column 0 of lane qn
         occ[w] |= 1u;
         if (v) mov[w] |= 1u;
-        vel[(size_t)w * 32u] = (int8_t)(PLAN ? (x.w & 0xFFu) : v);
+        vel[(size_t)w * 32u] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
         vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
         atomicAdd(&D.veh[id].x, 1u);
         slots[si].x = kSlotEmpty;
@@ -982,7 +1020,7 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
     run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
         const uint32_t w = nd.y + qn;
         occ[w] |= 1u;
-        vel[(size_t)w * 32u] = (PLAN && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
+        vel[(size_t)w * 32u] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
         vid[(size_t)w * 32u] = idw;
         atomicAdd(&D.link_time[m], 0ull - step);
         D.enter_step[idw & kIdMask] = (uint32_t)step;
@@ -1007,8 +1045,8 @@ __device__ __forceinline__ bool node_step(const ScenDev &D, uint32_t pos, bool c
 }
 
 // One node pass, one thread per link m (body of node_kernel and
-// plan_node_kernel).
-template <bool PLAN>
+// turn_node_kernel).
+template <bool TURNS>
 __device__ __forceinline__ void node_pass(unsigned long long (*red)[6], const ScenDev *__restrict__ table,
                                           const uint4 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
                                           uint32_t pos, uint32_t chunk_end) {
@@ -1038,7 +1076,7 @@ __device__ __forceinline__ void node_pass(unsigned long long (*red)[6], const Sc
             if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
             cur_rec = rec;
         }
-        if (m < td.z) node_link<PLAN>(D, m, nd, step, acc);
+        if (m < td.z) node_link<TURNS>(D, m, nd, step, acc);
     }
     if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
     span_mark((int)pos * 3 + 1, false);
@@ -1052,8 +1090,8 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
     node_pass<false>(red, table, tiles, n_tiles_p, pos, chunk_end);
 }
 
-// The same for scenarios with a turn table.
-__global__ void __launch_bounds__(kNodeThreads) plan_node_kernel(const ScenDev *__restrict__ table,
+// The same for scenarios with turn lanes or yield approaches.
+__global__ void __launch_bounds__(kNodeThreads) turn_node_kernel(const ScenDev *__restrict__ table,
                                                                  const uint4 *__restrict__ tiles,
                                                                  const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
                                                                  uint32_t chunk_end) {
@@ -1165,23 +1203,23 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
 }
 
 template <int TW>
-static void (*link_instance(bool plan))(const ScenDev *, const LinkTile *, const uint32_t *, uint32_t, uint32_t) {
-    return plan ? plan_link_kernel<TW> : link_kernel<TW>;
+static void (*link_instance(bool turns))(const ScenDev *, const LinkTile *, const uint32_t *, uint32_t, uint32_t) {
+    return turns ? turn_link_kernel<TW> : link_kernel<TW>;
 }
 
 void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool plan) {
+                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool turns) {
     if (tile_cap <= (uint32_t)kDefaultTileWords)
-        launch_pdl(link_instance<kDefaultTileWords>(plan), grid, LinkLaunch<kDefaultTileWords>::kThreads, pdl, s,
+        launch_pdl(link_instance<kDefaultTileWords>(turns), grid, LinkLaunch<kDefaultTileWords>::kThreads, pdl, s,
                    table, tiles, n_tiles, i, xfer ? 1u : 0u);
     else
-        launch_pdl(link_instance<kTileWords>(plan), grid, LinkLaunch<kTileWords>::kThreads, pdl, s, table, tiles,
+        launch_pdl(link_instance<kTileWords>(turns), grid, LinkLaunch<kTileWords>::kThreads, pdl, s, table, tiles,
                    n_tiles, i, xfer ? 1u : 0u);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool chunk_end, bool plan) {
-    launch_pdl(plan ? plan_node_kernel : node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i,
+                        cudaStream_t s, bool pdl, bool chunk_end, bool turns) {
+    launch_pdl(turns ? turn_node_kernel : node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i,
                chunk_end ? 1u : 0u);
 }
 
@@ -1230,11 +1268,11 @@ extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
 }
 #endif
 
-int max_link_blocks(uint32_t tile_cap, bool plan) {
+int max_link_blocks(uint32_t tile_cap, bool turns) {
     if (tile_cap <= (uint32_t)kDefaultTileWords) {
         // five blocks of the default instance need more shared memory than
         // the smallest L1/shared splits give
-        const void *fn = (const void *)link_instance<kDefaultTileWords>(plan);
+        const void *fn = (const void *)link_instance<kDefaultTileWords>(turns);
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
         return resident_blocks(fn, LinkLaunch<kDefaultTileWords>::kThreads);
     }
@@ -1242,12 +1280,12 @@ int max_link_blocks(uint32_t tile_cap, bool plan) {
     // default L1/shared split leaves for four blocks; the largest shared
     // share measured fastest on GB300 (config 3: 3.3e10 vs 2.4e10
     // vehicle-updates/s with the default split)
-    const void *fn = (const void *)link_instance<kTileWords>(plan);
+    const void *fn = (const void *)link_instance<kTileWords>(turns);
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     return resident_blocks(fn, LinkLaunch<kTileWords>::kThreads);
 }
-int max_node_blocks(bool plan) {
-    return resident_blocks(plan ? (const void *)plan_node_kernel : (const void *)node_kernel, kNodeThreads);
+int max_node_blocks(bool turns) {
+    return resident_blocks(turns ? (const void *)turn_node_kernel : (const void *)node_kernel, kNodeThreads);
 }
 
 }  // namespace tsim

@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
 class NetworkDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_uint32), ("n_links", ctypes.c_uint32), ("link_from", u32p),
                 ("link_to", u32p), ("link_cells", u32p), ("link_lanes", u32p), ("link_ring", u8p),
-                ("link_signal", u32p), ("turn_lanes", u8p)]
+                ("link_signal", u32p), ("turn_lanes", u8p), ("link_yield", u8p)]
 
 
 class Stats(ctypes.Structure):
@@ -167,10 +167,13 @@ class _NetArrays:
         self.ls = None if sig is None else np.ascontiguousarray(sig, np.uint32).reshape(-1)
         turn = getattr(net, "turn_lanes", None)
         self.tl = None if turn is None else np.ascontiguousarray(turn, np.uint8).reshape(-1)
+        ly = getattr(net, "link_yield", None)
+        self.ly = None if ly is None else np.ascontiguousarray(ly, np.uint8).reshape(-1)
         self.desc = NetworkDesc(net.n_nodes, net.n_links, _p(self.lf, ctypes.c_uint32), _p(self.lt, ctypes.c_uint32),
                                 _p(self.lc, ctypes.c_uint32), _p(self.ll, ctypes.c_uint32), _p(self.lr, ctypes.c_uint8),
                                 _p(self.ls, ctypes.c_uint32) if self.ls is not None else None,
-                                _p(self.tl, ctypes.c_uint8) if self.tl is not None else None)
+                                _p(self.tl, ctypes.c_uint8) if self.tl is not None else None,
+                                _p(self.ly, ctypes.c_uint8) if self.ly is not None else None)
 
 
 def footprint_bytes(scenario) -> int:

@@ -1,7 +1,9 @@
-"""Plan-following lane changes (turn lanes) on the GPU vs the CPU oracle,
-bit-exact, through the C ABI: hand-built cases, grids with one to four
-lanes, partial tiles, signals, batches that mix scenarios with and without
-a turn table, states written from the oracle, and checkpoints."""
+"""The intersection rules of Sec. 3 on the GPU vs the CPU oracle, bit-exact,
+through the C ABI: plan-following lane changes (turn lanes) and gap
+acceptance at unprotected turns (yield approaches) — hand-built cases, grids
+with one to four lanes, partial tiles, signals, batches that mix scenarios
+with and without those rules, states written from the oracle, and
+checkpoints."""
 import dataclasses
 
 import numpy as np
@@ -128,10 +130,12 @@ def test_state_from_the_oracle_and_checkpoint():
 
 
 @pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
-def test_batch_mixing_plans_and_no_plans_equals_alone(mode):
-    # members with and without a turn table share the plan-following launches
+def test_batch_mixing_rules_and_no_rules_equals_alone(mode):
+    # members with and without turn lanes or yield approaches share the
+    # intersection-rule launches
     scs = [N.small_grid_scenario(3 + i % 3, 2 + i % 3, 20 + 5 * i, 150 + 40 * i, 100, 400, gen_seed=40 + i,
-                                 seed=140 + i, turns=bool(i % 2)) for i in range(6)]
+                                 seed=140 + i, turns=bool(i % 2), yield_gap=5 + i if i % 3 == 2 else None)
+           for i in range(6)]
     alone = []
     for sc in scs:
         sim = T.Simulation(sc)
@@ -162,3 +166,75 @@ def test_malformed_turn_tables_are_rejected():
         sc.net.turn_lanes = np.array(bad, np.uint8)
         with pytest.raises(T.TsError, match="INVALID"):
             T.Simulation(sc)
+
+
+# ------------------------------------------------------------------ gap acceptance
+
+def _tee(placed, bufs, gap=5, p_cells=20, p=0):
+    sc = make_scenario([(2, 1, 20, 1), (0, 1, p_cells, 1), (1, 3, 20, 1)], 4, [[0, 2], [1, 2]], [0, 0], p=p,
+                       placed=placed, bufs=bufs, steps=30)
+    sc.net.link_yield = np.array([gap, 0, 0], np.uint8)
+    return sc
+
+
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_gap_acceptance_hand_cases_match_oracle(mode):
+    cases = [
+        _tee([(1, 1, 0, 10, 5)], [(0, 0, 0, 2)]),
+        _tee([(1, 1, 0, 5, 0)], [(0, 0, 0, 2)]),
+        _tee([(1, 1, 0, 0, 0)], [(0, 0, 0, 2)], gap=31, p_cells=4, p=0xFFFFFFFF),
+        _tee([(1, 1, 0, 1, 0)], [(0, 0, 0, 2)], gap=31, p_cells=4, p=0xFFFFFFFF),
+        # a 40-cell priority link: the gap of 31 cells spans two columns
+        _tee([(1, 1, 0, 9, 0)], [(0, 0, 0, 2)], gap=31, p_cells=40, p=0xFFFFFFFF),
+        _tee([(1, 1, 0, 8, 0)], [(0, 0, 0, 2)], gap=31, p_cells=40, p=0xFFFFFFFF),
+    ]
+    for sc in cases:
+        run_parity(sc, 30, chunk=1, state_every=1, mode=mode)
+
+
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+@pytest.mark.parametrize("case", [(3, 2, 20, 300, 1, 5, None, False, 4), (4, 3, 25, 700, 2, 5, 6, True, 9),
+                                  (4, 4, 40, 1200, 3, 5, 7, True, 31), (5, 2, 60, 2000, 4, 5, None, False, 12),
+                                  (4, 3, 33, 600, 5, 15, 8, False, 20)])
+def test_grids_with_yield_approaches_match_oracle(case, mode):
+    side, lanes, cells, trips, seed, vmax, lane_seed, turns, gap = case
+    sc = N.small_grid_scenario(side, lanes, cells, trips, 200, 800, gen_seed=seed, seed=seed * 3 + 5, vmax=vmax,
+                               turns=turns, lane_seed=lane_seed, yield_gap=gap)
+    o = run_parity(sc, 800, chunk=200, state_every=200, mode=mode)
+    assert int(o["arrived"][-1]) > 0
+
+
+def test_yield_with_signals_and_partial_tiles():
+    sc = N.small_grid_scenario(4, 3, 45, 1500, 200, 900, gen_seed=13, seed=14, signal=(40, 20), turns=True,
+                               lane_seed=15, yield_gap=6)
+    run_parity(sc, 900, chunk=300, state_every=300)
+    run_parity(sc, 900, chunk=300, state_every=300, tile_words=8, mode=T.STEP_FUSED)
+
+
+def test_config1_with_turn_lanes_and_yield_first_window():
+    sc = _with_turns(N.config1())
+    sc = dataclasses.replace(sc, net=dataclasses.replace(sc.net, link_yield=N.yield_by_lanes(sc.net, 8)))
+    run_parity(sc, 900, chunk=300, state_every=900)
+
+
+def test_yield_state_from_the_oracle():
+    sc = N.small_grid_scenario(4, 2, 30, 1500, 300, 900, gen_seed=25, seed=26, yield_gap=10)
+    orc = oracle.Oracle(sc)
+    orc.step(400)
+    s = orc.get_state()
+    init = N.InitialState(**{k: s[k] for k in ("cell_id", "cell_v", "buf_id", "buf_v", "cursor", "dep_head")},
+                          step=s["step"], arrived=s["arrived"], inserted=s["inserted"])
+    sim = T.Simulation(sc)
+    sim.write_state(init)
+    sim.step(300)
+    _cmp_stats(sim.stats_range(400, 300), orc.step(300), "from the oracle state")
+    _cmp_state(sim.read_state(), orc.get_state(), "after step 699")
+    sim.close()
+
+
+def test_malformed_yield_table_is_rejected():
+    sc = _tee([(1, 1, 0, 10, 5)], [(0, 0, 0, 2)])
+    T.Simulation(sc).close()
+    sc.net.link_yield = np.array([32, 0, 0], np.uint8)
+    with pytest.raises(T.TsError, match="INVALID"):
+        T.Simulation(sc)

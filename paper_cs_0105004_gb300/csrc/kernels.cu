@@ -148,10 +148,10 @@ __device__ __forceinline__ void prefetch_slots(const uint4 *__restrict__ slots, 
 // slot_lo) has a vehicle in cells max(1, cells - G) .. cells - 1 of its lane
 // in occ (the state after the step's moves; cell 0, which transfers write,
 // never counts).  G <= 31: at most the last two columns of a lane.
-__device__ __forceinline__ bool priority_gap_clear(const ScenDev &D, const uint32_t *__restrict__ occ,
-                                                   uint32_t slot_lo, uint32_t prio, uint32_t G) {
+__device__ __forceinline__ bool priority_gap_clear(const uint2 *__restrict__ slot_tail, const uint32_t *__restrict__ occ,
+                                                uint32_t slot_lo, uint32_t prio, uint32_t G) {
     for (uint32_t s = 0; s < prio; ++s) {
-        const uint2 tl = D.slot_tail[slot_lo + s];
+        const uint2 tl = slot_tail[slot_lo + s];
         const uint32_t L = tl.y & 0xFFFFFFu, lanes = tl.y >> 24;
         const uint32_t lo = L > G ? L - G : 1u;
         if (lo >= L) continue;
@@ -174,21 +174,22 @@ __device__ __forceinline__ bool priority_gap_clear(const ScenDev &D, const uint3
 // free_mask from free_cell0 (after the step's moves).  Calls
 // place(slot index, slot, lane) for every placement and returns the lanes
 // still free (for departures).  Any number of threads may evaluate the same
-// m on the same inputs and get the same placements.  TURNS: a vehicle of a
-// yield approach also needs the gap on the node's `prio` priority slots in
-// occ (priority_gap_clear).
+// m on the same inputs and get the same placements.  TURNS: with slot_gap,
+// a vehicle of a yield approach also needs the gap on the node's `prio`
+// priority slots in occ (priority_gap_clear).
 template <bool TURNS, class F>
 __device__ __forceinline__ uint32_t resolve_prefetched(const uint4 (&pre)[kSlotPrefetch],
                                                        const uint4 *__restrict__ slots, uint32_t slot_lo,
                                                        uint32_t cnt, uint32_t m, uint32_t lanes, uint32_t free_mask,
-                                                       const ScenDev &D, const uint32_t *__restrict__ occ,
-                                                       uint32_t prio, F &&place) {
+                                                       const uint8_t *__restrict__ slot_gap,
+                                                       const uint2 *__restrict__ slot_tail,
+                                                       const uint32_t *__restrict__ occ, uint32_t prio, F &&place) {
     auto visit = [&](const uint4 &x, uint32_t si) {
         if (x.x == kSlotEmpty || x.y != m || !free_mask) return;
         if constexpr (TURNS) {
-            if (D.slot_gap) {
-                const uint32_t G = D.slot_gap[si];
-                if (G && !priority_gap_clear(D, occ, slot_lo, prio, G)) return;
+            if (slot_gap) {
+                const uint32_t G = slot_gap[si];
+                if (G && !priority_gap_clear(slot_tail, occ, slot_lo, prio, G)) return;
             }
         }
         const uint32_t ks = (x.w >> 8) & 3u;
@@ -216,10 +217,13 @@ template <bool TURNS, class F>
 __device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ slots, const uint4 &nd, uint32_t m,
                                                       uint32_t free_mask, const ScenDev &D,
                                                       const uint32_t *__restrict__ occ, F &&place) {
+    // the gap tables are read once, before any placement's stores
+    const uint8_t *slot_gap = TURNS ? D.slot_gap : nullptr;
+    const uint2 *slot_tail = TURNS ? D.slot_tail : nullptr;
     uint4 pre[kSlotPrefetch];
     prefetch_slots(slots, nd.x, nd.z & 0xFFu, pre);
-    return resolve_prefetched<TURNS>(pre, slots, nd.x, nd.z & 0xFFu, m, (nd.z >> 8) & 0xFFu, free_mask, D, occ,
-                                     (nd.z >> 16) & 0xFFu, place);
+    return resolve_prefetched<TURNS>(pre, slots, nd.x, nd.z & 0xFFu, m, (nd.z >> 8) & 0xFFu, free_mask, slot_gap,
+                                     slot_tail, occ, (nd.z >> 16) & 0xFFu, place);
 }
 
 // Departures from parking onto link m after the transfers: the head of m's
@@ -350,6 +354,85 @@ __device__ __forceinline__ void list_append(SM &S, uint32_t &count, int w, uint3
     }
 }
 
+// Node transfers and departures into link l = S.lid[q] (which starts in this
+// tile) at the end of step t-1, for fused steps.  Returns the vehicles
+// placed on l.
+template <bool TURNS, class SM>
+__device__ __forceinline__ uint32_t xfer_into_link(SM &S, const ScenDev &D, int q, uint32_t t,
+                                                   const uint4 *__restrict__ sc, const uint32_t *__restrict__ oc,
+                                                   uint32_t l) {
+    const uint4 nd = D.nd_info[l];
+    uint32_t placed = 0u, moving = 0u;
+    unsigned long long acc2[6] = {0, 0, 0, 0, 0, 0};
+    int8_t *vel = D.vel[0];  // cell 0 was empty: its payload goes
+    uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
+    uint32_t fr = resolve_transfers<TURNS>(sc, nd, l, free_cell0(oc, nd), D, oc, [&](uint32_t, const uint4 &x,
+                                                                                    uint32_t qn) {
+        const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
+        placed |= 1u << qn;
+        if (v) moving |= 1u << qn;
+        const size_t pc = (size_t)(nd.y + qn) * 32u;
+        vel[pc] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
+        vid[pc] = x.x;  // id with the last-link flag of l
+        atomicAdd(&D.veh[id].x, 1u);
+        atomicAdd(&D.link_time[x.z], kLinkTimeOne + (t - 1u));
+        atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
+        D.enter_step[id] = t - 1u;
+        acc2[0] += 1;
+        acc2[2] += 1;
+        acc2[3] -= 1;
+        acc2[4] += v;
+        acc2[5] += vehicle_term(id, l, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+    });
+    run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
+        placed |= 1u << qn;
+        const size_t pc = (size_t)(nd.y + qn) * 32u;
+        vel[pc] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
+        vid[pc] = idw;
+        atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
+        D.enter_step[idw & kIdMask] = t - 1u;
+        acc2[1] += 1;
+        acc2[2] += 1;
+        acc2[5] += vehicle_term(idw & kIdMask, l, qn, 0u, 0u);
+    });
+    const uint32_t n_placed = (uint32_t)__popc(placed);  // they are updated in step t
+    if (placed)
+        for (int f = 0; f < 6; ++f)
+            if (acc2[f]) atomicAdd(&S.xacc[f], acc2[f]);
+    for (uint32_t m = placed; m; m &= m - 1u) {
+        const uint32_t qn = (uint32_t)(__ffs(m) - 1);
+        atomicOr(&S.occ0[S.lcw0[q] + qn], 1u);
+        if ((moving >> qn) & 1u) atomicOr(&S.mov0[S.lcw0[q] + qn], 1u);
+    }
+    return n_placed;
+}
+
+// Whether the buffer idx holding x is emptied by the node transfer of step
+// t-1 (the same resolution as the tile of x's next link computes).
+template <bool TURNS>
+__device__ __forceinline__ void buffer_emptied(const ScenDev &D, const uint4 *__restrict__ sc,
+                                               const uint32_t *__restrict__ oc, const uint4 &x, uint32_t idx,
+                                               bool &empty) {
+    const uint4 nd = D.nd_info[x.y];
+    resolve_transfers<TURNS>(sc, nd, x.y, free_cell0(oc, nd), D, oc,
+                             [&](uint32_t si, const uint4 &, uint32_t) { empty |= si == idx; });
+}
+
+// The intersection-rule versions out of line, so that their registers stay
+// out of link_buffers_phase.
+template <class SM>
+__device__ __noinline__ uint32_t xfer_into_link_turns(SM &S, const ScenDev &D, int q, uint32_t t,
+                                                      const uint4 *__restrict__ sc, const uint32_t *__restrict__ oc,
+                                                      uint32_t l) {
+    return xfer_into_link<true>(S, D, q, t, sc, oc, l);
+}
+__device__ __noinline__ bool buffer_emptied_turns(const ScenDev &D, const uint4 *__restrict__ sc,
+                                                  const uint32_t *__restrict__ oc, uint4 x, uint32_t idx) {
+    bool empty = false;
+    buffer_emptied<true>(D, sc, oc, x, idx, empty);
+    return empty;
+}
+
 // The link thread of link q (index in the tile): with do_xfer, completes the
 // node transfers and departures into q (if q starts in this tile) at the end
 // of step t-1; then sets up q's lane-end buffers for step t (if q ends in this
@@ -368,49 +451,10 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
     const uint32_t l = S.lid[q];
     if (do_xfer && S.lcw0[q] != 0xFFFFu) {
         // transfers and departures into l at the end of step t-1
-        const uint4 nd = D.nd_info[l];
-        uint32_t placed = 0u, moving = 0u;
-        unsigned long long acc2[6] = {0, 0, 0, 0, 0, 0};
-        int8_t *vel = D.vel[0];  // cell 0 was empty: its payload goes
-        uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
-        uint32_t fr = resolve_transfers<TURNS>(sc, nd, l, free_cell0(oc, nd), D, oc, [&](uint32_t, const uint4 &x,
-                                                                                        uint32_t qn) {
-            const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
-            placed |= 1u << qn;
-            if (v) moving |= 1u << qn;
-            const size_t pc = (size_t)(nd.y + qn) * 32u;
-            vel[pc] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
-            vid[pc] = x.x;  // id with the last-link flag of l
-            atomicAdd(&D.veh[id].x, 1u);
-            atomicAdd(&D.link_time[x.z], kLinkTimeOne + (t - 1u));
-            atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
-            D.enter_step[id] = t - 1u;
-            acc2[0] += 1;
-            acc2[2] += 1;
-            acc2[3] -= 1;
-            acc2[4] += v;
-            acc2[5] += vehicle_term(id, l, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
-        });
-        run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
-            placed |= 1u << qn;
-            const size_t pc = (size_t)(nd.y + qn) * 32u;
-            vel[pc] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
-            vid[pc] = idw;
-            atomicAdd(&D.link_time[l], 0ull - (unsigned long long)(t - 1u));
-            D.enter_step[idw & kIdMask] = t - 1u;
-            acc2[1] += 1;
-            acc2[2] += 1;
-            acc2[5] += vehicle_term(idw & kIdMask, l, qn, 0u, 0u);
-        });
-        n_placed = (uint32_t)__popc(placed);  // they are updated in step t
-        if (placed)
-            for (int f = 0; f < 6; ++f)
-                if (acc2[f]) atomicAdd(&S.xacc[f], acc2[f]);
-        for (uint32_t m = placed; m; m &= m - 1u) {
-            const uint32_t qn = (uint32_t)(__ffs(m) - 1);
-            atomicOr(&S.occ0[S.lcw0[q] + qn], 1u);
-            if ((moving >> qn) & 1u) atomicOr(&S.mov0[S.lcw0[q] + qn], 1u);
-        }
+        if constexpr (TURNS)
+            n_placed = xfer_into_link_turns(S, D, q, t, sc, oc, l);
+        else
+            n_placed = xfer_into_link<false>(S, D, q, t, sc, oc, l);
     }
     uint32_t open = 0u;
     if (S.lend[q]) {
@@ -429,9 +473,10 @@ __device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int
             const uint4 x = own[k];
             bool empty = x.x == kSlotEmpty;
             if (!empty && do_xfer) {
-                const uint4 nd = D.nd_info[x.y];
-                resolve_transfers<TURNS>(sc, nd, x.y, free_cell0(oc, nd), D, oc,
-                                         [&](uint32_t si, const uint4 &, uint32_t) { empty |= si == idx; });
+                if constexpr (TURNS)
+                    empty = buffer_emptied_turns(D, sc, oc, x, idx);
+                else
+                    buffer_emptied<false>(D, sc, oc, x, idx, empty);
             }
             if (empty) open |= 1u << k;
             sn[idx] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : x;

@@ -41,10 +41,11 @@ METRIC = "vehicle-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
 # dram__bytes_read.sum + dram__bytes_write.sum of one link_kernel launch
-# (plan_link_kernel for plan1) from an ncu --set full capture (caches
+# (turn_link_kernel for plan1 and yield1) from an ncu --set full capture (caches
 # flushed) at step 5,000 (--profile-window 5000:64).  Valid only while the
 # kernel is unchanged since that capture.
-LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0}
+LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0, "plan1": 4783616.0 + 7424.0,
+                      "yield1": 4325376.0 + 8704.0}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

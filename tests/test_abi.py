@@ -44,3 +44,16 @@ def test_footprint_grows_with_network():
     a = T.footprint_bytes(N.small_grid_scenario(3, 1, 10, 10, 10, 10))
     b = T.footprint_bytes(N.small_grid_scenario(5, 2, 60, 100, 10, 10))
     assert 0 < a < b
+
+
+def test_footprint_counts_the_intersection_tables():
+    # turn lanes add one byte per route entry and per traveller; yield
+    # approaches add nine bytes per link-end buffer (gap and lane tail)
+    from paper_cs_0105004_gb300.inputs import networks as N
+    plain = N.small_grid_scenario(4, 3, 20, 300, 100, 10, gen_seed=3)
+    turns = N.small_grid_scenario(4, 3, 20, 300, 100, 10, gen_seed=3, turns=True)
+    both = N.small_grid_scenario(4, 3, 20, 300, 100, 10, gen_seed=3, turns=True, yield_gap=5)
+    a, b, c = (T.footprint_bytes(s) for s in (plain, turns, both))
+    route_len = int(plain.demand.route_offsets[-1])
+    assert b - a == route_len + plain.demand.n
+    assert c - b == 9 * plain.net.n_lanes

@@ -230,11 +230,11 @@ __device__ __forceinline__ uint32_t resolve_transfers(const uint4 *__restrict__ 
 // queue enters the lowest free lane with v = 0 while lanes are free and its
 // departure step has come.  The head's departure step is kept beside the
 // head index, so a link with nothing due costs one load.  Calls
-// insert(queue entry, lane, queue index).
+// insert(queue entry, lane, queue index).  hd = dep_head[m], loaded by the
+// caller.
 template <class F>
-__device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
-                                               uint32_t free_mask, F &&insert) {
-    const uint2 hd = D.dep_head[m];
+__device__ __forceinline__ void run_departures_from(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
+                                                    const uint2 hd, uint32_t free_mask, F &&insert) {
     if (hd.y > t || !free_mask) return;  // y = ~0 once the queue is empty
     const uint32_t dep_end = nd.w;
     uint32_t h = hd.x, next;
@@ -248,6 +248,12 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
         insert(idw, qn, qi);
     } while (next <= t && free_mask);
     D.dep_head[m] = make_uint2(h, next);
+}
+
+template <class F>
+__device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd, uint32_t m, uint32_t t,
+                                               uint32_t free_mask, F &&insert) {
+    run_departures_from(D, nd, m, t, D.dep_head[m], free_mask, insert);
 }
 
 // ------------------------------------------------------------------ link kernel
@@ -1041,7 +1047,10 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
     uint4 *slots = D.slots[nxt];
     int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
     uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
-    // slots with next link m, and the cells 0 of m, are written by this thread only
+    // slots with next link m, the cells 0 of m and m's queue head are
+    // written by this thread only; the head is loaded with the node's buffers
+    // and m's cells 0, not after the transfers
+    const uint2 hd = D.dep_head[m];
     const uint32_t fr = resolve_transfers<TURNS>(slots, nd, m, free_cell0(occ, nd), D, occ,
                                                  [&](uint32_t si, const uint4 &x, uint32_t qn) {
         const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
@@ -1062,7 +1071,7 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
         acc[4] += v;
         acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
     });
-    run_departures(D, nd, m, (uint32_t)step, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
+    run_departures_from(D, nd, m, (uint32_t)step, hd, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
         const uint32_t w = nd.y + qn;
         occ[w] |= 1u;
         vel[(size_t)w * 32u] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;

@@ -916,11 +916,6 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                 if constexpr (TURNS) {
                     if (al && !((al >> k) & 1u)) open = 0u;  // the next turn is not taken from lane k
                 }
-                // a vehicle that can reach the end of a link that is not its
-                // last needs its route position there: load it now, so that the
-                // load overlaps the velocity update
-                uint2 ve = make_uint2(0u, 0u);
-                if (open && !last && dist < vmax) ve = D.veh[id];
                 const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, open, vmax);
                 if (v > g) v = g;                                                 // (ii) gap
                 if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;  // (iii) random
@@ -942,6 +937,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                         acc[5] -= v0;
                         acc_hash -= old_term;
                     } else {
+                        const uint2 ve = D.veh[id];
                         if (ve.x + 1u >= ve.y) {
                             atomicOr(&D.ctrl->error, kErrRoute);
                         } else {

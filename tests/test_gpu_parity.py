@@ -360,3 +360,56 @@ def test_config1_busy_window_from_the_oracle_state():
     _cmp_stats(sim.stats_range(2400, 300), orc.step(300), "config1 from step 2400")
     _cmp_state(sim.read_state(), orc.get_state(), "config1 after step 2699")
     sim.close()
+
+
+# ------------------------------------------------------------------ full-size networks of the other workloads
+
+def test_config3_batch_members_match_oracle():
+    # the batching workload's launch configuration: the first 16 full-size
+    # grid scenarios of its 256-member batch in one batch, 256-word tiles (the
+    # autotuner's pick), split steps; the largest (1.85 M lane-cells), the
+    # densest (483 k trips) and the smallest member checked step by step
+    # against the oracle
+    import torch
+    from paper_cs_0105004_gb300 import batching as Bt
+    steps = 360
+    scs = [N.config3_scenario(i) for i in range(16)]
+    sims = Bt.make_members(scs, tile_words=256)
+    b = T.Batch(len(sims))
+    b.add_many(sims, steps)
+    stream = torch.cuda.Stream()
+    b.step(steps, stream)
+    b.sync()
+    for i in (1, 4, 7):
+        orc = oracle.Oracle(scs[i])
+        _cmp_stats(sims[i].stats_range(0, steps), orc.step(steps), f"config3 member {i}")
+        _cmp_state(sims[i].read_state(), orc.get_state(), f"config3 member {i} after step {steps - 1}")
+        orc.close()
+    b.close()
+
+
+def test_config2_network_with_a_trip_sample_matches_oracle():
+    # the full config-2 network (200,000 links, 18.2 M lane-cells) with a
+    # sample of its 2 M trips: those whose origin is among the first 1,500
+    # distinct origins of the draw (so routes need 1,500 shortest-path trees),
+    # departures brought forward by 5,000 s (clamped at 0: about 40 % are due
+    # at step 0); 128-word tiles with re-tiling from the occupancy every 64
+    # steps; 300 steps against the oracle
+    net = N.planar_network(85_000, 100_000, 2)
+    rng = np.random.default_rng(2 + 7919)
+    o, d, dep = N.degree_weighted_trips(net, 2_000_000, 5400.0, 2400.0, 10800, rng)
+    _, first = np.unique(o, return_index=True)
+    origins = o[np.sort(first)[:1500]]
+    keep = np.nonzero(np.isin(o, origins))[0]
+    dep2 = np.maximum(dep[keep].astype(np.int64) - 5000, 0).astype(np.uint32)
+    sc = N.Scenario("config2-sample", net, N._demand(net, o[keep], d[keep], dep2), steps=300, seed=1)
+    sim = T.Simulation(sc, tile_words=128)
+    sim.set_load_balance(64, 768)
+    orc = oracle.Oracle(sc)
+    sim.step(300)
+    g = sim.stats_range(0, 300)
+    _cmp_stats(g, orc.step(300), "config2 sample")
+    _cmp_state(sim.read_state(), orc.get_state(), "config2 sample after step 299")
+    assert int(g["active"][-1]) > 10_000
+    sim.close()
+    orc.close()

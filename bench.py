@@ -80,7 +80,10 @@ def _node_launch_ms(node_ms, mode):
 def _workload(name):
     from paper_cs_0105004_gb300.inputs import networks as N
     sc = {"config1": N.config1, "config2": N.config2, "config0": N.config0, "plan1": N.config1,
-          "yield1": N.config1}[name]()
+          "yield1": N.config1, "signal1": N.config1}[name]()
+    if name == "signal1":
+        sc = dataclasses.replace(sc, name="config1-signals",
+                                 net=dataclasses.replace(sc.net, link_signal=N.signals_by_rank(sc.net, 60, 30)))
     if name in ("plan1", "yield1"):
         sc = dataclasses.replace(sc, name="config1-turn-lanes",
                                  net=dataclasses.replace(sc.net, turn_lanes=N.turn_lanes_by_rank(sc.net)))
@@ -94,6 +97,8 @@ def _workload(name):
         "plan1": "config 1 (20,024 links, 300,000 trips) with turn lanes: plan-following lane changes",
         "yield1": "config 1 (20,024 links, 300,000 trips) with turn lanes and gap acceptance (narrower "
                   "approaches yield, 8-cell gap)",
+        "signal1": "config 1 (20,024 links, 300,000 trips) with a 30 s / 30 s light at every approach of "
+                   "every node with two or more approaches",
     }[name]
     return sc, desc
 
@@ -344,8 +349,8 @@ def run_ours(args, rank, world, local_rank):
         dem = sc.demand
         h2d = (net.link_from.nbytes + net.link_to.nbytes + net.link_cells.nbytes + net.link_lanes.nbytes
                + net.link_ring.nbytes + dem.depart_step.nbytes + dem.route_offsets.nbytes + dem.route_links.nbytes
-               + sum(a.nbytes for a in (getattr(net, "turn_lanes", None), getattr(net, "link_yield", None))
-                     if a is not None))
+               + sum(a.nbytes for a in (getattr(net, "turn_lanes", None), getattr(net, "link_yield", None),
+                                        getattr(net, "link_signal", None)) if a is not None))
         d2h = 7 * 8
         times = []
         for k in range(args.e2e_jobs + 1):
@@ -633,7 +638,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty", "relax", "plan1",
-                                                  "yield1"])
+                                                  "yield1", "signal1"])
     ap.add_argument("--scenarios", type=int, default=256, help="config3: batch members")
     ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
     ap.add_argument("--seq-sample", type=int, default=256, help="config3: members run one by one for comparison")

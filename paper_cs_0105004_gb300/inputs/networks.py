@@ -438,6 +438,29 @@ def turn_lanes_by_rank(net: Network) -> np.ndarray:
     return out
 
 
+def signals_by_rank(net: Network, cycle: int, green: int) -> np.ndarray:
+    """A fixed-time light at the end of every non-ring link of any network:
+    the approaches of a node, in ascending link id, alternate between the
+    first `green` steps of each cycle (even rank) and the `green` steps that
+    follow (odd rank; green <= cycle / 2), so approaches of different rank
+    are never green together.  A node with one approach gets no light."""
+    ring = np.asarray(net.link_ring, bool)
+    to = np.asarray(net.link_to, np.int64)
+    sig = np.zeros((net.n_links, 3), np.uint32)
+    idx = np.nonzero(~ring)[0]
+    order = idx[np.lexsort((idx, to[idx]))]          # by end node, then link id
+    nodes = to[order]
+    start = np.r_[0, np.nonzero(np.diff(nodes))[0] + 1]
+    count = np.diff(np.r_[start, nodes.size])
+    rank = np.arange(nodes.size) - np.repeat(start, count)
+    many = np.repeat(count, count) > 1
+    lit = order[many]
+    sig[lit, 0] = cycle
+    sig[lit, 1] = green
+    sig[lit, 2] = np.where(rank[many] % 2 == 0, 0, cycle - green)  # (t + offset) mod cycle < green
+    return sig
+
+
 def grid_yield(net: Network, gap: int) -> np.ndarray:
     """Unprotected turns on a grid_network: links running north-south yield
     (acceptance gap `gap` cells) to links running east-west."""

@@ -284,6 +284,15 @@ def test_signalled_grids_match_oracle(case, mode):
     sim.close()
 
 
+def test_planar_network_with_signals_matches_oracle():
+    # a light at every approach of every node with two or more approaches
+    # (signals_by_rank), on a 900-node planar network
+    import dataclasses
+    sc = N._planar_config("planar-small", 900, 1060, 20000, 5, steps=900)
+    sc = dataclasses.replace(sc, net=dataclasses.replace(sc.net, link_signal=N.signals_by_rank(sc.net, 40, 20)))
+    run_parity(sc, 900, chunk=300, state_every=300)
+
+
 def test_car_waits_at_a_red_light_on_gpu():
     sc = make_scenario([(0, 1, 20, 1), (1, 2, 20, 1)], 3, [[0, 1]], [0], p=0, steps=30)
     sc.net.link_signal = np.array([[40, 20, 20], [0, 0, 0]], np.uint32)

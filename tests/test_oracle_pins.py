@@ -589,3 +589,19 @@ def test_gap_acceptance_matches_naive_restatement(case):
         assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
         assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
     assert int(so["arrived"]) > 0
+
+
+def test_signals_by_rank_alternate_at_every_node():
+    net = N.planar_network(300, 400, 4)
+    sig = N.signals_by_rank(net, 60, 30)
+    for n in range(net.n_nodes):
+        inc = sorted(np.nonzero(net.link_to == n)[0].tolist())
+        if len(inc) < 2:
+            assert all(sig[l, 0] == 0 for l in inc)
+            continue
+        for r, l in enumerate(inc):
+            assert sig[l].tolist() == [60, 30, 0 if r % 2 == 0 else 30]
+        # at every step the green approaches all have the same rank parity
+        for t in range(60):
+            green = [r % 2 for r, l in enumerate(inc) if (t + sig[l, 2]) % 60 < 30]
+            assert len(set(green)) == 1

@@ -253,6 +253,17 @@ size_t ts_footprint_bytes(const ts_network_desc *desc, uint32_t n_vehicles, uint
 /* Thread-local description of the last error. */
 const char *ts_last_error(void);
 
+/* The random draw of the velocity update (Sec. 3 rule (iii)) as the step
+ * kernels make it: host_out[i] = word 0 of Philox-4x32-10 (Salmon, Moraes,
+ * Dror, Shaw, SC'11) with counter (host_step[i], host_id[i], 0, 0) and key
+ * (seed & 0xffffffff, seed >> 32); vehicle host_id[i] slows down at step
+ * host_step[i] iff that word is below p_threshold.  For reproducing or
+ * auditing draws.  Host arrays of n entries; runs on the current device and
+ * returns when host_out is written.  TS_ERR_INVALID for a null array,
+ * TS_ERR_OOM, TS_ERR_CUDA. */
+ts_status ts_philox_words(uint32_t n, const uint32_t *host_step, const uint32_t *host_id, uint64_t seed,
+                          uint32_t *host_out);
+
 /* Frees the context and its device memory (waits for its stream). */
 void ts_destroy(ts_ctx *ctx);
 

@@ -465,6 +465,29 @@ const char *ts_last_error(void) { return g_err.c_str(); }
 
 uint32_t ts_launches_per_step(void) { return 1u; }
 
+ts_status ts_philox_words(uint32_t n, const uint32_t *host_step, const uint32_t *host_id, uint64_t seed,
+                          uint32_t *host_out) {
+    if (n == 0) return TS_OK;
+    if (!host_step || !host_id || !host_out) return fail(TS_ERR_INVALID, "null array");
+    uint32_t *d = nullptr;
+    const size_t bytes = 4ull * n;
+    if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TS_ERR_OOM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(d, host_step, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + n, host_id, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_philox_words(d, d + n, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32), n, d + 2ull * n,
+                            nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, d + 2ull * n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_philox_words");
+    return TS_OK;
+}
+
 size_t ts_footprint_bytes(const ts_network_desc *d, uint32_t n_vehicles, uint64_t route_len) {
     if (!d) return 0;
     uint64_t words = 0, slots = 0;

@@ -166,6 +166,10 @@ void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cu
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
 // adds the entry steps of vehicles on the network to out (a copy of link_time)
 void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s);
+// out[i] = word 0 of Philox-4x32-10, counter (c0[i], c1[i], 0, 0), key
+// (k0, k1): the slowdown draw of the link kernel (device arrays of n)
+void launch_philox_words(const uint32_t *c0, const uint32_t *c1, uint32_t k0, uint32_t k1, uint32_t n,
+                         uint32_t *out, cudaStream_t s);
 int max_link_blocks(uint32_t tile_cap, bool turns);
 int max_node_blocks(bool turns);
 // Sets the thread-local message returned by ts_last_error.

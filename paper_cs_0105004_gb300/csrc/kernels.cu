@@ -1241,6 +1241,21 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
 
 __global__ void set_target_kernel(Ctrl *ctrl, unsigned long long target) { ctrl->target = target; }
 
+// Word 0 of Philox-4x32-10 for counters (c0[i], c1[i], 0, 0), as the link
+// kernel draws it (ts_philox_words).
+__global__ void philox_words_kernel(const uint32_t *__restrict__ c0, const uint32_t *__restrict__ c1, uint32_t k0,
+                                    uint32_t k1, uint32_t n, uint32_t *__restrict__ out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = philox_word0(c0[i], c1[i], k0, k1);
+}
+
+void launch_philox_words(const uint32_t *c0, const uint32_t *c1, uint32_t k0, uint32_t k1, uint32_t n,
+                         uint32_t *out, cudaStream_t s) {
+    const uint32_t blocks = (n + 255u) / 256u;
+    const int grid = blocks == 0u ? 1 : (blocks > 4096u ? 4096 : (int)blocks);
+    philox_words_kernel<<<grid, 256, 0, s>>>(c0, c1, k0, k1, n, out);
+}
+
 template <typename... KArgs, typename... Args>
 static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};

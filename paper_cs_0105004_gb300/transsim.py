@@ -111,6 +111,7 @@ _API = {
     "ts_read_link_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32]),
     "ts_batch_set_step_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_launches_per_step": (ctypes.c_uint32, []),
+    "ts_philox_words": (ctypes.c_int, [ctypes.c_uint32, u32p, u32p, ctypes.c_uint64, u32p]),
     "ts_set_load_balance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
     "ts_ring_step_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Params), ctypes.c_uint64,
                                             ctypes.c_uint32] + [ctypes.c_void_p] * 8),
@@ -137,6 +138,17 @@ def lib():
 
 def exported_symbols():
     return list(_API)
+
+
+def philox_words(step, vehicle_id, seed: int) -> np.ndarray:
+    """Word 0 of Philox-4x32-10 for counters (step[i], vehicle_id[i], 0, 0)
+    and the seed's key, computed by the library's step-kernel draw."""
+    c0 = np.ascontiguousarray(step, np.uint32)
+    c1 = np.ascontiguousarray(vehicle_id, np.uint32)
+    out = np.zeros(c0.size, np.uint32)
+    _check(lib().ts_philox_words(c0.size, _p(c0, ctypes.c_uint32), _p(c1, ctypes.c_uint32), int(seed),
+                                 _p(out, ctypes.c_uint32)))
+    return out
 
 
 def _check(rc):

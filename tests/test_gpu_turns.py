@@ -238,3 +238,24 @@ def test_malformed_yield_table_is_rejected():
     sc.net.link_yield = np.array([32, 0, 0], np.uint8)
     with pytest.raises(T.TsError, match="INVALID"):
         T.Simulation(sc)
+
+
+@pytest.mark.parametrize("rules", [None, "all"])
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_every_route_of_a_2x2_grid_matches_oracle(rules, mode):
+    # one traveller per simple path of a 2x2 grid (24 paths), three rounds,
+    # step by step; "all": turn lanes, yield approaches and signals
+    from test_oracle_pins import _simple_paths
+    net = N.grid_network(2, 2, 12)
+    routes = _simple_paths(net) * 3
+    depart = [3 * (i // 24) + i % 5 for i in range(len(routes))]
+    off = np.zeros(len(routes) + 1, np.uint32)
+    off[1:] = np.cumsum([len(r) for r in routes])
+    dem = N.Demand(np.array(depart, np.uint32), off, np.array([x for r in routes for x in r], np.uint32))
+    if rules == "all":
+        net.turn_lanes = N.turn_lanes_by_rank(net)
+        net.link_yield = N.grid_yield(net, 4)
+        net.link_signal = N.grid_signals(net, 2, 12, 6)
+    sc = N.Scenario("grid2x2-all-routes", net, dem, steps=160, seed=5, p_threshold=N.P_THRESHOLD_0_2)
+    o = run_parity(sc, 160, chunk=1, state_every=1, mode=mode)
+    assert int(o["arrived"][-1]) == len(routes)

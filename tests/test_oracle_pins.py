@@ -605,3 +605,53 @@ def test_signals_by_rank_alternate_at_every_node():
         for t in range(60):
             green = [r % 2 for r, l in enumerate(inc) if (t + sig[l, 2]) % 60 < 30]
             assert len(set(green)) == 1
+
+
+def _simple_paths(net):
+    """Every simple path (no node twice) of the network, as link lists."""
+    out_links = {}
+    for l in range(net.n_links):
+        out_links.setdefault(int(net.link_from[l]), []).append(l)
+    paths = []
+
+    def grow(path, seen):
+        paths.append(list(path))
+        for l in out_links.get(int(net.link_to[path[-1]]), []):
+            if int(net.link_to[l]) not in seen:
+                grow(path + [l], seen | {int(net.link_to[l])})
+
+    for l in range(net.n_links):
+        grow([l], {int(net.link_from[l]), int(net.link_to[l])})
+    return paths
+
+
+@pytest.mark.parametrize("rules", [None, "turns", "yield", "all"])
+def test_every_route_of_a_2x2_grid_matches_naive_restatement(rules):
+    # 4 nodes, 8 links of 2 lanes x 12 cells: one traveller per simple path
+    # (all 24 of them, 1 to 3 links), three rounds of departures
+    net = N.grid_network(2, 2, 12)
+    paths = _simple_paths(net)
+    assert len(paths) == 24
+    routes = paths * 3
+    depart = [3 * (i // len(paths)) + i % 5 for i in range(len(routes))]
+    off = np.zeros(len(routes) + 1, np.uint32)
+    off[1:] = np.cumsum([len(r) for r in routes])
+    dem = N.Demand(np.array(depart, np.uint32), off, np.array([x for r in routes for x in r], np.uint32))
+    if rules in ("turns", "all"):
+        net.turn_lanes = N.turn_lanes_by_rank(net)
+    if rules in ("yield", "all"):
+        net.link_yield = N.grid_yield(net, 4)
+    if rules == "all":
+        net.link_signal = N.grid_signals(net, 2, 12, 6)
+    sc = N.Scenario("grid2x2-all-routes", net, dem, steps=160, seed=5, p_threshold=N.P_THRESHOLD_0_2)
+    o, b = oracle.Oracle(sc), Brute(sc)
+    for t in range(160):
+        so = o.step(1)[0]
+        sb = b.step()
+        for k, v in sb.items():
+            assert int(so[k]) == v, (t, k)
+        st = o.get_state()
+        ci, cv, bi, bv = b.state(sc.net)
+        assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
+        assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
+    assert int(so["arrived"]) == len(routes)

@@ -24,6 +24,10 @@
  * the lane with its current index (capped to the next link's lanes) first,
  * then the others ascending; departures enter with velocity 0 in the first
  * free lane, in (departure step, id) order.
+ * Options of the network (ts_network_desc): fixed-time signals at link
+ * ends, turn lanes (plan-following lane changes) and yield approaches (gap
+ * acceptance at unprotected turns), the intersection rules of Sec. 3; a
+ * network without them runs exactly the rules above.
  * Randomness: vehicle `id` slows down at step t iff word 0 of
  * Philox-4x32-10 with counter (t, id, 0, 0) and key (seed & 0xffffffff,
  * seed >> 32) is below p_threshold, so results do not depend on the

@@ -655,3 +655,35 @@ def test_every_route_of_a_2x2_grid_matches_naive_restatement(rules):
         assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
         assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)
     assert int(so["arrived"]) == len(routes)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_intersection_rules_match_naive_restatement(seed):
+    # arbitrary (not rank-structured) turn masks, random acceptance gaps
+    # (0..31), random signal cycles and offsets, lanes 1..4 per edge
+    rng = np.random.default_rng(100 + seed)
+    sc = N.small_grid_scenario(3, 4, int(rng.integers(8, 25)), int(rng.integers(80, 260)), 60, 220,
+                               gen_seed=seed + 50, seed=seed + 60, vmax=int(rng.integers(1, 9)), lane_seed=seed + 70)
+    net = sc.net
+    off = N.turn_table_offsets(net)
+    masks = np.zeros(int(off[-1]), np.uint8)
+    for l in range(net.n_links):
+        full = (1 << int(net.link_lanes[l])) - 1
+        masks[off[l]:off[l + 1]] = rng.integers(1, full + 1, int(off[l + 1] - off[l]))
+    net.turn_lanes = masks
+    net.link_yield = np.where(rng.random(net.n_links) < 0.4, rng.integers(1, 32, net.n_links), 0).astype(np.uint8)
+    cycle = rng.integers(0, 40, net.n_links)
+    cycle[cycle < 4] = 0
+    green = np.where(cycle > 0, rng.integers(1, np.maximum(cycle, 2)), 0)
+    offset = np.where(cycle > 0, rng.integers(0, np.maximum(cycle, 1)), 0)
+    net.link_signal = np.stack([cycle, green, offset], 1).astype(np.uint32)
+    o, b = oracle.Oracle(sc), Brute(sc)
+    for t in range(220):
+        so = o.step(1)[0]
+        sb = b.step()
+        for k, v in sb.items():
+            assert int(so[k]) == v, (t, k)
+        st = o.get_state()
+        ci, cv, bi, bv = b.state(sc.net)
+        assert np.array_equal(st["cell_id"], ci) and np.array_equal(st["cell_v"], cv)
+        assert np.array_equal(st["buf_id"], bi) and np.array_equal(st["buf_v"], bv)

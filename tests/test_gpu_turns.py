@@ -259,3 +259,13 @@ def test_every_route_of_a_2x2_grid_matches_oracle(rules, mode):
     sc = N.Scenario("grid2x2-all-routes", net, dem, steps=160, seed=5, p_threshold=N.P_THRESHOLD_0_2)
     o = run_parity(sc, 160, chunk=1, state_every=1, mode=mode)
     assert int(o["arrived"][-1]) == len(routes)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])
+def test_random_intersection_rules_match_oracle(seed, mode):
+    # arbitrary turn masks (also non-adjacent lanes), acceptance gaps and
+    # signal phases on a 3x3 grid (step by step) and a 6x6 grid
+    from test_oracle_pins import random_rules_scenario
+    run_parity(random_rules_scenario(seed), 220, chunk=1, state_every=1, mode=mode)
+    run_parity(random_rules_scenario(seed, side=6, steps=600), 600, chunk=200, state_every=200, mode=mode)

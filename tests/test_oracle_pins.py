@@ -657,13 +657,14 @@ def test_every_route_of_a_2x2_grid_matches_naive_restatement(rules):
     assert int(so["arrived"]) == len(routes)
 
 
-@pytest.mark.parametrize("seed", range(6))
-def test_random_intersection_rules_match_naive_restatement(seed):
-    # arbitrary (not rank-structured) turn masks, random acceptance gaps
-    # (0..31), random signal cycles and offsets, lanes 1..4 per edge
+def random_rules_scenario(seed, side=3, steps=220):
+    """A grid with arbitrary (not rank-structured) turn masks, random
+    acceptance gaps (0..31), random signal cycles and offsets and lanes 1..4
+    per edge, all drawn from `seed`."""
     rng = np.random.default_rng(100 + seed)
-    sc = N.small_grid_scenario(3, 4, int(rng.integers(8, 25)), int(rng.integers(80, 260)), 60, 220,
-                               gen_seed=seed + 50, seed=seed + 60, vmax=int(rng.integers(1, 9)), lane_seed=seed + 70)
+    sc = N.small_grid_scenario(side, 4, int(rng.integers(8, 25)), int(rng.integers(80, 260)) * (side - 2) ** 2,
+                               60, steps, gen_seed=seed + 50, seed=seed + 60, vmax=int(rng.integers(1, 9)),
+                               lane_seed=seed + 70)
     net = sc.net
     off = N.turn_table_offsets(net)
     masks = np.zeros(int(off[-1]), np.uint8)
@@ -677,6 +678,12 @@ def test_random_intersection_rules_match_naive_restatement(seed):
     green = np.where(cycle > 0, rng.integers(1, np.maximum(cycle, 2)), 0)
     offset = np.where(cycle > 0, rng.integers(0, np.maximum(cycle, 1)), 0)
     net.link_signal = np.stack([cycle, green, offset], 1).astype(np.uint32)
+    return sc
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_intersection_rules_match_naive_restatement(seed):
+    sc = random_rules_scenario(seed)
     o, b = oracle.Oracle(sc), Brute(sc)
     for t in range(220):
         so = o.step(1)[0]

@@ -12,7 +12,10 @@
 //                order (incoming link id, then lane), move to cell 0 of m;
 //                then departures from parking enter m.
 // (Fused steps fold the node transfer of step t-1 into the link kernel of
-// step t and run the node kernel once per chunk.)  Once per captured chunk
+// step t and run the node kernel once per chunk.)  turn_link_kernel and
+// turn_node_kernel are the same bodies with the intersection rules a network
+// may add (turn lanes for plan-following lane changes, yield approaches for
+// gap acceptance); signals need no other instance.  Once per captured chunk
 // of steps, advance_kernel closes the chunk's statistics and moves the step
 // counter; inside a chunk the step index of a launch is the chunk base plus
 // the launch's position.

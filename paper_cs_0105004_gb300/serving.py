@@ -37,16 +37,18 @@ class Job:
     finished: float = 0.0
     vehicle_updates: int = 0
     last_state_hash: int = 0
+    rejected: bool = False    # its footprint alone exceeds the memory budget
 
 
 @dataclass
 class ServeReport:
-    jobs: List[Job]
+    jobs: List[Job]           # served jobs, in completion order
     wall_s: float
     device_busy_s: float
     peak_active: int
     peak_bytes: int
     mean_active: float
+    rejected: List[Job] = field(default_factory=list)  # jobs larger than the whole budget
 
     def latencies(self):
         return np.array([j.finished - j.arrival for j in self.jobs])
@@ -58,7 +60,8 @@ class ServeReport:
                 "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
                 "vehicle_updates": int(upd), "vehicle_updates_per_s": upd / self.wall_s,
                 "wall_s": self.wall_s, "peak_active_jobs": self.peak_active,
-                "mean_active_jobs": self.mean_active, "peak_job_bytes": self.peak_bytes}
+                "mean_active_jobs": self.mean_active, "peak_job_bytes": self.peak_bytes,
+                "rejected_jobs": len(self.rejected)}
 
 
 def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int) -> np.ndarray:
@@ -97,6 +100,7 @@ class Server:
         active = {}     # jid -> (job, sim)
         used = 0
         done: List[Job] = []
+        rejected: List[Job] = []
         busy = 0.0
         peak_active = peak_bytes = 0
         active_samples = []
@@ -110,6 +114,13 @@ class Server:
                 j, f = building.pop(jid)
                 sim = f.result()
                 j.footprint = T.footprint_bytes(sim.scenario)
+                if j.footprint > self.budget:
+                    # it would wait for memory forever: refuse it
+                    sim.close()
+                    j.rejected = True
+                    j.finished = now()
+                    rejected.append(j)
+                    continue
                 ready.append((j, sim))
             adds = []
             while ready and used + ready[0][0].footprint <= self.budget and len(active) + len(adds) < self.capacity:
@@ -147,7 +158,7 @@ class Server:
                     done.append(j)
         wall = now()
         return ServeReport(done, wall, busy, peak_active, peak_bytes,
-                           float(np.mean(active_samples)) if active_samples else 0.0)
+                           float(np.mean(active_samples)) if active_samples else 0.0, rejected)
 
     def close(self):
         self.pool.shutdown()

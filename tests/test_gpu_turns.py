@@ -269,3 +269,17 @@ def test_random_intersection_rules_match_oracle(seed, mode):
     from test_oracle_pins import random_rules_scenario
     run_parity(random_rules_scenario(seed), 220, chunk=1, state_every=1, mode=mode)
     run_parity(random_rules_scenario(seed, side=6, steps=600), 600, chunk=200, state_every=200, mode=mode)
+
+
+def test_load_balancing_with_intersection_rules():
+    # re-tiling from the occupancy every 64 steps with a small vehicle budget
+    # (many partial tiles) under turn lanes, yield approaches and signals
+    sc = N.small_grid_scenario(5, 4, 70, 3500, 300, 1200, gen_seed=41, seed=42, turns=True, lane_seed=43,
+                               yield_gap=9, signal=(30, 15))
+    sim = T.Simulation(sc)
+    sim.set_load_balance(64, 128)
+    orc = oracle.Oracle(sc)
+    sim.step(1200)
+    _cmp_stats(sim.stats_range(0, 1200), orc.step(1200), "load balanced with rules")
+    _cmp_state(sim.read_state(), orc.get_state(), "load balanced with rules, final")
+    sim.close()

@@ -36,32 +36,37 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        P = ctypes.POINTER
-        u32p, u64p, i32p, i8p, u8p = P(ctypes.c_uint32), P(ctypes.c_uint64), P(ctypes.c_int32), P(ctypes.c_int8), P(ctypes.c_uint8)
-        L.oracle_create.restype = ctypes.c_void_p
-        L.oracle_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, u32p, u32p, u8p, u32p, u8p, u8p,
-                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
-        L.oracle_destroy.argtypes = [ctypes.c_void_p]
-        L.oracle_load_vehicles.restype = ctypes.c_int
-        L.oracle_load_vehicles.argtypes = [ctypes.c_void_p, ctypes.c_uint32, u32p, u32p, u32p]
-        L.oracle_step.restype = ctypes.c_int
-        L.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
-        L.oracle_n_cells.restype = ctypes.c_uint64
-        L.oracle_n_cells.argtypes = [ctypes.c_void_p]
-        L.oracle_n_lanes.restype = ctypes.c_uint32
-        L.oracle_n_lanes.argtypes = [ctypes.c_void_p]
-        L.oracle_get_state.argtypes = [ctypes.c_void_p, i32p, i8p, i32p, i8p, u32p, u32p, u64p]
-        L.oracle_set_state.restype = ctypes.c_int
-        L.oracle_set_state.argtypes = [ctypes.c_void_p, i32p, i8p, i32p, i8p, u32p, u32p, u64p]
-        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
-        L.oracle_splitmix64.restype = ctypes.c_uint64
-        L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
-        L.oracle_vehicle_term.restype = ctypes.c_uint64
-        L.oracle_vehicle_term.argtypes = [ctypes.c_uint32] * 5
-        L.oracle_link_times.argtypes = [ctypes.c_void_p, u64p, u64p]
-        _lib = L
+        _lib = bind(build())
     return _lib
+
+
+def bind(path: str):
+    """Loads a build of oracle.c from `path` and declares its functions."""
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    u32p, u64p, i32p, i8p, u8p = P(ctypes.c_uint32), P(ctypes.c_uint64), P(ctypes.c_int32), P(ctypes.c_int8), P(ctypes.c_uint8)
+    L.oracle_create.restype = ctypes.c_void_p
+    L.oracle_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, u32p, u32p, u8p, u32p, u8p, u8p,
+                                ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+    L.oracle_destroy.argtypes = [ctypes.c_void_p]
+    L.oracle_load_vehicles.restype = ctypes.c_int
+    L.oracle_load_vehicles.argtypes = [ctypes.c_void_p, ctypes.c_uint32, u32p, u32p, u32p]
+    L.oracle_step.restype = ctypes.c_int
+    L.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+    L.oracle_n_cells.restype = ctypes.c_uint64
+    L.oracle_n_cells.argtypes = [ctypes.c_void_p]
+    L.oracle_n_lanes.restype = ctypes.c_uint32
+    L.oracle_n_lanes.argtypes = [ctypes.c_void_p]
+    L.oracle_get_state.argtypes = [ctypes.c_void_p, i32p, i8p, i32p, i8p, u32p, u32p, u64p]
+    L.oracle_set_state.restype = ctypes.c_int
+    L.oracle_set_state.argtypes = [ctypes.c_void_p, i32p, i8p, i32p, i8p, u32p, u32p, u64p]
+    L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.oracle_splitmix64.restype = ctypes.c_uint64
+    L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
+    L.oracle_vehicle_term.restype = ctypes.c_uint64
+    L.oracle_vehicle_term.argtypes = [ctypes.c_uint32] * 5
+    L.oracle_link_times.argtypes = [ctypes.c_void_p, u64p, u64p]
+    return L
 
 
 def _p(a, t):

@@ -94,3 +94,21 @@ def test_routes_are_shortest_with_ties_to_the_smaller_predecessor(kind):
             u, v = int(net.link_from[x]), int(net.link_to[x])
             tight = [p for p in preds[v] if dist[p] + w[(p, v)] == dist[v]]
             assert u == min(tight)
+
+
+def test_config3_members():
+    # side U{10..60}, lanes U{1,2,3} and cells U{30..120} per edge (both
+    # directions alike), trips = round(d * lane-cells) with d in [0.1, 0.4],
+    # departures over the first 600 s
+    for i in range(6):
+        sc = N.config3_scenario(i)
+        net = sc.net
+        side = int(round(np.sqrt(net.n_nodes)))
+        assert side * side == net.n_nodes and 10 <= side <= 60
+        assert net.n_links == 4 * side * (side - 1)
+        assert np.array_equal(net.link_cells[0::2], net.link_cells[1::2])
+        assert net.link_cells.min() >= 30 and net.link_cells.max() <= 120
+        assert set(np.unique(net.link_lanes).tolist()) <= {1, 2, 3}
+        d = sc.demand.n / net.n_lane_cells
+        assert 0.1 - 1e-6 <= d <= 0.4 + 1e-6
+        assert sc.demand.depart_step.max() < 600 and sc.seed == 1000 + i

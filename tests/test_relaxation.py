@@ -81,3 +81,18 @@ def test_relaxation_with_the_oracle_moves_travellers_off_congested_links():
     assert its[1].run.vehicle_updates < its[0].run.vehicle_updates
     assert its[1].run.mean_link_time <= its[0].run.mean_link_time
     assert not np.array_equal(last.demand.route_links, sc.demand.route_links)
+
+
+def test_relaxation_keeps_the_intersection_rules():
+    # re-planning changes routes only; the network's turn lanes, yield
+    # approaches and signals stay, and every iteration still runs (oracle)
+    sc = N.small_grid_scenario(4, 3, 20, n_trips=500, window=120, steps=900, gen_seed=8, seed=3, turns=True,
+                               lane_seed=4, yield_gap=6, signal=(30, 15))
+    last, its = R.relax(sc, 3, fraction=0.1, seed=2, run=oracle_run)
+    assert [it.replanned for it in its] == [50, 50, 0]
+    assert last.net is sc.net
+    assert all(it.run.arrived > 0 for it in its)
+    assert not np.array_equal(last.demand.route_links, sc.demand.route_links)
+    # the last plans, run again, give the last iteration's result
+    again = oracle_run(last)
+    assert again.state_hash == its[-1].run.state_hash and again.arrived == its[-1].run.arrived

@@ -138,22 +138,26 @@ typedef struct {
  * reached but not yet on a link; arrived: cumulative arrivals; lane_changes,
  * transfers (buffer -> next link), inserted (from parking): counts within
  * this step; sum_v: sum of velocities of vehicles in cells; vehicle_updates:
- * vehicles that went through the velocity update this step; state_hash: sum
+ * vehicles that went through the velocity update this step; moving:
+ * vehicles in cells with v > 0 after the step (one standing in a jam has
+ * v = 0, so moving / active is the share of traffic that flows);
+ * state_hash: sum
  * modulo 2^64 over vehicles on links of splitmix64(A ^ splitmix64(B)),
  * A = id << 32 | link, B = cell << 16 | lane << 8 | v, with cell = link
  * length for a buffered vehicle (splitmix64 as published by Steele, Lea and
  * Flood, 2014). */
 typedef struct {
     uint64_t step, active, buffered, waiting, arrived, lane_changes, transfers, inserted, sum_v,
-        vehicle_updates, state_hash;
+        vehicle_updates, state_hash, moving;
 } ts_stats;
 
 /* Totals since the last ts_load_vehicles / ts_reset / ts_write_state:
  * steps run, vehicle updates, lane changes and transfers summed over those
  * steps; inserted and arrived are the cumulative counts of the state;
- * last_state_hash is the digest after the last step. */
+ * last_state_hash is the digest after the last step; moving and active are
+ * the per-step counts of ts_stats summed over those steps. */
 typedef struct {
-    uint64_t steps, vehicle_updates, lane_changes, transfers, inserted, arrived, last_state_hash;
+    uint64_t steps, vehicle_updates, lane_changes, transfers, inserted, arrived, last_state_hash, moving, active;
 } ts_totals;
 
 /* Optional device-memory provider (for example a framework's caching

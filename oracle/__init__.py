@@ -18,7 +18,7 @@ SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 STATS_FIELDS = ("step", "active", "buffered", "waiting", "arrived", "lane_changes", "transfers",
-                "inserted", "sum_v", "vehicle_updates", "state_hash")
+                "inserted", "sum_v", "vehicle_updates", "state_hash", "moving")
 STATS_DTYPE = np.dtype([(f, np.uint64) for f in STATS_FIELDS])
 
 

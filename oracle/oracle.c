@@ -83,7 +83,7 @@
 
 typedef struct {
     uint64_t step, active, buffered, waiting, arrived, lane_changes, transfers, inserted,
-        sum_v, vehicle_updates, state_hash;
+        sum_v, vehicle_updates, state_hash, moving;
 } oracle_stats;
 
 typedef struct oracle {
@@ -619,6 +619,7 @@ static void step_once(oracle *o, oracle_stats *st) {
                 if (id < 0) continue;
                 st->active++;
                 st->sum_v += (uint64_t)o->vel[id];
+                if (o->vel[id] > 0) st->moving++;   /* in a cell and not standing */
                 st->state_hash += vehicle_term((uint32_t)id, l, k, x, (uint32_t)o->vel[id]);
             }
             int32_t b = o->buf[o->lane_base[l] + k];

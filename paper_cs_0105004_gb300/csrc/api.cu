@@ -1180,6 +1180,7 @@ ts_status ts_read_stats_range(ts_ctx *c, uint64_t first, uint32_t n, ts_stats *o
         o.inserted = sum(t, kInserted);
         o.sum_v = sv;
         o.vehicle_updates = sum(t, kUpdates);
+        o.moving = sum(t, kMoving);
         o.state_hash = hs;
         o.arrived = arr;
         o.waiting = departed_upto(c, t) - ins;
@@ -1217,6 +1218,8 @@ ts_status ts_read_totals(ts_ctx *c, ts_totals *out, uint32_t timeout_ms) {
     out->inserted = h.inserted;
     out->arrived = h.arrived;
     out->last_state_hash = h.hash;
+    out->moving = h.tot_moving;
+    out->active = h.tot_active;
     return TS_OK;
 }
 

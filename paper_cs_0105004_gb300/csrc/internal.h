@@ -77,6 +77,7 @@ struct Ctrl {
     unsigned long long sum_v;     // sum of velocities of vehicles in cells
     unsigned long long hash;      // state digest
     unsigned long long tot_updates, tot_lane_changes, tot_transfers;  // since the last reset
+    unsigned long long tot_moving, tot_active;  // per-step counts summed since the last reset
     unsigned long long steps_run;
     unsigned int error;  // device-check flags (bitwise or)
     unsigned int pad;
@@ -93,10 +94,13 @@ constexpr unsigned kErrGeometry = 8u;   // a vehicle left the tile geometry
 // step, and the changes (modulo 2^64) of the state's running values.
 struct StatRec {
     unsigned long long vehicle_updates, lane_changes, transfers, inserted, arrived, d_active, d_buffered, d_sum_v,
-        d_hash;
-    unsigned long long pad[7];
+        d_hash, moving;
+    unsigned long long pad[6];
 };
-enum StatField { kUpdates = 0, kLaneChanges, kTransfers, kInserted, kArrived, kDActive, kDBuffered, kDSumV, kDHash };
+enum StatField {
+    kUpdates = 0, kLaneChanges, kTransfers, kInserted, kArrived, kDActive, kDBuffered, kDSumV, kDHash, kMoving,
+    kStatFields
+};
 static_assert(sizeof(StatRec) == 128, "StatRec is one line");
 
 struct ScenDev {

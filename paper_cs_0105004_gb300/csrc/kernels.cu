@@ -293,8 +293,8 @@ struct LinkSmem {
     uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
     uint32_t nlist[2];                // vehicles in the lane-change list and in the velocity list
     uint16_t code[kList];             // (local word << 5) | bit
-    unsigned long long red[kLinkThreads / 32][7];  // per warp (at most kLinkThreads threads)
-    unsigned long long xacc[6];       // node-transfer counts of the current previous-step record
+    unsigned long long red[kLinkThreads / 32][8];  // per warp (at most kLinkThreads threads)
+    unsigned long long xacc[7];       // node-transfer counts of the current previous-step record
     int ncols, nwords, ncore_words, nlinks;
 };
 
@@ -372,7 +372,7 @@ __device__ __forceinline__ uint32_t xfer_into_link(SM &S, const ScenDev &D, int 
                                                    uint32_t l) {
     const uint4 nd = D.nd_info[l];
     uint32_t placed = 0u, moving = 0u;
-    unsigned long long acc2[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long acc2[7] = {0, 0, 0, 0, 0, 0, 0};
     int8_t *vel = D.vel[0];  // cell 0 was empty: its payload goes
     uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
     uint32_t fr = resolve_transfers<TURNS>(sc, nd, l, free_cell0(oc, nd), D, oc, [&](uint32_t, const uint4 &x,
@@ -392,6 +392,7 @@ __device__ __forceinline__ uint32_t xfer_into_link(SM &S, const ScenDev &D, int 
         acc2[3] -= 1;
         acc2[4] += v;
         acc2[5] += vehicle_term(id, l, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+        acc2[6] += v ? 1u : 0u;
     });
     run_departures(D, nd, l, t - 1u, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
         placed |= 1u << qn;
@@ -406,7 +407,7 @@ __device__ __forceinline__ uint32_t xfer_into_link(SM &S, const ScenDev &D, int 
     });
     const uint32_t n_placed = (uint32_t)__popc(placed);  // they are updated in step t
     if (placed)
-        for (int f = 0; f < 6; ++f)
+        for (int f = 0; f < 7; ++f)
             if (acc2[f]) atomicAdd(&S.xacc[f], acc2[f]);
     for (uint32_t m = placed; m; m &= m - 1u) {
         const uint32_t qn = (uint32_t)(__ffs(m) - 1);
@@ -521,29 +522,30 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
     // statistics of the block: updates, lane changes, arrivals, and the changes
     // of active, buffered, sum of velocities and digest
-    static constexpr int kField[7] = {kUpdates, kLaneChanges, kArrived, kDActive, kDBuffered, kDSumV, kDHash};
+    static constexpr int kField[8] = {kUpdates, kLaneChanges, kArrived, kDActive, kDBuffered, kDSumV, kDHash,
+                                      kMoving};
     // counts in 32 bits (per block and step they stay far below 2^31; the
     // changes are signed), the digest change in 64
-    uint32_t acc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    uint32_t acc[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
     unsigned long long acc_hash = 0ull;
     auto flush_acc = [&](unsigned long long *rec) {
-        unsigned long long v[7] = {acc[0], acc[1], acc[2], (unsigned long long)(long long)(int)acc[3],
+        unsigned long long v[8] = {acc[0], acc[1], acc[2], (unsigned long long)(long long)(int)acc[3],
                                    (unsigned long long)(long long)(int)acc[4],
-                                   (unsigned long long)(long long)(int)acc[5], acc_hash};
-        block_flush<7, LinkLaunch<TW>::kThreads>(v, rec, kField, S.red);
+                                   (unsigned long long)(long long)(int)acc[5], acc_hash, acc[6]};
+        block_flush<8, LinkLaunch<TW>::kThreads>(v, rec, kField, S.red);
 #pragma unroll
-        for (int f = 0; f < 6; ++f) acc[f] = 0u;
+        for (int f = 0; f < 7; ++f) acc[f] = 0u;
         acc_hash = 0ull;
     };
     unsigned long long *cur_rec = nullptr;
     // with xfer set, the launch first completes the node transfers and
     // departures of the previous step (whose record gets these counts):
     // transfers, insertions and the changes of active, buffered, sum of v, digest
-    static constexpr int kField2[6] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash};
+    static constexpr int kField2[7] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash, kMoving};
     unsigned long long *cur_rec2 = nullptr;
-    if (threadIdx.x < 6) S.xacc[threadIdx.x] = 0ull;  // ordered by the first tile's barrier
+    if (threadIdx.x < 7) S.xacc[threadIdx.x] = 0ull;  // ordered by the first tile's barrier
     auto flush_xacc = [&]() {
-        if (threadIdx.x < 6 && S.xacc[threadIdx.x]) {
+        if (threadIdx.x < 7 && S.xacc[threadIdx.x]) {
             atomicAdd(cur_rec2 + kField2[threadIdx.x], S.xacc[threadIdx.x]);
             S.xacc[threadIdx.x] = 0ull;
         }
@@ -971,6 +973,7 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                     } else {
                         if (core) {
                             acc[5] += v - v0;
+                            acc[6] += v ? 1u : 0u;
                             acc_hash += vehicle_term(id, lid, (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v) - old_term;
                         }
                         if (S.ckind[dc] == 0) {
@@ -1043,7 +1046,7 @@ __global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMin
 // turn, and transfers from yield approaches wait for the gap.
 template <bool TURNS>
 __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const uint4 &nd, unsigned long long step,
-                                          unsigned long long (&acc)[6]) {
+                                          unsigned long long (&acc)[7]) {
     const int nxt = (int)((step + 1ull) & 1ull);
     uint32_t *occ = D.occ[nxt];
     uint32_t *mov = D.mov[nxt];
@@ -1073,6 +1076,7 @@ __device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const ui
         acc[3] -= 1;
         acc[4] += v;
         acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+        acc[6] += v ? 1u : 0u;
     });
     run_departures_from(D, nd, m, (uint32_t)step, hd, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
         const uint32_t w = nd.y + qn;
@@ -1104,13 +1108,13 @@ __device__ __forceinline__ bool node_step(const ScenDev &D, uint32_t pos, bool c
 // One node pass, one thread per link m (body of node_kernel and
 // turn_node_kernel).
 template <bool TURNS>
-__device__ __forceinline__ void node_pass(unsigned long long (*red)[6], const ScenDev *__restrict__ table,
+__device__ __forceinline__ void node_pass(unsigned long long (*red)[7], const ScenDev *__restrict__ table,
                                           const uint4 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
                                           uint32_t pos, uint32_t chunk_end) {
     const uint32_t n_tiles = *n_tiles_p;
     // transfers, insertions and the changes of active, buffered, sum of velocities, digest
-    static constexpr int kField[6] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash};
-    unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
+    static constexpr int kField[7] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash, kMoving};
+    unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
     pdl_trigger();
     span_mark((int)pos * 3 + 1, true);
@@ -1130,12 +1134,12 @@ __device__ __forceinline__ void node_pass(unsigned long long (*red)[6], const Sc
         }
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
+            if (cur_rec) block_flush<7, kNodeThreads>(acc, cur_rec, kField, red);
             cur_rec = rec;
         }
         if (m < td.z) node_link<TURNS>(D, m, nd, step, acc);
     }
-    if (cur_rec) block_flush<6, kNodeThreads>(acc, cur_rec, kField, red);
+    if (cur_rec) block_flush<7, kNodeThreads>(acc, cur_rec, kField, red);
     span_mark((int)pos * 3 + 1, false);
 }
 
@@ -1143,7 +1147,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__res
                                                             const uint4 *__restrict__ tiles,
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
                                                             uint32_t chunk_end) {
-    __shared__ unsigned long long red[kNodeThreads / 32][6];
+    __shared__ unsigned long long red[kNodeThreads / 32][7];
     node_pass<false>(red, table, tiles, n_tiles_p, pos, chunk_end);
 }
 
@@ -1152,7 +1156,7 @@ __global__ void __launch_bounds__(kNodeThreads) turn_node_kernel(const ScenDev *
                                                                  const uint4 *__restrict__ tiles,
                                                                  const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
                                                                  uint32_t chunk_end) {
-    __shared__ unsigned long long red[kNodeThreads / 32][6];
+    __shared__ unsigned long long red[kNodeThreads / 32][7];
     node_pass<true>(red, table, tiles, n_tiles_p, pos, chunk_end);
 }
 
@@ -1187,9 +1191,10 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
     const ScenDev &D = table[blockIdx.x];
     Ctrl *c = D.ctrl;
     if (c == nullptr) return;
-    constexpr int NF = 9;
+    constexpr int NF = kStatFields;
     __shared__ unsigned long long red[4][NF];
     __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_dact[kChunk];  // change of the vehicles in cells, per step of the chunk
     const unsigned long long base = c->base, target = c->target;
     const uint32_t g = base < target ? (uint32_t)min((unsigned long long)g_max, target - base) : 0u;
     const uint32_t nsub = D.n_sub;
@@ -1201,6 +1206,13 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
             reinterpret_cast<const unsigned long long *>(&D.stats[(size_t)(t & (kStatsRing - 1)) * nsub + r % nsub]);
 #pragma unroll
         for (int f = 0; f < NF; ++f) a[f] += R[f];
+    }
+    // per step: the change of the vehicles in cells, summed over its sub-records
+    if (threadIdx.x < g) {
+        unsigned long long s = 0;
+        for (uint32_t u = 0; u < nsub; ++u)
+            s += D.stats[(size_t)((base + threadIdx.x) & (kStatsRing - 1)) * nsub + u].d_active;
+        s_dact[threadIdx.x] = s;
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -1218,6 +1230,14 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
             c->tot_updates += sm[kUpdates];
             c->tot_lane_changes += sm[kLaneChanges];
             c->tot_transfers += sm[kTransfers];
+            c->tot_moving += sm[kMoving];
+            // vehicles in cells after each step of the chunk, summed
+            unsigned long long act = c->active, sum_act = 0;
+            for (uint32_t r = 0; r < g; ++r) {
+                act += s_dact[r];
+                sum_act += act;
+            }
+            c->tot_active += sum_act;
             c->arrived += sm[kArrived];
             c->inserted += sm[kInserted];
             c->active += sm[kDActive];

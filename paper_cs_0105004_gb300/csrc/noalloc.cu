@@ -133,6 +133,7 @@ __global__ void gather_ring_stats(const StatRec *recs, const Ctrl *ctrl, unsigne
     o.sum_v = ctrl->sum_v + sc[1][i];
     o.vehicle_updates = r->vehicle_updates;
     o.state_hash = ctrl->hash + sc[2][i];
+    o.moving = r->moving;
     out[i] = o;
 }
 

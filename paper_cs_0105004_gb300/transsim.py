@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtranssim.so")
 
 STATS_FIELDS = ("step", "active", "buffered", "waiting", "arrived", "lane_changes", "transfers", "inserted",
-                "sum_v", "vehicle_updates", "state_hash")
+                "sum_v", "vehicle_updates", "state_hash", "moving")
 STATS_DTYPE = np.dtype([(f, np.uint64) for f in STATS_FIELDS])
 
 TS_OK, TS_ERR_INVALID, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE, TS_ERR_DEVICE_CHECK = range(7)
@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in STATS_FIELDS]
 
 
-TOTALS_FIELDS = ("steps", "vehicle_updates", "lane_changes", "transfers", "inserted", "arrived", "last_state_hash")
+TOTALS_FIELDS = ("steps", "vehicle_updates", "lane_changes", "transfers", "inserted", "arrived", "last_state_hash",
+                 "moving", "active")
 
 
 class Totals(ctypes.Structure):

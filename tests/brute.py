@@ -218,7 +218,8 @@ class Brute:
         waiting = sum(1 for m, q in self.queue.items() for i in q if self.depart[i] <= t)
         return dict(step=t, active=len(new), buffered=len(self.buf), waiting=waiting, arrived=self.arrived,
                     lane_changes=lc, transfers=transfers, inserted=inserted,
-                    sum_v=sum(self.v[i] for i in new.values()), vehicle_updates=upd)
+                    sum_v=sum(self.v[i] for i in new.values()), vehicle_updates=upd,
+                    moving=sum(1 for i in new.values() if self.v[i] > 0))
 
     def state(self, net):
         import numpy as np

@@ -29,6 +29,7 @@ def checks():
         ("lane change needs room behind", P.test_lane_change_needs_room_behind),
         ("ring free flow", P.test_ring_free_flow_exact),
         ("ring jam", P.test_ring_jam_exact),
+        ("megajam dissolves", P.test_megajam_dissolves_one_car_per_step),
         ("link travel times", P.test_link_travel_times_by_hand),
         ("red light", P.test_car_waits_at_a_red_light_by_hand),
         ("wrong lane changes towards its turn", P.test_wrong_lane_changes_towards_its_turn_on_the_next_odd_step),

@@ -40,6 +40,7 @@ MUTANTS = {
     "yield check dropped": ("if (o->gap_accept[l] && !priority_gap_clear(o, o->cell, n, l)) continue;", ""),
     "travel time one step long": ("o->lt_sum[l] += t - o->t_enter[id];\n                    o->lt_cnt[l]++;\n                    o->t_enter[id] = (uint32_t)t;",
                                   "o->lt_sum[l] += t + 1 - o->t_enter[id];\n                    o->lt_cnt[l]++;\n                    o->t_enter[id] = (uint32_t)t;"),
+    "moving counts standing vehicles": ("if (o->vel[id] > 0) st->moving++;", "if (o->vel[id] >= 0) st->moving++;"),
     "digest drops the lane": ("uint64_t b = ((uint64_t)cell << 16) | ((uint64_t)lane << 8) | v;",
                               "uint64_t b = ((uint64_t)cell << 16) | v;"),
 }

@@ -1,24 +1,27 @@
 #!/usr/bin/env python
 """Throughput of the TRANSIMS cellular-automaton step on one GB300.
 
-One benchmark step is one whole simulation job: the Portland-shaped
-network (20,024 directed links, 8,500 nodes, 300,000 trips with
-shortest-path routes) simulated for 10,800 one-second time steps from the
-empty network, i.e. 3 simulated hours with lane change, velocity update,
-move and node transfer for every vehicle in every step.  Inputs are resident
-in device memory when the timed region starts; each timed job begins with a
-device-side reset to the empty network.
+One benchmark step is one whole simulation job on the scale-up network
+(seeded planar network of 200,000 directed links and 85,000 nodes, the size
+of the TIGER network of Sec. 8; 2,000,000 trips with shortest-path routes)
+simulated for 10,800 one-second time steps from the empty network, i.e. 3
+simulated hours of lane change, velocity update, move and node transfer for
+every vehicle in every step.  Inputs are resident in device memory when the
+timed region starts; each timed job begins with a device-side reset.
 
 Printed metric: vehicle-updates/s (vehicles that went through the velocity
 update, summed over steps, per second), with the multiple of real time
 (simulated seconds per wall-clock second, the paper's real-time ratio of
-Sec. 8) alongside.
+Sec. 8), the share of vehicles that move, and the link kernel's in-graph
+duration against the HBM roofline.  The oracle legs (the CPU baseline and
+--impl reference) time bounded windows from a seeded peak-hour state, and
+the GPU is timed on the same window.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload config2|config1|config0|config3|config4|empty|relax|plan1|yield1|signal1]
 
---impl reference times the plain CPU oracle (single thread) on bounded
-samples of the same workload.  With N > 1 (torchrun) every rank runs an
-independent replica of the job; there is no exchange between GPUs.
+With N > 1 (torchrun) every rank runs an independent replica of the job;
+there is no exchange between GPUs.
 """
 from __future__ import annotations
 
@@ -40,12 +43,8 @@ sys.path.insert(0, ROOT)
 METRIC = "vehicle-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 STEP_MODES = {"auto": 0, "fused": 1, "split": 2}
-# dram__bytes_read.sum + dram__bytes_write.sum of one link_kernel launch
-# (turn_link_kernel for plan1 and yield1) from an ncu --set full capture (caches
-# flushed) at step 5,000 (--profile-window 5000:64).  Valid only while the
-# kernel is unchanged since that capture.
-LINK_TRAFFIC_BYTES = {"config1": 4858880.0 + 1280.0, "plan1": 4783616.0 + 7424.0,
-                      "yield1": 4325376.0 + 8704.0}
+PEAK_STEP = 5400  # the departure peak (trips depart ~ Normal(5,400 s, 2,400 s))
+KERNEL_SRC = os.path.join(ROOT, "paper_cs_0105004_gb300", "csrc", "kernels.cu")
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -156,29 +155,49 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _loaded(sc, step=None):
+    """The seeded peak-hour state that the oracle legs and the GPU window
+    start from (inputs.networks.loaded_state: departed trips placed on their
+    routes, a share of the links queued up to their end)."""
+    import dataclasses
+    from paper_cs_0105004_gb300.inputs import networks as N
+    t = PEAK_STEP if step is None else step
+    return dataclasses.replace(sc, init=N.loaded_state(sc, t, seed=7))
+
+
+def _sample_steps(args, name, default_big, default_small):
+    v = getattr(args, name)
+    if v is not None:
+        return v
+    return default_big if args.workload == "config2" else default_small
+
+
 def _cpu_baseline(sc, sample_steps):
-    """The oracle as it stands, single thread, on the first sample_steps steps."""
+    """The oracle as it stands, single thread, on `sample_steps` steps from the
+    seeded peak-hour state."""
     import oracle
-    orc = oracle.Oracle(sc)
+    scl = _loaded(sc)
+    orc = oracle.Oracle(scl)
     t0 = time.perf_counter()
     st = orc.step(sample_steps)
     dt = time.perf_counter() - t0
     upd = int(st["vehicle_updates"].sum())
     orc.close()
     return {"value": upd / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{sc.name} steps 0..{sample_steps - 1} from the empty network, one thread, "
-                      f"{upd} vehicle updates in {dt:.1f} s",
+            "sample": f"{sc.name}: steps {PEAK_STEP}..{PEAK_STEP + sample_steps - 1} from the seeded peak-hour "
+                      f"state at step {PEAK_STEP}, one thread, {upd} vehicle updates in {dt:.1f} s",
             "x_real_time": sample_steps / dt}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the plain CPU oracle timed on bounded samples."""
+    """Reference arm: the plain CPU oracle timed on bounded samples of the
+    workload, consecutive windows from the seeded peak-hour state."""
     if rank != 0:
         return
     import oracle
     sc, desc = _workload(args.workload)
-    orc = oracle.Oracle(sc)
-    per = args.ref_sample_steps
+    per = _sample_steps(args, "ref_sample_steps", 10, 100)
+    orc = oracle.Oracle(_loaded(sc))
     for _ in range(args.warmup):
         orc.step(per)
     upd, dt = 0, 0.0
@@ -187,14 +206,17 @@ def run_reference(args, rank, world):
         st = orc.step(per)
         dt += time.perf_counter() - t0
         upd += int(st["vehicle_updates"].sum())
+    orc.close()
     value = upd / dt
-    sample = (f"{sc.name}: {args.steps} samples of {per} consecutive steps after {args.warmup * per} warm-up "
-              f"steps from the empty network, one thread")
+    first = PEAK_STEP + args.warmup * per
+    sample = (f"{sc.name}: {args.steps} samples of {per} consecutive steps (steps {first}.."
+              f"{first + args.steps * per - 1}) after {args.warmup * per} warm-up steps, from the seeded "
+              f"peak-hour state at step {PEAK_STEP}; one thread")
     line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "x_real_time": per * args.steps / dt,
-            "config": {"workload": desc, "steps_per_sample": per},
+            "config": {"workload": desc, "steps_per_sample": per, "from_state": f"peak-hour state at step {PEAK_STEP}"},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -246,6 +268,31 @@ def aggregate_over_ranks(t_region, work, dist, device):
     ww = torch.tensor([work], dtype=torch.float64, device=device)
     dist.all_reduce(ww, op=dist.ReduceOp.SUM)
     return float(tt.item()), float(ww.item())
+
+
+def kernel_sha():
+    """Short hash of the step kernels' source: a stored ncu traffic figure is
+    valid only for the kernel build it was captured from."""
+    import hashlib
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _profile_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summaries (a line 'bench-traffic: kernel=K workload=W kernel_sha=S
+    dram_bytes_per_launch=B' in profiles/*.md), or None when no summary was
+    taken from the current kernel source."""
+    import glob
+    import re
+    sha = kernel_sha()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for ln in open(path):
+            m = re.match(r"bench-traffic: kernel=(\S+) workload=(\S+) kernel_sha=(\S+) "
+                         r"dram_bytes_per_launch=([0-9.eE+]+)", ln.strip())
+            if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == sha:
+                return float(m.group(4)), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def run_ours(args, rank, world, local_rank):
@@ -315,33 +362,77 @@ def run_ours(args, rank, world, local_rank):
         t_region, work = aggregate_over_ranks(t_region, work, dist, dev)
     value = work / t_region
 
-    # per-kernel durations with CUDA events on the launching stream (one extra job)
-    sim.reset(stream)
-    link_ms, node_ms = sim.step_timed(steps_per_job, stream)
-    prof_tot = sim.totals()
-    if prof_tot != tot:
-        raise RuntimeError("profiled run differs from the timed run")
-    # algorithmic bytes: the link kernel reads+writes v (1 B) and id (4 B) of
-    # every vehicle and one occupancy bit per lane-cell, and completes the node
-    # transfers (~20 B each) and insertions (~10 B each) of the step before it
-    # (the node kernel does those of every 32nd step only)
-    link_bytes = 10.0 * updates + 0.25 * C * steps_per_job + 20.0 * tot["transfers"] + 10.0 * tot["inserted"]
-    node_launch_ms = _node_launch_ms(node_ms, args.step_mode)
-    link_s = float(link_ms.sum()) / 1000.0
-    node_s = float(node_launch_ms.sum()) / 1000.0
+    # the kernels' own durations inside the same graphs: one more job with
+    # kernel spans on (first block past the wait for the previous kernel to
+    # the last block's exit), bracketed by CUDA events on the same stream
+    sim.set_kernel_timing(True)
+    sim.kernel_times(reset=True)
+    with torch.cuda.stream(stream):
+        flush.fill_(7)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        job(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    timed_job_ms = a.elapsed_time(b)
+    kt = sim.kernel_times()
+    sim.set_kernel_timing(False)
+    if sim.totals() != tot:
+        raise RuntimeError("the job with kernel spans differs from the timed jobs")
+    link_us = 1e6 * kt["link_s"] / max(1, kt["link_launches"])
+    node_us = 1e6 * kt["node_s"] / max(1, kt["node_launches"])
+    # algorithmic bytes of one link-kernel launch: read + write of v (1 B) and
+    # id (4 B) of every vehicle it updates, and of one occupancy bit per
+    # lane-cell; in fused steps it also completes the previous step's node
+    # transfers (~20 B each) and insertions (~10 B each)
+    link_bytes = 10.0 * updates + 0.25 * C * steps_per_job
+    if args.step_mode == "fused":
+        link_bytes += 20.0 * tot["transfers"] + 10.0 * tot["inserted"]
+    link_bytes /= steps_per_job
     peak, peak_kind = _peaks()
-    achieved = link_bytes / link_s / 1e9
+    achieved = link_bytes / (link_us * 1e-6) / 1e9
     turns = getattr(net, "turn_lanes", None) is not None or getattr(net, "link_yield", None) is not None
     kernel = "turn_link_kernel" if turns else "link_kernel"
+    traffic, traffic_src = _profile_traffic(kernel, args.workload)
+    if args.traffic is not None:
+        traffic, traffic_src = args.traffic, "command line"
+    step_bytes = (10.0 * updates + 0.25 * C * steps_per_job + 20.0 * tot["transfers"]
+                  + 10.0 * tot["inserted"]) / steps_per_job
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": args.traffic if args.traffic is not None else LINK_TRAFFIC_BYTES.get(args.workload),
-                "avg_launch_us": 1e3 * float(link_ms.mean()),
-                "algorithmic_bytes_per_launch": link_bytes / steps_per_job,
-                "share_of_step_time": link_s / (link_s + node_s),
-                "launch_us_p50_p90_max": [round(1e3 * float(np.percentile(link_ms, q)), 2) for q in (50, 90, 100)],
-                "node_kernel": {"launches": int(node_launch_ms.size),
-                                "avg_launch_us": 1e3 * float(node_launch_ms.mean())}}
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                "traffic_source": traffic_src, "avg_launch_us": link_us,
+                "algorithmic_bytes_per_launch": link_bytes,
+                "timing": "in-graph kernel spans (%globaltimer) of one extra job, same graphs and launch shapes",
+                "span_job_ms": timed_job_ms, "spans_ms_per_job": 1e3 * (kt["link_s"] + kt["node_s"]),
+                "share_of_step_time": kt["link_s"] / max(1e-30, kt["link_s"] + kt["node_s"]),
+                "node_kernel": {"launches": kt["node_launches"], "avg_launch_us": node_us},
+                "whole_step": {"algorithmic_bytes": step_bytes,
+                               "achieved": step_bytes / (job_ms * 1e-3 / steps_per_job) / 1e9,
+                               "frac": step_bytes / (job_ms * 1e-3 / steps_per_job) / 1e9 / peak}}
+
+    # the same seeded peak-hour window the oracle legs time, on the GPU
+    window = None
+    if args.window_steps > 0 and rank == 0:
+        scl = _loaded(sc)
+        wsecs, wupd = [], None
+        for _ in range(3):
+            sim.write_state(scl.init)
+            with torch.cuda.stream(stream):
+                flush.fill_(3)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.step(args.window_steps, stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            wsecs.append(a.elapsed_time(b) / 1000.0)
+            u = sim.totals()["vehicle_updates"]
+            if wupd is not None and u != wupd:
+                raise RuntimeError("window runs differ")
+            wupd = u
+        window = {"value": wupd / float(np.median(wsecs)), "unit": METRIC, "from_step": PEAK_STEP,
+                  "steps": args.window_steps, "vehicle_updates": wupd,
+                  "us_per_step": 1e6 * float(np.median(wsecs)) / args.window_steps,
+                  "state": "seeded peak-hour state (inputs.networks.loaded_state, seed 7)"}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -351,11 +442,11 @@ def run_ours(args, rank, world, local_rank):
                + net.link_ring.nbytes + dem.depart_step.nbytes + dem.route_offsets.nbytes + dem.route_links.nbytes
                + sum(a.nbytes for a in (getattr(net, "turn_lanes", None), getattr(net, "link_yield", None),
                                         getattr(net, "link_signal", None)) if a is not None))
-        d2h = 7 * 8
+        d2h = 9 * 8
         times = []
         for k in range(args.e2e_jobs + 1):
             t0 = time.perf_counter()
-            s2 = T.Simulation(sc)
+            s2 = T.Simulation(sc, tile_words=args.tile_words)
             if args.load_balance:
                 s2.set_load_balance(args.load_balance, args.tile_vehicles or 6 * s2.tile_words)
             s2.set_step_mode(STEP_MODES[args.step_mode])
@@ -372,7 +463,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(sc, args.cpu_sample_steps)
+        cpu = _cpu_baseline(sc, _sample_steps(args, "cpu_sample_steps", 40, 300))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -381,14 +472,18 @@ def run_ours(args, rank, world, local_rank):
                 "x_real_time": steps_per_job / (job_ms / 1000.0),
                 "config": {"workload": desc, "steps_per_job": steps_per_job, "links": net.n_links,
                            "nodes": net.n_nodes, "trips": sc.demand.n, "lane_cells": C,
-                           "vehicle_updates_per_job": updates, "l2": "flushed (512 MB write) before every job; "
-                           "the simulation state stays resident across the steps of a job",
+                           "vehicle_updates_per_job": updates,
+                           "mean_vehicles_updated_per_step": updates / steps_per_job,
+                           "moving_share": tot["moving"] / max(1, tot["active"]),
+                           "arrived_per_job": tot["arrived"],
+                           "l2": "flushed (512 MB write) before every job; the simulation state stays resident "
+                                 "across the steps of a job",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "tile_words": sim.tile_words, "step_mode": args.step_mode,
                            "load_balance": {"every_steps": args.load_balance,
                                             "vehicles_per_tile": args.tile_vehicles or 6 * sim.tile_words},
                            "bit_exact_hash": str(tot["last_state_hash"])},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "window": window, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * _launches(steps_per_job, args.step_mode, args.load_balance),
                 "clocks": clocks, "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
@@ -637,7 +732,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config2", "config3", "config4", "empty", "relax", "plan1",
+    ap.add_argument("--workload", default="config2", choices=["config0", "config1", "config2", "config3", "config4", "empty", "relax", "plan1",
                                                   "yield1", "signal1"])
     ap.add_argument("--scenarios", type=int, default=256, help="config3: batch members")
     ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
@@ -654,8 +749,12 @@ def main():
     ap.add_argument("--relax-iters", type=int, default=4, help="relax: iterations")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=1800)
-    ap.add_argument("--ref-sample-steps", type=int, default=300)
+    ap.add_argument("--cpu-sample-steps", type=int, default=None,
+                    help="oracle steps of the CPU baseline from the peak-hour state (default 40 on config2, else 300)")
+    ap.add_argument("--ref-sample-steps", type=int, default=None,
+                    help="reference arm: oracle steps per sample (default 10 on config2, else 100)")
+    ap.add_argument("--window-steps", type=int, default=300,
+                    help="GPU steps timed from the peak-hour state the oracle legs start from")
     ap.add_argument("--tile-words", type=int, default=None, help="occupancy words per link tile (8..256)")
     ap.add_argument("--profile-window", default=None, metavar="S:N",
                     help="step unprofiled to S, then run N steps inside cudaProfilerStart/Stop, and exit")

@@ -296,10 +296,10 @@ ts_status ts_batch_sync(ts_batch *b, uint32_t timeout_ms);
 ts_status ts_ctx_step(ts_ctx *ctx, uint64_t *step);
 void ts_batch_destroy(ts_batch *b);
 
-/* Kernel launch shape: occupancy words (32-cell columns times lanes) per
- * link tile, 8..256 (default 128; tiles above 128 words run in a kernel
- * instance with larger blocks).  Results do not depend on it.
- * ts_tile_words returns the current value. */
+/* Kernel launch shape: at most this many occupancy words (32-cell columns
+ * times lanes) per warp tile, 8..256 (default 128); a warp tile also holds
+ * at most 32 columns, so values from 128 up give the same tiles.  Results
+ * do not depend on it.  ts_tile_words returns the current value. */
 ts_status ts_set_tile_words(ts_ctx *ctx, uint32_t words);
 uint32_t ts_tile_words(const ts_ctx *ctx);
 
@@ -348,9 +348,27 @@ ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode);
  * into the partition): every `every_steps` steps of a ts_step call
  * (0 = never; otherwise at least 32) the link tiles are rebuilt from the
  * current occupancy so that a tile holds at most `vehicles_per_tile`
- * vehicles (0 = no budget).  Each pass waits for the queued work and reads
- * the occupancy to the host.  Results do not depend on it. */
+ * vehicles (0 = no budget).  Each pass is a kernel enqueued on the step's
+ * stream, so ts_step stays asynchronous.  Waits (bounded) for the context's
+ * queued work; TS_ERR_STATE for a context in a batch.  Results do not
+ * depend on it. */
 ts_status ts_set_load_balance(ts_ctx *ctx, uint32_t every_steps, uint32_t vehicles_per_tile);
+
+/* Kernel timing inside the captured step graphs, for measurement.  With
+ * timing on, every link-kernel and node-kernel launch of ts_step records
+ * when its work started (the first of its blocks past the wait for the
+ * previous kernel) and ended (the last block's exit) on the GPU's global
+ * nanosecond timer, and each chunk's closing kernel adds the durations up on
+ * the device, so the kernels run exactly as in the untimed graphs apart
+ * from two timer reads per block.  ts_set_kernel_timing waits (bounded) for
+ * queued work and re-captures the graphs on its next ts_step.
+ * ts_read_kernel_times waits (at most timeout_ms) and writes host_out[4] =
+ * {link-kernel nanoseconds, link-kernel launches, node-kernel nanoseconds,
+ * node-kernel launches} summed since timing was first switched on or last
+ * reset (reset != 0 clears the sums after reading).  TS_ERR_STATE for a
+ * context in a batch. */
+ts_status ts_set_kernel_timing(ts_ctx *ctx, uint32_t on);
+ts_status ts_read_kernel_times(ts_ctx *ctx, uint64_t *host_out, uint32_t reset, uint32_t timeout_ms);
 
 /* Per-link travel times of completed link traversals since the last
  * ts_load_vehicles / ts_reset / ts_write_state: sum[l] = sum over vehicles

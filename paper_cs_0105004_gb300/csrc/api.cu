@@ -63,16 +63,17 @@ struct World {
     uint32_t capacity = 0;
     std::vector<ts_ctx *> members;      // slot -> context
     ScenDev *d_table = nullptr;
-    LinkTile *d_link_tiles = nullptr;
+    uint2 *d_link_tiles = nullptr;
     uint4 *d_node_tiles = nullptr;
     uint32_t *d_counts = nullptr;  // [0] link tiles, [1] node tiles, read by the kernels
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1;
-    uint32_t tile_cap = kDefaultTileWords;  // largest tile of the members (picks the link-kernel instance)
     bool turns = false;  // some member has turn lanes or yield approaches (picks the turn instances)
     uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
     std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
+    unsigned long long *d_span = nullptr;  // kernel spans (kSpanWords), allocated on first use
+    bool timing = false;                   // launches record their spans (ts_set_kernel_timing)
     bool fused() const;
     ~World();
     ts_status init(uint32_t cap);
@@ -90,7 +91,7 @@ struct ts_ctx {
     ts_params params{};
     // network (host copies)
     uint32_t n_nodes = 0, n_links = 0, n_ring = 0;
-    std::vector<uint32_t> from, to, cells, lanes, ncols, wbase, bpos, lane_base, col_in_tile;
+    std::vector<uint32_t> from, to, cells, lanes, ncols, wbase, bpos, lane_base, col_base;
     std::vector<uint8_t> ring;
     std::vector<uint64_t> cell_base;
     std::vector<uint32_t> node_in_off;
@@ -104,7 +105,12 @@ struct ts_ctx {
     uint32_t n_words = 0, n_slots = 0, n_lanes = 0;
     uint64_t n_lane_cells = 0;
     uint32_t tile_words = kDefaultTileWords;
-    std::vector<LinkTile> link_tiles;
+    std::vector<uint2> link_tiles;     // warp tiles (scenario index 0)
+    std::vector<uint32_t> tile_cuts;   // per tile: bit t set = it may be cut before its column t
+    uint32_t n_cols = 0;
+    uint2 *d_base_tiles = nullptr;     // the static tiles and their cut masks, for re-tiling on the device
+    uint32_t *d_cut_ok = nullptr;
+    size_t base_cap = 0;
     std::vector<uint4> node_tiles;
     uint32_t n_sub = 1;                // statistics sub-records per step (fixed at creation)
     uint32_t tile_vehicles = 1024;     // vehicle budget per tile when re-tiling from occupancy
@@ -153,6 +159,7 @@ struct ts_batch {
 
 World::~World() {
     drop_graphs();
+    if (d_span) cudaFree(d_span);
     if (d_table) cudaFree(d_table);
     if (d_counts) cudaFree(d_counts);
     if (d_link_tiles) cudaFree(d_link_tiles);
@@ -182,15 +189,15 @@ ts_status World::init(uint32_t cap) {
 // flight).  Captured graphs stay valid unless a tile array has to grow.
 ts_status World::rebuild() {
     std::vector<ScenDev> table(capacity);
-    std::vector<LinkTile> lt;
+    std::vector<uint2> lt;
     std::vector<uint4> nt;
     for (uint32_t s = 0; s < capacity; ++s) {
         memset(&table[s], 0, sizeof(ScenDev));
         ts_ctx *c = members[s];
         if (!c) continue;
         table[s] = c->sd;
-        for (LinkTile t : c->link_tiles) {
-            t.a.x = s;
+        for (uint2 t : c->link_tiles) {
+            t.x |= s;
             lt.push_back(t);
         }
         for (uint4 t : c->node_tiles) {
@@ -199,12 +206,20 @@ ts_status World::rebuild() {
         }
     }
     CK(cudaMemcpy(d_table, table.data(), sizeof(ScenDev) * capacity, cudaMemcpyHostToDevice));
-    if (lt.size() > link_cap) {
+    // room for re-tiling on the device: at most one tile per column
+    size_t need = lt.size();
+    bool lb = false;
+    for (ts_ctx *c : members)
+        if (c && c->retile_every) {
+            need = std::max<size_t>(need, c->n_cols);
+            lb = true;
+        }
+    if (need > link_cap) {
         drop_graphs();
         if (d_link_tiles) cudaFree(d_link_tiles);
         d_link_tiles = nullptr;
-        link_cap = std::max<size_t>(2 * lt.size(), lt.size() + 1024);
-        CK(cudaMalloc(&d_link_tiles, sizeof(LinkTile) * link_cap));
+        link_cap = std::max<size_t>(2 * need, need + 1024);
+        CK(cudaMalloc(&d_link_tiles, sizeof(uint2) * link_cap));
     }
     if (nt.size() > node_cap) {
         drop_graphs();
@@ -213,27 +228,25 @@ ts_status World::rebuild() {
         node_cap = std::max<size_t>(nt.size(), 2 * node_cap);
         CK(cudaMalloc(&d_node_tiles, sizeof(uint4) * node_cap));
     }
-    if (!lt.empty()) CK(cudaMemcpy(d_link_tiles, lt.data(), sizeof(LinkTile) * lt.size(), cudaMemcpyHostToDevice));
+    if (!lt.empty()) CK(cudaMemcpy(d_link_tiles, lt.data(), sizeof(uint2) * lt.size(), cudaMemcpyHostToDevice));
     if (!nt.empty()) CK(cudaMemcpy(d_node_tiles, nt.data(), sizeof(uint4) * nt.size(), cudaMemcpyHostToDevice));
     n_link_tiles = (uint32_t)lt.size();
     n_node_tiles = (uint32_t)nt.size();
     const uint32_t counts[2] = {n_link_tiles, n_node_tiles};
     CK(cudaMemcpy(d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
     // persistent grids: at most the resident blocks, and room for the tile
-    // count to double through load balancing before blocks loop over tiles
-    uint32_t cap = kDefaultTileWords;
+    // count to double through load balancing before warps loop over tiles
     bool pl = false;
     for (ts_ctx *c : members)
-        if (c) {
-            cap = std::max(cap, c->tile_words);
-            pl = pl || c->sd.route_turn != nullptr || c->sd.slot_gap != nullptr;
-        }
-    if (cap != tile_cap || pl != turns) {
+        if (c) pl = pl || c->sd.route_turn != nullptr || c->sd.slot_gap != nullptr;
+    if (pl != turns) {
         drop_graphs();
-        tile_cap = cap;
         turns = pl;
     }
-    const int gl = std::max(1, std::min<int>(2 * (int)n_link_tiles, max_link_blocks(tile_cap, turns)));
+    // re-tiling changes the tile count on the device: then the grid is every
+    // resident block
+    const int want = lb ? (1 << 30) : (int)((2ull * n_link_tiles + kLinkWarpsPerBlock - 1) / kLinkWarpsPerBlock);
+    const int gl = std::max(1, std::min<int>(want, max_link_blocks(turns)));
     const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks(turns)));
     if (gl > grid_l || gn != grid_n || gl < grid_l / 2) {
         drop_graphs();
@@ -265,13 +278,15 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
         if (it == graphs.end()) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+            unsigned long long *sp = timing ? d_span : nullptr;
             for (uint32_t i = 0; i < g; ++i) {
                 launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0,
-                                   tile_cap, turns);
+                                   turns, sp);
                 if (!fu || i + 1 == g)
-                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, turns);
+                    launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, turns,
+                                       sp);
             }
-            launch_advance_kernel(d_table, capacity, g, cap_stream, true);
+            launch_advance_kernel(d_table, capacity, g, cap_stream, true, sp);
             CK(cudaStreamEndCapture(cap_stream, &graph));
             cudaGraphExec_t exec;
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
@@ -329,69 +344,87 @@ ts_status wait_ctx(ts_ctx *c, uint32_t timeout_ms) {
     return s;
 }
 
-// Link tiles: runs of whole links with at most tile_words occupancy words
-// (all lanes), at most 128 columns and 128 links, or, for a longer link, runs
-// of its columns.  With per-word vehicle counts (wcount), a tile also holds at
-// most tile_vehicles vehicles, so jammed stretches get smaller tiles.  A split
-// of a non-periodic link must leave more than 2*vmax cells after it, so the
-// tile before a split never sees the link end; a too-short tail column is
-// merged into the tile before it.  Results do not depend on the tiling.
-void build_tiles(ts_ctx *c, const std::vector<uint32_t> *wcount) {
-    const uint32_t TW = c->tile_words, vmax = c->params.vmax, maxc = (uint32_t)kTileMaxCols - 1u;
-    const uint32_t VT = (wcount && c->tile_vehicles) ? c->tile_vehicles : 0xFFFFFFFFu;
-    auto col_veh = [&](uint32_t l, uint32_t j) -> uint32_t {
-        if (!wcount) return 0u;
-        uint32_t s = 0;
-        const uint32_t w0 = c->wbase[l] + j * c->lanes[l];
-        for (uint32_t k = 0; k < c->lanes[l]; ++k) s += (*wcount)[w0 + k];
-        return s;
-    };
+// Warp tiles: runs of at most 32 consecutive columns (link-major, then
+// column j) holding at most tile_words occupancy words (columns times
+// lanes).  A ring of at most 32 columns (and tile_words words) lies inside
+// one tile; a longer ring gets tiles of its own.  The last column of a link
+// is never separated from the one before it when it holds at most 2*vmax
+// cells, so the cells of a halo that a tile looks at are never within vmax
+// cells of a link end, and vehicles near a link end and its buffers are in
+// one tile.  Re-tiling from the occupancy (on the device) cuts these tiles
+// further where tile_cuts allows.  Results do not depend on the tiling.
+void build_tiles(ts_ctx *c) {
+    const uint32_t TW = std::max<uint32_t>(c->tile_words, 2u * (uint32_t)kMaxLanes), vmax = c->params.vmax;
+    const uint32_t MC = (uint32_t)kWarpTileCols;
     c->link_tiles.clear();
-    c->col_in_tile.assign(c->n_links, 0);
-    uint32_t start = 0, count = 0, words = 0, cols = 0, veh = 0;
+    uint32_t start = 0, n = 0, words = 0;
     auto flush = [&]() {
-        if (count) {
-            LinkTile t;
-            t.a = make_uint4(0u, start, count, 0u);
-            t.b = make_uint4(c->wbase[start], c->wbase[start] + words, 0u, 0u);
-            c->link_tiles.push_back(t);
-        }
-        count = words = cols = veh = 0;
+        if (n) c->link_tiles.push_back(make_uint2((n - 1u) << 24, start));
+        n = words = 0;
+    };
+    auto add = [&](uint32_t col, uint32_t w) {
+        if (n == 0) start = col;
+        ++n;
+        words += w;
     };
     for (uint32_t l = 0; l < c->n_links; ++l) {
-        const uint32_t nc = c->ncols[l], lanes = c->lanes[l], nw = nc * lanes;
-        uint32_t vl = 0;
-        if (wcount)
-            for (uint32_t j = 0; j < nc; ++j) vl += col_veh(l, j);
-        if (nw > TW || nc > maxc || vl > VT) {
-            flush();
-            uint32_t j = 0;
-            while (j < nc) {
-                uint32_t je = j + 1, v = col_veh(l, j);
-                while (je < nc && (je + 1 - j) * lanes <= TW && je + 1 - j <= maxc) {
-                    const uint32_t vn = col_veh(l, je);
-                    if (v + vn > VT) break;
-                    v += vn;
-                    ++je;
-                }
-                if (!c->ring[l] && je < nc && c->cells[l] - 32u * je < 2u * vmax + 1u) je = nc;
-                LinkTile t;
-                t.a = make_uint4(0u, l, kPartial | j, je);
-                t.b = make_uint4(c->wbase[l], c->cells[l], lanes | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
-                c->link_tiles.push_back(t);
-                j = je;
+        const uint32_t nc = c->ncols[l], lanes = c->lanes[l], c0 = c->col_base[l];
+        if (c->ring[l]) {
+            if (nc <= MC && nc * lanes <= TW) {
+                if (n + nc > MC || words + nc * lanes > TW) flush();
+                if (n == 0) start = c0;
+                n += nc;
+                words += nc * lanes;
+                continue;
             }
+            flush();
+            for (uint32_t j = 0; j < nc; ++j) {
+                if (n > 0 && (n + 1 > MC || words + lanes > TW)) flush();
+                add(c0 + j, lanes);
+            }
+            flush();
             continue;
         }
-        if (count > 0 && (words + nw > TW || cols + nc > maxc || veh + vl > VT || count == maxc)) flush();
-        if (count == 0) start = l;
-        c->col_in_tile[l] = cols;
-        ++count;
-        words += nw;
-        cols += nc;
-        veh += vl;
+        const bool short_tail = nc >= 2 && c->cells[l] - 32u * (nc - 1u) <= 2u * vmax;
+        for (uint32_t j = 0; j < nc; ++j) {
+            if (n > 0 && (n + 1 > MC || words + lanes > TW)) {
+                if (short_tail && j == nc - 1u && start + n - 1u == c0 + j - 1u) {
+                    // the short last column goes with the one before it
+                    if (n >= 2) {
+                        --n;
+                        words -= lanes;
+                        flush();
+                        add(c0 + j - 1u, lanes);
+                    }  // else the tile is that column alone: it takes the last one too
+                } else {
+                    flush();
+                }
+            }
+            add(c0 + j, lanes);
+        }
     }
     flush();
+    // where a tile may be cut by re-tiling: not before a short last column,
+    // not inside a ring that starts after the tile's first column
+    c->tile_cuts.assign(c->link_tiles.size(), 0u);
+    {
+        uint32_t l = 0;
+        for (size_t i = 0; i < c->link_tiles.size(); ++i) {
+            const uint2 t = c->link_tiles[i];
+            const uint32_t n = (t.x >> 24) + 1u;
+            uint32_t ok = 0u;
+            for (uint32_t k = 0; k < n; ++k) {
+                const uint32_t col = t.y + k;
+                while (c->col_base[l + 1] <= col) ++l;
+                const uint32_t j = col - c->col_base[l], nc = c->ncols[l];
+                bool allow = k > 0;
+                if (c->ring[l] && j > 0 && k > j) allow = false;
+                if (!c->ring[l] && j + 1 == nc && j >= 1 && c->cells[l] - 32u * j <= 2u * vmax) allow = false;
+                if (allow) ok |= 1u << k;
+            }
+            c->tile_cuts[i] = ok;
+        }
+    }
     c->node_tiles.clear();
     for (uint32_t m = 0; m < c->n_links; m += kNodeThreads)
         c->node_tiles.push_back(make_uint4(0u, m, std::min(c->n_links, m + (uint32_t)kNodeThreads), 0u));
@@ -400,9 +433,15 @@ void build_tiles(ts_ctx *c, const std::vector<uint32_t> *wcount) {
 ts_status upload_lk_info(ts_ctx *c) {
     std::vector<uint4> li(c->n_links);
     for (uint32_t l = 0; l < c->n_links; ++l)
-        li[l] = make_uint4(c->wbase[l], c->cells[l],
-                           c->lanes[l] | ((uint32_t)c->ring[l] << 8) | (c->col_in_tile[l] << 16), c->bpos[l]);
+        li[l] = make_uint4(c->wbase[l], c->cells[l], c->lanes[l] | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
     CK(cudaMemcpy(c->d_lk_info, li.data(), sizeof(uint4) * c->n_links, cudaMemcpyHostToDevice));
+    // per column: word of lane 0, link, j | lanes << 20 | ring << 23, cells
+    std::vector<uint4> ci(std::max<uint32_t>(c->n_cols, 1u));
+    for (uint32_t l = 0; l < c->n_links; ++l)
+        for (uint32_t j = 0; j < c->ncols[l]; ++j)
+            ci[c->col_base[l] + j] = make_uint4(c->wbase[l] + j * c->lanes[l], l,
+                                                j | (c->lanes[l] << 20) | ((uint32_t)c->ring[l] << 23), c->cells[l]);
+    CK(cudaMemcpy(const_cast<uint4 *>(c->sd.col_info), ci.data(), sizeof(uint4) * ci.size(), cudaMemcpyHostToDevice));
     return TS_OK;
 }
 
@@ -540,17 +579,20 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     // words, lanes, canonical cells
     c->ncols.resize(L);
     c->wbase.resize(L);
+    c->col_base.resize(L + 1);
     c->lane_base.resize(L + 1);
     uint64_t w = 0;
     c->lane_base[0] = 0;
     for (uint32_t l = 0; l < L; ++l) {
         c->ncols[l] = (c->cells[l] + 31u) / 32u;
         c->wbase[l] = (uint32_t)w;
+        c->col_base[l + 1] = c->col_base[l] + c->ncols[l];
         w += (uint64_t)c->ncols[l] * c->lanes[l];
         c->lane_base[l + 1] = c->lane_base[l] + c->lanes[l];
     }
     if (w >= (1ull << 31) / 32ull) return fail(TS_ERR_INVALID, "network too large");
     c->n_words = (uint32_t)w;
+    c->n_cols = c->col_base[L];
     c->n_lanes = c->lane_base[L];
     c->cell_base.resize(c->n_lanes + 1);
     c->cell_base[0] = 0;
@@ -607,12 +649,13 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
                 if (c->turn[j] == 0 || (c->turn[j] >> c->lanes[l]) != 0)
                     return fail(TS_ERR_INVALID, "a turn needs at least one lane of its link, and only lanes it has");
     }
-    build_tiles(c.get(), nullptr);
+    build_tiles(c.get());
     c->n_sub = c->link_tiles.size() >= 64 ? 8u : 1u;  // small networks keep one sub-record per step
     // device arrays of the network
     bool ok = true;
     auto &A = c->allocs;
     c->d_lk_info = alloc_in<uint4>(c.get(), A, L, ok);
+    uint4 *col_info = alloc_in<uint4>(c.get(), A, c->n_cols, ok);
     uint4 *nd_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint2 *sig_info = desc->link_signal ? alloc_in<uint2>(c.get(), A, L, ok) : nullptr;
     uint8_t *slot_gap = desc->link_yield ? alloc_in<uint8_t>(c.get(), A, c->n_slots, ok) : nullptr;
@@ -638,6 +681,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     }
     ScenDev &sd = c->sd;
     sd.lk_info = c->d_lk_info;
+    sd.col_info = col_info;
+    sd.n_cols = c->n_cols;
     sd.nd_info = nd_info;
     sd.sig_info = sig_info;
     sd.slot_gap = slot_gap;
@@ -683,7 +728,8 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
                 for (uint32_t k = 0; k < c->lanes[l]; ++k) {
                     sg[c->bpos[l] + k] = c->gap_accept[l];
                     tl[c->bpos[l] + k] = make_uint2(c->wbase[l] + (c->ncols[l] - 1u) * c->lanes[l] + k,
-                                                    c->cells[l] | (c->lanes[l] << 24));
+                                                    c->cells[l] | (c->lanes[l] << 24) |
+                                                        ((uint32_t)c->gap_accept[l] << 27));
                 }
         CK(cudaMemcpy(slot_gap, sg.data(), c->n_slots, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(slot_tail, tl.data(), sizeof(uint2) * c->n_slots, cudaMemcpyHostToDevice));
@@ -863,6 +909,8 @@ static ts_status reset_device_state(ts_ctx *c, cudaStream_t s) {
     return TS_OK;
 }
 
+static ts_status upload_base_tiles(ts_ctx *c);
+
 static ts_status ensure_own_world(ts_ctx *c) {
     if (!c->own) {
         c->own = new (std::nothrow) World();
@@ -968,9 +1016,11 @@ ts_status ts_set_tile_words(ts_ctx *c, uint32_t words) {
     st = wait_ctx(c, 60000);
     if (st != TS_OK) return st;
     c->tile_words = words;
-    build_tiles(c, nullptr);
-    st = upload_lk_info(c);
-    if (st != TS_OK) return st;
+    build_tiles(c);
+    if (c->retile_every) {
+        st = upload_base_tiles(c);
+        if (st != TS_OK) return st;
+    }
     if (c->own) return ensure_own_world(c);
     return TS_OK;
 }
@@ -994,23 +1044,37 @@ ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode) {
     return TS_OK;
 }
 
-// Load balancing between chunks: the tiles are rebuilt from the current
-// occupancy so that no tile carries more than tile_vehicles vehicles (the
-// counterpart of feeding measured load back into the partition).
-static ts_status retile(ts_ctx *c, cudaStream_t s) {
-    CK(cudaEventRecord(c->ev, s));
-    ts_status st = wait_ctx(c, 600000);
-    if (st != TS_OK) return st;
-    Ctrl h;
-    st = read_ctrl(c, &h);
-    if (st != TS_OK) return st;
-    std::vector<uint32_t> occ(c->n_words);
-    CK(cudaMemcpy(occ.data(), c->sd.occ[h.base & 1ull], 4ull * c->n_words, cudaMemcpyDeviceToHost));
-    for (auto &w : occ) w = (uint32_t)__builtin_popcount(w);
-    build_tiles(c, &occ);
-    st = upload_lk_info(c);
-    if (st != TS_OK) return st;
-    return c->own->rebuild();
+// The static tiles and their cut masks in device memory, for re-tiling.
+static ts_status upload_base_tiles(ts_ctx *c) {
+    const size_t n = c->link_tiles.size();
+    if (n > c->base_cap) {
+        if (c->d_base_tiles) cudaFree(c->d_base_tiles);
+        if (c->d_cut_ok) cudaFree(c->d_cut_ok);
+        c->d_base_tiles = nullptr;
+        c->d_cut_ok = nullptr;
+        c->base_cap = 0;
+        CK(cudaMalloc(&c->d_base_tiles, sizeof(uint2) * n));
+        CK(cudaMalloc(&c->d_cut_ok, sizeof(uint32_t) * n));
+        c->base_cap = n;
+    }
+    if (n) {
+        CK(cudaMemcpy(c->d_base_tiles, c->link_tiles.data(), sizeof(uint2) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_cut_ok, c->tile_cuts.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+    }
+    return TS_OK;
+}
+
+// Load balancing between chunks, enqueued on the stream like the steps: the
+// tiles are rebuilt on the device from the current occupancy so that no tile
+// carries more than tile_vehicles vehicles; the captured graphs read the
+// new tile count from device memory.
+static ts_status retile_async(ts_ctx *c, cudaStream_t s) {
+    World *w = c->own;
+    CK(cudaMemsetAsync(w->d_counts, 0, sizeof(uint32_t), s));
+    launch_retile(w->d_table, c->d_base_tiles, c->d_cut_ok, (uint32_t)c->link_tiles.size(),
+                  c->tile_vehicles ? c->tile_vehicles : 0xFFFFFFFFu, w->d_link_tiles, w->d_counts, s);
+    CK(cudaGetLastError());
+    return TS_OK;
 }
 
 ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
@@ -1040,11 +1104,55 @@ ts_status ts_step(ts_ctx *c, uint32_t n_steps, void *cuda_stream) {
         }
         done += seg;
         if (R && done < n_steps && (start + done) % R == 0) {
-            st = retile(c, s);
-            if (st != TS_OK) return st;
+            st = retile_async(c, s);
+            if (st != TS_OK) {
+                c->sticky = true;
+                return st;
+            }
         }
     }
     CK(cudaEventRecord(c->ev, s));
+    return TS_OK;
+}
+
+ts_status ts_set_kernel_timing(ts_ctx *c, uint32_t on) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (c->batch) return fail(TS_ERR_STATE, "context is stepped by its batch");
+    if (!c->loaded) return fail(TS_ERR_STATE, "no vehicles loaded");
+    if (!c->own) {
+        st = ensure_own_world(c);
+        if (st != TS_OK) return st;
+    }
+    st = wait_ctx(c, 60000);
+    if (st != TS_OK) return st;
+    World *w = c->own;
+    if (on && !w->d_span) {
+        CK(cudaMalloc(&w->d_span, sizeof(unsigned long long) * kSpanWords));
+        std::vector<unsigned long long> init(kSpanWords, 0ull);
+        for (uint32_t i = 0; i < kChunk * 2u; ++i) init[2u * i] = ~0ull;  // starts: none yet
+        CK(cudaMemcpy(w->d_span, init.data(), sizeof(unsigned long long) * kSpanWords, cudaMemcpyHostToDevice));
+    }
+    if ((on != 0) != w->timing) {
+        w->drop_graphs();  // the launches' span argument is part of the captured graphs
+        w->timing = on != 0;
+    }
+    return TS_OK;
+}
+
+ts_status ts_read_kernel_times(ts_ctx *c, uint64_t *out, uint32_t reset, uint32_t timeout_ms) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (!out) return fail(TS_ERR_INVALID, "null output");
+    st = wait_ctx(c, timeout_ms);
+    if (st != TS_OK) return st;
+    if (!c->own || !c->own->d_span) {
+        for (int i = 0; i < 4; ++i) out[i] = 0;
+        return TS_OK;
+    }
+    unsigned long long *acc = c->own->d_span + kChunk * 4u;
+    CK(cudaMemcpy(out, acc, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (reset) CK(cudaMemset(acc, 0, 4 * sizeof(unsigned long long)));
     return TS_OK;
 }
 
@@ -1053,8 +1161,16 @@ ts_status ts_set_load_balance(ts_ctx *c, uint32_t every_steps, uint32_t vehicles
     if (st != TS_OK) return st;
     if (every_steps && every_steps < kChunk) return fail(TS_ERR_INVALID, "load balancing at most every 32 steps");
     if (vehicles_per_tile && vehicles_per_tile < 128) return fail(TS_ERR_INVALID, "vehicle budget below 128");
+    if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
+    st = wait_ctx(c, 60000);  // the tile arrays are rewritten below
+    if (st != TS_OK) return st;
     c->retile_every = every_steps;
     c->tile_vehicles = vehicles_per_tile;
+    if (every_steps) {
+        st = upload_base_tiles(c);
+        if (st != TS_OK) return st;
+    }
+    if (c->own) return ensure_own_world(c);
     return TS_OK;
 }
 
@@ -1104,7 +1220,7 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
                 launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0,
-                                   w->tile_cap, w->turns);
+                                   w->turns);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu,
@@ -1524,6 +1640,8 @@ void ts_destroy(ts_ctx *c) {
     if (c->ev) cudaEventSynchronize(c->ev);
     if (c->stream) cudaStreamSynchronize(c->stream);
     delete c->own;
+    if (c->d_base_tiles) cudaFree(c->d_base_tiles);
+    if (c->d_cut_ok) cudaFree(c->d_cut_ok);
     free_list(c, c->veh_allocs);
     free_list(c, c->allocs);
     if (c->ev) cudaEventDestroy(c->ev);

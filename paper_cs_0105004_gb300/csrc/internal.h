@@ -53,11 +53,10 @@ constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kLastLinkBit = 0x80000000u;
 constexpr uint32_t kIdMask = 0x7FFFFFFFu;
 constexpr uint32_t kMaxCells = 1u << 22;      // cells per link (buffer digest packs 22 bits)
-constexpr int kTileWords = 256;               // occupancy words per link tile (all lanes), at most
-constexpr int kDefaultTileWords = 128;        // the default tile size
-constexpr int kTileMaxCols = 129;             // columns per tile (one-lane links, plus a merged tail)
-constexpr int kLinkThreads = 256;       // link-kernel block for large tiles (and the most threads of any)
-constexpr int kSmallTileThreads = 192;  // for default tiles: 140 words with halos, 5 blocks per SM
+constexpr int kTileWords = 256;               // tile_words setting: at most
+constexpr int kDefaultTileWords = 128;        // default: occupancy words (columns x lanes) per warp tile
+constexpr int kWarpTileCols = 32;             // columns per warp tile (one per lane)
+constexpr int kLinkWarpsPerBlock = 4;         // warps of one link-kernel block
 constexpr int kNodeThreads = 128;
 constexpr uint32_t kStatsRing = 4096;         // steps of statistics kept on the device
 constexpr uint32_t kChunk = 32;               // steps per captured graph
@@ -104,7 +103,10 @@ enum StatField {
 static_assert(sizeof(StatRec) == 128, "StatRec is one line");
 
 struct ScenDev {
-    const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8 | column in tile << 16, w slot base
+    const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8, w slot base
+    const uint4 *col_info;        // per column (link-major, then j): x word of lane 0, y link,
+                                  // z j | lanes << 20 | ring << 23, w link cells
+    uint32_t n_cols;
     const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8 |
                                   // priority slots << 16, w dep end
     const uint2 *sig_info;        // per link: signal cycle | green << 16, offset (nullptr: no signals)
@@ -134,18 +136,14 @@ struct ScenDev {
     const uint8_t *dep_turn;
     // gap acceptance (nullptr: none): per slot the acceptance gap G of its
     // link (0: a priority approach), and {word of the lane's last column,
-    // link cells | lanes << 24}; a node's priority slots come first, their
+    // link cells | lanes << 24 | acceptance gap << 27}; a node's priority slots come first, their
     // count in nd_info z bits 16..23
     const uint8_t *slot_gap;
     const uint2 *slot_tail;
 };
 
-// link tile, two uint4: whole links  {scen, l0, nl, 0}            {w_begin, w_end, 0, 0}
-//                       part of one link {scen, l, kPartial | j0, j1} {wbase, cells, lanes | ring << 8, slot base}
-constexpr uint32_t kPartial = 0x80000000u;
-struct LinkTile {
-    uint4 a, b;
-};
+// warp tile (uint2): x = scenario | (columns - 1) << 24, y = first column;
+// up to 32 consecutive columns of the scenario's col_info order
 // node tile: {scen, first link, end link, 0}
 
 // pdl: launch with programmatic stream serialization (overlaps this launch
@@ -155,26 +153,37 @@ struct LinkTile {
 // xfer: the launch first completes the node transfers and departures of the
 // previous step (the step at position i-1 of the chunk); without it, the
 // previous step must have been completed by node_kernel
-// tile_cap: the largest tile (occupancy words) among the tiles; picks the
-// kernel instance whose shared memory holds it
 // turns: some scenario of the table has turn lanes (plan-following lane
 // changes) or yield approaches (gap acceptance); picks the instances that
 // apply those rules
-void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool turns);
+// span: kernel-span buffer (nullptr: no timing), see kSpanWords
+// grid: blocks of kLinkWarpsPerBlock warps; each warp takes the tiles
+// warp, warp + all warps, ...
+void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
+                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span = nullptr);
 // chunk_end: the pass completes the last step each scenario ran in the
 // chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool chunk_end, bool turns);
-void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl);
+                        cudaStream_t s, bool pdl, bool chunk_end, bool turns, unsigned long long *span = nullptr);
+void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl,
+                           unsigned long long *span = nullptr);
+// Kernel-span buffer: per chunk position and kind (link, node) the launch's
+// first block entry and last block exit on %globaltimer, then per kind the
+// sum of launch durations (ns) and the launch count.
+constexpr uint32_t kSpanWords = kChunk * 4u + 4u;
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s);
+// Re-tiling on the device: the n_base static tiles of base, cut where
+// cut_ok[b] allows so that a tile holds at most vt vehicles of the current
+// state, written to out; *count (zeroed by the caller) becomes the tile count.
+void launch_retile(const ScenDev *table, const uint2 *base, const uint32_t *cut_ok, uint32_t n_base, uint32_t vt,
+                   uint2 *out, uint32_t *count, cudaStream_t s);
 // adds the entry steps of vehicles on the network to out (a copy of link_time)
 void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long *out, cudaStream_t s);
 // out[i] = word 0 of Philox-4x32-10, counter (c0[i], c1[i], 0, 0), key
 // (k0, k1): the slowdown draw of the link kernel (device arrays of n)
 void launch_philox_words(const uint32_t *c0, const uint32_t *c1, uint32_t k0, uint32_t k1, uint32_t n,
                          uint32_t *out, cudaStream_t s);
-int max_link_blocks(uint32_t tile_cap, bool turns);
+int max_link_blocks(bool turns);
 int max_node_blocks(bool turns);
 // Sets the thread-local message returned by ts_last_error.
 void set_last_error(const char *msg);

@@ -74,20 +74,30 @@ __device__ __forceinline__ void stamp(int ph, bool first) {
         s_phase_last = t;
     }
 }
-// [launch position * 3 + kernel kind][first block entry, last block exit]
-__device__ unsigned long long g_span[128][2];
-__device__ __forceinline__ void span_mark(int slot, bool enter) {
-    if (threadIdx.x == 0 && slot < 128) {
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (enter) atomicMin(&g_span[slot][0], t);
-        else atomicMax(&g_span[slot][1], t);
-    }
-}
 #else
 __device__ __forceinline__ void stamp(int, bool) {}
-__device__ __forceinline__ void span_mark(int, bool) {}
 #endif
+
+// Kernel spans (ts_set_kernel_timing): with a span buffer, thread 0 of every
+// block of a link or node launch at chunk position pos lowers the launch's
+// start to the time its wait for the previous kernel returned (so spans of
+// consecutive launches do not overlap under programmatic dependent launch)
+// and raises its end to its exit time, on the %globaltimer clock; the
+// chunk-closing kernel turns them into sums.
+// span layout: [kChunk][kind: 0 link, 1 node][start, end], then per kind
+// {sum of durations in ns, launches}.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void span_mark(unsigned long long *span, uint32_t pos, int kind, bool enter) {
+    if (span != nullptr && threadIdx.x == 0 && pos < kChunk) {
+        unsigned long long *s = span + (pos * 2u + (uint32_t)kind) * 2u;
+        if (enter) atomicMin(s, global_ns());
+        else atomicMax(s + 1, global_ns());
+    }
+}
 
 // Programmatic dependent launch: a kernel lets the next one in its stream
 // launch at once, and waits for its predecessor only before touching state.
@@ -155,7 +165,7 @@ __device__ __forceinline__ bool priority_gap_clear(const uint2 *__restrict__ slo
                                                 uint32_t slot_lo, uint32_t prio, uint32_t G) {
     for (uint32_t s = 0; s < prio; ++s) {
         const uint2 tl = slot_tail[slot_lo + s];
-        const uint32_t L = tl.y & 0xFFFFFFu, lanes = tl.y >> 24;
+        const uint32_t L = tl.y & 0xFFFFFFu, lanes = (tl.y >> 24) & 7u;
         const uint32_t lo = L > G ? L - G : 1u;
         if (lo >= L) continue;
         const uint32_t jl = (L - 1u) >> 5, jf = lo >> 5;
@@ -260,120 +270,198 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
 }
 
 // ------------------------------------------------------------------ link kernel
+//
+// A warp advances one warp tile at a time: up to 32 consecutive columns of
+// one scenario in col_info order (link-major, then column j), lane t owning
+// column t with all its lanes.  In the warp's shared-memory rows, slot
+// s = t + 1 holds column t, slot 0 the column left of the first one (left
+// halo) and slot n + 1 the column right of the last one (right halo), each
+// present only where such a neighbour exists outside the tile.  The phases
+// of a tile are separated by __syncwarp, never by a block barrier, so every
+// warp runs its own chain of dependent loads.  The host builds the tiles so
+// that a ring of at most 32 columns lies inside one tile (longer rings get
+// tiles of their own), and so that a link's last column is never separated
+// from the column before it when it holds at most 2*vmax cells: a halo then
+// never lies within vmax cells of a link end, and the vehicle that enters a
+// link-end buffer is handled by the warp that owns the buffer.
 
-constexpr int kCols = kTileMaxCols + 2;
+constexpr int kWarpCols = 32;
+constexpr int kSlots = kWarpCols + 2;
+constexpr int kRowWords = kMaxLanes * kSlots;
+constexpr int kCodes = 256;  // listed vehicles per round of a warp
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
-// Shared memory of one link-kernel block for tiles of at most TW occupancy
-// words (core + a merged tail column + a halo column on each side).
-template <int TW>
-struct LinkSmem {
-    static constexpr int kWords = TW + 4 + 2 * kMaxLanes;
-    static constexpr int kList = kWords * 32;  // every cell of a tile can hold a vehicle
-    uint32_t occ0[kWords];  // step t: occupancy, v > 0, payload buffer  // step t: occupancy, v > 0, payload buffer
-    uint32_t mov0[kWords];
-    uint32_t loc0[kWords];
-    uint32_t mv[kWords];    // vehicles that changed INTO the word's lane
-    uint32_t occ1[kWords];  // after the lane-change sub-step
-    uint32_t mov1[kWords];
-    uint32_t oocc[kWords];  // step t+1 (core words)
-    uint32_t omov[kWords];
-    uint32_t oloc[kWords];
-    uint32_t gw[kWords];    // global word index of each local word
-    uint8_t wcol[kWords], wlane[kWords];
-    uint16_t cw[kCols];             // local word of lane 0 of each column
-    uint32_t cx0[kCols];            // first cell of the column within its link
-    uint32_t cnear[kCols];          // cells within vmax of a (non-periodic) link end
-    int16_t right[kCols], left[kCols];
-    uint8_t clink[kCols], ckind[kCols];  // ckind: 0 core, 1 left halo, 2 right halo
-    uint32_t lcells[kTileMaxCols], lid[kTileMaxCols], lbpos[kTileMaxCols];
-    uint8_t llanes[kTileMaxCols], lring[kTileMaxCols], lexit[kTileMaxCols];  // lexit: lanes whose buffer is empty
-    uint8_t lend[kTileMaxCols];       // the link's end (and its buffers) is in this tile
-    uint8_t lgreen[kTileMaxCols];     // the light at the link's end is green in this step (1 without a signal)
-    uint2 lsig[kTileMaxCols];         // its signal: cycle | green << 16, offset
-    uint16_t lcw0[kTileMaxCols];      // local word of column 0 if the link starts in this tile, else 0xFFFF
-    uint32_t nlist[2];                // vehicles in the lane-change list and in the velocity list
-    uint16_t code[kList];             // (local word << 5) | bit
-    unsigned long long red[kLinkThreads / 32][8];  // per warp (at most kLinkThreads threads)
-    unsigned long long xacc[7];       // node-transfer counts of the current previous-step record
-    int ncols, nwords, ncore_words, nlinks;
+struct WarpSmem {
+    uint32_t o0[kRowWords];  // occupancy of step t (cell 0 placements of fused transfers or-ed in)
+    uint32_t m0[kRowWords];  // v > 0 at step t
+    uint32_t l0[kRowWords];  // which payload buffer holds each vehicle at step t
+    uint32_t mv[kRowWords];  // vehicles that changed INTO the word's lane
+    uint32_t o1[kRowWords];  // occupancy after the lane-change sub-step
+    uint32_t no[kRowWords];  // step t+1 (tile columns only)
+    uint32_t nm[kRowWords];
+    uint32_t nl[kRowWords];
+    uint32_t cw[kSlots];     // word of lane 0 of the slot's column, kNoSlot if the slot is empty
+    uint32_t cx0[kSlots];    // first cell of the column within its link
+    uint32_t ccells[kSlots];
+    uint32_t clink[kSlots];
+    uint32_t cnear[kSlots];  // cells within vmax of the link end (non-periodic links)
+    uint32_t cbpos[kSlots];  // first link-end buffer of the link
+    int8_t cleft[kSlots], cright[kSlots];  // neighbour slots, -1: none
+    uint8_t clanes[kSlots], cring[kSlots], ckind[kSlots];  // ckind: 0 tile column, 1 left halo, 2 right halo
+    uint8_t cexit[kSlots];   // lanes whose link-end buffer is free in this step (near columns)
+    uint8_t cgreen[kSlots];  // the light at the link end is green in this step (1 without a signal)
+    uint16_t code[kCodes];
 };
 
-template <class SM>
-__device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const SM &S, int c, int k, int i,
+template <int NW>
+struct LinkSmem {
+    WarpSmem w[NW];
+    unsigned long long red[NW][8];
+    unsigned long long *rec[NW];
+    unsigned long long red2[NW][7];
+    unsigned long long *rec2[NW];
+};
+
+__device__ __forceinline__ int wi(int k, int s) { return k * kSlots + s; }
+
+__device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const WarpSmem &S, int s, int k, int i,
                                               uint32_t dist, uint32_t open, uint32_t vmax) {
-    const uint32_t w0 = O[S.cw[c] + k];
-    const int r = S.right[c];
-    const uint32_t w1 = r >= 0 ? O[S.cw[r] + k] : 0u;
+    const uint32_t w0 = O[wi(k, s)];
+    const int r = S.cright[s];
+    const uint32_t w1 = r >= 0 ? O[wi(k, r)] : 0u;
     const unsigned long long win = (((unsigned long long)w1 << 32) | w0) >> (i + 1);
     uint32_t g = win ? (uint32_t)(__ffsll((long long)win) - 1) : 64u;
     if (g > dist) g = dist + open;
     return g < vmax ? g : vmax;
 }
 
-template <class SM>
-__device__ __forceinline__ bool room_behind(const uint32_t *O, const SM &S, int c, int k, int i,
-                                            uint32_t vmax) {
-    const int l = S.left[c];
-    const unsigned long long back = ((unsigned long long)O[S.cw[c] + k] << 32) | (l >= 0 ? O[S.cw[l] + k] : 0u);
-    const unsigned long long mask = ((2ull << vmax) - 1ull) << (32 + i - (int)vmax);
-    return (back & mask) == 0ull;
+__device__ __forceinline__ bool room_behind(const uint32_t *O, const WarpSmem &S, int s, int k, int i,
+                                            uint32_t back) {
+    const int l = S.cleft[s];
+    const unsigned long long w = ((unsigned long long)O[wi(k, s)] << 32) | (l >= 0 ? O[wi(k, l)] : 0u);
+    const unsigned long long mask = ((2ull << back) - 1ull) << (32 + i - (int)back);
+    return (w & mask) == 0ull;
 }
 
-// Bit x of the result: cell x+1 of the same lane is occupied (next word's bit
-// 0 for x = 31).
-template <class SM>
-__device__ __forceinline__ uint32_t ahead_mask(const uint32_t *O, const SM &S, int c, int k) {
-    const int r = S.right[c];
-    return (O[S.cw[c] + k] >> 1) | ((r >= 0 ? O[S.cw[r] + k] : 0u) << 31);
+// Bit x: cell x+1 of the same lane is occupied (bit 0 of the next column for x = 31).
+__device__ __forceinline__ uint32_t ahead_mask(const uint32_t *O, const WarpSmem &S, int s, int k) {
+    const int r = S.cright[s];
+    return (O[wi(k, s)] >> 1) | ((r >= 0 ? O[wi(k, r)] : 0u) << 31);
 }
 
-// Vehicles a tile must look at for lane changes: every one in its core
-// columns, the last vmax cells of a left halo column (they can move into the
-// core) and the first vmax cells of a right halo column (their lane changes
-// shape the cells the core vehicles look ahead into).
-__device__ __forceinline__ uint32_t lc_mask(uint8_t kind, uint32_t vmax) {
+// Vehicles a tile decides lane changes for: all of its own columns, the last
+// vmax cells of the left halo (they can move into the tile) and the first
+// vmax cells of the right halo (their changes shape the cells the tile's
+// last column looks ahead into).
+__device__ __forceinline__ uint32_t lc_mask(uint32_t kind, uint32_t vmax) {
     return kind == 0 ? 0xFFFFFFFFu : (kind == 1 ? ~((1u << (32 - vmax)) - 1u) : ((1u << vmax) - 1u));
 }
 
-// Vehicles a tile moves: its core, and the last vmax cells of a left halo.
-__device__ __forceinline__ uint32_t move_mask(uint8_t kind, uint32_t vmax) {
+// Vehicles a tile moves: its own columns and the last vmax cells of the left halo.
+__device__ __forceinline__ uint32_t move_mask(uint32_t kind, uint32_t vmax) {
     return kind == 0 ? 0xFFFFFFFFu : (kind == 1 ? ~((1u << (32 - vmax)) - 1u) : 0u);
 }
 
-// Appends the set bits of m (word w) to the block's vehicle list; one thread
-// per word, one shared-memory reservation per warp.
-template <class SM>
-__device__ __forceinline__ void list_append(SM &S, uint32_t &count, int w, uint32_t m) {
+__device__ __forceinline__ uint32_t near_mask(uint32_t ring, uint32_t cells, uint32_t x0, uint32_t vmax) {
+    if (ring) return 0u;
+    const int thr = (int)cells - 1 - (int)vmax - (int)x0;  // first cell within vmax of the end
+    return thr <= 0 ? 0xFFFFFFFFu : (thr >= 32 ? 0u : ~((1u << thr) - 1u));
+}
+
+// Runs `proc(code)` for every set bit of the lanes' word masks m[0..7]
+// (word index idx[q] of each), the warp's lanes sharing the work: rounds of
+// at most kCodes listed vehicles go through the warp's code list.
+template <class F>
+__device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[8], const int (&idx)[8], F &&proc) {
     const int lane = threadIdx.x & 31;
-    const uint32_t cnt = (uint32_t)__popc(m);
-    uint32_t inc = cnt;
+    for (;;) {
+        uint32_t cnt = 0u;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    uint32_t base = 0u;
-    if (lane == 31 && inc) base = atomicAdd(&count, inc);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    uint32_t r = base + inc - cnt;
-    while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        S.code[r++] = (uint16_t)((w << 5) | b);
+        for (int q = 0; q < 8; ++q) cnt += (uint32_t)__popc(m[q]);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        if (total == 0u) break;
+        uint32_t pos = inc - cnt;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            while (m[q] && pos < (uint32_t)kCodes) {
+                const int b = __ffs(m[q]) - 1;
+                m[q] &= m[q] - 1u;
+                S.code[pos++] = (uint16_t)((idx[q] << 5) | b);
+            }
+        }
+        __syncwarp();
+        const uint32_t nproc = total < (uint32_t)kCodes ? total : (uint32_t)kCodes;
+        for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) proc((uint32_t)S.code[e]);
+        __syncwarp();
     }
 }
 
-// Node transfers and departures into link l = S.lid[q] (which starts in this
-// tile) at the end of step t-1, for fused steps.  Returns the vehicles
-// placed on l.
-template <bool TURNS, class SM>
-__device__ __forceinline__ uint32_t xfer_into_link(SM &S, const ScenDev &D, int q, uint32_t t,
-                                                   const uint4 *__restrict__ sc, const uint32_t *__restrict__ oc,
-                                                   uint32_t l) {
+// Sum over the warp, then lane f adds field f's sum at rec + field[f].
+template <int NF>
+__device__ __forceinline__ void warp_flush(unsigned long long (&acc)[NF], unsigned long long *rec,
+                                           const int (&field)[NF]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        unsigned long long v = acc[f];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == f && v) atomicAdd(rec + field[f], v);
+        acc[f] = 0ull;
+    }
+}
+
+// At the end of the launch: the warps' sums of one record go out with one
+// atomic per field per block; a warp whose record differs from warp 0's
+// adds its own.
+template <int NW, int NF>
+__device__ __forceinline__ void block_end_flush(unsigned long long (&acc)[NF], unsigned long long *rec,
+                                                unsigned long long (*red)[NF], unsigned long long **recs,
+                                                const int (&field)[NF]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        unsigned long long v = acc[f];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][f] = v;
+        acc[f] = 0ull;
+    }
+    if (lane == 0) recs[warp] = rec;
+    __syncthreads();
+    if (threadIdx.x < NF) {
+        const int f = threadIdx.x;
+        unsigned long long s = 0ull;
+        unsigned long long *r0 = recs[0];
+        for (int w = 0; w < NW; ++w) {
+            if (recs[w] == nullptr) continue;
+            if (r0 == nullptr) r0 = recs[w];
+            if (recs[w] == r0) s += red[w][f];
+            else if (red[w][f]) atomicAdd(recs[w] + field[f], red[w][f]);
+        }
+        if (r0 && s) atomicAdd(r0 + field[f], s);
+    }
+}
+
+// Node transfers and departures into link l (whose column 0 this lane owns)
+// at the end of step t-1, for fused steps.  Returns the lanes of l whose
+// cell 0 received a vehicle (moving: with v > 0); acc2 gets the counts of
+// the previous step's record (transfers, insertions, changes of active,
+// buffered, sum of v, digest, moving).
+template <bool TURNS>
+__device__ __forceinline__ uint32_t xfer_into_link(const ScenDev &D, uint32_t t, const uint4 *__restrict__ sc,
+                                                   const uint32_t *__restrict__ oc, uint32_t l, uint32_t &moving,
+                                                   unsigned long long (&acc2)[7]) {
     const uint4 nd = D.nd_info[l];
-    uint32_t placed = 0u, moving = 0u;
-    unsigned long long acc2[7] = {0, 0, 0, 0, 0, 0, 0};
-    int8_t *vel = D.vel[0];  // cell 0 was empty: its payload goes
+    uint32_t placed = 0u;
+    moving = 0u;
+    int8_t *vel = D.vel[0];    // cell 0 was empty: its payload goes
     uint32_t *vid = D.vid[0];  // to buffer 0 (location bit 0)
     uint32_t fr = resolve_transfers<TURNS>(sc, nd, l, free_cell0(oc, nd), D, oc, [&](uint32_t, const uint4 &x,
                                                                                     uint32_t qn) {
@@ -405,281 +493,177 @@ __device__ __forceinline__ uint32_t xfer_into_link(SM &S, const ScenDev &D, int 
         acc2[2] += 1;
         acc2[5] += vehicle_term(idw & kIdMask, l, qn, 0u, 0u);
     });
-    const uint32_t n_placed = (uint32_t)__popc(placed);  // they are updated in step t
-    if (placed)
-        for (int f = 0; f < 7; ++f)
-            if (acc2[f]) atomicAdd(&S.xacc[f], acc2[f]);
-    for (uint32_t m = placed; m; m &= m - 1u) {
-        const uint32_t qn = (uint32_t)(__ffs(m) - 1);
-        atomicOr(&S.occ0[S.lcw0[q] + qn], 1u);
-        if ((moving >> qn) & 1u) atomicOr(&S.mov0[S.lcw0[q] + qn], 1u);
-    }
-    return n_placed;
+    return placed;
 }
 
 // Whether the buffer idx holding x is emptied by the node transfer of step
-// t-1 (the same resolution as the tile of x's next link computes).
+// t-1 (the same resolution as the warp owning x's next link computes).
 template <bool TURNS>
-__device__ __forceinline__ void buffer_emptied(const ScenDev &D, const uint4 *__restrict__ sc,
-                                               const uint32_t *__restrict__ oc, const uint4 &x, uint32_t idx,
-                                               bool &empty) {
+__device__ __forceinline__ bool buffer_emptied(const ScenDev &D, const uint4 *__restrict__ sc,
+                                               const uint32_t *__restrict__ oc, const uint4 &x, uint32_t idx) {
+    bool empty = false;
     const uint4 nd = D.nd_info[x.y];
     resolve_transfers<TURNS>(sc, nd, x.y, free_cell0(oc, nd), D, oc,
                              [&](uint32_t si, const uint4 &, uint32_t) { empty |= si == idx; });
-}
-
-// The intersection-rule versions out of line, so that their registers stay
-// out of link_buffers_phase.
-template <class SM>
-__device__ __noinline__ uint32_t xfer_into_link_turns(SM &S, const ScenDev &D, int q, uint32_t t,
-                                                      const uint4 *__restrict__ sc, const uint32_t *__restrict__ oc,
-                                                      uint32_t l) {
-    return xfer_into_link<true>(S, D, q, t, sc, oc, l);
-}
-__device__ __noinline__ bool buffer_emptied_turns(const ScenDev &D, const uint4 *__restrict__ sc,
-                                                  const uint32_t *__restrict__ oc, uint4 x, uint32_t idx) {
-    bool empty = false;
-    buffer_emptied<true>(D, sc, oc, x, idx, empty);
     return empty;
 }
 
-// The link thread of link q (index in the tile): with do_xfer, completes the
-// node transfers and departures into q (if q starts in this tile) at the end
-// of step t-1; then sets up q's lane-end buffers for step t (if q ends in this
-// tile).  Returns the vehicles placed on q.  Out of line, so that its
-// registers do not weigh on the rest of the step.  TURNS: velocity bytes and
-// buffer words carry the allowed lanes of the next turn, and transfers from
-// yield approaches wait for the gap.
-template <bool TURNS, class SM>
-__device__ __noinline__ uint32_t link_buffers_phase(SM &S, const ScenDev &D, int q, int cur, uint32_t t,
-                                                    bool do_xfer) {
-    const int nxt = cur ^ 1;
-    uint32_t n_placed = 0u;
+// The fused-step work of one lane, out of line so that its registers stay
+// out of the step: with first, the transfers and departures into the lane's
+// link (column 0) ending step t-1; with end, the link's lane-end buffers for
+// step t (empty, emptied by a transfer of step t-1, or still holding their
+// vehicle) copied into the next set.  Returns the free buffers (end) and
+// writes the cell-0 placements.
+template <bool TURNS>
+__device__ __noinline__ uint32_t fused_link_work(const ScenDev &D, uint32_t t, int cur, uint32_t link,
+                                                 uint32_t bpos, uint32_t lanes, bool first, bool end,
+                                                 uint32_t &placed, uint32_t &moving,
+                                                 unsigned long long (&acc2)[7]) {
     const uint4 *__restrict__ sc = D.slots[cur];
-    uint4 *__restrict__ sn = D.slots[nxt];
+    uint4 *__restrict__ sn = D.slots[cur ^ 1];
     const uint32_t *__restrict__ oc = D.occ[cur];
-    const uint32_t l = S.lid[q];
-    if (do_xfer && S.lcw0[q] != 0xFFFFu) {
-        // transfers and departures into l at the end of step t-1
-        if constexpr (TURNS)
-            n_placed = xfer_into_link_turns(S, D, q, t, sc, oc, l);
-        else
-            n_placed = xfer_into_link<false>(S, D, q, t, sc, oc, l);
-    }
+    placed = 0u;
+    moving = 0u;
+    if (first) placed = xfer_into_link<TURNS>(D, t, sc, oc, link, moving, acc2);
     uint32_t open = 0u;
-    if (S.lend[q]) {
-        // l's lane-end buffers for step t: empty, or emptied by a
-        // transfer of step t-1 (the same resolution as the tile of
-        // the next link computes), or still holding their vehicle
-        const uint32_t nl = S.llanes[q], b0 = S.lbpos[q];
-        uint4 own[kMaxLanes];
-#pragma unroll
-        for (int k = 0; k < kMaxLanes; ++k)
-            own[k] = (uint32_t)k < nl ? sc[b0 + k] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
-#pragma unroll
-        for (uint32_t k = 0; k < (uint32_t)kMaxLanes; ++k) {
-            if (k >= nl) break;
-            const uint32_t idx = b0 + k;
-            const uint4 x = own[k];
-            bool empty = x.x == kSlotEmpty;
-            if (!empty && do_xfer) {
-                if constexpr (TURNS)
-                    empty = buffer_emptied_turns(D, sc, oc, x, idx);
-                else
-                    buffer_emptied<false>(D, sc, oc, x, idx, empty);
-            }
+    if (end) {
+        for (uint32_t k = 0; k < lanes; ++k) {
+            const uint4 x = sc[bpos + k];
+            const bool empty = x.x == kSlotEmpty || buffer_emptied<TURNS>(D, sc, oc, x, bpos + k);
             if (empty) open |= 1u << k;
-            sn[idx] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : x;
+            sn[bpos + k] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : x;
         }
     }
-    S.lexit[q] = (uint8_t)open;
-    // the light at the link end (Sec. 3): while red, a virtual vehicle of
-    // maximum velocity zero stands at every lane end
-    const uint2 sg = S.lsig[q];
-    const uint32_t cycle = sg.x & 0xFFFFu, green = sg.x >> 16;
-    S.lgreen[q] = (uint8_t)(cycle == 0u || (t + sg.y) % cycle < green);
-    return n_placed;
+    return open;
 }
 
-// Threads of a link-kernel block for tiles of at most TW words: one per word
-// of the default tile (halos included), or 256 for the large tiles; as many
-// blocks per SM as 64 registers per thread allow.
-template <int TW>
-struct LinkLaunch {
-    static constexpr int kThreads = TW <= kDefaultTileWords ? kSmallTileThreads : kLinkThreads;
-    static constexpr int kMinBlocks = 65536 / (kThreads * 64);
-};
-
-// One launch of the link kernel (body of link_kernel and turn_link_kernel).
-// TURNS: the intersection rules of Sec. 3 a network may carry: plan-following
-// lane changes (every velocity byte carries the lanes A of its link from
-// which the vehicle may take its next turn) and gap acceptance at
-// unprotected turns (in the node transfers).
-template <int TW, bool TURNS>
-__device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__restrict__ table,
-                                          const LinkTile *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
-                                          uint32_t pos, uint32_t xfer) {
+// One launch of the link kernel (body of link_kernel and turn_link_kernel)
+// for NW warps per block.  TURNS: the intersection rules of Sec. 3 a network
+// may carry: plan-following lane changes (every velocity byte carries the
+// lanes A of its link from which the vehicle may take its next turn) and gap
+// acceptance at unprotected turns (in the node transfers).
+template <int NW, bool TURNS>
+__device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__restrict__ table,
+                                          const uint2 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
+                                          uint32_t pos, uint32_t xfer, unsigned long long *span) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem &S = SB.w[warp];
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
-    // statistics of the block: updates, lane changes, arrivals, and the changes
-    // of active, buffered, sum of velocities and digest
+    // statistics: updates, lane changes, arrivals, the changes of active,
+    // buffered, sum of velocities and digest, and the moving vehicles
     static constexpr int kField[8] = {kUpdates, kLaneChanges, kArrived, kDActive, kDBuffered, kDSumV, kDHash,
                                       kMoving};
-    // counts in 32 bits (per block and step they stay far below 2^31; the
-    // changes are signed), the digest change in 64
-    uint32_t acc[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    static constexpr int kField2[7] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash, kMoving};
+    uint32_t acc[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};  // counts (per warp and step far below 2^31), signed changes
     unsigned long long acc_hash = 0ull;
-    auto flush_acc = [&](unsigned long long *rec) {
-        unsigned long long v[8] = {acc[0], acc[1], acc[2], (unsigned long long)(long long)(int)acc[3],
-                                   (unsigned long long)(long long)(int)acc[4],
-                                   (unsigned long long)(long long)(int)acc[5], acc_hash, acc[6]};
-        block_flush<8, LinkLaunch<TW>::kThreads>(v, rec, kField, S.red);
+    unsigned long long acc2[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long *cur_rec = nullptr, *cur_rec2 = nullptr;
+    auto widen = [&](unsigned long long (&v)[8]) {
+        v[0] = acc[0];
+        v[1] = acc[1];
+        v[2] = acc[2];
+        v[3] = (unsigned long long)(long long)(int)acc[3];
+        v[4] = (unsigned long long)(long long)(int)acc[4];
+        v[5] = (unsigned long long)(long long)(int)acc[5];
+        v[6] = acc_hash;
+        v[7] = acc[6];
 #pragma unroll
         for (int f = 0; f < 7; ++f) acc[f] = 0u;
         acc_hash = 0ull;
     };
-    unsigned long long *cur_rec = nullptr;
-    // with xfer set, the launch first completes the node transfers and
-    // departures of the previous step (whose record gets these counts):
-    // transfers, insertions and the changes of active, buffered, sum of v, digest
-    static constexpr int kField2[7] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash, kMoving};
-    unsigned long long *cur_rec2 = nullptr;
-    if (threadIdx.x < 7) S.xacc[threadIdx.x] = 0ull;  // ordered by the first tile's barrier
-    auto flush_xacc = [&]() {
-        if (threadIdx.x < 7 && S.xacc[threadIdx.x]) {
-            atomicAdd(cur_rec2 + kField2[threadIdx.x], S.xacc[threadIdx.x]);
-            S.xacc[threadIdx.x] = 0ull;
-        }
-        __syncthreads();
-    };
     pdl_trigger();
-    span_mark((int)pos * 3, true);
     bool waited = false;
-    bool first = true;
-    stamp(0, true);
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const LinkTile td = tiles[tile];
-        const ScenDev &D = table[td.a.x];
+    const uint32_t nwarps = gridDim.x * (uint32_t)NW;
+    for (uint32_t tile = blockIdx.x * (uint32_t)NW + (uint32_t)warp; tile < n_tiles; tile += nwarps) {
+        const uint2 td = tiles[tile];
+        const ScenDev &D = table[td.x & 0xFFFFFFu];
         if (D.ctrl == nullptr) continue;
-        stamp(1, first);
+        const int n = (int)(td.x >> 24) + 1;
+        const uint32_t cb = td.y;
         const uint32_t vmax = D.vmax;
+        const int s = lane + 1;
+        const bool mine = lane < n;
 
-        // ---------------- tile geometry (static data: read before waiting)
-        const bool partial = (td.a.z & kPartial) != 0u;
-        auto near_mask = [&](uint32_t ring, uint32_t cells, uint32_t x0) -> uint32_t {
-            if (ring) return 0u;
-            const int thr = (int)cells - 1 - (int)vmax - (int)x0;  // first cell within vmax of the end
-            return thr <= 0 ? 0xFFFFFFFFu : (thr >= 32 ? 0u : ~((1u << thr) - 1u));
-        };
-        if (!partial) {
-            const int nl = (int)td.a.z;
-            const uint32_t wb = td.b.x;
-            const int nw = (int)(td.b.y - td.b.x);
-            for (int q = threadIdx.x; q < nl; q += blockDim.x) {
-                const uint4 li = D.lk_info[td.a.y + q];
-                S.lcells[q] = li.y;
-                S.llanes[q] = (uint8_t)(li.z & 0xFFu);
-                S.lring[q] = (uint8_t)((li.z >> 8) & 1u);
-                S.lid[q] = td.a.y + q;
-                S.lbpos[q] = li.w;
-                const int ncol = (int)((li.y + 31u) >> 5), c0 = (int)((li.z >> 16) & 0xFFu);
-                const uint32_t lanes = li.z & 0xFFu, ring = (li.z >> 8) & 1u;
-                S.lend[q] = (uint8_t)(ring ^ 1u);
-                S.lcw0[q] = ring ? (uint16_t)0xFFFFu : (uint16_t)(li.x - wb);
-                S.lsig[q] = D.sig_info ? D.sig_info[td.a.y + q] : make_uint2(0u, 0u);
-                for (int j = 0; j < ncol; ++j) {
-                    const int c = c0 + j;
-                    const uint32_t lw = li.x - wb + (uint32_t)j * lanes;
-                    S.cw[c] = (uint16_t)lw;
-                    S.cx0[c] = 32u * (uint32_t)j;
-                    S.cnear[c] = near_mask(ring, li.y, 32u * (uint32_t)j);
-                    S.clink[c] = (uint8_t)q;
-                    S.ckind[c] = 0;
-                    S.right[c] = (int16_t)(j + 1 < ncol ? c + 1 : (ring ? c0 : -1));
-                    S.left[c] = (int16_t)(j > 0 ? c - 1 : (ring ? c0 + ncol - 1 : -1));
-                    for (uint32_t k = 0; k < lanes; ++k) {
-                        S.wcol[lw + k] = (uint8_t)c;
-                        S.wlane[lw + k] = (uint8_t)k;
-                    }
+        // ---------------- geometry (static data: read before waiting)
+        uint32_t cw = kNoSlot, link = 0u, j = 0u, lanes = 0u, ring = 0u, cells = 0u, ncl = 0u, bpos = 0u;
+        uint2 sig = make_uint2(0u, 0u);
+        bool first = false, end = false;
+        if (mine) {
+            const uint4 ci = D.col_info[cb + (uint32_t)lane];
+            cw = ci.x;
+            link = ci.y;
+            j = ci.z & 0xFFFFFu;
+            lanes = (ci.z >> 20) & 7u;
+            ring = (ci.z >> 23) & 1u;
+            cells = ci.w;
+            ncl = (cells + 31u) >> 5;
+            first = !ring && j == 0u;
+            end = !ring && j + 1u == ncl;
+            int left, right;
+            if (j > 0u) left = lane > 0 ? s - 1 : 0;
+            else if (ring) left = lane + (int)ncl <= n ? lane + (int)ncl : 0;
+            else left = -1;
+            if (j + 1u < ncl) right = lane + 1 < n ? s + 1 : n + 1;
+            else if (ring) right = lane - (int)j >= 0 ? lane - (int)j + 1 : n + 1;
+            else right = -1;
+            const uint32_t near = near_mask(ring, cells, 32u * j, vmax);
+            if (near || end) {
+                bpos = D.lk_info[link].w;
+                if (D.sig_info) sig = D.sig_info[link];
+            }
+            S.cw[s] = cw;
+            S.cx0[s] = 32u * j;
+            S.ccells[s] = cells;
+            S.clink[s] = link;
+            S.cnear[s] = near;
+            S.cbpos[s] = bpos;
+            S.cleft[s] = (int8_t)left;
+            S.cright[s] = (int8_t)right;
+            S.clanes[s] = (uint8_t)lanes;
+            S.cring[s] = (uint8_t)ring;
+            S.ckind[s] = 0;
+            S.cexit[s] = 0;
+            S.cgreen[s] = 1;
+            // the halo columns, one lane each
+            if (lane == 0) {
+                uint32_t hw = kNoSlot, hj = 0u;
+                if (left == 0) {
+                    hj = j > 0u ? j - 1u : ncl - 1u;
+                    hw = j > 0u ? cw - lanes : cw + (ncl - 1u) * lanes;
                 }
-                if (q == nl - 1) S.ncols = c0 + ncol;
+                S.cw[0] = hw;
+                S.cx0[0] = 32u * hj;
+                S.ccells[0] = cells;
+                S.clink[0] = link;
+                S.cnear[0] = near_mask(ring, cells, 32u * hj, vmax);
+                S.cbpos[0] = 0u;
+                S.cleft[0] = -1;
+                S.cright[0] = 1;
+                S.clanes[0] = (uint8_t)lanes;
+                S.cring[0] = (uint8_t)ring;
+                S.ckind[0] = 1;
+                S.cexit[0] = 0;
+                S.cgreen[0] = 1;
             }
-            for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-                S.gw[w] = wb + w;
-                S.occ0[w] = 0u;
-                S.mov0[w] = 0u;
-                S.mv[w] = 0u;
-                S.oocc[w] = 0u;
-                S.omov[w] = 0u;
-                S.oloc[w] = 0u;
-            }
-            if (threadIdx.x == 0) {
-                S.nwords = nw;
-                S.ncore_words = nw;
-                S.nlinks = nl;
-            }
-        } else {
-            const uint32_t l = td.a.y, wbase = td.b.x, cells = td.b.y;
-            const uint32_t lanes = td.b.z & 0xFFu, ring = (td.b.z >> 8) & 1u;
-            const int ncol = (int)((cells + 31u) >> 5);
-            const int j0 = (int)(td.a.z & ~kPartial), j1 = (int)td.a.w;
-            const int ncore = j1 - j0;
-            const bool has_l = j0 > 0 || ring, has_r = j1 < ncol || ring;
-            const int hl = has_l ? ncore : -1;
-            const int hr = has_r ? ncore + (has_l ? 1 : 0) : -1;
-            const int ncols = ncore + (has_l ? 1 : 0) + (has_r ? 1 : 0);
-            for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-                int j;
-                uint8_t kind;
-                int16_t rr, ll;
-                if (c < ncore) {
-                    j = j0 + c;
-                    kind = 0;
-                    rr = (int16_t)(c + 1 < ncore ? c + 1 : hr);
-                    ll = (int16_t)(c > 0 ? c - 1 : hl);
-                } else if (c == hl) {
-                    j = j0 > 0 ? j0 - 1 : ncol - 1;
-                    kind = 1;
-                    rr = 0;
-                    ll = -1;
-                } else {
-                    j = j1 < ncol ? j1 : 0;
-                    kind = 2;
-                    rr = -1;
-                    ll = (int16_t)(ncore - 1);
+            if (lane == n - 1) {
+                uint32_t hw = kNoSlot, hj = 0u;
+                if (right == n + 1) {
+                    hj = j + 1u < ncl ? j + 1u : 0u;
+                    hw = j + 1u < ncl ? cw + lanes : cw - j * lanes;
                 }
-                const uint32_t lw = (uint32_t)c * lanes;
-                S.cw[c] = (uint16_t)lw;
-                S.cx0[c] = 32u * (uint32_t)j;
-                S.cnear[c] = near_mask(ring, cells, 32u * (uint32_t)j);
-                S.clink[c] = 0;
-                S.ckind[c] = kind;
-                S.right[c] = rr;
-                S.left[c] = ll;
-                for (uint32_t k = 0; k < lanes; ++k) {
-                    S.gw[lw + k] = wbase + (uint32_t)j * lanes + k;
-                    S.occ0[lw + k] = 0u;
-                    S.mov0[lw + k] = 0u;
-                    S.mv[lw + k] = 0u;
-                    S.oocc[lw + k] = 0u;
-                    S.omov[lw + k] = 0u;
-                    S.oloc[lw + k] = 0u;
-                    S.wcol[lw + k] = (uint8_t)c;
-                    S.wlane[lw + k] = (uint8_t)k;
-                }
-            }
-            if (threadIdx.x == 0) {
-                S.lcells[0] = cells;
-                S.llanes[0] = (uint8_t)lanes;
-                S.lring[0] = (uint8_t)ring;
-                S.lid[0] = l;
-                S.lbpos[0] = td.b.w;
-                S.lend[0] = (uint8_t)((!ring && j1 == ncol) ? 1u : 0u);
-                S.lcw0[0] = (!ring && j0 == 0) ? (uint16_t)0u : (uint16_t)0xFFFFu;
-                S.lsig[0] = D.sig_info ? D.sig_info[l] : make_uint2(0u, 0u);
-                S.ncols = ncols;
-                S.nwords = ncols * (int)lanes;
-                S.ncore_words = ncore * (int)lanes;
-                S.nlinks = 1;
+                S.cw[n + 1] = hw;
+                S.cx0[n + 1] = 32u * hj;
+                S.ccells[n + 1] = cells;
+                S.clink[n + 1] = link;
+                S.cnear[n + 1] = near_mask(ring, cells, 32u * hj, vmax);
+                S.cbpos[n + 1] = 0u;
+                S.cleft[n + 1] = (int8_t)n;
+                S.cright[n + 1] = -1;
+                S.clanes[n + 1] = (uint8_t)lanes;
+                S.cring[n + 1] = (uint8_t)ring;
+                S.ckind[n + 1] = 2;
+                S.cexit[n + 1] = 0;
+                S.cgreen[n + 1] = 1;
             }
         }
         // The step base and target change only between captured chunks (the
@@ -687,64 +671,115 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
         // they may be read before waiting for the previous kernel.
         const unsigned long long step = D.ctrl->base + pos;
         const bool active = step < D.ctrl->target;
-        if (threadIdx.x == 0) {
-            S.nlist[0] = 0u;
-            S.nlist[1] = 0u;
-        }
-        __syncthreads();
-        stamp(2, first);
+        __syncwarp();
         if (!active) continue;
         if (!waited) {
             pdl_wait();
             waited = true;
+            if (warp == 0) span_mark(span, pos, 0, true);  // the predecessor has completed: the work starts
         }
-        stamp(3, first);
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) flush_acc(cur_rec);
+            if (cur_rec) {
+                unsigned long long v[8];
+                widen(v);
+                warp_flush<8>(v, cur_rec, kField);
+            }
             cur_rec = rec;
         }
-        const uint32_t t = (uint32_t)step;
-        const int cur = (int)(step & 1ull), nxt = cur ^ 1;
-        const int d = (t & 1u) ? -1 : 1;
-        const int nwords = S.nwords, ncore_words = S.ncore_words;
-        // word phases: one thread per occupancy word, looping when a tile has
-        // more words than the block has threads
-
-        // with xfer, memory holds the state after the moves of step t-1 and
-        // the node transfers of t-1 are completed here, before step t
         const bool do_xfer = xfer != 0u;
         if (do_xfer) {
             unsigned long long *rec2 = reinterpret_cast<unsigned long long *>(stat_rec(D, step - 1ull));
             if (rec2 != cur_rec2) {
-                if (cur_rec2) flush_xacc();
+                if (cur_rec2) warp_flush<7>(acc2, cur_rec2, kField2);
                 cur_rec2 = rec2;
             }
         }
+        const uint32_t t = (uint32_t)step;
+        const int cur = (int)(step & 1ull), nxt = cur ^ 1;
+        const int d = (t & 1u) ? -1 : 1;
+        const int hs = lane == 0 ? 0 : (lane == 31 ? n + 1 : -1);  // the halo slot this lane handles
 
-        // ---------------- state of step t (occ0/mov0 start at zero: the word
-        // loads and the placements of the node transfers are or-ed in)
-        for (int w = threadIdx.x; w < nwords; w += LinkLaunch<TW>::kThreads) {
-            const uint32_t g = S.gw[w];
-            const uint32_t o = D.occ[cur][g];
-            if (o) {
-                atomicOr(&S.occ0[w], o);
-                atomicOr(&S.mov0[w], D.mov[cur][g]);
+        // ---------------- state of step t
+        if (mine) {
+            uint32_t placed = 0u, moving = 0u, open = 0u;
+            if (do_xfer && (first || end)) {
+                open = fused_link_work<TURNS>(D, t, cur, link, bpos, lanes, first, end, placed, moving, acc2);
+            } else if (end) {
+                const uint4 *__restrict__ sc = D.slots[cur];
+                uint4 *__restrict__ sn = D.slots[nxt];
+                uint4 own[kMaxLanes];
+#pragma unroll
+                for (int k = 0; k < kMaxLanes; ++k)
+                    own[k] = (uint32_t)k < lanes ? sc[bpos + k] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+#pragma unroll
+                for (int k = 0; k < kMaxLanes; ++k) {
+                    if ((uint32_t)k >= lanes) break;
+                    const bool empty = own[k].x == kSlotEmpty;
+                    if (empty) open |= 1u << k;
+                    sn[bpos + k] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : own[k];
+                }
             }
-            S.loc0[w] = o ? D.loc[cur][g] : 0u;
-            if (S.ckind[S.wcol[w]] == 0) acc[0] += (uint32_t)__popc(o);  // vehicle updates
+            uint32_t upd = 0u;
+#pragma unroll
+            for (int k = 0; k < kMaxLanes; ++k) {
+                if ((uint32_t)k >= lanes) break;
+                const uint32_t g = cw + (uint32_t)k;
+                const uint32_t o = D.occ[cur][g] | ((placed >> k) & 1u);
+                S.o0[wi(k, s)] = o;
+                S.m0[wi(k, s)] = (o ? D.mov[cur][g] : 0u) | ((moving >> k) & 1u);
+                S.l0[wi(k, s)] = o ? D.loc[cur][g] : 0u;
+                S.mv[wi(k, s)] = 0u;
+                S.no[wi(k, s)] = 0u;
+                S.nm[wi(k, s)] = 0u;
+                S.nl[wi(k, s)] = 0u;
+                upd += (uint32_t)__popc(o);
+            }
+            acc[0] += upd;  // vehicle updates
+            if (end) {
+                // the light at the link end (Sec. 3): while red, a virtual
+                // vehicle of maximum velocity zero stands at every lane end
+                const uint32_t cycle = sig.x & 0xFFFFu, green = sig.x >> 16;
+                const uint8_t gr = (uint8_t)(cycle == 0u || (t + sig.y) % cycle < green);
+                S.cexit[s] = (uint8_t)open;
+                S.cgreen[s] = gr;
+                if (lane > 0 && j > 0u) {  // the column before it (same link), if it is in this tile
+                    S.cexit[s - 1] = (uint8_t)open;
+                    S.cgreen[s - 1] = gr;
+                }
+            }
         }
-        {
-            // link threads, counted down from the last thread
-            const int q = LinkLaunch<TW>::kThreads - 1 - (int)threadIdx.x;
-            if (q < S.nlinks) acc[0] += link_buffers_phase<TURNS>(S, D, q, cur, t, do_xfer);
+        // the halo columns: state of step t (the cells of a halo that the tile
+        // looks at are never within vmax cells of a link end; a tile built
+        // otherwise is flagged)
+        for (int e = 0; e < 2; ++e) {
+            const int h = e == 0 ? 0 : n + 1;
+            if (lane != (e == 0 ? 0 : n - 1)) continue;
+            const uint32_t hw = S.cw[h];
+            if (hw == kNoSlot) continue;
+            if (S.cnear[h] & lc_mask(S.ckind[h], vmax)) atomicOr(&D.ctrl->error, kErrGeometry);
+            for (uint32_t k = 0; k < lanes; ++k) {
+                const uint32_t o = D.occ[cur][hw + k];
+                S.o0[wi(k, h)] = o;
+                S.m0[wi(k, h)] = o ? D.mov[cur][hw + k] : 0u;
+                S.l0[wi(k, h)] = o ? D.loc[cur][hw + k] : 0u;
+                S.mv[wi(k, h)] = 0u;
+            }
         }
-        __syncthreads();
-        stamp(4, first);
+        __syncwarp();
         const int8_t *__restrict__ vel0 = D.vel[0];
         const int8_t *__restrict__ vel1 = D.vel[1];
         const uint32_t *__restrict__ vid0 = D.vid[0];
         const uint32_t *__restrict__ vid1 = D.vid[1];
+        // the words this lane handles: its column (q 0..3) and its halo (q 4..7)
+        const bool hvalid = hs >= 0 && S.cw[hs] != kNoSlot;
+        int widx[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ss = q < 4 ? s : hs;
+            const bool ok = q < 4 ? mine : hvalid;
+            widx[q] = ok && (uint32_t)(q & 3) < (uint32_t)S.clanes[ok ? ss : 0] ? wi(q & 3, ss) : -1;
+        }
 
         // ---------------- sub-step 1: lane changes, decided on the state of step t.
         // A vehicle with v = 0 and an occupied cell ahead always has a reason to
@@ -753,55 +788,49 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
         // lane's next cell is free.  That is decided here for whole words.  A
         // vehicle with v = 0 and a free cell ahead has no reason to change.
         // Moving vehicles and vehicles near a link end are decided one by one.
-        const bool lc_on = D.lane_change != 0u;
-        if (lc_on) {
-            for (int wb = 0; wb < nwords; wb += LinkLaunch<TW>::kThreads) {  // uniform per warp (list_append)
-            const int w = wb + (int)threadIdx.x;
-            uint32_t listed = 0u;
-            if (w < nwords) {
-                const int c = S.wcol[w], k = S.wlane[w], kt = k + d;
-                const int q = S.clink[c];
-                if (kt >= 0 && kt < (int)S.llanes[q]) {
-                    const uint32_t o = S.occ0[w] & lc_mask(S.ckind[c], vmax);
-                    if (TURNS && o) {
-                        // the allowed lanes are in the payload: every vehicle
-                        // whose target cell is free is decided one by one
-                        listed = o & ~S.occ0[S.cw[c] + kt];
-                    } else if (o) {
-                        const uint32_t near = S.cnear[c];
-                        const uint32_t tw = S.occ0[S.cw[c] + kt];
-                        const int lf = S.left[c];
-                        const unsigned long long tt =
-                            ((unsigned long long)tw << 32) | (lf >= 0 ? S.occ0[S.cw[lf] + kt] : 0u);
-                        uint32_t behind = 0u;
-                        for (uint32_t j = 1; j <= vmax; ++j) behind |= (uint32_t)(tt >> (32 - j));
-                        const uint32_t ok = ahead_mask(S.occ0, S, c, k) & ~tw & ~behind & ~ahead_mask(S.occ0, S, c, kt);
-                        const uint32_t lcv0 = o & ~S.mov0[w] & ~near & ok;
-                        if (lcv0) {
-                            atomicOr(&S.mv[S.cw[c] + kt], lcv0);
-                            if (S.ckind[c] == 0) acc[1] += (uint32_t)__popc(lcv0);
-                        }
-                        listed = o & (S.mov0[w] | near);
+        if (D.lane_change != 0u) {
+            uint32_t lst[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                lst[q] = 0u;
+                if (widx[q] < 0) continue;
+                const int ss = q < 4 ? s : hs, k = q & 3, kt = k + d;
+                if (kt < 0 || kt >= (int)S.clanes[ss]) continue;
+                const uint32_t o = S.o0[widx[q]] & lc_mask(S.ckind[ss], vmax);
+                if (!o) continue;
+                if (TURNS) {
+                    // the allowed lanes are in the payload: every vehicle
+                    // whose target cell is free is decided one by one
+                    lst[q] = o & ~S.o0[wi(kt, ss)];
+                } else {
+                    const uint32_t near = S.cnear[ss];
+                    const uint32_t tw = S.o0[wi(kt, ss)];
+                    const int lf = S.cleft[ss];
+                    const unsigned long long tt =
+                        ((unsigned long long)tw << 32) | (lf >= 0 ? S.o0[wi(kt, lf)] : 0u);
+                    uint32_t behind = 0u;
+                    for (uint32_t b = 1; b <= vmax; ++b) behind |= (uint32_t)(tt >> (32 - b));
+                    const uint32_t ok = ahead_mask(S.o0, S, ss, k) & ~tw & ~behind & ~ahead_mask(S.o0, S, ss, kt);
+                    const uint32_t lcv0 = o & ~S.m0[widx[q]] & ~near & ok;
+                    if (lcv0) {
+                        S.mv[wi(kt, ss)] |= lcv0;  // this lane's own column (or halo)
+                        if (S.ckind[ss] == 0) acc[1] += (uint32_t)__popc(lcv0);
                     }
+                    lst[q] = o & (S.m0[widx[q]] | near);
                 }
             }
-            list_append(S, S.nlist[0], w, listed);
-            }
-            __syncthreads();
-            const uint32_t total = S.nlist[0];
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t code = S.code[e];
-                const int ww = code >> 5, i = code & 31;
-                const int c = S.wcol[ww], k = S.wlane[ww], kt = k + d;
-                if ((S.occ0[S.cw[c] + kt] >> i) & 1u) continue;  // target cell taken
-                const int q = S.clink[c];
-                const uint32_t ring = S.lring[q];
+            __syncwarp();
+            warp_list(S, lst, widx, [&](uint32_t code) {
+                const int ww = (int)(code >> 5), i = (int)(code & 31u);
+                const int k = ww / kSlots, c = ww - k * kSlots, kt = k + d;
+                if ((S.o0[wi(kt, c)] >> i) & 1u) return;  // target cell taken
+                const uint32_t ringc = S.cring[c];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
-                const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
+                const uint32_t dist = ringc ? 0xFFFFu : S.ccells[c] - 1u - x;
                 // payload at step t; the last-link flag matters only within
                 // vmax cells of the link end
-                const size_t p = (size_t)S.gw[ww] * 32u + (uint32_t)i;
-                const bool b1 = (S.loc0[ww] >> i) & 1u;
+                const size_t p = (size_t)(S.cw[c] + (uint32_t)k) * 32u + (uint32_t)i;
+                const bool b1 = (S.l0[ww] >> i) & 1u;
                 uint32_t v;
                 uint32_t al = 0xFu;  // lanes it may leave the link from
                 if constexpr (TURNS) {
@@ -818,90 +847,81 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                         // accepted behind the target cell shrinks from vmax to
                         // 0 over the link's last vmax cells
                         const uint32_t side = d > 0 ? al & ~((2u << k) - 1u) : al & ((1u << k) - 1u);
-                        if (side && room_behind(S.occ0, S, c, kt, i, dist < vmax ? dist : vmax)) {
-                            atomicOr(&S.mv[S.cw[c] + kt], 1u << i);
+                        if (side && room_behind(S.o0, S, c, kt, i, dist < vmax ? dist : vmax)) {
+                            atomicOr(&S.mv[wi(kt, c)], 1u << i);
                             if (S.ckind[c] == 0) acc[1] += 1;
                         }
-                        continue;
+                        return;
                     }
                     // the speed reason applies only into an allowed lane (and
                     // then both lanes are allowed: the gaps below need no
                     // closed link end)
-                    if (!((al >> kt) & 1u)) continue;
+                    if (!((al >> kt) & 1u)) return;
                 }
                 const uint32_t last = ((S.cnear[c] >> i) & 1u) ? (b1 ? vid1[p] : vid0[p]) >> 31 : 0u;
                 const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
-                const uint32_t g_own =
-                    gap_ahead(S.occ0, S, c, k, i, dist, (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q], vmax);
-                if (g_own >= want) continue;
-                const uint32_t g_tgt =
-                    gap_ahead(S.occ0, S, c, kt, i, dist, (((S.lexit[q] >> kt) & 1u) | last) & S.lgreen[q], vmax);
-                if (g_tgt > g_own && room_behind(S.occ0, S, c, kt, i, vmax)) {
-                    atomicOr(&S.mv[S.cw[c] + kt], 1u << i);
+                const uint32_t ex = S.cexit[c], gr = S.cgreen[c];
+                const uint32_t g_own = gap_ahead(S.o0, S, c, k, i, dist, (((ex >> k) & 1u) | last) & gr, vmax);
+                if (g_own >= want) return;
+                const uint32_t g_tgt = gap_ahead(S.o0, S, c, kt, i, dist, (((ex >> kt) & 1u) | last) & gr, vmax);
+                if (g_tgt > g_own && room_behind(S.o0, S, c, kt, i, vmax)) {
+                    atomicOr(&S.mv[wi(kt, c)], 1u << i);
                     if (S.ckind[c] == 0) acc[1] += 1;
                 }
-            }
+            });
         }
-        __syncthreads();
-        stamp(5, first);
+        __syncwarp();
 
         // ---------------- sub-step 2: velocity update and move.  A vehicle with
         // v = 0, an occupied cell ahead, no lane change and far from the link
         // end keeps v = 0 and its cell: its bits are copied, its payload stays.
         {
-            for (int wb = 0; wb < nwords; wb += LinkLaunch<TW>::kThreads) {  // uniform per warp (list_append)
-            const int w = wb + (int)threadIdx.x;
-            uint32_t listed = 0u;
-            if (w < nwords) {
-                const int c = S.wcol[w], k = S.wlane[w];
-                const uint8_t kind = S.ckind[c];
+            uint32_t lst[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                lst[q] = 0u;
+                if (widx[q] < 0) continue;
+                const int ss = q < 4 ? s : hs, k = q & 3;
+                const uint32_t kind = S.ckind[ss];
                 // the words after the lane-change sub-step, from the step-t
                 // words and the lane-change marks (mv: vehicles that changed
                 // into a word's lane; those leaving lane k went to k + d)
-                const int lanes = S.llanes[S.clink[c]];
+                const int nlanes = S.clanes[ss];
                 const int kf = k + d, kb = k - d;
-                const bool has_f = kf >= 0 && kf < lanes, has_b = kb >= 0 && kb < lanes;
-                const uint32_t arriving = S.mv[w];
-                const uint32_t leaving = has_f ? S.mv[S.cw[c] + kf] : 0u;
-                const uint32_t o1 = (S.occ0[w] & ~leaving) | arriving;
-                const uint32_t src_mov = (arriving && has_b) ? S.mov0[S.cw[c] + kb] : 0u;
-                const uint32_t m1 = (S.mov0[w] & ~leaving) | (src_mov & arriving);
-                S.occ1[w] = o1;
-                S.mov1[w] = m1;
-                const int r = S.right[c];
+                const bool has_f = kf >= 0 && kf < nlanes, has_b = kb >= 0 && kb < nlanes;
+                const uint32_t arriving = S.mv[widx[q]];
+                const uint32_t leaving = has_f ? S.mv[wi(kf, ss)] : 0u;
+                const uint32_t o1 = (S.o0[widx[q]] & ~leaving) | arriving;
+                const uint32_t src_mov = (arriving && has_b) ? S.m0[wi(kb, ss)] : 0u;
+                const uint32_t m1 = (S.m0[widx[q]] & ~leaving) | (src_mov & arriving);
+                S.o1[widx[q]] = o1;
+                const int r = S.cright[ss];
                 const uint32_t o1r =
-                    r >= 0 ? (S.occ0[S.cw[r] + k] & ~(has_f ? S.mv[S.cw[r] + kf] : 0u)) | S.mv[S.cw[r] + k] : 0u;
+                    r >= 0 ? (S.o0[wi(k, r)] & ~(has_f ? S.mv[wi(kf, r)] : 0u)) | S.mv[wi(k, r)] : 0u;
                 const uint32_t free_ahead = ~((o1 >> 1) | (o1r << 31));
-                const uint32_t busy = m1 | free_ahead | S.cnear[c] | arriving;
-                listed = o1 & busy & move_mask(kind, vmax);
+                const uint32_t busy = m1 | free_ahead | S.cnear[ss] | arriving;
+                lst[q] = o1 & busy & move_mask(kind, vmax);
                 if (kind == 0) {
                     const uint32_t inert = o1 & ~busy;
-                    if (inert) {
-                        atomicOr(&S.oocc[w], inert);
-                        atomicOr(&S.oloc[w], inert & S.loc0[w]);
-                    }
+                    S.no[widx[q]] = inert;
+                    S.nl[widx[q]] = inert & S.l0[widx[q]];
                 }
             }
-            list_append(S, S.nlist[1], w, listed);
-            }
-            __syncthreads();
-            const uint32_t total = S.nlist[1];
+            __syncwarp();
             int8_t *__restrict__ velw0 = D.vel[0];
             int8_t *__restrict__ velw1 = D.vel[1];
             uint32_t *__restrict__ vidw0 = D.vid[0];
             uint32_t *__restrict__ vidw1 = D.vid[1];
             const uint32_t key0 = D.seed_lo, key1 = D.seed_hi, pthr = D.p_threshold;
-            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const uint32_t code = S.code[e];
-                const int ww = code >> 5, i = code & 31;
-                const int c = S.wcol[ww];
-                const int k = S.wlane[ww];
+            warp_list(S, lst, widx, [&](uint32_t code) {
+                const int ww = (int)(code >> 5), i = (int)(code & 31u);
+                const int k = ww / kSlots, c = ww - k * kSlots;
                 const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
                 // payload from where the vehicle was at step t; no thread of
                 // this step writes a buffer that a step-t occupant is read from
-                const int sw = S.cw[c] + ks;
-                const size_t ps = (size_t)S.gw[sw] * 32u + (uint32_t)i;
-                const bool sb1 = (S.loc0[sw] >> i) & 1u;
+                const int sw = wi(ks, c);
+                const size_t ps = (size_t)(S.cw[c] + (uint32_t)ks) * 32u + (uint32_t)i;
+                const bool sb1 = (S.l0[sw] >> i) & 1u;
                 const uint32_t idw = sb1 ? vid1[ps] : vid0[ps];
                 uint32_t v0, al = 0u;  // al: allowed lanes of the next turn (0: any)
                 if constexpr (TURNS) {
@@ -911,26 +931,26 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                 } else {
                     v0 = (uint32_t)(sb1 ? vel1[ps] : vel0[ps]);
                 }
-                const int q = S.clink[c];
                 const uint32_t id = idw & kIdMask, last = idw >> 31;
-                const uint32_t ring = S.lring[q];
+                const uint32_t ringc = S.cring[c];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
-                const uint32_t dist = ring ? 0xFFFFu : S.lcells[q] - 1u - x;
+                const uint32_t cellsc = S.ccells[c];
+                const uint32_t dist = ringc ? 0xFFFFu : cellsc - 1u - x;
                 uint32_t v = v0 + 1u < vmax ? v0 + 1u : vmax;  // (i) accelerate
-                uint32_t open = (((S.lexit[q] >> k) & 1u) | last) & S.lgreen[q];
+                uint32_t open = (((S.cexit[c] >> k) & 1u) | last) & S.cgreen[c];
                 if constexpr (TURNS) {
                     if (al && !((al >> k) & 1u)) open = 0u;  // the next turn is not taken from lane k
                 }
-                const uint32_t g = gap_ahead(S.occ1, S, c, k, i, dist, open, vmax);
+                const uint32_t g = gap_ahead(S.o1, S, c, k, i, dist, open, vmax);
                 if (v > g) v = g;                                                 // (ii) gap
                 if (v > 0u && philox_word0(t, id, key0, key1) < pthr) v -= 1u;  // (iii) random
                 const bool core = S.ckind[c] == 0;
-                const uint32_t lid = S.lid[q];
-                // the tile whose core held the vehicle at step t accounts for it
+                const uint32_t lid = S.clink[c];
+                // the tile whose column held the vehicle at step t accounts for it
                 const unsigned long long old_term = core ? vehicle_term(id, lid, (uint32_t)ks, x, v0) : 0ull;
-                if (!ring && x + v >= S.lcells[q]) {
-                    // reaches the link end; a split leaves more than 2*vmax cells
-                    // after it, so such a vehicle is always in this tile's core
+                if (!ringc && x + v >= cellsc) {
+                    // reaches the link end: only from a near column, which is
+                    // always a column of this tile
                     if (!core) {
                         atomicOr(&D.ctrl->error, kErrGeometry);
                     } else if (last) {
@@ -948,24 +968,24 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                         } else {
                             const uint32_t m = D.route_links[ve.x + 1u];
                             const uint32_t fl = (ve.x + 2u == ve.y) ? kLastLinkBit : 0u;
-                            if (!((S.lexit[q] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
+                            if (!((S.cexit[c] >> k) & 1u)) atomicOr(&D.ctrl->error, kErrSlotTaken);
                             uint32_t vb = v;  // with the allowed lanes of the turn after m
                             if constexpr (TURNS) {
                                 if (D.route_turn) vb |= (uint32_t)D.route_turn[ve.x + 1u] << 4;
                             }
-                            D.slots[nxt][S.lbpos[q] + (uint32_t)k] =
-                                make_uint4(id | fl, m, lid, vb | ((uint32_t)k << 8) | (S.lcells[q] << 10));
+                            D.slots[nxt][S.cbpos[c] + (uint32_t)k] =
+                                make_uint4(id | fl, m, lid, vb | ((uint32_t)k << 8) | (cellsc << 10));
                             acc[3] -= 1;
                             acc[4] += 1;
                             acc[5] -= v0;
-                            acc_hash += vehicle_term(id, lid, (uint32_t)k, S.lcells[q], v) - old_term;
+                            acc_hash += vehicle_term(id, lid, (uint32_t)k, cellsc, v) - old_term;
                         }
                     }
                 } else {
                     int ni = i + (int)v;
                     int dc = c;
                     if (ni >= 32) {
-                        dc = S.right[c];
+                        dc = S.cright[c];
                         ni -= 32;
                     }
                     if (dc < 0) {
@@ -977,118 +997,166 @@ __device__ __forceinline__ void link_step(LinkSmem<TW> &S, const ScenDev *__rest
                             acc_hash += vehicle_term(id, lid, (uint32_t)k, S.cx0[dc] + (uint32_t)ni, v) - old_term;
                         }
                         if (S.ckind[dc] == 0) {
-                            const int dw = S.cw[dc] + k;
+                            const int dw = wi(k, dc);
                             const uint32_t bit = 1u << ni;
                             // write the payload buffer that no reader of this step uses
-                            const bool b1 = (S.occ0[dw] & bit) ? !(S.loc0[dw] & bit) : false;
-                            const size_t pd = (size_t)S.gw[dw] * 32u + (uint32_t)ni;
+                            const bool b1 = (S.o0[dw] & bit) ? !(S.l0[dw] & bit) : false;
+                            const size_t pd = (size_t)(S.cw[dc] + (uint32_t)k) * 32u + (uint32_t)ni;
                             const int8_t vb = (int8_t)(TURNS ? (v | (al << 4)) : v);
                             if (b1) {
                                 velw1[pd] = vb;
                                 vidw1[pd] = idw;
-                                atomicOr(&S.oloc[dw], bit);
+                                atomicOr(&S.nl[dw], bit);
                             } else {
                                 velw0[pd] = vb;
                                 vidw0[pd] = idw;
                             }
-                            const uint32_t old = atomicOr(&S.oocc[dw], bit);
+                            const uint32_t old = atomicOr(&S.no[dw], bit);
                             if (old & bit) atomicOr(&D.ctrl->error, kErrCellTaken);
-                            if (v) atomicOr(&S.omov[dw], bit);
+                            if (v) atomicOr(&S.nm[dw], bit);
                         }
                     }
                 }
+            });
+        }
+
+        // ---------------- the state of step t+1 of this lane's column
+        if (mine) {
+#pragma unroll
+            for (int k = 0; k < kMaxLanes; ++k) {
+                if ((uint32_t)k >= lanes) break;
+                const uint32_t g = cw + (uint32_t)k;
+                D.occ[nxt][g] = S.no[wi(k, s)];
+                D.mov[nxt][g] = S.nm[wi(k, s)];
+                D.loc[nxt][g] = S.nl[wi(k, s)];
             }
         }
-        __syncthreads();
-        stamp(6, first);
-
-        // ---------------- write the state of step t+1 and the buffer states
-        for (int w = threadIdx.x; w < ncore_words; w += LinkLaunch<TW>::kThreads) {
-            const uint32_t g = S.gw[w];
-            D.occ[nxt][g] = S.oocc[w];
-            D.mov[nxt][g] = S.omov[w];
-            D.loc[nxt][g] = S.oloc[w];
-        }
-        __syncthreads();
-        stamp(7, first);
-        first = false;
+        __syncwarp();
     }
-    if (cur_rec) flush_acc(cur_rec);
-    if (cur_rec2) flush_xacc();
-    stamp(9, true);
-    span_mark((int)pos * 3, false);
+    {
+        unsigned long long v[8];
+        widen(v);
+        block_end_flush<NW, 8>(v, cur_rec, SB.red, SB.rec, kField);
+        if (xfer) {
+            __syncthreads();
+            block_end_flush<NW, 7>(acc2, cur_rec2, SB.red2, SB.rec2, kField2);
+        }
+    }
+    span_mark(span, pos, 0, false);
 }
 
-template <int TW>
-__global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
-    link_kernel(const ScenDev *__restrict__ table, const LinkTile *__restrict__ tiles,
-                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer) {
-    __shared__ LinkSmem<TW> S;
-    link_step<TW, false>(S, table, tiles, n_tiles_p, pos, xfer);
+constexpr int kLinkWarps = kLinkWarpsPerBlock;
+constexpr int kLinkBlock = kLinkWarps * 32;
+
+__global__ void __launch_bounds__(kLinkBlock, 8)
+    link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
+                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer, unsigned long long *span) {
+    __shared__ LinkSmem<kLinkWarps> S;
+    link_step<kLinkWarps, false>(S, table, tiles, n_tiles_p, pos, xfer, span);
 }
 
 // The same with the intersection rules (scenarios with turn lanes or yield
 // approaches).
-template <int TW>
-__global__ void __launch_bounds__(LinkLaunch<TW>::kThreads, LinkLaunch<TW>::kMinBlocks)
-    turn_link_kernel(const ScenDev *__restrict__ table, const LinkTile *__restrict__ tiles,
-                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer) {
-    __shared__ LinkSmem<TW> S;
-    link_step<TW, true>(S, table, tiles, n_tiles_p, pos, xfer);
+__global__ void __launch_bounds__(kLinkBlock, 8)
+    turn_link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
+                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer, unsigned long long *span) {
+    __shared__ LinkSmem<kLinkWarps> S;
+    link_step<kLinkWarps, true>(S, table, tiles, n_tiles_p, pos, xfer, span);
 }
 
 // ------------------------------------------------------------------ node kernel
+//
+// One thread per link m, NT links per block.  Before resolving, a block
+// stages the link-end buffers of the upstream nodes of all its links (and,
+// with yield approaches, their lane-tail records) into shared memory with
+// one flattened load, so no thread walks a long slot list through dependent
+// global loads; a thread whose node's buffers do not fit the stage reads
+// them from global memory.
 
-// Node transfers and departures into link m (nd = nd_info[m]) at the end of
-// step `step`, on the state after that step's moves; acc gets the transfers,
-// insertions and the changes of active, buffered, sum of velocities, digest.
-// TURNS: velocity bytes and buffer words carry the allowed lanes of the next
-// turn, and transfers from yield approaches wait for the gap.
+constexpr int kStageSlots = 1536;  // staged buffers per block
+
+template <int NT, bool TAILS>
+struct NodeSmem {
+    uint32_t off[NT + 1];  // first staged entry of each thread's node buffers
+    uint32_t lo[NT];       // first buffer of each thread's upstream node
+    uint4 stage[kStageSlots];
+    uint2 tail[TAILS ? kStageSlots : 1];
+    uint32_t wsum[NT / 32];
+    unsigned long long red[NT / 32][7];
+};
+
+// Gap acceptance with the node's staged tail records (x word of the lane's
+// last column, y cells | lanes << 24 | acceptance gap << 27): true iff no
+// priority lane of the node has a vehicle in its cells max(1, L - G) .. L - 1
+// in occ.  All tail words are loaded before any test.
+__device__ __forceinline__ bool gap_clear_staged(const uint2 *tails, const uint32_t *__restrict__ occ, uint32_t prio,
+                                                 uint32_t G) {
+    uint32_t hit = 0u;
+#pragma unroll 4
+    for (uint32_t s = 0; s < prio; ++s) {
+        const uint2 tl = tails[s];
+        const uint32_t L = tl.y & 0xFFFFFFu, lanes = (tl.y >> 24) & 7u;
+        const uint32_t lo = L > G ? L - G : 1u;
+        if (lo >= L) continue;
+        const uint32_t jl = (L - 1u) >> 5, jf = lo >> 5;  // G <= 31: at most two columns
+        const uint32_t b = (L - 1u) & 31u;
+        const uint32_t a = jf == jl ? (lo & 31u) : 0u;
+        hit |= occ[tl.x] & (0xFFFFFFFFu >> (31u - b)) & (0xFFFFFFFFu << a);
+        if (jf < jl) hit |= occ[tl.x - lanes] & (0xFFFFFFFFu << (lo & 31u));
+    }
+    return hit == 0u;
+}
+
+// Node transfer into link m from staged buffers st[0..cnt) of its upstream
+// node (global indices slot_lo ..): the same placements as
+// resolve_transfers.
+template <bool TURNS, class F>
+__device__ __forceinline__ uint32_t resolve_staged(const uint4 *st, const uint2 *tails, uint32_t slot_lo, uint32_t cnt,
+                                                   uint32_t m, uint32_t lanes, uint32_t free_mask,
+                                                   const uint32_t *__restrict__ occ, uint32_t prio, F &&place) {
+    for (uint32_t s = 0; s < cnt && free_mask; ++s) {
+        const uint4 x = st[s];
+        if (x.x == kSlotEmpty || x.y != m) continue;
+        if constexpr (TURNS) {
+            if (tails) {
+                const uint32_t G = tails[s].y >> 27;
+                if (G && !gap_clear_staged(tails, occ, prio, G)) continue;
+            }
+        }
+        const uint32_t ks = (x.w >> 8) & 3u;
+        const uint32_t pref = ks < lanes - 1u ? ks : lanes - 1u;
+        uint32_t qn;
+        if ((free_mask >> pref) & 1u) {
+            qn = pref;
+        } else {
+            const uint32_t rest = free_mask & ~(1u << pref);
+            if (!rest) continue;
+            qn = (uint32_t)(__ffs(rest) - 1);
+        }
+        free_mask &= ~(1u << qn);
+        place(slot_lo + s, x, qn);
+    }
+    return free_mask;
+}
+
+// resolve_transfers for a node whose buffers are not staged, out of line:
+// returns the placements (at most one per lane of m) in order.
 template <bool TURNS>
-__device__ __forceinline__ void node_link(const ScenDev &D, uint32_t m, const uint4 &nd, unsigned long long step,
-                                          unsigned long long (&acc)[7]) {
-    const int nxt = (int)((step + 1ull) & 1ull);
-    uint32_t *occ = D.occ[nxt];
-    uint32_t *mov = D.mov[nxt];
-    uint4 *slots = D.slots[nxt];
-    int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
-    uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
-    // slots with next link m, the cells 0 of m and m's queue head are
-    // written by this thread only; the head is loaded with the node's buffers
-    // and m's cells 0, not after the transfers
-    const uint2 hd = D.dep_head[m];
-    const uint32_t fr = resolve_transfers<TURNS>(slots, nd, m, free_cell0(occ, nd), D, occ,
-                                                 [&](uint32_t si, const uint4 &x, uint32_t qn) {
-        const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
-        const uint32_t w = nd.y + qn;  // column 0 of lane qn
-        occ[w] |= 1u;
-        if (v) mov[w] |= 1u;
-        vel[(size_t)w * 32u] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
-        vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
-        atomicAdd(&D.veh[id].x, 1u);
-        slots[si].x = kSlotEmpty;
-        // travel times: + the exit step on the link left, - the entry step on m
-        atomicAdd(&D.link_time[x.z], kLinkTimeOne + step);
-        atomicAdd(&D.link_time[m], 0ull - step);
-        D.enter_step[id] = (uint32_t)step;
-        acc[0] += 1;
-        acc[2] += 1;
-        acc[3] -= 1;
-        acc[4] += v;
-        acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
-        acc[6] += v ? 1u : 0u;
+__device__ __noinline__ uint32_t resolve_unstaged(const uint4 *__restrict__ slots, uint4 nd, uint32_t m,
+                                                  uint32_t free_mask, const ScenDev &D,
+                                                  const uint32_t *__restrict__ occ, uint32_t (&si)[kMaxLanes],
+                                                  uint4 (&xs)[kMaxLanes], uint32_t (&qs)[kMaxLanes],
+                                                  uint32_t &free_out) {
+    uint32_t n = 0u;
+    free_out = resolve_transfers<TURNS>(slots, nd, m, free_mask, D, occ, [&](uint32_t i, const uint4 &x, uint32_t q) {
+        if (n < (uint32_t)kMaxLanes) {
+            si[n] = i;
+            xs[n] = x;
+            qs[n] = q;
+        }
+        ++n;
     });
-    run_departures_from(D, nd, m, (uint32_t)step, hd, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
-        const uint32_t w = nd.y + qn;
-        occ[w] |= 1u;
-        vel[(size_t)w * 32u] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
-        vid[(size_t)w * 32u] = idw;
-        atomicAdd(&D.link_time[m], 0ull - step);
-        D.enter_step[idw & kIdMask] = (uint32_t)step;
-        acc[1] += 1;
-        acc[2] += 1;
-        acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
-    });
+    return n;
 }
 
 // The step of a node pass at chunk position pos: per step (split steps) the
@@ -1105,59 +1173,209 @@ __device__ __forceinline__ bool node_step(const ScenDev &D, uint32_t pos, bool c
     return true;
 }
 
-// One node pass, one thread per link m (body of node_kernel and
-// turn_node_kernel).
-template <bool TURNS>
-__device__ __forceinline__ void node_pass(unsigned long long (*red)[7], const ScenDev *__restrict__ table,
+// One node pass (body of node_kernel and turn_node_kernel): node transfers
+// and departures into every link m at the end of the step, on the state
+// after that step's moves.  acc gets the transfers, insertions and the
+// changes of active, buffered, sum of velocities, digest, and the moving
+// vehicles placed.  TURNS: velocity bytes and buffer words carry the allowed
+// lanes of the next turn, and transfers from yield approaches wait for the
+// gap.
+template <int NT, bool TURNS>
+__device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev *__restrict__ table,
                                           const uint4 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
-                                          uint32_t pos, uint32_t chunk_end) {
+                                          uint32_t pos, uint32_t chunk_end, unsigned long long *span) {
     const uint32_t n_tiles = *n_tiles_p;
-    // transfers, insertions and the changes of active, buffered, sum of velocities, digest
     static constexpr int kField[7] = {kTransfers, kInserted, kDActive, kDBuffered, kDSumV, kDHash, kMoving};
     unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_trigger();
-    span_mark((int)pos * 3 + 1, true);
     bool waited = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint4 td = tiles[tile];
         const ScenDev &D = table[td.x];
         if (D.ctrl == nullptr) continue;
         const uint32_t m = td.y + threadIdx.x;
-        const uint4 nd = m < td.z ? D.nd_info[m] : make_uint4(0u, 0u, 0u, 0u);  // static
+        const bool has = m < td.z;
+        const uint4 nd = has ? D.nd_info[m] : make_uint4(0u, 0u, 0u, 0u);  // static
         // base and target are constant within a captured chunk
         unsigned long long step;
         if (!node_step(D, pos, chunk_end != 0u, step)) continue;
+        // staging offsets: exclusive scan of the buffer counts over the block
+        const uint32_t cnt = nd.z & 0xFFu;
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) S.wsum[warp] = inc;
+        __syncthreads();
+        uint32_t base = 0u;
+        for (int w = 0; w < warp; ++w) base += S.wsum[w];
+        const uint32_t off = base + inc - cnt;
+        S.off[threadIdx.x] = off;
+        S.lo[threadIdx.x] = nd.x;
+        if (threadIdx.x == NT - 1) S.off[NT] = off + cnt;
+        __syncthreads();
         if (!waited) {
             pdl_wait();
             waited = true;
+            if (threadIdx.x == 0) span_mark(span, pos, 1, true);
         }
+        const int nxt = (int)((step + 1ull) & 1ull);
+        uint32_t *occ = D.occ[nxt];
+        uint32_t *mov = D.mov[nxt];
+        uint4 *slots = D.slots[nxt];
+        // this thread's inputs (m's cells 0 and queue head) with the staged loads
+        const uint2 hd = has ? D.dep_head[m] : make_uint2(0u, 0xFFFFFFFFu);
+        const uint32_t free0 = has ? free_cell0(occ, nd) : 0u;
+        const uint32_t total = S.off[NT];
+        const uint32_t lim = total < (uint32_t)kStageSlots ? total : (uint32_t)kStageSlots;
+        const bool tails = TURNS && D.slot_tail != nullptr;
+#pragma unroll 4
+        for (uint32_t e = threadIdx.x; e < lim; e += NT) {
+            // owner: the last thread whose range starts at or before e
+            uint32_t i = 0u;
+#pragma unroll
+            for (uint32_t h = NT / 2; h > 0; h >>= 1)
+                if (S.off[i + h] <= e) i += h;
+            const uint32_t si = S.lo[i] + (e - S.off[i]);
+            S.stage[e] = slots[si];
+            if constexpr (TURNS) {
+                if (tails) S.tail[e] = D.slot_tail[si];
+            }
+        }
+        __syncthreads();
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
-            if (cur_rec) block_flush<7, kNodeThreads>(acc, cur_rec, kField, red);
+            if (cur_rec) block_flush<7, NT>(acc, cur_rec, kField, S.red);
             cur_rec = rec;
         }
-        if (m < td.z) node_link<TURNS>(D, m, nd, step, acc);
+        if (has) {
+            int8_t *vel = D.vel[0];   // a vehicle placed in an empty cell 0 keeps its
+            uint32_t *vid = D.vid[0];  // payload in buffer 0 (location bit 0)
+            auto place = [&](uint32_t si, const uint4 &x, uint32_t qn) {
+                const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
+                const uint32_t w = nd.y + qn;  // column 0 of lane qn
+                occ[w] |= 1u;
+                if (v) mov[w] |= 1u;
+                vel[(size_t)w * 32u] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
+                vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
+                atomicAdd(&D.veh[id].x, 1u);
+                slots[si].x = kSlotEmpty;
+                // travel times: + the exit step on the link left, - the entry step on m
+                atomicAdd(&D.link_time[x.z], kLinkTimeOne + step);
+                atomicAdd(&D.link_time[m], 0ull - step);
+                D.enter_step[id] = (uint32_t)step;
+                acc[0] += 1;
+                acc[2] += 1;
+                acc[3] -= 1;
+                acc[4] += v;
+                acc[5] += vehicle_term(id, m, qn, 0u, v) - vehicle_term(id, x.z, ks, x.w >> 10, v);
+                acc[6] += v ? 1u : 0u;
+            };
+            const uint32_t lanes = (nd.z >> 8) & 0xFFu, prio = (nd.z >> 16) & 0xFFu;
+            uint32_t fr;
+            if (off + cnt <= (uint32_t)kStageSlots)
+                fr = resolve_staged<TURNS>(S.stage + off, tails ? S.tail + off : nullptr, nd.x, cnt, m, lanes, free0,
+                                           occ, prio, place);
+            else {
+                uint32_t si[kMaxLanes], qs[kMaxLanes];
+                uint4 xs[kMaxLanes];
+                const uint32_t np = resolve_unstaged<TURNS>(slots, nd, m, free0, D, occ, si, xs, qs, fr);
+                for (uint32_t q = 0; q < np && q < (uint32_t)kMaxLanes; ++q) place(si[q], xs[q], qs[q]);
+            }
+            run_departures_from(D, nd, m, (uint32_t)step, hd, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
+                const uint32_t w = nd.y + qn;
+                occ[w] |= 1u;
+                vel[(size_t)w * 32u] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
+                vid[(size_t)w * 32u] = idw;
+                atomicAdd(&D.link_time[m], 0ull - step);
+                D.enter_step[idw & kIdMask] = (uint32_t)step;
+                acc[1] += 1;
+                acc[2] += 1;
+                acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
+            });
+        }
+        __syncthreads();  // the stage is rewritten by the next tile
     }
-    if (cur_rec) block_flush<7, kNodeThreads>(acc, cur_rec, kField, red);
-    span_mark((int)pos * 3 + 1, false);
+    if (cur_rec) block_flush<7, NT>(acc, cur_rec, kField, S.red);
+    span_mark(span, pos, 1, false);
 }
 
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const ScenDev *__restrict__ table,
                                                             const uint4 *__restrict__ tiles,
                                                             const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
-                                                            uint32_t chunk_end) {
-    __shared__ unsigned long long red[kNodeThreads / 32][7];
-    node_pass<false>(red, table, tiles, n_tiles_p, pos, chunk_end);
+                                                            uint32_t chunk_end, unsigned long long *span) {
+    __shared__ NodeSmem<kNodeThreads, false> S;
+    node_pass<kNodeThreads, false>(S, table, tiles, n_tiles_p, pos, chunk_end, span);
 }
 
 // The same for scenarios with turn lanes or yield approaches.
 __global__ void __launch_bounds__(kNodeThreads) turn_node_kernel(const ScenDev *__restrict__ table,
                                                                  const uint4 *__restrict__ tiles,
                                                                  const uint32_t *__restrict__ n_tiles_p, uint32_t pos,
-                                                                 uint32_t chunk_end) {
-    __shared__ unsigned long long red[kNodeThreads / 32][7];
-    node_pass<true>(red, table, tiles, n_tiles_p, pos, chunk_end);
+                                                                 uint32_t chunk_end, unsigned long long *span) {
+    __shared__ NodeSmem<kNodeThreads, true> S;
+    node_pass<kNodeThreads, true>(S, table, tiles, n_tiles_p, pos, chunk_end, span);
+}
+
+// ------------------------------------------------------------------ load balancing
+
+// Re-tiling from the occupancy (the counterpart of feeding measured load
+// back into the partition): one warp per static tile counts the vehicles of
+// each of its columns in the current state and cuts the tile greedily where
+// the running count would exceed vt, at the positions cut_ok allows (bit t: a
+// cut before column t keeps the tiling rules); the sub-tiles go to out, in
+// any order, and count (zero before the launch) becomes their number.
+__global__ void __launch_bounds__(128) retile_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ base,
+                                                     const uint32_t *__restrict__ cut_ok, uint32_t n_base, uint32_t vt,
+                                                     uint2 *__restrict__ out, uint32_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x / 32u, nw = gridDim.x * wpb;
+    for (uint32_t b = blockIdx.x * wpb + (threadIdx.x >> 5); b < n_base; b += nw) {
+        const uint2 td = base[b];
+        const uint32_t scen = td.x & 0xFFFFFFu;
+        const int n = (int)(td.x >> 24) + 1;
+        const ScenDev &D = table[scen];
+        uint32_t cnt = 0u;
+        if (lane < n && D.ctrl != nullptr) {
+            const uint4 ci = D.col_info[td.y + (uint32_t)lane];
+            const uint32_t lanes = (ci.z >> 20) & 7u;
+            const uint32_t *occ = D.occ[D.ctrl->base & 1ull];
+            for (uint32_t k = 0; k < lanes; ++k) cnt += (uint32_t)__popc(occ[ci.x + k]);
+        }
+        const uint32_t ok = cut_ok[b];
+        uint32_t cuts = 0u, sum = __shfl_sync(0xffffffffu, cnt, 0);
+        for (int t = 1; t < 32; ++t) {
+            const uint32_t c = __shfl_sync(0xffffffffu, cnt, t);
+            if (t >= n) continue;
+            if (sum + c > vt && ((ok >> t) & 1u)) {
+                cuts |= 1u << t;
+                sum = c;
+            } else {
+                sum += c;
+            }
+        }
+        const uint32_t starts = cuts | 1u;
+        uint32_t at = 0u;
+        if (lane == 0) at = atomicAdd(count, (uint32_t)__popc(starts));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (lane < n && ((starts >> lane) & 1u)) {
+            const uint32_t later = starts & ~((2u << lane) - 1u);
+            const int end = later ? __ffs((int)later) - 1 : n;
+            const uint32_t rank = (uint32_t)__popc(starts & ((1u << lane) - 1u));
+            out[at + rank] = make_uint2(scen | ((uint32_t)(end - lane - 1) << 24), td.y + (uint32_t)lane);
+        }
+    }
+}
+
+void launch_retile(const ScenDev *table, const uint2 *base, const uint32_t *cut_ok, uint32_t n_base, uint32_t vt,
+                   uint2 *out, uint32_t *count, cudaStream_t s) {
+    const uint32_t blocks = (n_base + 3u) / 4u;
+    const int grid = blocks == 0u ? 1 : (blocks > 4096u ? 4096 : (int)blocks);
+    retile_kernel<<<grid, 128, 0, s>>>(table, base, cut_ok, n_base, vt, out, count);
 }
 
 // ------------------------------------------------------------------ link travel times
@@ -1185,9 +1403,23 @@ void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long 
 
 // One block per scenario: sums the statistics of the g steps just run,
 // moves the step counter and clears the records of the next chunk.
-__global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict__ table, uint32_t g_max) {
-    span_mark((int)g_max * 3 + 2, true);
+__global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict__ table, uint32_t g_max,
+                                                      unsigned long long *span) {
     pdl_wait();
+    if (span != nullptr && blockIdx.x == 0 && threadIdx.x < 2) {
+        // the chunk's launches of one kind: durations into the sums, spans reset
+        const uint32_t kind = threadIdx.x;
+        unsigned long long *acc = span + kChunk * 4u + kind * 2u;
+        for (uint32_t p = 0; p < g_max; ++p) {
+            unsigned long long *s = span + (p * 2u + kind) * 2u;
+            if (s[1] > s[0]) {
+                acc[0] += s[1] - s[0];
+                acc[1] += 1ull;
+            }
+            s[0] = ~0ull;
+            s[1] = 0ull;
+        }
+    }
     const ScenDev &D = table[blockIdx.x];
     Ctrl *c = D.ctrl;
     if (c == nullptr) return;
@@ -1259,7 +1491,6 @@ __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict_
         unsigned long long *z = reinterpret_cast<unsigned long long *>(D.stats + (size_t)(t & (kStatsRing - 1)) * nsub);
         z[u % per] = 0ull;
     }
-    span_mark((int)g_max * 3 + 2, false);
 }
 
 __global__ void set_target_kernel(Ctrl *ctrl, unsigned long long target) { ctrl->target = target; }
@@ -1294,29 +1525,21 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int TW>
-static void (*link_instance(bool turns))(const ScenDev *, const LinkTile *, const uint32_t *, uint32_t, uint32_t) {
-    return turns ? turn_link_kernel<TW> : link_kernel<TW>;
-}
-
-void launch_link_kernel(const ScenDev *table, const LinkTile *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, uint32_t tile_cap, bool turns) {
-    if (tile_cap <= (uint32_t)kDefaultTileWords)
-        launch_pdl(link_instance<kDefaultTileWords>(turns), grid, LinkLaunch<kDefaultTileWords>::kThreads, pdl, s,
-                   table, tiles, n_tiles, i, xfer ? 1u : 0u);
-    else
-        launch_pdl(link_instance<kTileWords>(turns), grid, LinkLaunch<kTileWords>::kThreads, pdl, s, table, tiles,
-                   n_tiles, i, xfer ? 1u : 0u);
+void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
+                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span) {
+    launch_pdl(turns ? turn_link_kernel : link_kernel, grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i,
+               xfer ? 1u : 0u, span);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool chunk_end, bool turns) {
+                        cudaStream_t s, bool pdl, bool chunk_end, bool turns, unsigned long long *span) {
     launch_pdl(turns ? turn_node_kernel : node_kernel, grid, kNodeThreads, pdl, s, table, tiles, n_tiles, i,
-               chunk_end ? 1u : 0u);
+               chunk_end ? 1u : 0u, span);
 }
 
-void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl) {
-    launch_pdl(advance_kernel, (int)n_scen, 128, pdl, s, table, g);
+void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl,
+                           unsigned long long *span) {
+    launch_pdl(advance_kernel, (int)n_scen, 128, pdl, s, table, g, span);
 }
 
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s) {
@@ -1347,34 +1570,13 @@ extern "C" int ts_debug_phase_sums(unsigned long long *out, int reset) {
     }
     return cudaMemcpyFromSymbol(out, g_phase_sum, sizeof(unsigned long long) * kPhases) == cudaSuccess ? 0 : -1;
 }
-extern "C" int ts_debug_spans(unsigned long long *out, int reset) {
-    if (reset) {
-        unsigned long long init[128][2];
-        for (int i = 0; i < 128; ++i) {
-            init[i][0] = ~0ull;
-            init[i][1] = 0ull;
-        }
-        return cudaMemcpyToSymbol(g_span, init, sizeof(init)) == cudaSuccess ? 0 : -1;
-    }
-    return cudaMemcpyFromSymbol(out, g_span, sizeof(unsigned long long) * 256) == cudaSuccess ? 0 : -1;
-}
 #endif
 
-int max_link_blocks(uint32_t tile_cap, bool turns) {
-    if (tile_cap <= (uint32_t)kDefaultTileWords) {
-        // five blocks of the default instance need more shared memory than
-        // the smallest L1/shared splits give
-        const void *fn = (const void *)link_instance<kDefaultTileWords>(turns);
-        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
-        return resident_blocks(fn, LinkLaunch<kDefaultTileWords>::kThreads);
-    }
-    // the large-tile instance needs more shared memory per block than the
-    // default L1/shared split leaves for four blocks; the largest shared
-    // share measured fastest on GB300 (config 3: 3.3e10 vs 2.4e10
-    // vehicle-updates/s with the default split)
-    const void *fn = (const void *)link_instance<kTileWords>(turns);
+int max_link_blocks(bool turns) {
+    // eight blocks of four warps per SM need the largest shared-memory share of L1
+    const void *fn = turns ? (const void *)turn_link_kernel : (const void *)link_kernel;
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    return resident_blocks(fn, LinkLaunch<kTileWords>::kThreads);
+    return resident_blocks(fn, kLinkBlock);
 }
 int max_node_blocks(bool turns) {
     return resident_blocks(turns ? (const void *)turn_node_kernel : (const void *)node_kernel, kNodeThreads);

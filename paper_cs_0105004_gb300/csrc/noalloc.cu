@@ -13,6 +13,7 @@
 // bitplanes) lives in one file-scope __device__ array, fixed in size, that
 // every device which loads this library holds until the process exits.
 #include <algorithm>
+#include <cuda.h>
 #include <mutex>
 #include <vector>
 
@@ -25,31 +26,66 @@ namespace {
 
 constexpr uint32_t kNoAllocMaxCells = 1u << 17;  // cells per lane
 constexpr uint32_t kNoAllocMaxSteps = 1024;      // steps per call
-constexpr uint32_t kNoAllocMaxTiles =  // 4096 columns in runs of kDefaultTileWords / lanes columns
-    (kNoAllocMaxCells / 32u + (uint32_t)(kDefaultTileWords / kMaxLanes) - 1u) / (uint32_t)(kDefaultTileWords / kMaxLanes);
-constexpr uint32_t kNoAllocMaxWords = kNoAllocMaxCells / 32u * (uint32_t)kMaxLanes;
+constexpr uint32_t kNoAllocMaxCols = kNoAllocMaxCells / 32u;
+constexpr uint32_t kNoAllocMaxTiles = (kNoAllocMaxCols + kWarpTileCols - 1) / kWarpTileCols;
+constexpr uint32_t kNoAllocMaxWords = kNoAllocMaxCols * (uint32_t)kMaxLanes;
 
 // Byte offsets inside the scratch array.
 constexpr size_t kOffTable = 0;
-constexpr size_t kOffCtrl = 256;
-constexpr size_t kOffLink = 512;
-constexpr size_t kOffCount = 768;
-constexpr size_t kOffTiles = 1024;
-constexpr size_t kOffStats = kOffTiles + ((sizeof(LinkTile) * kNoAllocMaxTiles + 255u) / 256u) * 256u;
+constexpr size_t kOffCtrl = 512;
+constexpr size_t kOffLink = 768;
+constexpr size_t kOffCount = 1024;
+constexpr size_t kOffTiles = 1280;
+constexpr size_t kOffCols = kOffTiles + ((sizeof(uint2) * kNoAllocMaxTiles + 255u) / 256u) * 256u;
+constexpr size_t kOffStats = kOffCols + sizeof(uint4) * kNoAllocMaxCols;
 constexpr size_t kOffPlanes = kOffStats + sizeof(StatRec) * kStatsRing;  // mov0, mov1, loc0, loc1
 constexpr size_t kScratchBytes = kOffPlanes + 4ull * 4ull * kNoAllocMaxWords;
 
-static_assert(sizeof(ScenDev) <= 256, "table entry fits its slot");
+static_assert(sizeof(ScenDev) <= 512, "table entry fits its slot");
 static_assert(sizeof(Ctrl) <= 256, "control block fits its slot");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// Device address of the scratch array for the context current on each
+// device ordinal (looked up once per device and context).
 std::mutex g_mu;
-std::vector<unsigned char *> g_scratch_ptr;  // per device ordinal, from cudaGetSymbolAddress
+struct ScratchAddr {
+    CUcontext ctx;
+    unsigned char *ptr;
+};
+std::vector<ScratchAddr> g_scratch;
+typedef CUresult (*CtxGetCurrent)(CUcontext *);
+CtxGetCurrent g_ctx_get = nullptr;
 
 ts_status bad(ts_status s, const char *msg) {
     set_last_error(msg);
     return s;
+}
+
+// Writes this call's scenario entry, control block, link record, tile list
+// and column table into the scratch (all of it rewritten by every call) and
+// clears the statistics ring.  One ring link of ncols columns and `lanes`
+// lanes: tiles of 32 columns (one tile if the ring has at most 32).
+__global__ void setup_ring(ScenDev sd, Ctrl ctrl, uint4 link, uint32_t ncols, uint32_t lanes, ScenDev *table,
+                           Ctrl *d_ctrl, uint4 *d_link, uint32_t *d_count, uint2 *tiles, uint4 *cols,
+                           StatRec *stats) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const uint32_t n_tiles = (ncols + kWarpTileCols - 1) / kWarpTileCols;
+    if (tid == 0) {
+        *table = sd;
+        *d_ctrl = ctrl;
+        *d_link = link;
+        *d_count = n_tiles;
+    }
+    for (uint32_t j = tid; j < ncols; j += nth)
+        cols[j] = make_uint4(j * lanes, 0u, j | (lanes << 20) | (1u << 23), link.y);
+    for (uint32_t i = tid; i < n_tiles; i += nth) {
+        const uint32_t c0 = i * kWarpTileCols;
+        const uint32_t n = ncols - c0 < (uint32_t)kWarpTileCols ? ncols - c0 : (uint32_t)kWarpTileCols;
+        tiles[i] = make_uint2((n - 1u) << 24, c0);
+    }
+    unsigned long long *z = reinterpret_cast<unsigned long long *>(stats);
+    for (uint32_t i = tid; i < kStatsRing * (uint32_t)(sizeof(StatRec) / 8); i += nth) z[i] = 0ull;
 }
 
 // Derives the moving and location bitplanes of the caller's state of step
@@ -158,52 +194,57 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     if (!dev_occ0 || !dev_occ1 || !dev_vel0 || !dev_vel1 || !dev_vid0 || !dev_vid1 || !dev_stats_out)
         return bad(TS_ERR_INVALID, "null buffer");
     if (n_steps == 0) return TS_OK;
+    // an error left pending by earlier work of the caller is reported as
+    // such, and not taken for a failure of this call's launches
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) return bad(TS_ERR_CUDA, "a CUDA error was pending before the call");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return bad(TS_ERR_CUDA, "cudaGetDevice failed");
     unsigned char *base = nullptr;
     {
-        // once per device, with that device current: the host-side name of the
-        // array is not a device address, so ask the runtime for it
+        // once per device and context, with that device current: the
+        // host-side name of the array is not a device address, so ask the
+        // runtime for it (again after the device's context was replaced, for
+        // example by cudaDeviceReset)
         std::lock_guard<std::mutex> lock(g_mu);
-        if ((size_t)dev >= g_scratch_ptr.size()) g_scratch_ptr.resize((size_t)dev + 1, nullptr);
-        if (!g_scratch_ptr[dev]) {
+        CUcontext ctx = nullptr;
+        if (g_ctx_get == nullptr) {
+            // the driver's cuCtxGetCurrent through the runtime (the library
+            // does not link the driver library itself)
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                g_ctx_get = reinterpret_cast<CtxGetCurrent>(fn);
+        }
+        if (g_ctx_get == nullptr || g_ctx_get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+        if ((size_t)dev >= g_scratch.size()) g_scratch.resize((size_t)dev + 1, ScratchAddr{nullptr, nullptr});
+        ScratchAddr &sa = g_scratch[dev];
+        if (!sa.ptr || ctx == nullptr || sa.ctx != ctx) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
                 return bad(TS_ERR_CUDA, "cudaGetSymbolAddress failed");
-            g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+            sa.ptr = static_cast<unsigned char *>(p);
+            sa.ctx = ctx;
         }
-        base = g_scratch_ptr[dev];
+        base = sa.ptr;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     ScenDev *d_table = reinterpret_cast<ScenDev *>(base + kOffTable);
     Ctrl *d_ctrl = reinterpret_cast<Ctrl *>(base + kOffCtrl);
     uint4 *d_link = reinterpret_cast<uint4 *>(base + kOffLink);
-    LinkTile *d_tiles = reinterpret_cast<LinkTile *>(base + kOffTiles);
+    uint2 *d_tiles = reinterpret_cast<uint2 *>(base + kOffTiles);
+    uint4 *d_cols = reinterpret_cast<uint4 *>(base + kOffCols);
     uint32_t *d_count = reinterpret_cast<uint32_t *>(base + kOffCount);
     StatRec *d_stats = reinterpret_cast<StatRec *>(base + kOffStats);
     uint32_t *d_planes = reinterpret_cast<uint32_t *>(base + kOffPlanes);
 
-    // tiles: the whole ring if it fits one tile, else runs of columns whose
-    // halos wrap around the ring
     const uint32_t ncols = cells / 32u, words = ncols * lanes;
-    std::vector<LinkTile> tiles;
-    if (words <= (uint32_t)kDefaultTileWords) {
-        LinkTile t;
-        t.a = make_uint4(0u, 0u, 1u, 0u);
-        t.b = make_uint4(0u, words, 0u, 0u);
-        tiles.push_back(t);
-    } else {
-        const uint32_t per = (uint32_t)kDefaultTileWords / lanes;
-        for (uint32_t j = 0; j < ncols; j += per) {
-            LinkTile t;
-            t.a = make_uint4(0u, 0u, kPartial | j, j + per < ncols ? j + per : ncols);
-            t.b = make_uint4(0u, cells, lanes | (1u << 8), 0u);
-            tiles.push_back(t);
-        }
-    }
-    if (tiles.size() > kNoAllocMaxTiles) return bad(TS_ERR_INVALID, "ring too large");
+    const uint32_t n_tiles = (ncols + kWarpTileCols - 1) / kWarpTileCols;
     ScenDev sd{};
     sd.lk_info = d_link;
+    sd.col_info = d_cols;
+    sd.n_cols = ncols;
     sd.occ[0] = dev_occ0;
     sd.occ[1] = dev_occ1;
     sd.mov[0] = d_planes;
@@ -227,24 +268,24 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     ctrl.base = first_step;
     ctrl.target = first_step + n_steps;
     const uint4 link = make_uint4(0u, cells, lanes | (1u << 8), 0u);
-    const uint32_t n_tiles = (uint32_t)tiles.size();
-    // the scratch keeps the previous call's contents: rewrite all of it that
-    // this call reads, and clear the statistics and running values it
-    // accumulates into
-    if (cudaMemcpyAsync(d_table, &sd, sizeof(sd), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_ctrl, &ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_link, &link, sizeof(link), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_count, &n_tiles, sizeof(n_tiles), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(LinkTile) * tiles.size(), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemsetAsync(d_stats, 0, sizeof(StatRec) * kStatsRing, s) != cudaSuccess)
-        return bad(TS_ERR_CUDA, "scratch set-up copy failed");
+    // the scratch keeps the previous call's contents: the set-up kernel
+    // rewrites all of it that this call reads (its arguments travel by value,
+    // no host buffer is involved) and clears the statistics it accumulates
+    // into; every launch is checked as it is made
     const uint32_t cur = (uint32_t)(first_step & 1ull), fin = (uint32_t)((first_step + n_steps) & 1ull);
+    setup_ring<<<32, 256, 0, s>>>(sd, ctrl, link, ncols, lanes, d_table, d_ctrl, d_link, d_count, d_tiles, d_cols,
+                                  d_stats);
+    if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "set-up kernel launch failed");
     prep_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, lanes, words, cur);
-    const int grid = std::max(1, std::min<int>((int)tiles.size(), max_link_blocks(kDefaultTileWords, false)));
-    for (uint32_t i = 0; i < n_steps; ++i)
-        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false, false, kDefaultTileWords, false);
+    if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");
+    const int want = (int)((n_tiles + kLinkWarpsPerBlock - 1) / kLinkWarpsPerBlock);
+    const int grid = std::max(1, std::min<int>(want, max_link_blocks(false)));
+    for (uint32_t i = 0; i < n_steps; ++i) {
+        launch_link_kernel(d_table, d_tiles, d_count, i, grid, s, false, false, false);
+        if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "step kernel launch failed");
+    }
     finish_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, words, fin);
+    if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");
     gather_ring_stats<<<1, kNoAllocMaxSteps, 0, s>>>(d_stats, d_ctrl, first_step, n_steps, dev_stats_out);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");
     return TS_OK;

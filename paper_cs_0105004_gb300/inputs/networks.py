@@ -549,3 +549,81 @@ def config3_scenario(i: int, demand_scale: float = 1.0, steps: int = 3600) -> Sc
         return net, _demand(net, o, d, dep)
     net, dem = _cached(f"config3-v1-{i}-{demand_scale}", make)
     return Scenario(f"config3[{i}]", net, dem, steps=steps, seed=1000 + i)
+
+
+# ---------------------------------------------------------------- a loaded network state
+
+def loaded_state(sc: Scenario, step: int, seed: int, jam_share: float = 0.3,
+                 buffer_share: float = 0.5) -> InitialState:
+    """A seeded state of scenario `sc` at `step` with its traffic on the network.
+
+    Stands in for a peak-hour state (the paper's step time grows with
+    congestion, Sec. 8) without running any simulation: it places vehicles,
+    it evaluates no driving rule.  Every trip whose departure step is before
+    `step` has left its queue; it sits on a link of its route drawn
+    uniformly (its cursor).  A share `jam_share` of the links hold their
+    vehicles as a queue packed from the link end backwards over the lanes,
+    with v = 0, and each lane of such a link hands its front vehicle to the
+    lane's link-end buffer with probability `buffer_share` (if that vehicle
+    has a next link); the other links hold theirs in distinct cells drawn
+    uniformly, with v uniform in 0..vmax.  Vehicles for which a link has no
+    cell left count as arrived.
+    """
+    net, dem = sc.net, sc.demand
+    rng = np.random.default_rng(seed)
+    n = dem.n
+    off = dem.route_offsets.astype(np.int64)
+    rlen = np.diff(off)
+    departed = np.nonzero(dem.depart_step < step)[0]
+    cursor = np.zeros(n, np.uint32)
+    cur = np.floor(rng.random(departed.size) * rlen[departed]).astype(np.int64)
+    cursor[departed] = cur
+    link_of = dem.route_links[off[departed] + cur].astype(np.int64)
+    L = net.n_links
+    cells = net.link_cells.astype(np.int64)
+    lanes = net.link_lanes.astype(np.int64)
+    jam = (rng.random(L) < jam_share) & (net.link_ring == 0)
+    # every lane-cell of every link, ranked within its link: from the link end
+    # backwards over the lanes on a jammed link, in a random order elsewhere
+    lb, cb = net.lane_base(), net.lane_cell_base()
+    C = int(cb[-1])
+    lane_of_cell = np.repeat(np.arange(net.n_lanes), np.diff(cb))
+    lane_link = np.repeat(np.arange(L), lanes)
+    cl = lane_link[lane_of_cell]
+    ck = lane_of_cell - lb[cl]
+    cx = np.arange(C, dtype=np.int64) - cb[lane_of_cell]
+    key = np.where(jam[cl], (cells[cl] - 1 - cx) * lanes[cl] + ck, rng.random(C) * cells[cl] * lanes[cl])
+    order = np.lexsort((key, cl))
+    first = np.zeros(L + 1, np.int64)
+    np.cumsum(cells * lanes, out=first[1:])
+    # vehicles of each link in a random order, matched to its ranked cells
+    vorder = np.lexsort((rng.random(departed.size), link_of))
+    vl = link_of[vorder]
+    vstart = np.searchsorted(vl, np.arange(L))
+    rank = np.arange(departed.size) - vstart[vl]
+    fits = rank < cells[vl] * lanes[vl]
+    ids = departed[vorder][fits]
+    slot = order[first[vl[fits]] + rank[fits]]
+    cell_id = np.full(C, -1, np.int32)
+    cell_v = np.zeros(C, np.int8)
+    cell_id[slot] = ids
+    v = rng.integers(0, sc.vmax + 1, ids.size)
+    cell_v[slot] = np.where(jam[cl[slot]], 0, v).astype(np.int8)
+    # front vehicles of jammed lanes into the link-end buffers
+    buf_id = np.full(net.n_lanes, -1, np.int32)
+    buf_v = np.zeros(net.n_lanes, np.int8)
+    front = cb[1:] - 1                      # last cell of every lane
+    fid = cell_id[front]
+    lane_l = lane_link
+    take = (fid >= 0) & jam[lane_l] & (rng.random(net.n_lanes) < buffer_share)
+    take &= cursor[np.maximum(fid, 0)] + 1 < rlen[np.maximum(fid, 0)]
+    buf_id[take] = fid[take]
+    cell_id[front[take]] = -1
+    cell_v[front[take]] = 0
+    # departure queues: entries with departure step before `step` have left
+    first_link = dem.route_links[off[:-1]].astype(np.int64)
+    dep_head = np.bincount(first_link[departed], minlength=L).astype(np.uint32)
+    on = int(ids.size)
+    return InitialState(cell_id=cell_id, cell_v=cell_v, buf_id=buf_id, buf_v=buf_v, cursor=cursor,
+                        dep_head=dep_head, step=int(step), arrived=int(departed.size - on),
+                        inserted=int(departed.size))

@@ -114,6 +114,8 @@ _API = {
     "ts_launches_per_step": (ctypes.c_uint32, []),
     "ts_philox_words": (ctypes.c_int, [ctypes.c_uint32, u32p, u32p, ctypes.c_uint64, u32p]),
     "ts_set_load_balance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
+    "ts_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_read_kernel_times": (ctypes.c_int, [ctypes.c_void_p, u64p, ctypes.c_uint32, ctypes.c_uint32]),
     "ts_ring_step_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Params), ctypes.c_uint64,
                                             ctypes.c_uint32] + [ctypes.c_void_p] * 8),
 }
@@ -289,6 +291,17 @@ class Simulation:
         _check(lib().ts_read_link_times(self.h, tsum.ctypes.data_as(ctypes.c_void_p),
                                         tcnt.ctypes.data_as(ctypes.c_void_p), timeout_ms))
         return tsum, tcnt
+
+    def set_kernel_timing(self, on: bool):
+        """Launches of later ts_step calls record their spans inside the graphs."""
+        _check(lib().ts_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self, reset: bool = False, timeout_ms: int = 600000) -> dict:
+        """Summed in-graph durations: link/node kernel seconds and launch counts."""
+        out = np.zeros(4, np.uint64)
+        _check(lib().ts_read_kernel_times(self.h, _p(out, ctypes.c_uint64), 1 if reset else 0, timeout_ms))
+        return {"link_s": int(out[0]) * 1e-9, "link_launches": int(out[1]),
+                "node_s": int(out[2]) * 1e-9, "node_launches": int(out[3])}
 
     def set_step_mode(self, mode: int):
         """STEP_AUTO, STEP_FUSED or STEP_SPLIT; results do not depend on it."""

@@ -5,6 +5,8 @@ velocities, 32-bit Philox words against an integer threshold, 64-bit digest
 sums), so the CUDA library and the oracle must agree on every field of every
 step and on the full state.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -373,30 +375,6 @@ def test_config1_busy_window_from_the_oracle_state():
 
 # ------------------------------------------------------------------ full-size networks of the other workloads
 
-def test_config3_batch_members_match_oracle():
-    # the batching workload's launch configuration: the first 16 full-size
-    # grid scenarios of its 256-member batch in one batch, 256-word tiles (the
-    # autotuner's pick), split steps; the largest (1.85 M lane-cells), the
-    # densest (483 k trips) and the smallest member checked step by step
-    # against the oracle
-    import torch
-    from paper_cs_0105004_gb300 import batching as Bt
-    steps = 360
-    scs = [N.config3_scenario(i) for i in range(16)]
-    sims = Bt.make_members(scs, tile_words=256)
-    b = T.Batch(len(sims))
-    b.add_many(sims, steps)
-    stream = torch.cuda.Stream()
-    b.step(steps, stream)
-    b.sync()
-    for i in (1, 4, 7):
-        orc = oracle.Oracle(scs[i])
-        _cmp_stats(sims[i].stats_range(0, steps), orc.step(steps), f"config3 member {i}")
-        _cmp_state(sims[i].read_state(), orc.get_state(), f"config3 member {i} after step {steps - 1}")
-        orc.close()
-    b.close()
-
-
 def test_config2_network_with_a_trip_sample_matches_oracle():
     # the full config-2 network (200,000 links, 18.2 M lane-cells) with a
     # sample of its 2 M trips: those whose origin is among the first 1,500
@@ -422,3 +400,118 @@ def test_config2_network_with_a_trip_sample_matches_oracle():
     assert int(g["active"][-1]) > 10_000
     sim.close()
     orc.close()
+
+
+# ------------------------------------------------------------------ the loaded regime
+
+def test_config1_departure_peak_from_the_oracle_state():
+    # full-size config 1 from the oracle's own state at step 5,400, the
+    # departure peak (most of the network jammed), 300 steps on both sides
+    # with the bench's load balancing
+    sc = N.config1()
+    orc = oracle.Oracle(sc)
+    orc.step(5400)
+    s = orc.get_state()
+    init = N.InitialState(**{k: s[k] for k in ("cell_id", "cell_v", "buf_id", "buf_v", "cursor", "dep_head")},
+                          step=s["step"], arrived=s["arrived"], inserted=s["inserted"])
+    sim = T.Simulation(sc)
+    sim.set_load_balance(64, 768)
+    sim.write_state(init)
+    sim.step(300)
+    g = sim.stats_range(5400, 300)
+    _cmp_stats(g, orc.step(300), "config1 from step 5400")
+    _cmp_state(sim.read_state(), orc.get_state(), "config1 after step 5699")
+    assert int(g["active"].min()) > 50_000
+    sim.close()
+    orc.close()
+
+
+def test_config2_full_demand_peak_window():
+    # the full config-2 network with all 2 M trips, from the seeded
+    # peak-hour state at step 5,400 that both sides load (about 618 k
+    # vehicles on links, a third of the links queued to their end, link-end
+    # buffers taken); 300 steps with the bench's tiles and re-tiling every
+    # 64 steps, so tiles at the 768-vehicle budget are compared too
+    import dataclasses
+    sc = N.config2()
+    scl = dataclasses.replace(sc, init=N.loaded_state(sc, 5400, seed=7))
+    orc = oracle.Oracle(scl)
+    st0 = orc.get_state()
+    sim = T.Simulation(scl, tile_words=128)
+    sim.set_load_balance(64, 768)
+    _cmp_state(sim.read_state(), st0, "config2 peak state as loaded")
+    sim.step(300)
+    g = sim.stats_range(5400, 300)
+    o = orc.step(300)
+    _cmp_stats(g, o, "config2 from the peak state")
+    s = orc.get_state()
+    _cmp_state(sim.read_state(), s, "config2 after step 5699")
+    check_invariants(scl, s, o[-1])
+    assert int(g["active"].min()) > 500_000 and int(g["transfers"].sum()) > 10_000
+    sim.close()
+    orc.close()
+
+
+def _oracle_member(i, steps):
+    import oracle as O
+    sc = N.config3_scenario(i)
+    orc = O.Oracle(sc)
+    st = orc.step(steps)
+    s = orc.get_state()
+    orc.close()
+    return st, s
+
+
+def test_config3_all_16_batch_members_match_oracle():
+    # every member of the 16-scenario batch against the oracle (oracle runs in
+    # spawned worker processes)
+    import multiprocessing as mp
+    import torch
+    from paper_cs_0105004_gb300 import batching as Bt
+    steps = 360
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        ref = pool.starmap(_oracle_member, [(i, steps) for i in range(16)])
+    scs = [N.config3_scenario(i) for i in range(16)]
+    sims = Bt.make_members(scs, tile_words=128)
+    b = T.Batch(len(sims))
+    b.add_many(sims, steps)
+    stream = torch.cuda.Stream()
+    b.step(steps, stream)
+    b.sync()
+    for i in range(16):
+        _cmp_stats(sims[i].stats_range(0, steps), ref[i][0], f"config3 member {i}")
+        _cmp_state(sims[i].read_state(), ref[i][1], f"config3 member {i} after step {steps - 1}")
+    b.close()
+
+
+def test_three_lane_circle_on_the_gpu():
+    # the 3-lane circle of Sec. 5 at density 0.2 and p = 0.2 (the oracle pin
+    # checks its flow per lane against the 1-lane circle): GPU = oracle
+    sc = _ring(1024, int(0.2 * 1024 * 3), 3, N.P_THRESHOLD_0_2, rng_seed=11)
+    o = run_parity(sc, 2000, chunk=500, state_every=1000)
+    assert int(o["lane_changes"].sum()) > 0
+
+
+def test_kernel_spans_inside_the_graphs():
+    # kernel timing on: the same results, one link and one node launch per
+    # step, and the summed spans inside the CUDA-event time of the run
+    import torch
+    sc = N.config0()
+    sim = T.Simulation(sc)
+    sim.step(640)
+    ref = sim.stats_range(0, 640)
+    sim.reset()
+    sim.set_kernel_timing(True)
+    s = torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    sim.step(640, s)
+    b.record(s)
+    b.synchronize()
+    kt = sim.kernel_times()
+    _cmp_stats(sim.stats_range(0, 640), ref, "with kernel spans")
+    assert kt["link_launches"] == 640 and kt["node_launches"] == 640
+    assert 0 < kt["link_s"] + kt["node_s"] <= a.elapsed_time(b) / 1000.0
+    sim.kernel_times(reset=True)
+    assert sim.kernel_times()["link_launches"] == 0
+    sim.close()

@@ -738,10 +738,11 @@ def main():
     ap.add_argument("--tune-sample", type=int, default=32, help="config3: members used by the autotuner")
     ap.add_argument("--seq-sample", type=int, default=256, help="config3: members run one by one for comparison")
     ap.add_argument("--rate", type=float, default=20.0, help="config4: job arrivals per second")
-    ap.add_argument("--duration", type=float, default=60.0, help="config4: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=600.0, help="config4: seconds of arrivals")
     ap.add_argument("--time-scale", type=float, default=1.0, help="config4: arrival clock factor")
     ap.add_argument("--serve-mix", type=float, nargs=3, default=[60, 10, 30], help="config4: config0 config1 grid")
-    ap.add_argument("--grid-pool", type=int, default=16, help="config4: distinct grid networks")
+    ap.add_argument("--grid-pool", type=int, default=256,
+                    help="config4: distinct grid networks (the config-3 members), each job with its own seed")
     ap.add_argument("--budget-gb", type=float, default=160.0, help="config4: device memory for jobs")
     ap.add_argument("--chunk", type=int, default=128, help="config4: steps per batch step")
     ap.add_argument("--serve-compare", type=int, default=1, help="config4: also serve the stream one job at a time")

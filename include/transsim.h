@@ -320,7 +320,7 @@ uint32_t ts_tile_words(const ts_ctx *ctx);
  * statistics of steps first_step .. first_step+n_steps-1 (buffered, waiting,
  * arrived, transfers and inserted are 0 on a ring).  Asynchronous on
  * cuda_stream; device consistency flags are not reported by this call.
- * Scratch: a fixed array of about 790 KB in device memory, held by every
+ * Scratch: a fixed array of about 900 KB in device memory, held by every
  * device that loads the library until the process exits.  All calls share
  * it, so calls that overlap on the GPU (other streams, other threads) race;
  * each call rewrites and clears what it uses.  The first call on a device

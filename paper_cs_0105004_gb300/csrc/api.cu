@@ -92,6 +92,7 @@ struct ts_ctx {
     // network (host copies)
     uint32_t n_nodes = 0, n_links = 0, n_ring = 0;
     std::vector<uint32_t> from, to, cells, lanes, ncols, wbase, bpos, lane_base, col_base;
+    std::vector<uint32_t> sig_cycle_green, sig_offset;  // per link: cycle | green << 16, offset (0: no signal)
     std::vector<uint8_t> ring;
     std::vector<uint64_t> cell_base;
     std::vector<uint32_t> node_in_off;
@@ -435,13 +436,17 @@ ts_status upload_lk_info(ts_ctx *c) {
     for (uint32_t l = 0; l < c->n_links; ++l)
         li[l] = make_uint4(c->wbase[l], c->cells[l], c->lanes[l] | ((uint32_t)c->ring[l] << 8), c->bpos[l]);
     CK(cudaMemcpy(c->d_lk_info, li.data(), sizeof(uint4) * c->n_links, cudaMemcpyHostToDevice));
-    // per column: word of lane 0, link, j | lanes << 20 | ring << 23, cells
-    std::vector<uint4> ci(std::max<uint32_t>(c->n_cols, 1u));
+    // per column: word of lane 0, link, j | lanes << 20 | ring << 23, cells;
+    // and its link's first link-end buffer and signal
+    std::vector<uint4> ci(std::max<uint32_t>(c->n_cols, 1u)), ca(ci.size(), make_uint4(0u, 0u, 0u, 0u));
     for (uint32_t l = 0; l < c->n_links; ++l)
-        for (uint32_t j = 0; j < c->ncols[l]; ++j)
+        for (uint32_t j = 0; j < c->ncols[l]; ++j) {
             ci[c->col_base[l] + j] = make_uint4(c->wbase[l] + j * c->lanes[l], l,
                                                 j | (c->lanes[l] << 20) | ((uint32_t)c->ring[l] << 23), c->cells[l]);
+            ca[c->col_base[l] + j] = make_uint4(c->bpos[l], c->sig_cycle_green[l], c->sig_offset[l], 0u);
+        }
     CK(cudaMemcpy(const_cast<uint4 *>(c->sd.col_info), ci.data(), sizeof(uint4) * ci.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(const_cast<uint4 *>(c->sd.col_aux), ca.data(), sizeof(uint4) * ca.size(), cudaMemcpyHostToDevice));
     return TS_OK;
 }
 
@@ -656,6 +661,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     auto &A = c->allocs;
     c->d_lk_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint4 *col_info = alloc_in<uint4>(c.get(), A, c->n_cols, ok);
+    uint4 *col_aux = alloc_in<uint4>(c.get(), A, c->n_cols, ok);
     uint4 *nd_info = alloc_in<uint4>(c.get(), A, L, ok);
     uint2 *sig_info = desc->link_signal ? alloc_in<uint2>(c.get(), A, L, ok) : nullptr;
     uint8_t *slot_gap = desc->link_yield ? alloc_in<uint8_t>(c.get(), A, c->n_slots, ok) : nullptr;
@@ -682,6 +688,7 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     ScenDev &sd = c->sd;
     sd.lk_info = c->d_lk_info;
     sd.col_info = col_info;
+    sd.col_aux = col_aux;
     sd.n_cols = c->n_cols;
     sd.nd_info = nd_info;
     sd.sig_info = sig_info;
@@ -710,6 +717,13 @@ ts_status ts_create_network(const ts_network_desc *desc, const ts_params *params
     sd.lane_change = params->lane_change ? 1u : 0u;
     sd.n_links = L;
     sd.n_sub = c->n_sub;
+    c->sig_cycle_green.assign(L, 0u);
+    c->sig_offset.assign(L, 0u);
+    if (desc->link_signal)
+        for (uint32_t l = 0; l < L; ++l) {
+            c->sig_cycle_green[l] = desc->link_signal[3 * l] | (desc->link_signal[3 * l + 1] << 16);
+            c->sig_offset[l] = desc->link_signal[3 * l + 2];
+        }
     st = upload_lk_info(c.get());
     if (st != TS_OK) return st;
     for (uint32_t *p : {occ0, occ1, mov0, mov1, loc0, loc1}) CK(cudaMemset(p, 0, 4ull * c->n_words));

@@ -55,7 +55,7 @@ constexpr uint32_t kIdMask = 0x7FFFFFFFu;
 constexpr uint32_t kMaxCells = 1u << 22;      // cells per link (buffer digest packs 22 bits)
 constexpr int kTileWords = 256;               // tile_words setting: at most
 constexpr int kDefaultTileWords = 128;        // default: occupancy words (columns x lanes) per warp tile
-constexpr int kWarpTileCols = 32;             // columns per warp tile (one per lane)
+constexpr int kWarpTileCols = 30;             // columns per warp tile (lanes 1..30; lanes 0, 31: halos)
 constexpr int kLinkWarpsPerBlock = 4;         // warps of one link-kernel block
 constexpr int kNodeThreads = 128;
 constexpr uint32_t kStatsRing = 4096;         // steps of statistics kept on the device
@@ -106,6 +106,7 @@ struct ScenDev {
     const uint4 *lk_info;         // x wbase, y cells, z lanes | ring << 8, w slot base
     const uint4 *col_info;        // per column (link-major, then j): x word of lane 0, y link,
                                   // z j | lanes << 20 | ring << 23, w link cells
+    const uint4 *col_aux;         // per column: x first link-end buffer of its link, y z its signal, w 0
     uint32_t n_cols;
     const uint4 *nd_info;         // per link m: x first slot of from(m), y wbase, z slot count | lanes << 8 |
                                   // priority slots << 16, w dep end

@@ -271,22 +271,22 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
 
 // ------------------------------------------------------------------ link kernel
 //
-// A warp advances one warp tile at a time: up to 32 consecutive columns of
-// one scenario in col_info order (link-major, then column j), lane t owning
-// column t with all its lanes.  In the warp's shared-memory rows, slot
-// s = t + 1 holds column t, slot 0 the column left of the first one (left
-// halo) and slot n + 1 the column right of the last one (right halo), each
-// present only where such a neighbour exists outside the tile.  The phases
-// of a tile are separated by __syncwarp, never by a block barrier, so every
-// warp runs its own chain of dependent loads.  The host builds the tiles so
-// that a ring of at most 32 columns lies inside one tile (longer rings get
-// tiles of their own), and so that a link's last column is never separated
-// from the column before it when it holds at most 2*vmax cells: a halo then
-// never lies within vmax cells of a link end, and the vehicle that enters a
-// link-end buffer is handled by the warp that owns the buffer.
+// A warp advances one warp tile at a time: up to 30 consecutive columns of
+// one scenario in col_info order (link-major, then column j).  Every lane
+// owns one slot of the warp's shared-memory rows: lanes 1..n the tile's
+// columns, lane 0 the column left of the first one (left halo) and lane
+// n + 1 the column right of the last one (right halo), the halos present
+// only where such a neighbour exists outside the tile.  A lane handles all
+// lanes of its column.  The phases of a tile are separated by __syncwarp,
+// never by a block barrier, so every warp runs its own chain of dependent
+// loads.  The host builds the tiles so that a ring of at most 30 columns
+// lies inside one tile (longer rings get tiles of their own), and so that a
+// link's last column is never separated from the column before it when it
+// holds at most 2*vmax cells: the cells of a halo that the tile looks at
+// are then never within vmax cells of a link end, and the vehicle that
+// enters a link-end buffer is handled by the warp that owns the buffer.
 
-constexpr int kWarpCols = 32;
-constexpr int kSlots = kWarpCols + 2;
+constexpr int kSlots = 32;  // slot = lane
 constexpr int kRowWords = kMaxLanes * kSlots;
 constexpr int kCodes = 256;  // listed vehicles per round of a warp
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
@@ -368,16 +368,16 @@ __device__ __forceinline__ uint32_t near_mask(uint32_t ring, uint32_t cells, uin
     return thr <= 0 ? 0xFFFFFFFFu : (thr >= 32 ? 0u : ~((1u << thr) - 1u));
 }
 
-// Runs `proc(code)` for every set bit of the lanes' word masks m[0..7]
-// (word index idx[q] of each), the warp's lanes sharing the work: rounds of
-// at most kCodes listed vehicles go through the warp's code list.
+// Runs `proc(code)` for every set bit of the lanes' word masks m[k] (word
+// (k, slot) of the lane's own slot), the warp's lanes sharing the work:
+// rounds of at most kCodes listed vehicles go through the warp's code list.
 template <class F>
-__device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[8], const int (&idx)[8], F &&proc) {
+__device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[kMaxLanes], int slot, F &&proc) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         uint32_t cnt = 0u;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) cnt += (uint32_t)__popc(m[q]);
+        for (int q = 0; q < kMaxLanes; ++q) cnt += (uint32_t)__popc(m[q]);
         uint32_t inc = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -388,11 +388,11 @@ __device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[8], const i
         if (total == 0u) break;
         uint32_t pos = inc - cnt;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < kMaxLanes; ++q) {
             while (m[q] && pos < (uint32_t)kCodes) {
                 const int b = __ffs(m[q]) - 1;
                 m[q] &= m[q] - 1u;
-                S.code[pos++] = (uint16_t)((idx[q] << 5) | b);
+                S.code[pos++] = (uint16_t)((wi(q, slot) << 5) | b);
             }
         }
         __syncwarp();
@@ -571,101 +571,80 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         for (int f = 0; f < 7; ++f) acc[f] = 0u;
         acc_hash = 0ull;
     };
-    pdl_trigger();
     bool waited = false;
     const uint32_t nwarps = gridDim.x * (uint32_t)NW;
+    const int s = lane;  // this lane's slot
     for (uint32_t tile = blockIdx.x * (uint32_t)NW + (uint32_t)warp; tile < n_tiles; tile += nwarps) {
+        // the next kernel may launch once every block has begun its last
+        // round of tiles (warp 0 has the most tiles of its block): launched
+        // earlier, its waiting blocks would hold registers and shared memory
+        // this launch still needs
+        if (warp == 0 && tile + nwarps >= n_tiles) pdl_trigger();
         const uint2 td = tiles[tile];
         const ScenDev &D = table[td.x & 0xFFFFFFu];
         if (D.ctrl == nullptr) continue;
         const int n = (int)(td.x >> 24) + 1;
         const uint32_t cb = td.y;
         const uint32_t vmax = D.vmax;
-        const int s = lane + 1;
-        const bool mine = lane < n;
 
-        // ---------------- geometry (static data: read before waiting)
-        uint32_t cw = kNoSlot, link = 0u, j = 0u, lanes = 0u, ring = 0u, cells = 0u, ncl = 0u, bpos = 0u;
-        uint2 sig = make_uint2(0u, 0u);
-        bool first = false, end = false;
-        if (mine) {
-            const uint4 ci = D.col_info[cb + (uint32_t)lane];
-            cw = ci.x;
-            link = ci.y;
-            j = ci.z & 0xFFFFFu;
-            lanes = (ci.z >> 20) & 7u;
-            ring = (ci.z >> 23) & 1u;
-            cells = ci.w;
-            ncl = (cells + 31u) >> 5;
-            first = !ring && j == 0u;
-            end = !ring && j + 1u == ncl;
-            int left, right;
-            if (j > 0u) left = lane > 0 ? s - 1 : 0;
-            else if (ring) left = lane + (int)ncl <= n ? lane + (int)ncl : 0;
-            else left = -1;
-            if (j + 1u < ncl) right = lane + 1 < n ? s + 1 : n + 1;
-            else if (ring) right = lane - (int)j >= 0 ? lane - (int)j + 1 : n + 1;
-            else right = -1;
-            const uint32_t near = near_mask(ring, cells, 32u * j, vmax);
-            if (near || end) {
-                bpos = D.lk_info[link].w;
-                if (D.sig_info) sig = D.sig_info[link];
+        // ---------------- geometry (static data: read before waiting).  The
+        // halo lanes read the column next to theirs and step to their own.
+        const bool core = lane >= 1 && lane <= n, lh = lane == 0, rh = lane == n + 1;
+        uint4 ci = make_uint4(0u, 0u, 0u, 0u), ca = make_uint4(0u, 0u, 0u, 0u);
+        if (core || lh || rh) ci = D.col_info[core ? cb + (uint32_t)lane - 1u : (lh ? cb : cb + (uint32_t)n - 1u)];
+        if (core) ca = D.col_aux[cb + (uint32_t)lane - 1u];
+        uint32_t cw = ci.x, j = ci.z & 0xFFFFFu;
+        const uint32_t link = ci.y, lanes = (ci.z >> 20) & 7u, ring = (ci.z >> 23) & 1u, cells = ci.w;
+        const uint32_t ncl = (cells + 31u) >> 5;
+        int left = -1, right = -1;
+        bool exists = core;
+        if (core) {
+            if (j > 0u) left = lane - 1;  // lane - 1 = 0: the left halo
+            else if (ring) left = lane + (int)ncl - 1 <= n ? lane + (int)ncl - 1 : 0;
+            if (j + 1u < ncl) right = lane + 1;  // lane + 1 = n + 1: the right halo
+            else if (ring) right = lane - (int)j >= 1 ? lane - (int)j : n + 1;
+        } else if (lh) {
+            // left of the first column: its column j - 1, or the ring's last
+            // column when the ring does not fit the tile
+            if (j > 0u) {
+                exists = true;
+                j -= 1u;
+                cw -= lanes;
+            } else if (ring && ncl > (uint32_t)n) {
+                exists = true;
+                j = ncl - 1u;
+                cw += (ncl - 1u) * lanes;
             }
-            S.cw[s] = cw;
-            S.cx0[s] = 32u * j;
-            S.ccells[s] = cells;
-            S.clink[s] = link;
-            S.cnear[s] = near;
-            S.cbpos[s] = bpos;
-            S.cleft[s] = (int8_t)left;
-            S.cright[s] = (int8_t)right;
-            S.clanes[s] = (uint8_t)lanes;
-            S.cring[s] = (uint8_t)ring;
-            S.ckind[s] = 0;
-            S.cexit[s] = 0;
-            S.cgreen[s] = 1;
-            // the halo columns, one lane each
-            if (lane == 0) {
-                uint32_t hw = kNoSlot, hj = 0u;
-                if (left == 0) {
-                    hj = j > 0u ? j - 1u : ncl - 1u;
-                    hw = j > 0u ? cw - lanes : cw + (ncl - 1u) * lanes;
-                }
-                S.cw[0] = hw;
-                S.cx0[0] = 32u * hj;
-                S.ccells[0] = cells;
-                S.clink[0] = link;
-                S.cnear[0] = near_mask(ring, cells, 32u * hj, vmax);
-                S.cbpos[0] = 0u;
-                S.cleft[0] = -1;
-                S.cright[0] = 1;
-                S.clanes[0] = (uint8_t)lanes;
-                S.cring[0] = (uint8_t)ring;
-                S.ckind[0] = 1;
-                S.cexit[0] = 0;
-                S.cgreen[0] = 1;
+            right = 1;
+        } else if (rh) {
+            if (j + 1u < ncl) {
+                exists = true;
+                j += 1u;
+                cw += lanes;
+            } else if (ring && j + 1u > (uint32_t)n) {
+                exists = true;
+                cw -= j * lanes;
+                j = 0u;
             }
-            if (lane == n - 1) {
-                uint32_t hw = kNoSlot, hj = 0u;
-                if (right == n + 1) {
-                    hj = j + 1u < ncl ? j + 1u : 0u;
-                    hw = j + 1u < ncl ? cw + lanes : cw - j * lanes;
-                }
-                S.cw[n + 1] = hw;
-                S.cx0[n + 1] = 32u * hj;
-                S.ccells[n + 1] = cells;
-                S.clink[n + 1] = link;
-                S.cnear[n + 1] = near_mask(ring, cells, 32u * hj, vmax);
-                S.cbpos[n + 1] = 0u;
-                S.cleft[n + 1] = (int8_t)n;
-                S.cright[n + 1] = -1;
-                S.clanes[n + 1] = (uint8_t)lanes;
-                S.cring[n + 1] = (uint8_t)ring;
-                S.ckind[n + 1] = 2;
-                S.cexit[n + 1] = 0;
-                S.cgreen[n + 1] = 1;
-            }
+            left = n;
         }
+        const uint32_t kind = core ? 0u : (lh ? 1u : 2u);
+        const uint32_t near = exists ? near_mask(ring, cells, 32u * j, vmax) : 0u;
+        const bool first = core && !ring && j == 0u, end = core && !ring && j + 1u == ncl;
+        const uint32_t bpos = ca.x;
+        S.cw[s] = exists ? cw : kNoSlot;
+        S.cx0[s] = 32u * j;
+        S.ccells[s] = cells;
+        S.clink[s] = link;
+        S.cnear[s] = near;
+        S.cbpos[s] = bpos;
+        S.cleft[s] = (int8_t)left;
+        S.cright[s] = (int8_t)right;
+        S.clanes[s] = (uint8_t)(exists ? lanes : 0u);
+        S.cring[s] = (uint8_t)ring;
+        S.ckind[s] = (uint8_t)kind;
+        S.cexit[s] = 0;
+        S.cgreen[s] = 1;
         // The step base and target change only between captured chunks (the
         // chunk-closing kernel has finished before a chunk's first launch), so
         // they may be read before waiting for the previous kernel.
@@ -698,88 +677,73 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         const uint32_t t = (uint32_t)step;
         const int cur = (int)(step & 1ull), nxt = cur ^ 1;
         const int d = (t & 1u) ? -1 : 1;
-        const int hs = lane == 0 ? 0 : (lane == 31 ? n + 1 : -1);  // the halo slot this lane handles
 
-        // ---------------- state of step t
-        if (mine) {
-            uint32_t placed = 0u, moving = 0u, open = 0u;
-            if (do_xfer && (first || end)) {
-                open = fused_link_work<TURNS>(D, t, cur, link, bpos, lanes, first, end, placed, moving, acc2);
-            } else if (end) {
-                const uint4 *__restrict__ sc = D.slots[cur];
-                uint4 *__restrict__ sn = D.slots[nxt];
-                uint4 own[kMaxLanes];
+        // ---------------- state of step t: every load before any store
+        uint32_t o[kMaxLanes], mo[kMaxLanes], lo[kMaxLanes];
 #pragma unroll
-                for (int k = 0; k < kMaxLanes; ++k)
-                    own[k] = (uint32_t)k < lanes ? sc[bpos + k] : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+        for (int k = 0; k < kMaxLanes; ++k) {
+            const bool w = exists && (uint32_t)k < lanes;
+            o[k] = w ? D.occ[cur][cw + (uint32_t)k] : 0u;
+            mo[k] = w ? D.mov[cur][cw + (uint32_t)k] : 0u;
+            lo[k] = w ? D.loc[cur][cw + (uint32_t)k] : 0u;
+        }
+        uint4 own[kMaxLanes];
+        const bool plain_end = end && !do_xfer;
 #pragma unroll
-                for (int k = 0; k < kMaxLanes; ++k) {
-                    if ((uint32_t)k >= lanes) break;
-                    const bool empty = own[k].x == kSlotEmpty;
-                    if (empty) open |= 1u << k;
-                    sn[bpos + k] = empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : own[k];
-                }
-            }
-            uint32_t upd = 0u;
+        for (int k = 0; k < kMaxLanes; ++k)
+            own[k] = plain_end && (uint32_t)k < lanes ? D.slots[cur][bpos + (uint32_t)k]
+                                                      : make_uint4(kSlotEmpty, 0u, 0u, 0u);
+        uint32_t placed = 0u, moving = 0u, open = 0u;
+        if (do_xfer && (first || end)) {
+            open = fused_link_work<TURNS>(D, t, cur, link, bpos, lanes, first, end, placed, moving, acc2);
+        } else if (end) {
+            // l's lane-end buffers for step t: empty (the node pass of step
+            // t-1 has emptied transferred ones) or still holding their vehicle
 #pragma unroll
             for (int k = 0; k < kMaxLanes; ++k) {
                 if ((uint32_t)k >= lanes) break;
-                const uint32_t g = cw + (uint32_t)k;
-                const uint32_t o = D.occ[cur][g] | ((placed >> k) & 1u);
-                S.o0[wi(k, s)] = o;
-                S.m0[wi(k, s)] = (o ? D.mov[cur][g] : 0u) | ((moving >> k) & 1u);
-                S.l0[wi(k, s)] = o ? D.loc[cur][g] : 0u;
-                S.mv[wi(k, s)] = 0u;
-                S.no[wi(k, s)] = 0u;
-                S.nm[wi(k, s)] = 0u;
-                S.nl[wi(k, s)] = 0u;
-                upd += (uint32_t)__popc(o);
-            }
-            acc[0] += upd;  // vehicle updates
-            if (end) {
-                // the light at the link end (Sec. 3): while red, a virtual
-                // vehicle of maximum velocity zero stands at every lane end
-                const uint32_t cycle = sig.x & 0xFFFFu, green = sig.x >> 16;
-                const uint8_t gr = (uint8_t)(cycle == 0u || (t + sig.y) % cycle < green);
-                S.cexit[s] = (uint8_t)open;
-                S.cgreen[s] = gr;
-                if (lane > 0 && j > 0u) {  // the column before it (same link), if it is in this tile
-                    S.cexit[s - 1] = (uint8_t)open;
-                    S.cgreen[s - 1] = gr;
-                }
+                const bool empty = own[k].x == kSlotEmpty;
+                if (empty) open |= 1u << k;
+                D.slots[nxt][bpos + (uint32_t)k] =
+                    empty ? make_uint4(kSlotEmpty, kSlotEmpty, kSlotEmpty, kSlotEmpty) : own[k];
             }
         }
-        // the halo columns: state of step t (the cells of a halo that the tile
-        // looks at are never within vmax cells of a link end; a tile built
-        // otherwise is flagged)
-        for (int e = 0; e < 2; ++e) {
-            const int h = e == 0 ? 0 : n + 1;
-            if (lane != (e == 0 ? 0 : n - 1)) continue;
-            const uint32_t hw = S.cw[h];
-            if (hw == kNoSlot) continue;
-            if (S.cnear[h] & lc_mask(S.ckind[h], vmax)) atomicOr(&D.ctrl->error, kErrGeometry);
-            for (uint32_t k = 0; k < lanes; ++k) {
-                const uint32_t o = D.occ[cur][hw + k];
-                S.o0[wi(k, h)] = o;
-                S.m0[wi(k, h)] = o ? D.mov[cur][hw + k] : 0u;
-                S.l0[wi(k, h)] = o ? D.loc[cur][hw + k] : 0u;
-                S.mv[wi(k, h)] = 0u;
+        uint32_t upd = 0u;
+#pragma unroll
+        for (int k = 0; k < kMaxLanes; ++k) {
+            if (!exists || (uint32_t)k >= lanes) continue;
+            const uint32_t ok = o[k] | ((placed >> k) & 1u);
+            S.o0[wi(k, s)] = ok;
+            S.m0[wi(k, s)] = mo[k] | ((moving >> k) & 1u);
+            S.l0[wi(k, s)] = lo[k];
+            S.mv[wi(k, s)] = 0u;
+            S.no[wi(k, s)] = 0u;
+            S.nm[wi(k, s)] = 0u;
+            S.nl[wi(k, s)] = 0u;
+            upd += (uint32_t)__popc(ok);
+        }
+        if (core) acc[0] += upd;  // vehicle updates
+        if (end) {
+            // the light at the link end (Sec. 3): while red, a virtual
+            // vehicle of maximum velocity zero stands at every lane end
+            const uint32_t cycle = ca.y & 0xFFFFu, green = ca.y >> 16;
+            const uint8_t gr = (uint8_t)(cycle == 0u || (t + ca.z) % cycle < green);
+            S.cexit[s] = (uint8_t)open;
+            S.cgreen[s] = gr;
+            if (lane > 1 && j > 0u) {  // the column before it (same link), a column of this tile
+                S.cexit[s - 1] = (uint8_t)open;
+                S.cgreen[s - 1] = gr;
             }
         }
+        // the cells of a halo that the tile looks at are never within vmax
+        // cells of a link end; a tile built otherwise is flagged
+        if (!core && exists && (near & lc_mask(kind, vmax))) atomicOr(&D.ctrl->error, kErrGeometry);
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, exists ? lanes : 0u);
         __syncwarp();
         const int8_t *__restrict__ vel0 = D.vel[0];
         const int8_t *__restrict__ vel1 = D.vel[1];
         const uint32_t *__restrict__ vid0 = D.vid[0];
         const uint32_t *__restrict__ vid1 = D.vid[1];
-        // the words this lane handles: its column (q 0..3) and its halo (q 4..7)
-        const bool hvalid = hs >= 0 && S.cw[hs] != kNoSlot;
-        int widx[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int ss = q < 4 ? s : hs;
-            const bool ok = q < 4 ? mine : hvalid;
-            widx[q] = ok && (uint32_t)(q & 3) < (uint32_t)S.clanes[ok ? ss : 0] ? wi(q & 3, ss) : -1;
-        }
 
         // ---------------- sub-step 1: lane changes, decided on the state of step t.
         // A vehicle with v = 0 and an occupied cell ahead always has a reason to
@@ -789,38 +753,35 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         // vehicle with v = 0 and a free cell ahead has no reason to change.
         // Moving vehicles and vehicles near a link end are decided one by one.
         if (D.lane_change != 0u) {
-            uint32_t lst[8];
+            uint32_t lst[kMaxLanes] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                lst[q] = 0u;
-                if (widx[q] < 0) continue;
-                const int ss = q < 4 ? s : hs, k = q & 3, kt = k + d;
-                if (kt < 0 || kt >= (int)S.clanes[ss]) continue;
-                const uint32_t o = S.o0[widx[q]] & lc_mask(S.ckind[ss], vmax);
-                if (!o) continue;
+            for (int k = 0; k < kMaxLanes; ++k) {
+                if ((uint32_t)k >= kmax) break;
+                const int kt = k + d;
+                if (!exists || (uint32_t)k >= lanes || kt < 0 || kt >= (int)lanes) continue;
+                const uint32_t oc = S.o0[wi(k, s)] & lc_mask(kind, vmax);
+                if (!oc) continue;
                 if (TURNS) {
                     // the allowed lanes are in the payload: every vehicle
                     // whose target cell is free is decided one by one
-                    lst[q] = o & ~S.o0[wi(kt, ss)];
+                    lst[k] = oc & ~S.o0[wi(kt, s)];
                 } else {
-                    const uint32_t near = S.cnear[ss];
-                    const uint32_t tw = S.o0[wi(kt, ss)];
-                    const int lf = S.cleft[ss];
+                    const uint32_t tw = S.o0[wi(kt, s)];
                     const unsigned long long tt =
-                        ((unsigned long long)tw << 32) | (lf >= 0 ? S.o0[wi(kt, lf)] : 0u);
+                        ((unsigned long long)tw << 32) | (left >= 0 ? S.o0[wi(kt, left)] : 0u);
                     uint32_t behind = 0u;
                     for (uint32_t b = 1; b <= vmax; ++b) behind |= (uint32_t)(tt >> (32 - b));
-                    const uint32_t ok = ahead_mask(S.o0, S, ss, k) & ~tw & ~behind & ~ahead_mask(S.o0, S, ss, kt);
-                    const uint32_t lcv0 = o & ~S.m0[widx[q]] & ~near & ok;
+                    const uint32_t okm = ahead_mask(S.o0, S, s, k) & ~tw & ~behind & ~ahead_mask(S.o0, S, s, kt);
+                    const uint32_t lcv0 = oc & ~S.m0[wi(k, s)] & ~near & okm;
                     if (lcv0) {
-                        S.mv[wi(kt, ss)] |= lcv0;  // this lane's own column (or halo)
-                        if (S.ckind[ss] == 0) acc[1] += (uint32_t)__popc(lcv0);
+                        S.mv[wi(kt, s)] |= lcv0;  // this lane's own slot
+                        if (core) acc[1] += (uint32_t)__popc(lcv0);
                     }
-                    lst[q] = o & (S.m0[widx[q]] | near);
+                    lst[k] = oc & (S.m0[wi(k, s)] | near);
                 }
             }
             __syncwarp();
-            warp_list(S, lst, widx, [&](uint32_t code) {
+            warp_list(S, lst, s, [&](uint32_t code) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
                 const int k = ww / kSlots, c = ww - k * kSlots, kt = k + d;
                 if ((S.o0[wi(kt, c)] >> i) & 1u) return;  // target cell taken
@@ -876,35 +837,31 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         // v = 0, an occupied cell ahead, no lane change and far from the link
         // end keeps v = 0 and its cell: its bits are copied, its payload stays.
         {
-            uint32_t lst[8];
+            uint32_t lst[kMaxLanes] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                lst[q] = 0u;
-                if (widx[q] < 0) continue;
-                const int ss = q < 4 ? s : hs, k = q & 3;
-                const uint32_t kind = S.ckind[ss];
+            for (int k = 0; k < kMaxLanes; ++k) {
+                if ((uint32_t)k >= kmax) break;
+                if (!exists || (uint32_t)k >= lanes) continue;
                 // the words after the lane-change sub-step, from the step-t
                 // words and the lane-change marks (mv: vehicles that changed
                 // into a word's lane; those leaving lane k went to k + d)
-                const int nlanes = S.clanes[ss];
                 const int kf = k + d, kb = k - d;
-                const bool has_f = kf >= 0 && kf < nlanes, has_b = kb >= 0 && kb < nlanes;
-                const uint32_t arriving = S.mv[widx[q]];
-                const uint32_t leaving = has_f ? S.mv[wi(kf, ss)] : 0u;
-                const uint32_t o1 = (S.o0[widx[q]] & ~leaving) | arriving;
-                const uint32_t src_mov = (arriving && has_b) ? S.m0[wi(kb, ss)] : 0u;
-                const uint32_t m1 = (S.m0[widx[q]] & ~leaving) | (src_mov & arriving);
-                S.o1[widx[q]] = o1;
-                const int r = S.cright[ss];
+                const bool has_f = kf >= 0 && kf < (int)lanes, has_b = kb >= 0 && kb < (int)lanes;
+                const uint32_t arriving = S.mv[wi(k, s)];
+                const uint32_t leaving = has_f ? S.mv[wi(kf, s)] : 0u;
+                const uint32_t o1 = (S.o0[wi(k, s)] & ~leaving) | arriving;
+                const uint32_t src_mov = (arriving && has_b) ? S.m0[wi(kb, s)] : 0u;
+                const uint32_t m1 = (S.m0[wi(k, s)] & ~leaving) | (src_mov & arriving);
+                S.o1[wi(k, s)] = o1;
                 const uint32_t o1r =
-                    r >= 0 ? (S.o0[wi(k, r)] & ~(has_f ? S.mv[wi(kf, r)] : 0u)) | S.mv[wi(k, r)] : 0u;
+                    right >= 0 ? (S.o0[wi(k, right)] & ~(has_f ? S.mv[wi(kf, right)] : 0u)) | S.mv[wi(k, right)] : 0u;
                 const uint32_t free_ahead = ~((o1 >> 1) | (o1r << 31));
-                const uint32_t busy = m1 | free_ahead | S.cnear[ss] | arriving;
-                lst[q] = o1 & busy & move_mask(kind, vmax);
-                if (kind == 0) {
+                const uint32_t busy = m1 | free_ahead | near | arriving;
+                lst[k] = o1 & busy & move_mask(kind, vmax);
+                if (core) {
                     const uint32_t inert = o1 & ~busy;
-                    S.no[widx[q]] = inert;
-                    S.nl[widx[q]] = inert & S.l0[widx[q]];
+                    S.no[wi(k, s)] = inert;
+                    S.nl[wi(k, s)] = inert & S.l0[wi(k, s)];
                 }
             }
             __syncwarp();
@@ -913,7 +870,7 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             uint32_t *__restrict__ vidw0 = D.vid[0];
             uint32_t *__restrict__ vidw1 = D.vid[1];
             const uint32_t key0 = D.seed_lo, key1 = D.seed_hi, pthr = D.p_threshold;
-            warp_list(S, lst, widx, [&](uint32_t code) {
+            warp_list(S, lst, s, [&](uint32_t code) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
                 const int k = ww / kSlots, c = ww - k * kSlots;
                 const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
@@ -1021,7 +978,7 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         }
 
         // ---------------- the state of step t+1 of this lane's column
-        if (mine) {
+        if (core) {
 #pragma unroll
             for (int k = 0; k < kMaxLanes; ++k) {
                 if ((uint32_t)k >= lanes) break;
@@ -1042,13 +999,14 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             block_end_flush<NW, 7>(acc2, cur_rec2, SB.red2, SB.rec2, kField2);
         }
     }
+    pdl_trigger();  // blocks without tiles
     span_mark(span, pos, 0, false);
 }
 
 constexpr int kLinkWarps = kLinkWarpsPerBlock;
 constexpr int kLinkBlock = kLinkWarps * 32;
 
-__global__ void __launch_bounds__(kLinkBlock, 8)
+__global__ void __launch_bounds__(kLinkBlock, 6)
     link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
                 const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer, unsigned long long *span) {
     __shared__ LinkSmem<kLinkWarps> S;
@@ -1057,7 +1015,7 @@ __global__ void __launch_bounds__(kLinkBlock, 8)
 
 // The same with the intersection rules (scenarios with turn lanes or yield
 // approaches).
-__global__ void __launch_bounds__(kLinkBlock, 8)
+__global__ void __launch_bounds__(kLinkBlock, 6)
     turn_link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
                      const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer, unsigned long long *span) {
     __shared__ LinkSmem<kLinkWarps> S;
@@ -1073,7 +1031,7 @@ __global__ void __launch_bounds__(kLinkBlock, 8)
 // global loads; a thread whose node's buffers do not fit the stage reads
 // them from global memory.
 
-constexpr int kStageSlots = 1536;  // staged buffers per block
+constexpr int kStageSlots = 1024;  // staged buffers per block
 
 template <int NT, bool TAILS>
 struct NodeSmem {
@@ -1189,9 +1147,9 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
     unsigned long long acc[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned long long *cur_rec = nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    pdl_trigger();
     bool waited = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (tile + gridDim.x >= n_tiles) pdl_trigger();  // the block's last tile (see link_step)
         const uint4 td = tiles[tile];
         const ScenDev &D = table[td.x];
         if (D.ctrl == nullptr) continue;
@@ -1301,6 +1259,7 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
         __syncthreads();  // the stage is rewritten by the next tile
     }
     if (cur_rec) block_flush<7, NT>(acc, cur_rec, kField, S.red);
+    pdl_trigger();
     span_mark(span, pos, 1, false);
 }
 
@@ -1573,13 +1532,17 @@ extern "C" int ts_debug_phase_sums(unsigned long long *out, int reset) {
 #endif
 
 int max_link_blocks(bool turns) {
-    // eight blocks of four warps per SM need the largest shared-memory share of L1
+    // six blocks of four warps per SM (80 registers a thread: fewer spills
+    // than at 64 with eight blocks, measured faster on the 20,024- and
+    // 200,000-link networks) need the largest shared-memory share of L1
     const void *fn = turns ? (const void *)turn_link_kernel : (const void *)link_kernel;
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     return resident_blocks(fn, kLinkBlock);
 }
 int max_node_blocks(bool turns) {
-    return resident_blocks(turns ? (const void *)turn_node_kernel : (const void *)node_kernel, kNodeThreads);
+    const void *fn = turns ? (const void *)turn_node_kernel : (const void *)node_kernel;
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return resident_blocks(fn, kNodeThreads);
 }
 
 }  // namespace tsim

@@ -37,7 +37,8 @@ constexpr size_t kOffLink = 768;
 constexpr size_t kOffCount = 1024;
 constexpr size_t kOffTiles = 1280;
 constexpr size_t kOffCols = kOffTiles + ((sizeof(uint2) * kNoAllocMaxTiles + 255u) / 256u) * 256u;
-constexpr size_t kOffStats = kOffCols + sizeof(uint4) * kNoAllocMaxCols;
+constexpr size_t kOffAux = kOffCols + sizeof(uint4) * kNoAllocMaxCols;
+constexpr size_t kOffStats = kOffAux + sizeof(uint4) * kNoAllocMaxCols;
 constexpr size_t kOffPlanes = kOffStats + sizeof(StatRec) * kStatsRing;  // mov0, mov1, loc0, loc1
 constexpr size_t kScratchBytes = kOffPlanes + 4ull * 4ull * kNoAllocMaxWords;
 
@@ -65,20 +66,22 @@ ts_status bad(ts_status s, const char *msg) {
 // Writes this call's scenario entry, control block, link record, tile list
 // and column table into the scratch (all of it rewritten by every call) and
 // clears the statistics ring.  One ring link of ncols columns and `lanes`
-// lanes: tiles of 32 columns (one tile if the ring has at most 32).
+// lanes: tiles of 30 columns (one tile if the ring has at most 30).
 __global__ void setup_ring(ScenDev sd, Ctrl ctrl, uint4 link, uint32_t ncols, uint32_t lanes, ScenDev *table,
-                           Ctrl *d_ctrl, uint4 *d_link, uint32_t *d_count, uint2 *tiles, uint4 *cols,
+                           Ctrl *d_ctrl, uint4 *d_link, uint32_t *d_count, uint2 *tiles, uint4 *cols, uint4 *aux,
                            StatRec *stats) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    const uint32_t n_tiles = (ncols + kWarpTileCols - 1) / kWarpTileCols;
+    const uint32_t n_tiles = (ncols + kWarpTileCols - 1) / kWarpTileCols;  // whole ring if it fits one tile
     if (tid == 0) {
         *table = sd;
         *d_ctrl = ctrl;
         *d_link = link;
         *d_count = n_tiles;
     }
-    for (uint32_t j = tid; j < ncols; j += nth)
+    for (uint32_t j = tid; j < ncols; j += nth) {
         cols[j] = make_uint4(j * lanes, 0u, j | (lanes << 20) | (1u << 23), link.y);
+        aux[j] = make_uint4(0u, 0u, 0u, 0u);  // a ring has no link-end buffers and no signal
+    }
     for (uint32_t i = tid; i < n_tiles; i += nth) {
         const uint32_t c0 = i * kWarpTileCols;
         const uint32_t n = ncols - c0 < (uint32_t)kWarpTileCols ? ncols - c0 : (uint32_t)kWarpTileCols;
@@ -235,6 +238,7 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     uint4 *d_link = reinterpret_cast<uint4 *>(base + kOffLink);
     uint2 *d_tiles = reinterpret_cast<uint2 *>(base + kOffTiles);
     uint4 *d_cols = reinterpret_cast<uint4 *>(base + kOffCols);
+    uint4 *d_aux = reinterpret_cast<uint4 *>(base + kOffAux);
     uint32_t *d_count = reinterpret_cast<uint32_t *>(base + kOffCount);
     StatRec *d_stats = reinterpret_cast<StatRec *>(base + kOffStats);
     uint32_t *d_planes = reinterpret_cast<uint32_t *>(base + kOffPlanes);
@@ -244,6 +248,7 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     ScenDev sd{};
     sd.lk_info = d_link;
     sd.col_info = d_cols;
+    sd.col_aux = d_aux;
     sd.n_cols = ncols;
     sd.occ[0] = dev_occ0;
     sd.occ[1] = dev_occ1;
@@ -274,7 +279,7 @@ ts_status ts_ring_step_noalloc(uint32_t cells, uint32_t lanes, const ts_params *
     // into; every launch is checked as it is made
     const uint32_t cur = (uint32_t)(first_step & 1ull), fin = (uint32_t)((first_step + n_steps) & 1ull);
     setup_ring<<<32, 256, 0, s>>>(sd, ctrl, link, ncols, lanes, d_table, d_ctrl, d_link, d_count, d_tiles, d_cols,
-                                  d_stats);
+                                  d_aux, d_stats);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "set-up kernel launch failed");
     prep_ring<<<(words + 255u) / 256u, 256, 0, s>>>(sd, lanes, words, cur);
     if (cudaGetLastError() != cudaSuccess) return bad(TS_ERR_CUDA, "kernel launch failed");

@@ -5,7 +5,9 @@ thread when it arrives; it is admitted to the running batch as soon as its
 device footprint fits the memory budget; every batch step advances all
 admitted jobs by a chunk of time steps, each towards its own target; a job
 that reaches its target leaves the batch, its totals are read and its memory
-returns to the pool.  State stays on the device between steps, and jobs that
+returns to the pool.  Two batches alternate on the stream, so the host's
+admission and retirement work on one overlaps the other's chunk on the
+device.  State stays on the device between steps, and jobs that
 arrive while others run overlap with them on the GPU.  Because each job keeps
 its own seed, step counter and statistics, its results are the same alone and
 in any mix.
@@ -75,12 +77,18 @@ def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int) -> np.ndar
 
 
 class Server:
+    """Two batches take turns on the stream: while the device runs one
+    batch's chunk of steps, the host retires and admits jobs on the other
+    and queues its chunk behind the running one, so admission and
+    retirement never leave the device idle.  A job joins whichever batch is
+    being served when it is admitted; `capacity` bounds the jobs of both."""
+
     def __init__(self, budget_bytes: int, capacity: int = 1024, chunk_steps: int = 128, workers: int = 4):
         import torch
         self.budget = budget_bytes
         self.chunk = chunk_steps
         self.stream = torch.cuda.Stream()
-        self.batch = T.Batch(capacity)
+        self.batches = [T.Batch(capacity), T.Batch(capacity)]
         self.capacity = capacity
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
 
@@ -96,15 +104,17 @@ class Server:
         now = lambda: time.perf_counter() - t0
         pending = list(jobs)
         building = {}   # jid -> (job, future)
-        ready = []      # (job, sim) built, waiting for memory
-        active = {}     # jid -> (job, sim)
+        ready = []      # (job, sim) built, waiting for memory, in arrival order
+        active = [{}, {}]   # per batch: jid -> (job, sim)
+        queued = [False, False]  # a chunk of the batch is enqueued and not yet waited for
         used = 0
         done: List[Job] = []
         rejected: List[Job] = []
         busy = 0.0
         peak_active = peak_bytes = 0
         active_samples = []
-        while pending or building or ready or active:
+        cur = 0
+        while pending or building or ready or active[0] or active[1]:
             t = now()
             while pending and pending[0].arrival * time_scale <= t:
                 j = pending.pop(0)
@@ -122,44 +132,60 @@ class Server:
                     rejected.append(j)
                     continue
                 ready.append((j, sim))
+            ready.sort(key=lambda r: (r[0].arrival, r[0].jid))
+            b = self.batches[cur]
+            if queued[cur]:
+                # this batch's chunk ran before the other one's (still queued
+                # or running); wait for it (bounded) and retire finished jobs
+                b0 = time.perf_counter()
+                b.sync()
+                busy += time.perf_counter() - b0
+                queued[cur] = False
+                for jid in list(active[cur]):
+                    j, sim = active[cur][jid]
+                    if sim.current_step() >= j.steps:
+                        tot = sim.totals()
+                        j.vehicle_updates = tot["vehicle_updates"]
+                        j.last_state_hash = tot["last_state_hash"]
+                        j.finished = now()
+                        b.remove(sim)
+                        sim.close()
+                        used -= j.footprint
+                        del active[cur][jid]
+                        done.append(j)
+            # first come, first served: the head of the queue is admitted
+            # when it fits, and nothing overtakes it
             adds = []
-            while ready and used + ready[0][0].footprint <= self.budget and len(active) + len(adds) < self.capacity:
+            n_active = len(active[0]) + len(active[1])
+            while ready and used + ready[0][0].footprint <= self.budget and n_active + len(adds) < self.capacity:
                 j, sim = ready.pop(0)
                 j.admitted = now()
                 used += j.footprint
                 adds.append((j, sim))
-            for steps in sorted({j.steps for j, _ in adds}):
-                group = [(j, s) for j, s in adds if j.steps == steps]
-                self.batch.add_many([s for _, s in group], steps)
-                for j, s in group:
-                    active[j.jid] = (j, s)
-            peak_active = max(peak_active, len(active))
+            i = 0
+            while i < len(adds):  # runs of equal targets, in arrival order
+                e = i
+                while e < len(adds) and adds[e][0].steps == adds[i][0].steps:
+                    e += 1
+                b.add_many([s for _, s in adds[i:e]], adds[i][0].steps)
+                for j, s in adds[i:e]:
+                    active[cur][j.jid] = (j, s)
+                i = e
+            peak_active = max(peak_active, len(active[0]) + len(active[1]))
             peak_bytes = max(peak_bytes, used)
-            if not active:
+            if active[cur]:
+                active_samples.append(len(active[0]) + len(active[1]))
+                b.step(self.chunk, self.stream)
+                queued[cur] = True
+            elif not queued[cur ^ 1]:
                 nxt = pending[0].arrival * time_scale - now() if pending else 0.0
                 time.sleep(max(0.0, min(nxt, 0.002)) if not building else 0.0005)
-                continue
-            active_samples.append(len(active))
-            b0 = time.perf_counter()
-            self.batch.step(self.chunk, self.stream)
-            self.batch.sync()
-            busy += time.perf_counter() - b0
-            for jid in list(active):
-                j, sim = active[jid]
-                if sim.current_step() >= j.steps:
-                    tot = sim.totals()
-                    j.vehicle_updates = tot["vehicle_updates"]
-                    j.last_state_hash = tot["last_state_hash"]
-                    j.finished = now()
-                    self.batch.remove(sim)
-                    sim.close()
-                    used -= j.footprint
-                    del active[jid]
-                    done.append(j)
+            cur ^= 1
         wall = now()
         return ServeReport(done, wall, busy, peak_active, peak_bytes,
                            float(np.mean(active_samples)) if active_samples else 0.0, rejected)
 
     def close(self):
         self.pool.shutdown()
-        self.batch.close()
+        for b in self.batches:
+            b.close()

@@ -515,3 +515,21 @@ def test_kernel_spans_inside_the_graphs():
     sim.kernel_times(reset=True)
     assert sim.kernel_times()["link_launches"] == 0
     sim.close()
+
+
+def test_load_balancing_keeps_ts_step_asynchronous():
+    # re-tiling from the occupancy is a kernel on the step stream: ts_step
+    # returns while the steps still run (a zero-deadline read times out), and
+    # the result equals the oracle
+    sc = N.small_grid_scenario(5, 3, 70, n_trips=6000, window=400, steps=3000, gen_seed=12, seed=31)
+    sim = T.Simulation(sc)
+    sim.set_load_balance(64, 128)
+    sim.step(64)  # captures the graphs
+    sim.stats()
+    sim.step(sc.steps - 64)
+    with pytest.raises(T.TsError, match="TIMEOUT"):
+        sim.stats(timeout_ms=0)
+    orc = oracle.Oracle(sc)
+    _cmp_stats(sim.stats_range(0, sc.steps), orc.step(sc.steps), "load balanced on the device")
+    _cmp_state(sim.read_state(), orc.get_state(), "load balanced on the device, final")
+    sim.close()

@@ -2,6 +2,8 @@
 import numpy as np
 import pytest
 
+import oracle
+
 from paper_cs_0105004_gb300 import batching as Bt
 from paper_cs_0105004_gb300 import serving as Sv
 from paper_cs_0105004_gb300 import transsim as T
@@ -39,6 +41,12 @@ def test_served_jobs_equal_their_single_runs():
         assert j.vehicle_updates == a["vehicle_updates"]
         assert j.last_state_hash == a["last_state_hash"]
         assert j.finished >= j.admitted >= j.arrival
+        # and the oracle's run of the same job
+        orc = oracle.Oracle(scs[j.jid])
+        o = orc.step(steps)
+        orc.close()
+        assert j.vehicle_updates == int(o["vehicle_updates"].sum())
+        assert j.last_state_hash == int(o["state_hash"][-1])
     assert rep.peak_active > 1  # jobs overlapped on the device
 
 

@@ -348,7 +348,8 @@ ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode);
  * into the partition): every `every_steps` steps of a ts_step call
  * (0 = never; otherwise at least 32) the link tiles are rebuilt from the
  * current occupancy so that a tile holds at most `vehicles_per_tile`
- * vehicles (0 = no budget).  Each pass is a kernel enqueued on the step's
+ * vehicles (0 = no budget, else at least 32; a single column is never cut,
+ * so a tile may exceed the budget by one column's vehicles).  Each pass is a kernel enqueued on the step's
  * stream, so ts_step stays asynchronous.  Waits (bounded) for the context's
  * queued work; TS_ERR_STATE for a context in a batch.  Results do not
  * depend on it. */

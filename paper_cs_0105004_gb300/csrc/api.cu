@@ -1174,7 +1174,7 @@ ts_status ts_set_load_balance(ts_ctx *c, uint32_t every_steps, uint32_t vehicles
     ts_status st = check_ctx(c);
     if (st != TS_OK) return st;
     if (every_steps && every_steps < kChunk) return fail(TS_ERR_INVALID, "load balancing at most every 32 steps");
-    if (vehicles_per_tile && vehicles_per_tile < 128) return fail(TS_ERR_INVALID, "vehicle budget below 128");
+    if (vehicles_per_tile && vehicles_per_tile < 32) return fail(TS_ERR_INVALID, "vehicle budget below 32");
     if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
     st = wait_ctx(c, 60000);  // the tile arrays are rewritten below
     if (st != TS_OK) return st;

@@ -402,6 +402,47 @@ __device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[kMaxLanes],
     }
 }
 
+// The same with each vehicle's step split in two: load(code, a, b) fetches
+// what it needs from global memory (its step-t payload, which no thread
+// writes during the step) and proc(code, a, b) completes it.  (Issuing two
+// vehicles' loads before processing either was measured slower on the
+// 200,000-link network: 55.6 vs 47.4 us per launch.)
+template <class L, class F>
+__device__ __forceinline__ void warp_list2(WarpSmem &S, uint32_t (&m)[kMaxLanes], int slot, L &&load, F &&proc) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t cnt = 0u;
+#pragma unroll
+        for (int q = 0; q < kMaxLanes; ++q) cnt += (uint32_t)__popc(m[q]);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        if (total == 0u) break;
+        uint32_t pos = inc - cnt;
+#pragma unroll
+        for (int q = 0; q < kMaxLanes; ++q) {
+            while (m[q] && pos < (uint32_t)kCodes) {
+                const int b = __ffs(m[q]) - 1;
+                m[q] &= m[q] - 1u;
+                S.code[pos++] = (uint16_t)((wi(q, slot) << 5) | b);
+            }
+        }
+        __syncwarp();
+        const uint32_t nproc = total < (uint32_t)kCodes ? total : (uint32_t)kCodes;
+        for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
+            const uint32_t c = S.code[e];
+            uint32_t a, b;
+            load(c, a, b);
+            proc(c, a, b);
+        }
+        __syncwarp();
+    }
+}
+
 // Sum over the warp, then lane f adds field f's sum at rec + field[f].
 template <int NF>
 __device__ __forceinline__ void warp_flush(unsigned long long (&acc)[NF], unsigned long long *rec,
@@ -538,14 +579,16 @@ __device__ __noinline__ uint32_t fused_link_work(const ScenDev &D, uint32_t t, i
 }
 
 // One launch of the link kernel (body of link_kernel and turn_link_kernel)
-// for NW warps per block.  TURNS: the intersection rules of Sec. 3 a network
+// for NW warps per block.  XFER (fused steps): the launch first completes the
+// node transfers and departures of the previous step, the tiles of a link's
+// first and last columns resolving them.  TURNS: the intersection rules of Sec. 3 a network
 // may carry: plan-following lane changes (every velocity byte carries the
 // lanes A of its link from which the vehicle may take its next turn) and gap
 // acceptance at unprotected turns (in the node transfers).
-template <int NW, bool TURNS>
+template <int NW, bool TURNS, bool XFER>
 __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__restrict__ table,
                                           const uint2 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
-                                          uint32_t pos, uint32_t xfer, unsigned long long *span) {
+                                          uint32_t pos, unsigned long long *span) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &S = SB.w[warp];
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
@@ -666,8 +709,8 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             }
             cur_rec = rec;
         }
-        const bool do_xfer = xfer != 0u;
-        if (do_xfer) {
+        constexpr bool do_xfer = XFER;
+        if constexpr (do_xfer) {
             unsigned long long *rec2 = reinterpret_cast<unsigned long long *>(stat_rec(D, step - 1ull));
             if (rec2 != cur_rec2) {
                 if (cur_rec2) warp_flush<7>(acc2, cur_rec2, kField2);
@@ -694,9 +737,14 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             own[k] = plain_end && (uint32_t)k < lanes ? D.slots[cur][bpos + (uint32_t)k]
                                                       : make_uint4(kSlotEmpty, 0u, 0u, 0u);
         uint32_t placed = 0u, moving = 0u, open = 0u;
-        if (do_xfer && (first || end)) {
-            open = fused_link_work<TURNS>(D, t, cur, link, bpos, lanes, first, end, placed, moving, acc2);
-        } else if (end) {
+        bool fused_done = false;
+        if constexpr (XFER) {
+            if (first || end) {
+                open = fused_link_work<TURNS>(D, t, cur, link, bpos, lanes, first, end, placed, moving, acc2);
+                fused_done = true;
+            }
+        }
+        if (!fused_done && end) {
             // l's lane-end buffers for step t: empty (the node pass of step
             // t-1 has emptied transferred ones) or still holding their vehicle
 #pragma unroll
@@ -781,25 +829,33 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
                 }
             }
             __syncwarp();
-            warp_list(S, lst, s, [&](uint32_t code) {
+            // payload at step t (velocity byte; the id only within vmax
+            // cells of the link end, for its last-link flag)
+            auto lcload = [&](uint32_t code, uint32_t &byte, uint32_t &idw) {
+                const int ww = (int)(code >> 5), i = (int)(code & 31u);
+                const int k = ww / kSlots, c = ww - k * kSlots, kt = k + d;
+                byte = 0u;
+                idw = 0u;
+                if ((S.o0[wi(kt, c)] >> i) & 1u) return;  // target cell taken: not needed
+                const size_t p = (size_t)(S.cw[c] + (uint32_t)k) * 32u + (uint32_t)i;
+                const bool b1 = (S.l0[ww] >> i) & 1u;
+                byte = (uint32_t)(uint8_t)(b1 ? vel1[p] : vel0[p]);
+                if ((S.cnear[c] >> i) & 1u) idw = b1 ? vid1[p] : vid0[p];
+            };
+            warp_list2(S, lst, s, lcload, [&](uint32_t code, uint32_t byte, uint32_t idw) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
                 const int k = ww / kSlots, c = ww - k * kSlots, kt = k + d;
                 if ((S.o0[wi(kt, c)] >> i) & 1u) return;  // target cell taken
                 const uint32_t ringc = S.cring[c];
                 const uint32_t x = S.cx0[c] + (uint32_t)i;
                 const uint32_t dist = ringc ? 0xFFFFu : S.ccells[c] - 1u - x;
-                // payload at step t; the last-link flag matters only within
-                // vmax cells of the link end
-                const size_t p = (size_t)(S.cw[c] + (uint32_t)k) * 32u + (uint32_t)i;
-                const bool b1 = (S.l0[ww] >> i) & 1u;
                 uint32_t v;
                 uint32_t al = 0xFu;  // lanes it may leave the link from
                 if constexpr (TURNS) {
-                    const uint32_t byte = (uint32_t)(uint8_t)(b1 ? vel1[p] : vel0[p]);
                     v = byte & 0xFu;
                     if (byte >> 4) al = byte >> 4;
                 } else {
-                    v = (uint32_t)(b1 ? vel1[p] : vel0[p]);
+                    v = byte;
                 }
                 if constexpr (TURNS) {
                     if (!((al >> k) & 1u)) {
@@ -819,7 +875,7 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
                     // closed link end)
                     if (!((al >> kt) & 1u)) return;
                 }
-                const uint32_t last = ((S.cnear[c] >> i) & 1u) ? (b1 ? vid1[p] : vid0[p]) >> 31 : 0u;
+                const uint32_t last = idw >> 31;  // 0 outside the near cells
                 const uint32_t want = v + 1u < vmax ? v + 1u : vmax;
                 const uint32_t ex = S.cexit[c], gr = S.cgreen[c];
                 const uint32_t g_own = gap_ahead(S.o0, S, c, k, i, dist, (((ex >> k) & 1u) | last) & gr, vmax);
@@ -870,23 +926,27 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             uint32_t *__restrict__ vidw0 = D.vid[0];
             uint32_t *__restrict__ vidw1 = D.vid[1];
             const uint32_t key0 = D.seed_lo, key1 = D.seed_hi, pthr = D.p_threshold;
-            warp_list(S, lst, s, [&](uint32_t code) {
+            // payload from where the vehicle was at step t; no thread of
+            // this step writes a buffer that a step-t occupant is read from
+            auto vload = [&](uint32_t code, uint32_t &idw, uint32_t &byte) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
                 const int k = ww / kSlots, c = ww - k * kSlots;
                 const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
-                // payload from where the vehicle was at step t; no thread of
-                // this step writes a buffer that a step-t occupant is read from
-                const int sw = wi(ks, c);
                 const size_t ps = (size_t)(S.cw[c] + (uint32_t)ks) * 32u + (uint32_t)i;
-                const bool sb1 = (S.l0[sw] >> i) & 1u;
-                const uint32_t idw = sb1 ? vid1[ps] : vid0[ps];
+                const bool sb1 = (S.l0[wi(ks, c)] >> i) & 1u;
+                idw = sb1 ? vid1[ps] : vid0[ps];
+                byte = (uint32_t)(uint8_t)(sb1 ? vel1[ps] : vel0[ps]);
+            };
+            warp_list2(S, lst, s, vload, [&](uint32_t code, uint32_t idw, uint32_t byte) {
+                const int ww = (int)(code >> 5), i = (int)(code & 31u);
+                const int k = ww / kSlots, c = ww - k * kSlots;
+                const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
                 uint32_t v0, al = 0u;  // al: allowed lanes of the next turn (0: any)
                 if constexpr (TURNS) {
-                    const uint32_t byte = (uint32_t)(uint8_t)(sb1 ? vel1[ps] : vel0[ps]);
                     v0 = byte & 0xFu;
                     al = byte >> 4;
                 } else {
-                    v0 = (uint32_t)(sb1 ? vel1[ps] : vel0[ps]);
+                    v0 = byte;
                 }
                 const uint32_t id = idw & kIdMask, last = idw >> 31;
                 const uint32_t ringc = S.cring[c];
@@ -994,7 +1054,7 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         unsigned long long v[8];
         widen(v);
         block_end_flush<NW, 8>(v, cur_rec, SB.red, SB.rec, kField);
-        if (xfer) {
+        if constexpr (XFER) {
             __syncthreads();
             block_end_flush<NW, 7>(acc2, cur_rec2, SB.red2, SB.rec2, kField2);
         }
@@ -1006,40 +1066,42 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
 constexpr int kLinkWarps = kLinkWarpsPerBlock;
 constexpr int kLinkBlock = kLinkWarps * 32;
 
+template <bool XFER>
 __global__ void __launch_bounds__(kLinkBlock, 6)
     link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
-                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer, unsigned long long *span) {
+                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span) {
     __shared__ LinkSmem<kLinkWarps> S;
-    link_step<kLinkWarps, false>(S, table, tiles, n_tiles_p, pos, xfer, span);
+    link_step<kLinkWarps, false, XFER>(S, table, tiles, n_tiles_p, pos, span);
 }
 
 // The same with the intersection rules (scenarios with turn lanes or yield
 // approaches).
+template <bool XFER>
 __global__ void __launch_bounds__(kLinkBlock, 6)
     turn_link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
-                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, uint32_t xfer, unsigned long long *span) {
+                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span) {
     __shared__ LinkSmem<kLinkWarps> S;
-    link_step<kLinkWarps, true>(S, table, tiles, n_tiles_p, pos, xfer, span);
+    link_step<kLinkWarps, true, XFER>(S, table, tiles, n_tiles_p, pos, span);
 }
 
 // ------------------------------------------------------------------ node kernel
 //
-// One thread per link m, NT links per block.  Before resolving, a block
-// stages the link-end buffers of the upstream nodes of all its links (and,
+// One thread per link m, NT links per block.  Before resolving, each warp
+// stages the link-end buffers of the upstream nodes of its 32 links (and,
 // with yield approaches, their lane-tail records) into shared memory with
 // one flattened load, so no thread walks a long slot list through dependent
-// global loads; a thread whose node's buffers do not fit the stage reads
-// them from global memory.
+// global loads; a thread whose node's buffers do not fit the warp's stage
+// reads them from global memory.  Warps synchronise only among their own
+// lanes.
 
-constexpr int kStageSlots = 1024;  // staged buffers per block
+constexpr int kStageSlots = 256;  // staged buffers per warp
 
 template <int NT, bool TAILS>
 struct NodeSmem {
-    uint32_t off[NT + 1];  // first staged entry of each thread's node buffers
-    uint32_t lo[NT];       // first buffer of each thread's upstream node
-    uint4 stage[kStageSlots];
-    uint2 tail[TAILS ? kStageSlots : 1];
-    uint32_t wsum[NT / 32];
+    uint32_t off[NT / 32][33];  // first staged entry of each lane's node buffers; [32]: the warp's total
+    uint32_t lo[NT / 32][32];   // first buffer of each lane's upstream node
+    uint4 stage[NT / 32][kStageSlots];
+    uint2 tail[NT / 32][TAILS ? kStageSlots : 1];
     unsigned long long red[NT / 32][7];
 };
 
@@ -1097,24 +1159,36 @@ __device__ __forceinline__ uint32_t resolve_staged(const uint4 *st, const uint2 
     return free_mask;
 }
 
-// resolve_transfers for a node whose buffers are not staged, out of line:
-// returns the placements (at most one per lane of m) in order.
-template <bool TURNS>
-__device__ __noinline__ uint32_t resolve_unstaged(const uint4 *__restrict__ slots, uint4 nd, uint32_t m,
-                                                  uint32_t free_mask, const ScenDev &D,
-                                                  const uint32_t *__restrict__ occ, uint32_t (&si)[kMaxLanes],
-                                                  uint4 (&xs)[kMaxLanes], uint32_t (&qs)[kMaxLanes],
-                                                  uint32_t &free_out) {
-    uint32_t n = 0u;
-    free_out = resolve_transfers<TURNS>(slots, nd, m, free_mask, D, occ, [&](uint32_t i, const uint4 &x, uint32_t q) {
-        if (n < (uint32_t)kMaxLanes) {
-            si[n] = i;
-            xs[n] = x;
-            qs[n] = q;
+// Node transfer into link m reading its upstream node's buffers from global
+// memory one by one (for nodes whose buffers do not fit a warp's stage): the
+// same placements as resolve_staged.
+template <bool TURNS, class F>
+__device__ __forceinline__ uint32_t resolve_global(const uint4 *slots, uint32_t slot_lo, uint32_t cnt, uint32_t m,
+                                                   uint32_t lanes, uint32_t free_mask, const ScenDev &D,
+                                                   const uint32_t *__restrict__ occ, uint32_t prio, F &&place) {
+    for (uint32_t s = 0; s < cnt && free_mask; ++s) {
+        const uint4 x = slots[slot_lo + s];
+        if (x.x == kSlotEmpty || x.y != m) continue;
+        if constexpr (TURNS) {
+            if (D.slot_gap) {
+                const uint32_t G = D.slot_gap[slot_lo + s];
+                if (G && !priority_gap_clear(D.slot_tail, occ, slot_lo, prio, G)) continue;
+            }
         }
-        ++n;
-    });
-    return n;
+        const uint32_t ks = (x.w >> 8) & 3u;
+        const uint32_t pref = ks < lanes - 1u ? ks : lanes - 1u;
+        uint32_t qn;
+        if ((free_mask >> pref) & 1u) {
+            qn = pref;
+        } else {
+            const uint32_t rest = free_mask & ~(1u << pref);
+            if (!rest) continue;
+            qn = (uint32_t)(__ffs(rest) - 1);
+        }
+        free_mask &= ~(1u << qn);
+        place(slot_lo + s, x, qn);
+    }
+    return free_mask;
 }
 
 // The step of a node pass at chunk position pos: per step (split steps) the
@@ -1159,7 +1233,7 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
         // base and target are constant within a captured chunk
         unsigned long long step;
         if (!node_step(D, pos, chunk_end != 0u, step)) continue;
-        // staging offsets: exclusive scan of the buffer counts over the block
+        // staging offsets: exclusive scan of the buffer counts over the warp
         const uint32_t cnt = nd.z & 0xFFu;
         uint32_t inc = cnt;
 #pragma unroll
@@ -1167,15 +1241,11 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
             const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
-        if (lane == 31) S.wsum[warp] = inc;
-        __syncthreads();
-        uint32_t base = 0u;
-        for (int w = 0; w < warp; ++w) base += S.wsum[w];
-        const uint32_t off = base + inc - cnt;
-        S.off[threadIdx.x] = off;
-        S.lo[threadIdx.x] = nd.x;
-        if (threadIdx.x == NT - 1) S.off[NT] = off + cnt;
-        __syncthreads();
+        const uint32_t off = inc - cnt;
+        S.off[warp][lane] = off;
+        S.lo[warp][lane] = nd.x;
+        if (lane == 31) S.off[warp][32] = inc;
+        __syncwarp();
         if (!waited) {
             pdl_wait();
             waited = true;
@@ -1188,23 +1258,23 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
         // this thread's inputs (m's cells 0 and queue head) with the staged loads
         const uint2 hd = has ? D.dep_head[m] : make_uint2(0u, 0xFFFFFFFFu);
         const uint32_t free0 = has ? free_cell0(occ, nd) : 0u;
-        const uint32_t total = S.off[NT];
+        const uint32_t total = S.off[warp][32];
         const uint32_t lim = total < (uint32_t)kStageSlots ? total : (uint32_t)kStageSlots;
         const bool tails = TURNS && D.slot_tail != nullptr;
 #pragma unroll 4
-        for (uint32_t e = threadIdx.x; e < lim; e += NT) {
-            // owner: the last thread whose range starts at or before e
+        for (uint32_t e = (uint32_t)lane; e < lim; e += 32u) {
+            // owner: the last lane whose range starts at or before e
             uint32_t i = 0u;
 #pragma unroll
-            for (uint32_t h = NT / 2; h > 0; h >>= 1)
-                if (S.off[i + h] <= e) i += h;
-            const uint32_t si = S.lo[i] + (e - S.off[i]);
-            S.stage[e] = slots[si];
+            for (uint32_t h = 16; h > 0; h >>= 1)
+                if (S.off[warp][i + h] <= e) i += h;
+            const uint32_t si = S.lo[warp][i] + (e - S.off[warp][i]);
+            S.stage[warp][e] = slots[si];
             if constexpr (TURNS) {
-                if (tails) S.tail[e] = D.slot_tail[si];
+                if (tails) S.tail[warp][e] = D.slot_tail[si];
             }
         }
-        __syncthreads();
+        __syncwarp();
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
             if (cur_rec) block_flush<7, NT>(acc, cur_rec, kField, S.red);
@@ -1236,14 +1306,10 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
             const uint32_t lanes = (nd.z >> 8) & 0xFFu, prio = (nd.z >> 16) & 0xFFu;
             uint32_t fr;
             if (off + cnt <= (uint32_t)kStageSlots)
-                fr = resolve_staged<TURNS>(S.stage + off, tails ? S.tail + off : nullptr, nd.x, cnt, m, lanes, free0,
-                                           occ, prio, place);
-            else {
-                uint32_t si[kMaxLanes], qs[kMaxLanes];
-                uint4 xs[kMaxLanes];
-                const uint32_t np = resolve_unstaged<TURNS>(slots, nd, m, free0, D, occ, si, xs, qs, fr);
-                for (uint32_t q = 0; q < np && q < (uint32_t)kMaxLanes; ++q) place(si[q], xs[q], qs[q]);
-            }
+                fr = resolve_staged<TURNS>(S.stage[warp] + off, tails ? S.tail[warp] + off : nullptr, nd.x, cnt, m,
+                                           lanes, free0, occ, prio, place);
+            else  // a node whose buffers do not fit the stage: straight from global memory
+                fr = resolve_global<TURNS>(slots, nd.x, cnt, m, lanes, free0, D, occ, prio, place);
             run_departures_from(D, nd, m, (uint32_t)step, hd, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
                 const uint32_t w = nd.y + qn;
                 occ[w] |= 1u;
@@ -1256,7 +1322,7 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
                 acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
             });
         }
-        __syncthreads();  // the stage is rewritten by the next tile
+        __syncwarp();  // the stage is rewritten by the next tile
     }
     if (cur_rec) block_flush<7, NT>(acc, cur_rec, kField, S.red);
     pdl_trigger();
@@ -1484,10 +1550,15 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+static void (*link_instance(bool turns, bool xfer))(const ScenDev *, const uint2 *, const uint32_t *, uint32_t,
+                                                     unsigned long long *) {
+    if (turns) return xfer ? turn_link_kernel<true> : turn_link_kernel<false>;
+    return xfer ? link_kernel<true> : link_kernel<false>;
+}
+
 void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span) {
-    launch_pdl(turns ? turn_link_kernel : link_kernel, grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i,
-               xfer ? 1u : 0u, span);
+    launch_pdl(link_instance(turns, xfer), grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i, span);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
@@ -1535,9 +1606,10 @@ int max_link_blocks(bool turns) {
     // six blocks of four warps per SM (80 registers a thread: fewer spills
     // than at 64 with eight blocks, measured faster on the 20,024- and
     // 200,000-link networks) need the largest shared-memory share of L1
-    const void *fn = turns ? (const void *)turn_link_kernel : (const void *)link_kernel;
-    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    return resident_blocks(fn, kLinkBlock);
+    for (int x = 0; x < 2; ++x)
+        cudaFuncSetAttribute((const void *)link_instance(turns, x != 0), cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    return resident_blocks((const void *)link_instance(turns, false), kLinkBlock);
 }
 int max_node_blocks(bool turns) {
     const void *fn = turns ? (const void *)turn_node_kernel : (const void *)node_kernel;

@@ -530,14 +530,16 @@ def run_config3(args):
     steps = args.job_steps or 3600
     scs = [N.config3_scenario(i) for i in range(args.scenarios)]
     stream = torch.cuda.Stream()
+    mode_names = {v: k for k, v in STEP_MODES.items()}
     if args.tune_sample > 0:
-        best, timings = Bt.autotune_tile_words(scs[:args.tune_sample], stream, window=256)
+        best, timings = Bt.autotune(scs[:args.tune_sample], stream, window=256)
     else:
-        best, timings = (args.tile_words or 256), {}
-    sims = Bt.make_members(scs, tile_words=best)
+        best, timings = (args.tile_words or 128, 0, STEP_MODES[args.step_mode]), {}
+    sims = Bt.make_members(scs, tile_words=best[0])
     batch = T.Batch(len(sims))
-    batch.set_step_mode(STEP_MODES[args.step_mode])
     batch.add_many(sims, steps)
+    Bt.apply_shape(batch, best)
+    chosen_mode = "fused" if best[2] == STEP_MODES["fused"] else "split"
     for _ in range(args.warmup):
         Bt.run_batched(sims, steps, stream, batch)
     sampler = ClockSampler(0)
@@ -562,15 +564,17 @@ def run_config3(args):
             "config": {"workload": f"{args.scenarios} grid scenarios (side 10-60, 1-3 lanes, 30-120 cells, "
                                    f"0.1-0.4 trips per lane-cell), {steps} steps each, one batch",
                        "lane_cells": lane_cells, "trips": int(sum(sc.demand.n for sc in scs)),
-                       "vehicle_updates_per_run": runs[0].vehicle_updates, "tile_words": best,
-                       "step_mode": args.step_mode,
-                       "autotune_seconds": {str(k): v for k, v in timings.items()},
+                       "vehicle_updates_per_run": runs[0].vehicle_updates,
+                       "launch_shape": {"tile_words": best[0], "link_blocks_per_sm": best[1] or "all resident",
+                                        "step_mode": chosen_mode},
+                       "autotune_seconds": {f"tile_words={k[0]} blocks_per_sm={k[1]} {mode_names[k[2]]}": v
+                                            for k, v in sorted(timings.items(), key=lambda kv: kv[1])},
                        "l2": "inputs larger than L2"},
             "sequential": None if seq is None else {"value": seq.updates_per_s, "unit": METRIC,
                                                     "scenarios": args.seq_sample, "seconds": seq.seconds},
             "batched_over_sequential": None if seq is None else value / seq.updates_per_s,
             "cpu_baseline": None if args.no_cpu_baseline else _cpu_baseline_grids(args.scenarios, 600),
-            "gpu_launches": args.steps * (_launches(steps, args.step_mode) - 1 + args.scenarios),
+            "gpu_launches": args.steps * (_launches(steps, chosen_mode) - 1 + args.scenarios),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     for s_ in sims:

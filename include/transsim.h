@@ -303,6 +303,15 @@ void ts_batch_destroy(ts_batch *b);
 ts_status ts_set_tile_words(ts_ctx *ctx, uint32_t words);
 uint32_t ts_tile_words(const ts_ctx *ctx);
 
+/* Kernel launch shape: the link kernel's grid, at most blocks_per_sm
+ * blocks (of four independent warps, each taking one warp tile at a time)
+ * per SM, 1..64; 0 (default) = every block that can be resident, so each
+ * warp takes about tiles / (resident warps) tiles in turn.  Results do not
+ * depend on it.  Waits (bounded) for queued work; the graphs are captured
+ * again.  TS_ERR_STATE for a context in a batch (set the batch's). */
+ts_status ts_set_link_grid(ts_ctx *ctx, uint32_t blocks_per_sm);
+ts_status ts_batch_set_link_grid(ts_batch *b, uint32_t blocks_per_sm);
+
 /* Advances a periodic ring road held in caller-owned device buffers by
  * n_steps steps, without allocating any device memory.  The paper has no
  * counterpart to this call: it exists for callers that cannot let a

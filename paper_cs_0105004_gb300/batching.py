@@ -7,9 +7,10 @@ each paying its own launches.  Each member keeps its own seed, step counter,
 target step and statistics, so its results are identical to running it
 alone.
 
-The launch shape (occupancy words per link tile) is chosen by a small
-autotuner: it times a short window of the batch for each candidate shape and
-keeps the fastest.  The shape never changes results.
+The launch shape (occupancy words per warp tile, the link kernel's blocks
+per SM, fused or split steps) is chosen by a small autotuner: it times a
+short window of the batch for each candidate shape and keeps the fastest.
+The shape never changes results, which the autotuner checks.
 """
 from __future__ import annotations
 
@@ -48,23 +49,45 @@ def _timed(fn, stream):
     return a.elapsed_time(b) / 1000.0
 
 
-def autotune_tile_words(scenarios, stream, candidates: Sequence[int] = (64, 128, 256), window: int = 256):
-    """Times `window` batch steps from the empty network for every candidate
-    tile size and returns (best, {candidate: seconds})."""
-    timings = {}
-    for tw in candidates:
+def autotune(scenarios, stream, tile_words: Sequence[int] = (32, 64, 128), grids: Sequence[int] = (0, 4, 2),
+             modes: Sequence[int] = (T.STEP_SPLIT, T.STEP_FUSED), window: int = 256):
+    """Times `window` batch steps from the empty network for every launch
+    shape (occupancy words per warp tile x link-kernel blocks per SM, 0 =
+    every resident block x fused or split steps) and returns
+    (best, {(tile_words, blocks_per_sm, mode): seconds}).  Every shape must
+    give the same totals and digests, which is checked."""
+    table, ref = {}, None
+    for tw in tile_words:
         sims = make_members(scenarios, tile_words=tw)
         b = T.Batch(len(sims))
         b.add_many(sims, window)
-        b.step(32, stream)  # capture and warm
-        b.sync()
-        b.reset(window, stream)
-        timings[tw] = _timed(lambda: b.step(window, stream), stream)
+        for grid in grids:
+            b.set_link_grid(grid)
+            for mode in modes:
+                b.set_step_mode(mode)
+                b.reset(window, stream)
+                b.step(32, stream)  # capture and warm
+                b.sync()
+                b.reset(window, stream)
+                table[(tw, grid, mode)] = _timed(lambda: b.step(window, stream), stream)
+                res = [(t["vehicle_updates"], t["last_state_hash"]) for t in (m.totals() for m in sims)]
+                if ref is None:
+                    ref = res
+                elif res != ref:
+                    raise RuntimeError(f"launch shape {(tw, grid, mode)} changed the results")
         b.close()
-        for s in sims:
-            s.close()
-    best = min(timings, key=timings.get)
-    return best, timings
+        for m in sims:
+            m.close()
+    best = min(table, key=table.get)
+    return best, table
+
+
+def apply_shape(batch, shape):
+    """Sets a batch's grid and step mode from an autotune() shape (the tile
+    words are fixed when its members are made)."""
+    _, grid, mode = shape
+    batch.set_link_grid(grid)
+    batch.set_step_mode(mode)
 
 
 def run_batched(sims, steps: int, stream, batch: Optional[T.Batch] = None) -> BatchRun:

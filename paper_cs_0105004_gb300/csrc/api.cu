@@ -50,6 +50,17 @@ ts_status wait_event(cudaEvent_t ev, uint32_t timeout_ms) {
     }
 }
 
+// Waits (at most timeout_ms) for the work queued on s so far.
+constexpr uint32_t kHostWaitMs = 300000;  // internal waits of the library's own calls
+ts_status sync_stream(cudaStream_t s, uint32_t timeout_ms = kHostWaitMs) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, s);
+    ts_status st = e == cudaSuccess ? wait_event(ev, timeout_ms) : cuda_fail(e, "cudaEventRecord");
+    cudaEventDestroy(ev);
+    return st;
+}
+
 }  // namespace
 
 void tsim::set_last_error(const char *msg) { g_err = msg; }
@@ -68,9 +79,10 @@ struct World {
     uint32_t *d_counts = nullptr;  // [0] link tiles, [1] node tiles, read by the kernels
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
-    int grid_l = 1, grid_n = 1;
+    int grid_l = 1, grid_n = 1, grid_cap = 0;
     bool turns = false;  // some member has turn lanes or yield approaches (picks the turn instances)
     uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
+    uint32_t link_blocks_per_sm = 0;  // cap on the link kernel's grid per SM (0: every resident block)
     std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
     unsigned long long *d_span = nullptr;  // kernel spans (kSpanWords), allocated on first use
     bool timing = false;                   // launches record their spans (ts_set_kernel_timing)
@@ -117,6 +129,7 @@ struct ts_ctx {
     uint32_t tile_vehicles = 1024;     // vehicle budget per tile when re-tiling from occupancy
     uint32_t retile_every = 0;         // steps between load-balancing passes (0 = static tiles)
     uint32_t step_mode = TS_STEP_AUTO; // for the context's own world
+    uint32_t link_blocks_per_sm = 0;   // for the context's own world (ts_set_link_grid)
     // vehicles
     bool loaded = false;
     uint32_t n_veh = 0;
@@ -247,12 +260,19 @@ ts_status World::rebuild() {
     // re-tiling changes the tile count on the device: then the grid is every
     // resident block
     const int want = lb ? (1 << 30) : (int)((2ull * n_link_tiles + kLinkWarpsPerBlock - 1) / kLinkWarpsPerBlock);
-    const int gl = std::max(1, std::min<int>(want, max_link_blocks(turns)));
+    int cap = max_link_blocks(turns);
+    if (link_blocks_per_sm) {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+        cap = std::min(cap, (int)link_blocks_per_sm * std::max(sms, 1));
+    }
+    const int gl = std::max(1, std::min<int>(want, cap));
     const int gn = std::max(1, std::min<int>((int)n_node_tiles, max_node_blocks(turns)));
-    if (gl > grid_l || gn != grid_n || gl < grid_l / 2) {
+    if (gl > grid_l || gn != grid_n || gl < grid_l / 2 || cap != grid_cap) {
         drop_graphs();
         grid_l = gl;
         grid_n = gn;
+        grid_cap = cap;
     }
     return TS_OK;
 }
@@ -329,7 +349,8 @@ T *alloc_in(ts_ctx *c, std::vector<std::pair<void *, size_t>> &lst, size_t count
 // Reads the control block (after the context's work is complete).
 ts_status read_ctrl(ts_ctx *c, Ctrl *out) {
     CK(cudaMemcpyAsync(out, c->sd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    const ts_status sw = sync_stream(c->stream);
+    if (sw != TS_OK) return sw;
     if (out->error) {
         c->sticky = true;
         char buf[96];
@@ -490,7 +511,8 @@ ts_status reset_ctrl(ts_ctx *c, uint64_t step, uint64_t arrived, uint64_t insert
     h.hash = hash;
     CK(cudaMemcpyAsync(c->sd.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->sd.stats, 0, sizeof(StatRec) * kStatsRing * c->n_sub, s));
-    CK(cudaStreamSynchronize(s));
+    const ts_status sw = sync_stream(s);
+    if (sw != TS_OK) return sw;
     c->host_step = step;
     return TS_OK;
 }
@@ -797,8 +819,14 @@ static ts_status upload_large(void *dst, const void *src, size_t bytes, cudaStre
     int buf = 0;
     for (size_t off = 0; off < bytes && e == cudaSuccess; off += kStage, buf ^= 1) {
         const size_t n = std::min(kStage, bytes - off);
-        if (off >= 2 * kStage) e = cudaEventSynchronize(done[buf]);  // this buffer's previous copy
-        if (e != cudaSuccess) break;
+        if (off >= 2 * kStage) {  // this buffer's previous copy, bounded
+            const ts_status sw = wait_event(done[buf], kHostWaitMs);
+            if (sw != TS_OK) {
+                cudaEventDestroy(done[0]);
+                cudaEventDestroy(done[1]);
+                return sw;
+            }
+        }
         char *st = static_cast<char *>(stage[buf]);
         std::vector<std::thread> pool;
         for (size_t t = 1; t < nt; ++t)
@@ -808,12 +836,11 @@ static ts_status upload_large(void *dst, const void *src, size_t bytes, cudaStre
         e = cudaMemcpyAsync(to + off, st, n, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaEventRecord(done[buf], s);
     }
-    const cudaError_t e2 = cudaStreamSynchronize(s);
+    const ts_status sw = e == cudaSuccess ? sync_stream(s) : TS_OK;
     cudaEventDestroy(done[0]);
     cudaEventDestroy(done[1]);
     if (e != cudaSuccess) return cuda_fail(e, "route upload");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "route upload");
-    return TS_OK;
+    return sw;
 }
 
 // Allowed lanes of the turn after route entry j (of a route ending before
@@ -934,6 +961,7 @@ static ts_status ensure_own_world(ts_ctx *c) {
     }
     c->own->members[0] = c;
     c->own->mode = c->step_mode;
+    c->own->link_blocks_per_sm = c->link_blocks_per_sm;
     return c->own->rebuild();
 }
 
@@ -1015,7 +1043,8 @@ ts_status ts_load_vehicles(ts_ctx *c, uint32_t n, const uint32_t *dep, const uin
     if (st != TS_OK) return st;
     st = reset_device_state(c, c->stream);
     if (st != TS_OK) return st;
-    CK(cudaStreamSynchronize(c->stream));
+    st = sync_stream(c->stream);
+    if (st != TS_OK) return st;
     c->host_step = 0;
     c->loaded = true;
     CK(cudaEventRecord(c->ev, c->stream));
@@ -1049,6 +1078,27 @@ ts_status ts_set_step_mode(ts_ctx *c, uint32_t mode) {
     c->step_mode = mode;
     if (c->own) c->own->mode = mode;
     return TS_OK;
+}
+
+ts_status ts_set_link_grid(ts_ctx *c, uint32_t blocks_per_sm) {
+    ts_status st = check_ctx(c);
+    if (st != TS_OK) return st;
+    if (blocks_per_sm > 64) return fail(TS_ERR_INVALID, "at most 64 blocks per SM");
+    if (c->batch) return fail(TS_ERR_STATE, "context is in a batch");
+    st = wait_ctx(c, 60000);
+    if (st != TS_OK) return st;
+    c->link_blocks_per_sm = blocks_per_sm;
+    if (c->own) return ensure_own_world(c);
+    return TS_OK;
+}
+
+ts_status ts_batch_set_link_grid(ts_batch *b, uint32_t blocks_per_sm) {
+    if (!b) return fail(TS_ERR_INVALID, "null batch");
+    if (blocks_per_sm > 64) return fail(TS_ERR_INVALID, "at most 64 blocks per SM");
+    ts_status st = wait_event(b->ev, 60000);  // the graphs may be rebuilt
+    if (st != TS_OK) return st;
+    b->w.link_blocks_per_sm = blocks_per_sm;
+    return b->w.rebuild();
 }
 
 ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode) {
@@ -1247,8 +1297,7 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
         }
     }
     if (rs == TS_OK) {
-        const cudaError_t e = cudaEventSynchronize(ev[3ull * n_steps - 1]);
-        if (e != cudaSuccess) rs = cuda_fail(e, "cudaEventSynchronize");
+        rs = wait_event(ev[3ull * n_steps - 1], kHostWaitMs);
     }
     for (uint32_t i = 0; i < n_steps && rs == TS_OK; ++i) {
         cudaEventElapsedTime(&link_ms[i], ev[3ull * i], ev[3ull * i + 1]);
@@ -1366,7 +1415,8 @@ ts_status ts_read_link_times(ts_ctx *c, uint64_t *sum, uint64_t *count, uint32_t
     if (c->n_veh) launch_link_time_fix(c->sd, c->n_veh, c->d_lt_tmp, c->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(sum, c->d_lt_tmp, 8ull * c->n_links, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    st = sync_stream(c->stream, timeout_ms);
+    if (st != TS_OK) return st;
     for (uint32_t l = 0; l < c->n_links; ++l) {
         count[l] = sum[l] >> 40;
         sum[l] &= kLinkTimeOne - 1ull;

@@ -291,7 +291,16 @@ constexpr int kRowWords = kMaxLanes * kSlots;
 constexpr int kCodes = 256;  // listed vehicles per round of a warp
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
+// How much of a warp's next tile is copied in while it works on the current
+// one: 0 nothing, 1 its descriptor and column records, 2 also its columns'
+// words of step t.
+constexpr int kPrefetch = 0;
+
 struct WarpSmem {
+    uint4 pf_ci[kPrefetch >= 1 ? kSlots : 1], pf_ca[kPrefetch >= 1 ? kSlots : 1];
+    uint32_t pf_o[kPrefetch >= 2 ? kRowWords : 1], pf_m[kPrefetch >= 2 ? kRowWords : 1],
+        pf_l[kPrefetch >= 2 ? kRowWords : 1];
+    uint2 pf_td;
     uint32_t o0[kRowWords];  // occupancy of step t (cell 0 placements of fused transfers or-ed in)
     uint32_t m0[kRowWords];  // v > 0 at step t
     uint32_t l0[kRowWords];  // which payload buffer holds each vehicle at step t
@@ -323,6 +332,62 @@ struct LinkSmem {
 };
 
 __device__ __forceinline__ int wi(int k, int s) { return k * kSlots + s; }
+
+// Asynchronous global-to-shared copies (no registers involved); a lane's
+// copies are complete after cp_async_wait_all, other lanes' after that and
+// a __syncwarp.
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    if (bytes == 16) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The column of slot `lane` in a tile of n columns from its record ci (the
+// halo lanes pass the record of the column next to theirs): word of lane 0,
+// column j, neighbour slots, and whether the slot holds a column at all.
+struct ColGeo {
+    uint32_t cw, j;
+    int left, right;
+    bool exists;
+};
+__device__ __forceinline__ ColGeo col_geometry(const uint4 &ci, int lane, int n) {
+    const bool core = lane >= 1 && lane <= n, lh = lane == 0, rh = lane == n + 1;
+    const uint32_t lanes = (ci.z >> 20) & 7u, ring = (ci.z >> 23) & 1u, ncl = (ci.w + 31u) >> 5;
+    ColGeo g{ci.x, ci.z & 0xFFFFFu, -1, -1, core};
+    if (core) {
+        if (g.j > 0u) g.left = lane - 1;  // lane - 1 = 0: the left halo
+        else if (ring) g.left = lane + (int)ncl - 1 <= n ? lane + (int)ncl - 1 : 0;
+        if (g.j + 1u < ncl) g.right = lane + 1;  // lane + 1 = n + 1: the right halo
+        else if (ring) g.right = lane - (int)g.j >= 1 ? lane - (int)g.j : n + 1;
+    } else if (lh) {
+        // left of the first column: its column j - 1, or the ring's last
+        // column when the ring does not fit the tile
+        if (g.j > 0u) {
+            g.exists = true;
+            g.j -= 1u;
+            g.cw -= lanes;
+        } else if (ring && ncl > (uint32_t)n) {
+            g.exists = true;
+            g.j = ncl - 1u;
+            g.cw += (ncl - 1u) * lanes;
+        }
+        g.right = 1;
+    } else if (rh) {
+        if (g.j + 1u < ncl) {
+            g.exists = true;
+            g.j += 1u;
+            g.cw += lanes;
+        } else if (ring && g.j + 1u > (uint32_t)n) {
+            g.exists = true;
+            g.cw -= g.j * lanes;
+            g.j = 0u;
+        }
+        g.left = n;
+    }
+    return g;
+}
 
 __device__ __forceinline__ uint32_t gap_ahead(const uint32_t *O, const WarpSmem &S, int s, int k, int i,
                                               uint32_t dist, uint32_t open, uint32_t vmax) {
@@ -617,13 +682,22 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
     bool waited = false;
     const uint32_t nwarps = gridDim.x * (uint32_t)NW;
     const int s = lane;  // this lane's slot
+    // what the prefetch area holds for the tile about to start: its
+    // descriptor, its column records, its columns' words of step t
+    bool pf_td = false, pf_geo = false, pf_state = false;
     for (uint32_t tile = blockIdx.x * (uint32_t)NW + (uint32_t)warp; tile < n_tiles; tile += nwarps) {
         // the next kernel may launch once every block has begun its last
         // round of tiles (warp 0 has the most tiles of its block): launched
         // earlier, its waiting blocks would hold registers and shared memory
         // this launch still needs
         if (warp == 0 && tile + nwarps >= n_tiles) pdl_trigger();
-        const uint2 td = tiles[tile];
+        if (pf_td) {
+            cp_async_wait_all();
+            __syncwarp();
+        }
+        const uint2 td = pf_td ? S.pf_td : tiles[tile];
+        const bool geo_ready = pf_geo, state_ready = pf_state;
+        pf_td = pf_geo = pf_state = false;
         const ScenDev &D = table[td.x & 0xFFFFFFu];
         if (D.ctrl == nullptr) continue;
         const int n = (int)(td.x >> 24) + 1;
@@ -634,43 +708,16 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         // halo lanes read the column next to theirs and step to their own.
         const bool core = lane >= 1 && lane <= n, lh = lane == 0, rh = lane == n + 1;
         uint4 ci = make_uint4(0u, 0u, 0u, 0u), ca = make_uint4(0u, 0u, 0u, 0u);
-        if (core || lh || rh) ci = D.col_info[core ? cb + (uint32_t)lane - 1u : (lh ? cb : cb + (uint32_t)n - 1u)];
-        if (core) ca = D.col_aux[cb + (uint32_t)lane - 1u];
-        uint32_t cw = ci.x, j = ci.z & 0xFFFFFu;
+        if (core || lh || rh)
+            ci = geo_ready ? S.pf_ci[lane]
+                           : D.col_info[core ? cb + (uint32_t)lane - 1u : (lh ? cb : cb + (uint32_t)n - 1u)];
+        if (core) ca = geo_ready ? S.pf_ca[lane] : D.col_aux[cb + (uint32_t)lane - 1u];
+        const ColGeo geo = col_geometry(ci, lane, n);
+        const uint32_t cw = geo.cw, j = geo.j;
+        const int left = geo.left, right = geo.right;
+        const bool exists = geo.exists;
         const uint32_t link = ci.y, lanes = (ci.z >> 20) & 7u, ring = (ci.z >> 23) & 1u, cells = ci.w;
         const uint32_t ncl = (cells + 31u) >> 5;
-        int left = -1, right = -1;
-        bool exists = core;
-        if (core) {
-            if (j > 0u) left = lane - 1;  // lane - 1 = 0: the left halo
-            else if (ring) left = lane + (int)ncl - 1 <= n ? lane + (int)ncl - 1 : 0;
-            if (j + 1u < ncl) right = lane + 1;  // lane + 1 = n + 1: the right halo
-            else if (ring) right = lane - (int)j >= 1 ? lane - (int)j : n + 1;
-        } else if (lh) {
-            // left of the first column: its column j - 1, or the ring's last
-            // column when the ring does not fit the tile
-            if (j > 0u) {
-                exists = true;
-                j -= 1u;
-                cw -= lanes;
-            } else if (ring && ncl > (uint32_t)n) {
-                exists = true;
-                j = ncl - 1u;
-                cw += (ncl - 1u) * lanes;
-            }
-            right = 1;
-        } else if (rh) {
-            if (j + 1u < ncl) {
-                exists = true;
-                j += 1u;
-                cw += lanes;
-            } else if (ring && j + 1u > (uint32_t)n) {
-                exists = true;
-                cw -= j * lanes;
-                j = 0u;
-            }
-            left = n;
-        }
         const uint32_t kind = core ? 0u : (lh ? 1u : 2u);
         const uint32_t near = exists ? near_mask(ring, cells, 32u * j, vmax) : 0u;
         const bool first = core && !ring && j == 0u, end = core && !ring && j + 1u == ncl;
@@ -720,15 +767,22 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         const uint32_t t = (uint32_t)step;
         const int cur = (int)(step & 1ull), nxt = cur ^ 1;
         const int d = (t & 1u) ? -1 : 1;
+        // prefetch, stage 1: the next tile's descriptor
+        const uint32_t tile_n = tile + nwarps;
+        if (kPrefetch >= 1 && tile_n < n_tiles) {
+            if (lane == 0) cp_async(&S.pf_td, &tiles[tile_n], 8);
+            pf_td = true;
+        }
 
         // ---------------- state of step t: every load before any store
         uint32_t o[kMaxLanes], mo[kMaxLanes], lo[kMaxLanes];
 #pragma unroll
         for (int k = 0; k < kMaxLanes; ++k) {
             const bool w = exists && (uint32_t)k < lanes;
-            o[k] = w ? D.occ[cur][cw + (uint32_t)k] : 0u;
-            mo[k] = w ? D.mov[cur][cw + (uint32_t)k] : 0u;
-            lo[k] = w ? D.loc[cur][cw + (uint32_t)k] : 0u;
+            const bool pre = kPrefetch >= 2 && state_ready;
+            o[k] = w ? (pre ? S.pf_o[wi(k, s)] : D.occ[cur][cw + (uint32_t)k]) : 0u;
+            mo[k] = w ? (pre ? S.pf_m[wi(k, s)] : D.mov[cur][cw + (uint32_t)k]) : 0u;
+            lo[k] = w ? (pre ? S.pf_l[wi(k, s)] : D.loc[cur][cw + (uint32_t)k]) : 0u;
         }
         uint4 own[kMaxLanes];
         const bool plain_end = end && !do_xfer;
@@ -888,6 +942,22 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             });
         }
         __syncwarp();
+        // prefetch, stage 2: the next tile's column records (when it is a
+        // tile of the same scenario: the same step and state buffers)
+        if (pf_td) {
+            cp_async_wait_all();
+            __syncwarp();
+            const uint2 tn = S.pf_td;
+            if ((tn.x & 0xFFFFFFu) == (td.x & 0xFFFFFFu)) {
+                const int nn = (int)(tn.x >> 24) + 1;
+                const bool cn = lane >= 1 && lane <= nn, ln = lane == 0, rn = lane == nn + 1;
+                if (cn || ln || rn)
+                    cp_async(&S.pf_ci[lane],
+                             &D.col_info[cn ? tn.y + (uint32_t)lane - 1u : (ln ? tn.y : tn.y + (uint32_t)nn - 1u)], 16);
+                if (cn) cp_async(&S.pf_ca[lane], &D.col_aux[tn.y + (uint32_t)lane - 1u], 16);
+                pf_geo = true;
+            }
+        }
 
         // ---------------- sub-step 2: velocity update and move.  A vehicle with
         // v = 0, an occupied cell ahead, no lane change and far from the link
@@ -921,6 +991,25 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
                 }
             }
             __syncwarp();
+            // prefetch, stage 3: the next tile's words of step t (read-only
+            // during the step)
+            if (kPrefetch >= 2 && pf_geo) {
+                cp_async_wait_all();
+                __syncwarp();
+                const int nn = (int)(S.pf_td.x >> 24) + 1;
+                if (lane <= nn + 1) {
+                    const uint4 cin = S.pf_ci[lane];
+                    const ColGeo gn = col_geometry(cin, lane, nn);
+                    const uint32_t ln = (cin.z >> 20) & 7u;
+                    if (gn.exists)
+                        for (uint32_t k = 0; k < ln; ++k) {
+                            cp_async(&S.pf_o[wi((int)k, lane)], &D.occ[cur][gn.cw + k], 4);
+                            cp_async(&S.pf_m[wi((int)k, lane)], &D.mov[cur][gn.cw + k], 4);
+                            cp_async(&S.pf_l[wi((int)k, lane)], &D.loc[cur][gn.cw + k], 4);
+                        }
+                }
+                pf_state = true;
+            }
             int8_t *__restrict__ velw0 = D.vel[0];
             int8_t *__restrict__ velw1 = D.vel[1];
             uint32_t *__restrict__ vidw0 = D.vid[0];
@@ -1602,18 +1691,24 @@ extern "C" int ts_debug_phase_sums(unsigned long long *out, int reset) {
 }
 #endif
 
+// Shared-memory share of the unified L1/shared storage the kernels ask for,
+// in percent of the maximum: the rest stays L1, which holds the payload
+// lines a tile's lane-change phase loads and its velocity phase reads again.
+constexpr int kLinkCarveout = 100;
+constexpr int kNodeCarveout = 100;
+
 int max_link_blocks(bool turns) {
     // six blocks of four warps per SM (80 registers a thread: fewer spills
     // than at 64 with eight blocks, measured faster on the 20,024- and
     // 200,000-link networks) need the largest shared-memory share of L1
     for (int x = 0; x < 2; ++x)
         cudaFuncSetAttribute((const void *)link_instance(turns, x != 0), cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+                             kLinkCarveout);
     return resident_blocks((const void *)link_instance(turns, false), kLinkBlock);
 }
 int max_node_blocks(bool turns) {
     const void *fn = turns ? (const void *)turn_node_kernel : (const void *)node_kernel;
-    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, kNodeCarveout);
     return resident_blocks(fn, kNodeThreads);
 }
 

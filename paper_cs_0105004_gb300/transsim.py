@@ -115,6 +115,8 @@ _API = {
     "ts_philox_words": (ctypes.c_int, [ctypes.c_uint32, u32p, u32p, ctypes.c_uint64, u32p]),
     "ts_set_load_balance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
     "ts_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_set_link_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "ts_batch_set_link_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "ts_read_kernel_times": (ctypes.c_int, [ctypes.c_void_p, u64p, ctypes.c_uint32, ctypes.c_uint32]),
     "ts_ring_step_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(Params), ctypes.c_uint64,
                                             ctypes.c_uint32] + [ctypes.c_void_p] * 8),
@@ -292,6 +294,10 @@ class Simulation:
                                         tcnt.ctypes.data_as(ctypes.c_void_p), timeout_ms))
         return tsum, tcnt
 
+    def set_link_grid(self, blocks_per_sm: int):
+        """Link-kernel blocks per SM (0: every resident block); results do not depend on it."""
+        _check(lib().ts_set_link_grid(self.h, blocks_per_sm))
+
     def set_kernel_timing(self, on: bool):
         """Launches of later ts_step calls record their spans inside the graphs."""
         _check(lib().ts_set_kernel_timing(self.h, 1 if on else 0))
@@ -389,6 +395,9 @@ class Batch:
 
     def set_step_mode(self, mode: int):
         _check(lib().ts_batch_set_step_mode(self.h, mode))
+
+    def set_link_grid(self, blocks_per_sm: int):
+        _check(lib().ts_batch_set_link_grid(self.h, blocks_per_sm))
 
     def sync(self, timeout_ms: int = 600000):
         _check(lib().ts_batch_sync(self.h, timeout_ms))

@@ -64,10 +64,14 @@ def test_batched_run_equals_sequential_runs():
     import torch
     scs = [N.config3_scenario(i, demand_scale=0.05, steps=400) for i in range(4)]
     stream = torch.cuda.Stream()
-    best, timings = Bt.autotune_tile_words(scs, stream, window=64)
-    assert best in timings
-    sims = Bt.make_members(scs, tile_words=best)
-    b = Bt.run_batched(sims, 400, stream)
+    best, timings = Bt.autotune(scs, stream, tile_words=(32, 128), grids=(0, 2), window=64)
+    assert best in timings and len(timings) == 8
+    sims = Bt.make_members(scs, tile_words=best[0])
+    batch = T.Batch(len(sims))
+    batch.add_many(sims, 400)
+    Bt.apply_shape(batch, best)
+    b = Bt.run_batched(sims, 400, stream, batch)
+    batch.close()
     s = Bt.run_sequential(sims, 400, stream)
     assert b.per_member_updates == s.per_member_updates
     for sim in sims:

@@ -243,7 +243,7 @@ def run_profile_window(args):
         sc, _ = _workload(args.workload)
         sim = T.Simulation(sc, tile_words=args.tile_words)
         if args.load_balance:
-            sim.set_load_balance(args.load_balance, args.tile_vehicles or 6 * sim.tile_words)
+            sim.set_load_balance(args.load_balance, args.tile_vehicles or 512)
         sim.set_step_mode(STEP_MODES[args.step_mode])
         sims = [sim]
         advance = lambda k: sim.step(k, stream)
@@ -278,17 +278,18 @@ def kernel_sha():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _profile_traffic(kernel, workload):
+def _profile_traffic(kernel, workload, tag="bench-traffic"):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    summaries (a line 'bench-traffic: kernel=K workload=W kernel_sha=S
-    dram_bytes_per_launch=B' in profiles/*.md), or None when no summary was
-    taken from the current kernel source."""
+    summaries (a line '<tag>: kernel=K workload=W kernel_sha=S
+    dram_bytes_per_launch=B' in profiles/*.md; tag bench-traffic: caches
+    flushed before the launch, bench-traffic-warm: caches left warm), or None
+    when no summary was taken from the current kernel source."""
     import glob
     import re
     sha = kernel_sha()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for ln in open(path):
-            m = re.match(r"bench-traffic: kernel=(\S+) workload=(\S+) kernel_sha=(\S+) "
+            m = re.match(re.escape(tag) + r": kernel=(\S+) workload=(\S+) kernel_sha=(\S+) "
                          r"dram_bytes_per_launch=([0-9.eE+]+)", ln.strip())
             if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == sha:
                 return float(m.group(4)), os.path.relpath(path, ROOT)
@@ -309,8 +310,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sim = T.Simulation(sc, tile_words=args.tile_words)
+    # the re-tiling budget (vehicles per warp tile): given, or tuned on the
+    # first warm-up jobs, one candidate each, the fastest kept
+    tune = [] if (args.tile_vehicles or not args.load_balance) else [128, 256, 512]
+    if len(tune) + 2 > args.warmup:
+        tune = []  # the first warm-up job captures the graphs, the last runs the choice
+    budget = args.tile_vehicles or 512
     if args.load_balance:
-        sim.set_load_balance(args.load_balance, args.tile_vehicles or 6 * sim.tile_words)
+        sim.set_load_balance(args.load_balance, budget)
     sim.set_step_mode(STEP_MODES[args.step_mode])
     net = sc.net
     C = net.n_lane_cells
@@ -321,10 +328,21 @@ def run_ours(args, rank, world, local_rank):
 
     # warm-up jobs (also capture the CUDA graphs)
     ref_tot = None
-    for _ in range(args.warmup):
+    tuned = {}
+    for w in range(args.warmup):
+        if 1 <= w <= len(tune):
+            sim.set_load_balance(args.load_balance, tune[w - 1])
+        elif w == len(tune) + 1 and tune:
+            budget = min(tuned, key=tuned.get)
+            sim.set_load_balance(args.load_balance, budget)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
+            a.record(stream)
             job(stream)
+            b.record(stream)
         stream.synchronize()
+        if 1 <= w <= len(tune):
+            tuned[tune[w - 1]] = a.elapsed_time(b)
         tot = sim.totals()
         if ref_tot is not None and tot != ref_tot:
             raise RuntimeError("two runs of the same job differ")
@@ -394,13 +412,15 @@ def run_ours(args, rank, world, local_rank):
     turns = getattr(net, "turn_lanes", None) is not None or getattr(net, "link_yield", None) is not None
     kernel = "turn_link_kernel" if turns else "link_kernel"
     traffic, traffic_src = _profile_traffic(kernel, args.workload)
+    traffic_warm, _ = _profile_traffic(kernel, args.workload, "bench-traffic-warm")
     if args.traffic is not None:
         traffic, traffic_src = args.traffic, "command line"
     step_bytes = (10.0 * updates + 0.25 * C * steps_per_job + 20.0 * tot["transfers"]
                   + 10.0 * tot["inserted"]) / steps_per_job
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
-                "traffic_source": traffic_src, "avg_launch_us": link_us,
+                "traffic_source": traffic_src, "traffic_note": "ncu, caches flushed before the launch",
+                "traffic_warm_l2": traffic_warm, "avg_launch_us": link_us,
                 "algorithmic_bytes_per_launch": link_bytes,
                 "timing": "in-graph kernel spans (%globaltimer) of one extra job, same graphs and launch shapes",
                 "span_job_ms": timed_job_ms, "spans_ms_per_job": 1e3 * (kt["link_s"] + kt["node_s"]),
@@ -448,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             s2 = T.Simulation(sc, tile_words=args.tile_words)
             if args.load_balance:
-                s2.set_load_balance(args.load_balance, args.tile_vehicles or 6 * s2.tile_words)
+                s2.set_load_balance(args.load_balance, budget)
             s2.set_step_mode(STEP_MODES[args.step_mode])
             s2.step(steps_per_job)
             t2 = s2.totals()
@@ -480,8 +500,8 @@ def run_ours(args, rank, world, local_rank):
                                  "across the steps of a job",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "tile_words": sim.tile_words, "step_mode": args.step_mode,
-                           "load_balance": {"every_steps": args.load_balance,
-                                            "vehicles_per_tile": args.tile_vehicles or 6 * sim.tile_words},
+                           "load_balance": {"every_steps": args.load_balance, "vehicles_per_tile": budget,
+                                            "tuned_on_warmup_ms": {str(k): round(v, 2) for k, v in tuned.items()}},
                            "bit_exact_hash": str(tot["last_state_hash"])},
                 "roofline": roofline, "window": window, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * _launches(steps_per_job, args.step_mode, args.load_balance),
@@ -767,7 +787,8 @@ def main():
                     help="fused: one launch per step; split: link and node kernel per step")
     ap.add_argument("--load-balance", type=int, default=512, help="re-tile from the occupancy every N steps (0 = off)")
     ap.add_argument("--tile-vehicles", type=int, default=None,
-                    help="vehicle budget per tile when re-tiling (default: 6 per occupancy word of a tile)")
+                    help="vehicle budget per warp tile when re-tiling (default: tuned on the warm-up jobs among "
+                         "128, 256 and 512 when there are at least four, else 512)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per link_kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

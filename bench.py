@@ -66,16 +66,6 @@ def _launches(steps, mode, every=0, start=0):
     return n
 
 
-def _node_launch_ms(node_ms, mode):
-    """Durations of the node-kernel launches of a ts_step_timed run (fused
-    steps launch it for the last step of each chunk of 32 only)."""
-    import numpy as np
-    if mode != "fused":
-        return node_ms
-    n = node_ms.size
-    return np.concatenate([node_ms[31::32], node_ms[-1:] if n % 32 else node_ms[:0]])
-
-
 def _workload(name):
     from paper_cs_0105004_gb300.inputs import networks as N
     sc = {"config1": N.config1, "config2": N.config2, "config0": N.config0, "plan1": N.config1,
@@ -636,12 +626,17 @@ def run_empty(args):
     sampler.start()
     secs = [job() for _ in range(args.steps)]
     clocks = sampler.stop()
-    sim.reset(stream)
-    lm, nm = sim.step_timed(min(steps, 2048), stream)
+    # the kernels' durations inside the same graphs (kernel spans of one more job)
+    sim.set_kernel_timing(True)
+    sim.kernel_times(reset=True)
+    job()
+    kt = sim.kernel_times()
+    sim.set_kernel_timing(False)
     sec = sum(secs)
     C = sc.net.n_lane_cells
     peak, src = _peaks()
-    link_us = float(np.mean(lm)) * 1e3
+    link_us = 1e6 * kt["link_s"] / max(1, kt["link_launches"])
+    node_us = 1e6 * kt["node_s"] / max(1, kt["node_launches"])
     line = {"metric": "lane-cell updates/s", "value": C * steps * args.steps / sec, "unit": "lane-cell updates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -653,7 +648,8 @@ def run_empty(args):
             "roofline": {"bound": "hbm", "kernel": "link_kernel", "achieved": 0.25 * C / (link_us * 1e-6) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": 0.25 * C / (link_us * 1e-6) / 1e9 / peak,
                          "peak_source": src, "traffic": None, "avg_launch_us": link_us,
-                         "node_kernel_avg_launch_us": float(np.mean(_node_launch_ms(nm, args.step_mode))) * 1e3},
+                         "timing": "in-graph kernel spans of one extra job",
+                         "node_kernel_avg_launch_us": node_us},
             "gpu_launches": args.steps * _launches(steps, args.step_mode),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
@@ -746,7 +742,10 @@ def run_config4(args):
             "config": {"workload": f"Poisson {args.rate}/s jobs for {args.duration} s, mix config0:config1:grid = "
                                    f"{args.serve_mix}, {steps} steps per job, arrival clock x{args.time_scale}",
                        "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
-            "serving": summ, "one_job_at_a_time": one, "clocks": clocks}
+            "serving": summ, "one_job_at_a_time": one,
+            "served_over_one_at_a_time": (None if one is None else
+                                          summ["vehicle_updates_per_s"] / one["vehicle_updates_per_s"]),
+            "gpu_launches": summ["chunks"] * (2 * args.chunk + (args.chunk + 31) // 32), "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

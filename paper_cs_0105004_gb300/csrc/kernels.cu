@@ -289,6 +289,10 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
 constexpr int kSlots = 32;  // slot = lane
 constexpr int kRowWords = kMaxLanes * kSlots;
 constexpr int kCodes = 256;  // listed vehicles per round of a warp
+// 1: a lane copies the payload words of all its listed vehicles of a round
+// into shared memory (cp.async) before processing any, so it waits one
+// memory round trip per round instead of one per vehicle
+constexpr int kStagePayload = 1;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 // How much of a warp's next tile is copied in while it works on the current
@@ -320,6 +324,7 @@ struct WarpSmem {
     uint8_t cexit[kSlots];   // lanes whose link-end buffer is free in this step (near columns)
     uint8_t cgreen[kSlots];  // the light at the link end is green in this step (1 without a signal)
     uint16_t code[kCodes];
+    uint32_t pla[kStagePayload ? kCodes : 1], plb[kStagePayload ? kCodes : 1];  // staged payload words
 };
 
 template <int NW>
@@ -467,13 +472,16 @@ __device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[kMaxLanes],
     }
 }
 
-// The same with each vehicle's step split in two: load(code, a, b) fetches
-// what it needs from global memory (its step-t payload, which no thread
-// writes during the step) and proc(code, a, b) completes it.  (Issuing two
-// vehicles' loads before processing either was measured slower on the
-// 200,000-link network: 55.6 vs 47.4 us per launch.)
-template <class L, class F>
-__device__ __forceinline__ void warp_list2(WarpSmem &S, uint32_t (&m)[kMaxLanes], int slot, L &&load, F &&proc) {
+// The same with each vehicle's step split in two: addr(code, pa, pb) gives
+// the global 32-bit words its step needs (its step-t payload, which no
+// thread writes during the step; nullptr: not needed) and proc(code, wa, wb)
+// completes it from their values.  With kStagePayload the words of all the
+// lane's vehicles of a round are copied to shared memory before any is
+// processed.  (Loading two vehicles' payload into registers before
+// processing either was measured slower on the 200,000-link network: 55.6
+// vs 47.4 us per launch.)
+template <class A, class F>
+__device__ __forceinline__ void warp_list2(WarpSmem &S, uint32_t (&m)[kMaxLanes], int slot, A &&addr, F &&proc) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         uint32_t cnt = 0u;
@@ -498,15 +506,35 @@ __device__ __forceinline__ void warp_list2(WarpSmem &S, uint32_t (&m)[kMaxLanes]
         }
         __syncwarp();
         const uint32_t nproc = total < (uint32_t)kCodes ? total : (uint32_t)kCodes;
-        for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
-            const uint32_t c = S.code[e];
-            uint32_t a, b;
-            load(c, a, b);
-            proc(c, a, b);
+        if constexpr (kStagePayload != 0) {
+            for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
+                const uint32_t *pa = nullptr, *pb = nullptr;
+                addr((uint32_t)S.code[e], pa, pb);
+                if (pa) cp_async(&S.pla[e], pa, 4);
+                else S.pla[e] = 0u;
+                if (pb) cp_async(&S.plb[e], pb, 4);
+                else S.plb[e] = 0u;
+            }
+            cp_async_wait_all();  // this lane's own copies: it alone reads them
+            for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) proc((uint32_t)S.code[e], S.pla[e], S.plb[e]);
+        } else {
+            for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
+                const uint32_t c = S.code[e];
+                const uint32_t *pa = nullptr, *pb = nullptr;
+                addr(c, pa, pb);
+                proc(c, pa ? *pa : 0u, pb ? *pb : 0u);
+            }
         }
         __syncwarp();
     }
 }
+
+// The aligned 32-bit word holding byte p of an int8 array (whose length is
+// a multiple of 4), and the byte's value from that word.
+__device__ __forceinline__ const uint32_t *byte_word(const int8_t *a, size_t p) {
+    return reinterpret_cast<const uint32_t *>(a + (p & ~(size_t)3));
+}
+__device__ __forceinline__ uint32_t word_byte(uint32_t w, uint32_t p) { return (w >> (8u * (p & 3u))) & 0xFFu; }
 
 // Sum over the warp, then lane f adds field f's sum at rec + field[f].
 template <int NF>
@@ -885,19 +913,18 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             __syncwarp();
             // payload at step t (velocity byte; the id only within vmax
             // cells of the link end, for its last-link flag)
-            auto lcload = [&](uint32_t code, uint32_t &byte, uint32_t &idw) {
+            auto lcaddr = [&](uint32_t code, const uint32_t *&pv, const uint32_t *&pid) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
                 const int k = ww / kSlots, c = ww - k * kSlots, kt = k + d;
-                byte = 0u;
-                idw = 0u;
                 if ((S.o0[wi(kt, c)] >> i) & 1u) return;  // target cell taken: not needed
                 const size_t p = (size_t)(S.cw[c] + (uint32_t)k) * 32u + (uint32_t)i;
                 const bool b1 = (S.l0[ww] >> i) & 1u;
-                byte = (uint32_t)(uint8_t)(b1 ? vel1[p] : vel0[p]);
-                if ((S.cnear[c] >> i) & 1u) idw = b1 ? vid1[p] : vid0[p];
+                pv = byte_word(b1 ? vel1 : vel0, p);
+                if ((S.cnear[c] >> i) & 1u) pid = (b1 ? vid1 : vid0) + p;
             };
-            warp_list2(S, lst, s, lcload, [&](uint32_t code, uint32_t byte, uint32_t idw) {
+            warp_list2(S, lst, s, lcaddr, [&](uint32_t code, uint32_t vword, uint32_t idw) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
+                const uint32_t byte = word_byte(vword, (uint32_t)i);
                 const int k = ww / kSlots, c = ww - k * kSlots, kt = k + d;
                 if ((S.o0[wi(kt, c)] >> i) & 1u) return;  // target cell taken
                 const uint32_t ringc = S.cring[c];
@@ -1017,17 +1044,18 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
             const uint32_t key0 = D.seed_lo, key1 = D.seed_hi, pthr = D.p_threshold;
             // payload from where the vehicle was at step t; no thread of
             // this step writes a buffer that a step-t occupant is read from
-            auto vload = [&](uint32_t code, uint32_t &idw, uint32_t &byte) {
+            auto vaddr = [&](uint32_t code, const uint32_t *&pid, const uint32_t *&pv) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
                 const int k = ww / kSlots, c = ww - k * kSlots;
                 const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
                 const size_t ps = (size_t)(S.cw[c] + (uint32_t)ks) * 32u + (uint32_t)i;
                 const bool sb1 = (S.l0[wi(ks, c)] >> i) & 1u;
-                idw = sb1 ? vid1[ps] : vid0[ps];
-                byte = (uint32_t)(uint8_t)(sb1 ? vel1[ps] : vel0[ps]);
+                pid = (sb1 ? vid1 : vid0) + ps;
+                pv = byte_word(sb1 ? vel1 : vel0, ps);
             };
-            warp_list2(S, lst, s, vload, [&](uint32_t code, uint32_t idw, uint32_t byte) {
+            warp_list2(S, lst, s, vaddr, [&](uint32_t code, uint32_t idw, uint32_t vword) {
                 const int ww = (int)(code >> 5), i = (int)(code & 31u);
+                const uint32_t byte = word_byte(vword, (uint32_t)i);
                 const int k = ww / kSlots, c = ww - k * kSlots;
                 const int ks = ((S.mv[ww] >> i) & 1u) ? k - d : k;  // lane at step t
                 uint32_t v0, al = 0u;  // al: allowed lanes of the next turn (0: any)
@@ -1346,11 +1374,23 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
         uint4 *slots = D.slots[nxt];
         // this thread's inputs (m's cells 0 and queue head) with the staged loads
         const uint2 hd = has ? D.dep_head[m] : make_uint2(0u, 0xFFFFFFFFu);
-        const uint32_t free0 = has ? free_cell0(occ, nd) : 0u;
+        // m's column-0 words (this thread is their only writer in the pass):
+        // loaded once, changed bits written once at the end
+        const uint32_t mlanes = (nd.z >> 8) & 0xFFu;
+        uint32_t o4[kMaxLanes], m4[kMaxLanes];
+        uint32_t free0 = 0u;
+#pragma unroll
+        for (int k = 0; k < kMaxLanes; ++k) {
+            const bool w = has && (uint32_t)k < mlanes;
+            o4[k] = w ? occ[nd.y + (uint32_t)k] : 1u;
+            m4[k] = w ? mov[nd.y + (uint32_t)k] : 0u;
+            free0 |= ((o4[k] & 1u) ^ 1u) << k;
+        }
+        uint32_t placed = 0u, moved = 0u;
         const uint32_t total = S.off[warp][32];
         const uint32_t lim = total < (uint32_t)kStageSlots ? total : (uint32_t)kStageSlots;
         const bool tails = TURNS && D.slot_tail != nullptr;
-#pragma unroll 4
+        // every copy is issued before any is waited for (one round trip)
         for (uint32_t e = (uint32_t)lane; e < lim; e += 32u) {
             // owner: the last lane whose range starts at or before e
             uint32_t i = 0u;
@@ -1358,11 +1398,12 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
             for (uint32_t h = 16; h > 0; h >>= 1)
                 if (S.off[warp][i + h] <= e) i += h;
             const uint32_t si = S.lo[warp][i] + (e - S.off[warp][i]);
-            S.stage[warp][e] = slots[si];
+            cp_async(&S.stage[warp][e], &slots[si], 16);
             if constexpr (TURNS) {
-                if (tails) S.tail[warp][e] = D.slot_tail[si];
+                if (tails) cp_async(&S.tail[warp][e], &D.slot_tail[si], 8);
             }
         }
+        cp_async_wait_all();
         __syncwarp();
         unsigned long long *rec = reinterpret_cast<unsigned long long *>(stat_rec(D, step));
         if (rec != cur_rec) {
@@ -1375,8 +1416,8 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
             auto place = [&](uint32_t si, const uint4 &x, uint32_t qn) {
                 const uint32_t id = x.x & kIdMask, v = x.w & (TURNS ? 0xFu : 0xFFu), ks = (x.w >> 8) & 3u;
                 const uint32_t w = nd.y + qn;  // column 0 of lane qn
-                occ[w] |= 1u;
-                if (v) mov[w] |= 1u;
+                placed |= 1u << qn;
+                if (v) moved |= 1u << qn;
                 vel[(size_t)w * 32u] = (int8_t)(TURNS ? (x.w & 0xFFu) : v);
                 vid[(size_t)w * 32u] = x.x;  // id with the last-link flag of m
                 atomicAdd(&D.veh[id].x, 1u);
@@ -1401,7 +1442,7 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
                 fr = resolve_global<TURNS>(slots, nd.x, cnt, m, lanes, free0, D, occ, prio, place);
             run_departures_from(D, nd, m, (uint32_t)step, hd, fr, [&](uint32_t idw, uint32_t qn, uint32_t qi) {
                 const uint32_t w = nd.y + qn;
-                occ[w] |= 1u;
+                placed |= 1u << qn;
                 vel[(size_t)w * 32u] = (TURNS && D.dep_turn) ? (int8_t)(D.dep_turn[qi] << 4) : (int8_t)0;
                 vid[(size_t)w * 32u] = idw;
                 atomicAdd(&D.link_time[m], 0ull - step);
@@ -1410,6 +1451,11 @@ __device__ __forceinline__ void node_pass(NodeSmem<NT, TURNS> &S, const ScenDev 
                 acc[2] += 1;
                 acc[5] += vehicle_term(idw & kIdMask, m, qn, 0u, 0u);
             });
+#pragma unroll
+            for (int k = 0; k < kMaxLanes; ++k) {
+                if ((placed >> k) & 1u) occ[nd.y + (uint32_t)k] = o4[k] | 1u;
+                if ((moved >> k) & 1u) mov[nd.y + (uint32_t)k] = m4[k] | 1u;
+            }
         }
         __syncwarp();  // the stage is rewritten by the next tile
     }
@@ -1692,10 +1738,12 @@ extern "C" int ts_debug_phase_sums(unsigned long long *out, int reset) {
 #endif
 
 // Shared-memory share of the unified L1/shared storage the kernels ask for,
-// in percent of the maximum: the rest stays L1, which holds the payload
-// lines a tile's lane-change phase loads and its velocity phase reads again.
-constexpr int kLinkCarveout = 100;
-constexpr int kNodeCarveout = 100;
+// in percent of the maximum (228 KB); the rest stays L1, which holds the
+// payload lines a tile's lane-change phase loads and its velocity phase
+// reads again.  Measured on GB300 (config 2, link kernel per launch): 60 %
+// 47.0 us, 100 % 48.3, 70 % 56.4, 50 % 49.8, 40 % 67.6.
+constexpr int kLinkCarveout = 60;
+constexpr int kNodeCarveout = 50;
 
 int max_link_blocks(bool turns) {
     // six blocks of four warps per SM (80 registers a thread: fewer spills

@@ -51,6 +51,7 @@ class ServeReport:
     peak_bytes: int
     mean_active: float
     rejected: List[Job] = field(default_factory=list)  # jobs larger than the whole budget
+    chunks: int = 0           # batch steps enqueued (each `chunk_steps` steps of one batch)
 
     def latencies(self):
         return np.array([j.finished - j.arrival for j in self.jobs])
@@ -63,7 +64,7 @@ class ServeReport:
                 "vehicle_updates": int(upd), "vehicle_updates_per_s": upd / self.wall_s,
                 "wall_s": self.wall_s, "peak_active_jobs": self.peak_active,
                 "mean_active_jobs": self.mean_active, "peak_job_bytes": self.peak_bytes,
-                "rejected_jobs": len(self.rejected)}
+                "rejected_jobs": len(self.rejected), "chunks": self.chunks}
 
 
 def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int) -> np.ndarray:
@@ -114,6 +115,7 @@ class Server:
         peak_active = peak_bytes = 0
         active_samples = []
         cur = 0
+        chunks = 0
         while pending or building or ready or active[0] or active[1]:
             t = now()
             while pending and pending[0].arrival * time_scale <= t:
@@ -177,13 +179,14 @@ class Server:
                 active_samples.append(len(active[0]) + len(active[1]))
                 b.step(self.chunk, self.stream)
                 queued[cur] = True
+                chunks += 1
             elif not queued[cur ^ 1]:
                 nxt = pending[0].arrival * time_scale - now() if pending else 0.0
                 time.sleep(max(0.0, min(nxt, 0.002)) if not building else 0.0005)
             cur ^= 1
         wall = now()
         return ServeReport(done, wall, busy, peak_active, peak_bytes,
-                           float(np.mean(active_samples)) if active_samples else 0.0, rejected)
+                           float(np.mean(active_samples)) if active_samples else 0.0, rejected, chunks)
 
     def close(self):
         self.pool.shutdown()

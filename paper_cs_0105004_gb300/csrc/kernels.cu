@@ -289,10 +289,6 @@ __device__ __forceinline__ void run_departures(const ScenDev &D, const uint4 &nd
 constexpr int kSlots = 32;  // slot = lane
 constexpr int kRowWords = kMaxLanes * kSlots;
 constexpr int kCodes = 256;  // listed vehicles per round of a warp
-// 1: a lane copies the payload words of all its listed vehicles of a round
-// into shared memory (cp.async) before processing any, so it waits one
-// memory round trip per round instead of one per vehicle
-constexpr int kStagePayload = 1;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 // How much of a warp's next tile is copied in while it works on the current
@@ -324,7 +320,6 @@ struct WarpSmem {
     uint8_t cexit[kSlots];   // lanes whose link-end buffer is free in this step (near columns)
     uint8_t cgreen[kSlots];  // the light at the link end is green in this step (1 without a signal)
     uint16_t code[kCodes];
-    uint32_t pla[kStagePayload ? kCodes : 1], plb[kStagePayload ? kCodes : 1];  // staged payload words
 };
 
 template <int NW>
@@ -475,11 +470,10 @@ __device__ __forceinline__ void warp_list(WarpSmem &S, uint32_t (&m)[kMaxLanes],
 // The same with each vehicle's step split in two: addr(code, pa, pb) gives
 // the global 32-bit words its step needs (its step-t payload, which no
 // thread writes during the step; nullptr: not needed) and proc(code, wa, wb)
-// completes it from their values.  With kStagePayload the words of all the
-// lane's vehicles of a round are copied to shared memory before any is
-// processed.  (Loading two vehicles' payload into registers before
-// processing either was measured slower on the 200,000-link network: 55.6
-// vs 47.4 us per launch.)
+// completes it from their values.  (Measured on the 200,000-link network:
+// loading two vehicles' payload into registers before processing either,
+// 55.6 vs 47.4 us per launch; copying all of a lane's payload words of a
+// round into shared memory first, 47.2-48.5 vs 46.4 us.)
 template <class A, class F>
 __device__ __forceinline__ void warp_list2(WarpSmem &S, uint32_t (&m)[kMaxLanes], int slot, A &&addr, F &&proc) {
     const int lane = threadIdx.x & 31;
@@ -506,24 +500,11 @@ __device__ __forceinline__ void warp_list2(WarpSmem &S, uint32_t (&m)[kMaxLanes]
         }
         __syncwarp();
         const uint32_t nproc = total < (uint32_t)kCodes ? total : (uint32_t)kCodes;
-        if constexpr (kStagePayload != 0) {
-            for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
-                const uint32_t *pa = nullptr, *pb = nullptr;
-                addr((uint32_t)S.code[e], pa, pb);
-                if (pa) cp_async(&S.pla[e], pa, 4);
-                else S.pla[e] = 0u;
-                if (pb) cp_async(&S.plb[e], pb, 4);
-                else S.plb[e] = 0u;
-            }
-            cp_async_wait_all();  // this lane's own copies: it alone reads them
-            for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) proc((uint32_t)S.code[e], S.pla[e], S.plb[e]);
-        } else {
-            for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
-                const uint32_t c = S.code[e];
-                const uint32_t *pa = nullptr, *pb = nullptr;
-                addr(c, pa, pb);
-                proc(c, pa ? *pa : 0u, pb ? *pb : 0u);
-            }
+        for (uint32_t e = (uint32_t)lane; e < nproc; e += 32u) {
+            const uint32_t c = S.code[e];
+            const uint32_t *pa = nullptr, *pb = nullptr;
+            addr(c, pa, pb);
+            proc(c, pa ? *pa : 0u, pb ? *pb : 0u);
         }
         __syncwarp();
     }
@@ -1741,7 +1722,7 @@ extern "C" int ts_debug_phase_sums(unsigned long long *out, int reset) {
 // in percent of the maximum (228 KB); the rest stays L1, which holds the
 // payload lines a tile's lane-change phase loads and its velocity phase
 // reads again.  Measured on GB300 (config 2, link kernel per launch): 60 %
-// 47.0 us, 100 % 48.3, 70 % 56.4, 50 % 49.8, 40 % 67.6.
+// 46.4-47.0 us, 56 % 51.8, 100 % 48.3, 70 % 56.4, 50 % 49.8, 40 % 67.6.
 constexpr int kLinkCarveout = 60;
 constexpr int kNodeCarveout = 50;
 

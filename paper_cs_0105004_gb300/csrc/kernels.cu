@@ -729,6 +729,8 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         const uint32_t ncl = (cells + 31u) >> 5;
         const uint32_t kind = core ? 0u : (lh ? 1u : 2u);
         const uint32_t near = exists ? near_mask(ring, cells, 32u * j, vmax) : 0u;
+        // the link's last cell, when it lies in this column
+        const uint32_t endb = (exists && !ring && cells - 1u - 32u * j < 32u) ? 1u << (cells - 1u - 32u * j) : 0u;
         const bool first = core && !ring && j == 0u, end = core && !ring && j + 1u == ncl;
         const uint32_t bpos = ca.x;
         S.cw[s] = exists ? cw : kNoSlot;
@@ -862,7 +864,11 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         // target cell and the vmax cells behind it are empty and the target
         // lane's next cell is free.  That is decided here for whole words.  A
         // vehicle with v = 0 and a free cell ahead has no reason to change.
-        // Moving vehicles and vehicles near a link end are decided one by one.
+        // Both hold within vmax of a link end too: the gaps compared are 0 and
+        // whether the next cell of the target lane (inside the link) is free,
+        // neither of which looks past the end.  Moving vehicles and a vehicle
+        // in a link's last cell (whose gaps do: the end's state, its last-link
+        // flag) are decided one by one.
         if (D.lane_change != 0u) {
             uint32_t lst[kMaxLanes] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -883,12 +889,18 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
                     uint32_t behind = 0u;
                     for (uint32_t b = 1; b <= vmax; ++b) behind |= (uint32_t)(tt >> (32 - b));
                     const uint32_t okm = ahead_mask(S.o0, S, s, k) & ~tw & ~behind & ~ahead_mask(S.o0, S, s, kt);
-                    const uint32_t lcv0 = oc & ~S.m0[wi(k, s)] & ~near & okm;
+                    const uint32_t lcv0 = oc & ~S.m0[wi(k, s)] & ~endb & okm;
                     if (lcv0) {
                         S.mv[wi(kt, s)] |= lcv0;  // this lane's own slot
                         if (core) acc[1] += (uint32_t)__popc(lcv0);
                     }
-                    lst[k] = oc & (S.m0[wi(k, s)] | near);
+                    // a vehicle with vmax free cells ahead, more than vmax
+                    // cells before the end, has a gap of vmax: no reason
+                    const unsigned long long ow =
+                        ((unsigned long long)(right >= 0 ? S.o0[wi(k, right)] : 0u) << 32) | S.o0[wi(k, s)];
+                    uint32_t busy_ahead = 0u;
+                    for (uint32_t b = 1; b <= vmax; ++b) busy_ahead |= (uint32_t)(ow >> b);
+                    lst[k] = oc & ((S.m0[wi(k, s)] & (busy_ahead | near)) | endb);
                 }
             }
             __syncwarp();
@@ -968,8 +980,9 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         }
 
         // ---------------- sub-step 2: velocity update and move.  A vehicle with
-        // v = 0, an occupied cell ahead, no lane change and far from the link
-        // end keeps v = 0 and its cell: its bits are copied, its payload stays.
+        // v = 0, an occupied cell ahead and no lane change keeps v = 0 and its
+        // cell (its gap is 0 wherever it stands, link end or not): its bits are
+        // copied, its payload stays.
         {
             uint32_t lst[kMaxLanes] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -990,7 +1003,7 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
                 const uint32_t o1r =
                     right >= 0 ? (S.o0[wi(k, right)] & ~(has_f ? S.mv[wi(kf, right)] : 0u)) | S.mv[wi(k, right)] : 0u;
                 const uint32_t free_ahead = ~((o1 >> 1) | (o1r << 31));
-                const uint32_t busy = m1 | free_ahead | near | arriving;
+                const uint32_t busy = m1 | free_ahead | arriving;
                 lst[k] = o1 & busy & move_mask(kind, vmax);
                 if (core) {
                     const uint32_t inert = o1 & ~busy;
@@ -1470,6 +1483,14 @@ __global__ void __launch_bounds__(kNodeThreads) turn_node_kernel(const ScenDev *
 // the running count would exceed vt, at the positions cut_ok allows (bit t: a
 // cut before column t keeps the tiling rules); the sub-tiles go to out, in
 // any order, and count (zero before the launch) becomes their number.
+// Re-tiling weight of a moving vehicle against a standing one: a standing
+// vehicle with an occupied cell ahead is advanced with whole-word bit
+// operations, a moving one goes through the per-vehicle lists.
+#ifndef TS_MOVING_WEIGHT
+#define TS_MOVING_WEIGHT 1
+#endif
+constexpr uint32_t kMovingWeight = TS_MOVING_WEIGHT;
+
 __global__ void __launch_bounds__(128) retile_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ base,
                                                      const uint32_t *__restrict__ cut_ok, uint32_t n_base, uint32_t vt,
                                                      uint2 *__restrict__ out, uint32_t *__restrict__ count) {
@@ -1485,7 +1506,9 @@ __global__ void __launch_bounds__(128) retile_kernel(const ScenDev *__restrict__
             const uint4 ci = D.col_info[td.y + (uint32_t)lane];
             const uint32_t lanes = (ci.z >> 20) & 7u;
             const uint32_t *occ = D.occ[D.ctrl->base & 1ull];
-            for (uint32_t k = 0; k < lanes; ++k) cnt += (uint32_t)__popc(occ[ci.x + k]);
+            const uint32_t *mov = D.mov[D.ctrl->base & 1ull];
+            for (uint32_t k = 0; k < lanes; ++k)
+                cnt += (uint32_t)__popc(occ[ci.x + k]) + (kMovingWeight - 1u) * (uint32_t)__popc(mov[ci.x + k]);
         }
         const uint32_t ok = cut_ok[b];
         uint32_t cuts = 0u, sum = __shfl_sync(0xffffffffu, cnt, 0);

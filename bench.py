@@ -233,7 +233,7 @@ def run_profile_window(args):
         sc, _ = _workload(args.workload)
         sim = T.Simulation(sc, tile_words=args.tile_words)
         if args.load_balance:
-            sim.set_load_balance(args.load_balance, args.tile_vehicles or 512)
+            sim.set_load_balance(args.load_balance, args.tile_vehicles or 1024)
         sim.set_step_mode(STEP_MODES[args.step_mode])
         sims = [sim]
         advance = lambda k: sim.step(k, stream)
@@ -300,12 +300,13 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     sim = T.Simulation(sc, tile_words=args.tile_words)
-    # the re-tiling budget (vehicles per warp tile): given, or tuned on the
+    # the re-tiling budget (load per warp tile, a moving vehicle counting 8,
+    # a standing one 1): given, or tuned on the
     # first warm-up jobs, one candidate each, the fastest kept
-    tune = [] if (args.tile_vehicles or not args.load_balance) else [128, 256, 512]
+    tune = [] if (args.tile_vehicles or not args.load_balance) else [256, 512, 1024]
     if len(tune) + 2 > args.warmup:
         tune = []  # the first warm-up job captures the graphs, the last runs the choice
-    budget = args.tile_vehicles or 512
+    budget = args.tile_vehicles or 1024
     if args.load_balance:
         sim.set_load_balance(args.load_balance, budget)
     sim.set_step_mode(STEP_MODES[args.step_mode])
@@ -786,8 +787,9 @@ def main():
                     help="fused: one launch per step; split: link and node kernel per step")
     ap.add_argument("--load-balance", type=int, default=512, help="re-tile from the occupancy every N steps (0 = off)")
     ap.add_argument("--tile-vehicles", type=int, default=None,
-                    help="vehicle budget per warp tile when re-tiling (default: tuned on the warm-up jobs among "
-                         "128, 256 and 512 when there are at least four, else 512)")
+                    help="re-tiling budget per warp tile, a moving vehicle counting 8 and a standing one 1 "
+                         "(default: tuned on the warm-up jobs among 256, 512 and 1024 when there are at least five, "
+                         "else 1024)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per link_kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

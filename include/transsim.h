@@ -356,9 +356,11 @@ ts_status ts_batch_set_step_mode(ts_batch *b, uint32_t mode);
 /* Load balancing (the counterpart of feeding measured per-link load back
  * into the partition): every `every_steps` steps of a ts_step call
  * (0 = never; otherwise at least 32) the link tiles are rebuilt from the
- * current occupancy so that a tile holds at most `vehicles_per_tile`
- * vehicles (0 = no budget, else at least 32; a single column is never cut,
- * so a tile may exceed the budget by one column's vehicles).  Each pass is a kernel enqueued on the step's
+ * current occupancy so that a tile's load stays within `vehicles_per_tile`,
+ * a moving vehicle counting 8 and a standing one 1 (standing vehicles are
+ * mostly advanced 32 cells at a time, moving ones one by one) (0 = no
+ * budget, else at least 32; a single column is never cut, so a tile may
+ * exceed the budget by one column's load).  Each pass is a kernel enqueued on the step's
  * stream, so ts_step stays asynchronous.  Waits (bounded) for the context's
  * queued work; TS_ERR_STATE for a context in a batch.  Results do not
  * depend on it. */

@@ -1487,7 +1487,7 @@ __global__ void __launch_bounds__(kNodeThreads) turn_node_kernel(const ScenDev *
 // vehicle with an occupied cell ahead is advanced with whole-word bit
 // operations, a moving one goes through the per-vehicle lists.
 #ifndef TS_MOVING_WEIGHT
-#define TS_MOVING_WEIGHT 1
+#define TS_MOVING_WEIGHT 8
 #endif
 constexpr uint32_t kMovingWeight = TS_MOVING_WEIGHT;
 

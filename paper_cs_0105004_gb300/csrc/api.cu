@@ -81,6 +81,7 @@ struct World {
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1, grid_cap = 0;
     bool turns = false;  // some member has turn lanes or yield approaches (picks the turn instances)
+    bool vmax5 = false;  // every member has vmax = 5 (picks the instances compiled for it)
     uint32_t mode = TS_STEP_AUTO;  // fused or split steps (ts_set_step_mode)
     uint32_t link_blocks_per_sm = 0;  // cap on the link kernel's grid per SM (0: every resident block)
     std::map<uint32_t, cudaGraphExec_t> graphs;  // by chunk length | fused << 16
@@ -250,12 +251,16 @@ ts_status World::rebuild() {
     CK(cudaMemcpy(d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
     // persistent grids: at most the resident blocks, and room for the tile
     // count to double through load balancing before warps loop over tiles
-    bool pl = false;
+    bool pl = false, v5 = true;
     for (ts_ctx *c : members)
-        if (c) pl = pl || c->sd.route_turn != nullptr || c->sd.slot_gap != nullptr;
-    if (pl != turns) {
+        if (c) {
+            pl = pl || c->sd.route_turn != nullptr || c->sd.slot_gap != nullptr;
+            v5 = v5 && c->sd.vmax == 5u;
+        }
+    if (pl != turns || v5 != vmax5) {
         drop_graphs();
         turns = pl;
+        vmax5 = v5;
     }
     // re-tiling changes the tile count on the device: then the grid is every
     // resident block
@@ -302,7 +307,7 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             unsigned long long *sp = timing ? d_span : nullptr;
             for (uint32_t i = 0; i < g; ++i) {
                 launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0,
-                                   turns, sp);
+                                   turns, sp, vmax5);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, turns,
                                        sp);
@@ -1284,7 +1289,7 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
                 launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0,
-                                   w->turns);
+                                   w->turns, nullptr, w->vmax5);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu,

@@ -87,6 +87,7 @@ constexpr unsigned kErrCellTaken = 1u;  // two vehicles for one cell
 constexpr unsigned kErrSlotTaken = 2u;  // buffer entry into an occupied buffer
 constexpr unsigned kErrRoute = 4u;      // route cursor past the route end
 constexpr unsigned kErrGeometry = 8u;   // a vehicle left the tile geometry
+constexpr unsigned kErrInstance = 16u;  // a tile's scenario does not fit the kernel instance launched
 
 // One statistics sub-record per step; n_sub of them per step, each on its own
 // 128-byte line, so that block flushes spread over L2 slices.  Counts of the
@@ -160,8 +161,12 @@ struct ScenDev {
 // span: kernel-span buffer (nullptr: no timing), see kSpanWords
 // grid: blocks of kLinkWarpsPerBlock warps; each warp takes the tiles
 // warp, warp + all warps, ...
+// vmax5: every scenario of the table has vmax = 5 (the paper's value): picks
+// the instances compiled for that constant (a scenario that does not is
+// flagged, not stepped)
 void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span = nullptr);
+                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span = nullptr,
+                        bool vmax5 = false);
 // chunk_end: the pass completes the last step each scenario ran in the
 // chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,

@@ -658,8 +658,11 @@ __device__ __noinline__ uint32_t fused_link_work(const ScenDev &D, uint32_t t, i
 // first and last columns resolving them.  TURNS: the intersection rules of Sec. 3 a network
 // may carry: plan-following lane changes (every velocity byte carries the
 // lanes A of its link from which the vehicle may take its next turn) and gap
-// acceptance at unprotected turns (in the node transfers).
-template <int NW, bool TURNS, bool XFER>
+// acceptance at unprotected turns (in the node transfers).  VM: 0, or the
+// vmax every scenario of the launch has, as a compile-time constant (the
+// masks, gap windows and loops over the vmax cells behind or ahead of a
+// vehicle then fold into fixed bit operations).
+template <int NW, bool TURNS, bool XFER, int VM>
 __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__restrict__ table,
                                           const uint2 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
                                           uint32_t pos, unsigned long long *span) {
@@ -709,9 +712,13 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         pf_td = pf_geo = pf_state = false;
         const ScenDev &D = table[td.x & 0xFFFFFFu];
         if (D.ctrl == nullptr) continue;
+        if (VM != 0 && D.vmax != (uint32_t)VM) {
+            if (lane == 0) atomicOr(&D.ctrl->error, kErrInstance);
+            continue;
+        }
         const int n = (int)(td.x >> 24) + 1;
         const uint32_t cb = td.y;
-        const uint32_t vmax = D.vmax;
+        const uint32_t vmax = VM != 0 ? (uint32_t)VM : D.vmax;
 
         // ---------------- geometry (static data: read before waiting).  The
         // halo lanes read the column next to theirs and step to their own.
@@ -1177,22 +1184,22 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
 constexpr int kLinkWarps = kLinkWarpsPerBlock;
 constexpr int kLinkBlock = kLinkWarps * 32;
 
-template <bool XFER>
+template <bool XFER, int VM>
 __global__ void __launch_bounds__(kLinkBlock, 6)
     link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
                 const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span) {
     __shared__ LinkSmem<kLinkWarps> S;
-    link_step<kLinkWarps, false, XFER>(S, table, tiles, n_tiles_p, pos, span);
+    link_step<kLinkWarps, false, XFER, VM>(S, table, tiles, n_tiles_p, pos, span);
 }
 
 // The same with the intersection rules (scenarios with turn lanes or yield
 // approaches).
-template <bool XFER>
+template <bool XFER, int VM>
 __global__ void __launch_bounds__(kLinkBlock, 6)
     turn_link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
                      const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span) {
     __shared__ LinkSmem<kLinkWarps> S;
-    link_step<kLinkWarps, true, XFER>(S, table, tiles, n_tiles_p, pos, span);
+    link_step<kLinkWarps, true, XFER, VM>(S, table, tiles, n_tiles_p, pos, span);
 }
 
 // ------------------------------------------------------------------ node kernel
@@ -1689,15 +1696,19 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-static void (*link_instance(bool turns, bool xfer))(const ScenDev *, const uint2 *, const uint32_t *, uint32_t,
-                                                     unsigned long long *) {
-    if (turns) return xfer ? turn_link_kernel<true> : turn_link_kernel<false>;
-    return xfer ? link_kernel<true> : link_kernel<false>;
+static void (*link_instance(bool turns, bool xfer, bool vmax5))(const ScenDev *, const uint2 *, const uint32_t *,
+                                                                 uint32_t, unsigned long long *) {
+    if (vmax5) {
+        if (turns) return xfer ? turn_link_kernel<true, 5> : turn_link_kernel<false, 5>;
+        return xfer ? link_kernel<true, 5> : link_kernel<false, 5>;
+    }
+    if (turns) return xfer ? turn_link_kernel<true, 0> : turn_link_kernel<false, 0>;
+    return xfer ? link_kernel<true, 0> : link_kernel<false, 0>;
 }
 
 void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span) {
-    launch_pdl(link_instance(turns, xfer), grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i, span);
+                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span, bool vmax5) {
+    launch_pdl(link_instance(turns, xfer, vmax5), grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i, span);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
@@ -1753,10 +1764,10 @@ int max_link_blocks(bool turns) {
     // six blocks of four warps per SM (80 registers a thread: fewer spills
     // than at 64 with eight blocks, measured faster on the 20,024- and
     // 200,000-link networks) need the largest shared-memory share of L1
-    for (int x = 0; x < 2; ++x)
-        cudaFuncSetAttribute((const void *)link_instance(turns, x != 0), cudaFuncAttributePreferredSharedMemoryCarveout,
-                             kLinkCarveout);
-    return resident_blocks((const void *)link_instance(turns, false), kLinkBlock);
+    for (int x = 0; x < 4; ++x)
+        cudaFuncSetAttribute((const void *)link_instance(turns, (x & 1) != 0, (x & 2) != 0),
+                             cudaFuncAttributePreferredSharedMemoryCarveout, kLinkCarveout);
+    return resident_blocks((const void *)link_instance(turns, false, false), kLinkBlock);
 }
 int max_node_blocks(bool turns) {
     const void *fn = turns ? (const void *)turn_node_kernel : (const void *)node_kernel;

@@ -233,6 +233,43 @@ def test_batch_equals_alone(mode):
     b.close()
 
 
+def test_batch_switches_between_vmax_instances():
+    # members with vmax 5 run in the instances compiled for vmax 5; a member
+    # with another vmax joining the batch switches it to the general ones,
+    # and its leaving switches it back: every member's steps stay those of
+    # its single run, which for the vmax-7 member is checked against the oracle
+    import torch
+    scs = [N.small_grid_scenario(4, 2, 30, 300, 100, 300, gen_seed=31, seed=71),
+           N.small_grid_scenario(3, 3, 25, 250, 100, 300, gen_seed=32, seed=72),
+           N.small_grid_scenario(4, 2, 27, 300, 100, 300, gen_seed=33, seed=73, vmax=7)]
+    alone = []
+    for sc in scs:
+        sim = T.Simulation(sc)
+        sim.step(300)
+        alone.append(sim.stats_range(0, 300))
+        sim.close()
+    orc = oracle.Oracle(scs[2])
+    o = orc.step(300)
+    orc.close()
+    assert [int(x) for x in o["state_hash"]] == [int(r["state_hash"]) for r in alone[2]]
+    stream = torch.cuda.Stream()
+    b = T.Batch(4)
+    sims = [T.Simulation(sc) for sc in scs]
+    b.add(sims[0], 300)
+    b.add(sims[1], 300)
+    b.step(96, stream)       # vmax-5 instances
+    b.add(sims[2], 300)
+    b.step(96, stream)       # general instances
+    b.remove(sims[2])
+    b.step(300, stream)      # vmax-5 instances again
+    b.sync()
+    sims[2].step(204)        # the vmax-7 member alone
+    for s, ref, name in zip(sims, alone, ("first", "second", "vmax 7")):
+        assert s.current_step() == 300
+        _cmp_stats(s.stats_range(0, 300), ref, name)
+    b.close()
+
+
 # ------------------------------------------------------------------ link travel times
 
 @pytest.mark.parametrize("mode", [T.STEP_FUSED, T.STEP_SPLIT])

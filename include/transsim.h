@@ -322,7 +322,9 @@ ts_status ts_batch_set_link_grid(ts_batch *b, uint32_t blocks_per_sm);
  * Layout of the caller's buffers, W = cells/32 * lanes words: dev_occ0/1
  * [W] uint32 occupancy words, word (column j, lane k) = j*lanes + k, bit i =
  * cell 32j+i; dev_vel0/1 [32*W] int8 velocities and dev_vid0/1 [32*W]
- * uint32 vehicle ids (below 2^31) at word*32 + bit.  The state of step
+ * uint32 vehicle ids at word*32 + bit; ids must be below 2^31 (bit 31 is
+ * the kernels' last-link flag: an id with it set is not checked and gives
+ * undefined movement and statistics).  The state of step
  * first_step is read from buffer set (first_step & 1) and the state after
  * the last step is written to set ((first_step + n_steps) & 1); the other
  * set is overwritten.  dev_stats_out [n_steps] (device memory) receives the

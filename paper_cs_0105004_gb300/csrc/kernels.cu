@@ -860,6 +860,20 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
         if (!core && exists && (near & lc_mask(kind, vmax))) atomicOr(&D.ctrl->error, kErrGeometry);
         const uint32_t kmax = __reduce_max_sync(0xffffffffu, exists ? lanes : 0u);
         __syncwarp();
+        if (!__any_sync(0xffffffffu, upd != 0u)) {
+            // no vehicle in the tile or its halos: the next state's words are empty
+            if (core) {
+#pragma unroll
+                for (int k = 0; k < kMaxLanes; ++k) {
+                    if ((uint32_t)k >= lanes) break;
+                    const uint32_t g = cw + (uint32_t)k;
+                    D.occ[nxt][g] = 0u;
+                    D.mov[nxt][g] = 0u;
+                    D.loc[nxt][g] = 0u;
+                }
+            }
+            continue;
+        }
         const int8_t *__restrict__ vel0 = D.vel[0];
         const int8_t *__restrict__ vel1 = D.vel[1];
         const uint32_t *__restrict__ vid0 = D.vid[0];

@@ -76,7 +76,8 @@ struct World {
     ScenDev *d_table = nullptr;
     uint2 *d_link_tiles = nullptr;
     uint4 *d_node_tiles = nullptr;
-    uint32_t *d_counts = nullptr;  // [0] link tiles, [1] node tiles, read by the kernels
+    uint32_t *d_counts = nullptr;  // [0] link tiles, [1] node tiles, read by the kernels; then the link
+                                   // kernels' tile claim counters, one per chunk position
     size_t link_cap = 0, node_cap = 0;
     uint32_t n_link_tiles = 0, n_node_tiles = 0;
     int grid_l = 1, grid_n = 1, grid_cap = 0;
@@ -194,8 +195,8 @@ ts_status World::init(uint32_t cap) {
     CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     CK(cudaMalloc(&d_table, sizeof(ScenDev) * cap));
     CK(cudaMemset(d_table, 0, sizeof(ScenDev) * cap));
-    CK(cudaMalloc(&d_counts, 2 * sizeof(uint32_t)));
-    CK(cudaMemset(d_counts, 0, 2 * sizeof(uint32_t)));
+    CK(cudaMalloc(&d_counts, (2 + kChunk) * sizeof(uint32_t)));
+    CK(cudaMemset(d_counts, 0, (2 + kChunk) * sizeof(uint32_t)));
     return TS_OK;
 }
 
@@ -307,12 +308,12 @@ ts_status World::run(uint32_t n, cudaStream_t s) {
             unsigned long long *sp = timing ? d_span : nullptr;
             for (uint32_t i = 0; i < g; ++i) {
                 launch_link_kernel(d_table, d_link_tiles, d_counts, i, grid_l, cap_stream, i > 0, fu && i > 0,
-                                   turns, sp, vmax5);
+                                   turns, sp, vmax5, d_counts + 2);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(d_table, d_node_tiles, d_counts + 1, i, grid_n, cap_stream, true, fu, turns,
                                        sp);
             }
-            launch_advance_kernel(d_table, capacity, g, cap_stream, true, sp);
+            launch_advance_kernel(d_table, capacity, g, cap_stream, true, sp, d_counts + 2);
             CK(cudaStreamEndCapture(cap_stream, &graph));
             cudaGraphExec_t exec;
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1289,14 +1290,14 @@ ts_status ts_step_timed(ts_ctx *c, uint32_t n_steps, void *cuda_stream, float *l
                 const size_t e = 3ull * (b + i);
                 cudaEventRecord(ev[e], s);
                 launch_link_kernel(w->d_table, w->d_link_tiles, w->d_counts, i, w->grid_l, s, false, fu && i > 0,
-                                   w->turns, nullptr, w->vmax5);
+                                   w->turns, nullptr, w->vmax5, w->d_counts + 2);
                 cudaEventRecord(ev[e + 1], s);
                 if (!fu || i + 1 == g)
                     launch_node_kernel(w->d_table, w->d_node_tiles, w->d_counts + 1, i, w->grid_n, s, false, fu,
                                        w->turns);
                 cudaEventRecord(ev[e + 2], s);
             }
-            launch_advance_kernel(w->d_table, w->capacity, g, s, false);
+            launch_advance_kernel(w->d_table, w->capacity, g, s, false, nullptr, w->d_counts + 2);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) rs = cuda_fail(e, "kernel launch");
         }

@@ -159,20 +159,23 @@ struct ScenDev {
 // changes) or yield approaches (gap acceptance); picks the instances that
 // apply those rules
 // span: kernel-span buffer (nullptr: no timing), see kSpanWords
-// grid: blocks of kLinkWarpsPerBlock warps; each warp takes the tiles
-// warp, warp + all warps, ...
+// grid: blocks of kLinkWarpsPerBlock warps; each warp takes the tile of its
+// index, then the tiles warp + all warps, ... or, with tile_ctr (kChunk
+// counters, one per chunk position, zero at the chunk's start), all warps +
+// the next value it claims from tile_ctr[i]
 // vmax5: every scenario of the table has vmax = 5 (the paper's value): picks
 // the instances compiled for that constant (a scenario that does not is
 // flagged, not stepped)
 void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span = nullptr,
-                        bool vmax5 = false);
+                        bool vmax5 = false, uint32_t *tile_ctr = nullptr);
 // chunk_end: the pass completes the last step each scenario ran in the
 // chunk (after fused steps); else step i of the chunk only
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
                         cudaStream_t s, bool pdl, bool chunk_end, bool turns, unsigned long long *span = nullptr);
+// tile_ctr: the link kernels' claim counters (kChunk), zeroed for the next chunk
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl,
-                           unsigned long long *span = nullptr);
+                           unsigned long long *span = nullptr, uint32_t *tile_ctr = nullptr);
 // Kernel-span buffer: per chunk position and kind (link, node) the launch's
 // first block entry and last block exit on %globaltimer, then per kind the
 // sum of launch durations (ns) and the launch count.

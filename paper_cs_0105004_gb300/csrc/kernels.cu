@@ -665,7 +665,7 @@ __device__ __noinline__ uint32_t fused_link_work(const ScenDev &D, uint32_t t, i
 template <int NW, bool TURNS, bool XFER, int VM>
 __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__restrict__ table,
                                           const uint2 *__restrict__ tiles, const uint32_t *__restrict__ n_tiles_p,
-                                          uint32_t pos, unsigned long long *span) {
+                                          uint32_t pos, unsigned long long *span, uint32_t *tile_ctr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &S = SB.w[warp];
     const uint32_t n_tiles = *n_tiles_p;  // changes only between graph launches
@@ -697,7 +697,15 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
     // what the prefetch area holds for the tile about to start: its
     // descriptor, its column records, its columns' words of step t
     bool pf_td = false, pf_geo = false, pf_state = false;
-    for (uint32_t tile = blockIdx.x * (uint32_t)NW + (uint32_t)warp; tile < n_tiles; tile += nwarps) {
+    // a warp's first tile is given by its index; after it, with a claim
+    // counter for this chunk position and more tiles than warps, it takes
+    // the next unclaimed tile (claimed while the current one runs, so warps
+    // whose tiles ran short take more), else every nwarps-th
+    uint32_t *const ctr = tile_ctr != nullptr && n_tiles > nwarps ? tile_ctr + pos : nullptr;
+    uint32_t claim = 0u;
+    for (uint32_t tile = blockIdx.x * (uint32_t)NW + (uint32_t)warp; tile < n_tiles;
+         tile = ctr != nullptr ? nwarps + __shfl_sync(0xffffffffu, claim, 0) : tile + nwarps) {
+        if (ctr != nullptr && lane == 0) claim = atomicAdd(ctr, 1u);
         // the next kernel may launch once every block has begun its last
         // round of tiles (warp 0 has the most tiles of its block): launched
         // earlier, its waiting blocks would hold registers and shared memory
@@ -1201,9 +1209,10 @@ constexpr int kLinkBlock = kLinkWarps * 32;
 template <bool XFER, int VM>
 __global__ void __launch_bounds__(kLinkBlock, 6)
     link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
-                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span) {
+                const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span,
+                uint32_t *tile_ctr) {
     __shared__ LinkSmem<kLinkWarps> S;
-    link_step<kLinkWarps, false, XFER, VM>(S, table, tiles, n_tiles_p, pos, span);
+    link_step<kLinkWarps, false, XFER, VM>(S, table, tiles, n_tiles_p, pos, span, tile_ctr);
 }
 
 // The same with the intersection rules (scenarios with turn lanes or yield
@@ -1211,9 +1220,10 @@ __global__ void __launch_bounds__(kLinkBlock, 6)
 template <bool XFER, int VM>
 __global__ void __launch_bounds__(kLinkBlock, 6)
     turn_link_kernel(const ScenDev *__restrict__ table, const uint2 *__restrict__ tiles,
-                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span) {
+                     const uint32_t *__restrict__ n_tiles_p, uint32_t pos, unsigned long long *span,
+                     uint32_t *tile_ctr) {
     __shared__ LinkSmem<kLinkWarps> S;
-    link_step<kLinkWarps, true, XFER, VM>(S, table, tiles, n_tiles_p, pos, span);
+    link_step<kLinkWarps, true, XFER, VM>(S, table, tiles, n_tiles_p, pos, span, tile_ctr);
 }
 
 // ------------------------------------------------------------------ node kernel
@@ -1589,8 +1599,10 @@ void launch_link_time_fix(const ScenDev &sd, uint32_t n_veh, unsigned long long 
 // One block per scenario: sums the statistics of the g steps just run,
 // moves the step counter and clears the records of the next chunk.
 __global__ void __launch_bounds__(128) advance_kernel(const ScenDev *__restrict__ table, uint32_t g_max,
-                                                      unsigned long long *span) {
+                                                      unsigned long long *span, uint32_t *tile_ctr) {
     pdl_wait();
+    // the next chunk's tile claims start from zero
+    if (tile_ctr != nullptr && blockIdx.x == 0 && threadIdx.x < kChunk) tile_ctr[threadIdx.x] = 0u;
     if (span != nullptr && blockIdx.x == 0 && threadIdx.x < 2) {
         // the chunk's launches of one kind: durations into the sums, spans reset
         const uint32_t kind = threadIdx.x;
@@ -1711,7 +1723,7 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, bool pdl
 }
 
 static void (*link_instance(bool turns, bool xfer, bool vmax5))(const ScenDev *, const uint2 *, const uint32_t *,
-                                                                 uint32_t, unsigned long long *) {
+                                                                 uint32_t, unsigned long long *, uint32_t *) {
     if (vmax5) {
         if (turns) return xfer ? turn_link_kernel<true, 5> : turn_link_kernel<false, 5>;
         return xfer ? link_kernel<true, 5> : link_kernel<false, 5>;
@@ -1721,8 +1733,10 @@ static void (*link_instance(bool turns, bool xfer, bool vmax5))(const ScenDev *,
 }
 
 void launch_link_kernel(const ScenDev *table, const uint2 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
-                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span, bool vmax5) {
-    launch_pdl(link_instance(turns, xfer, vmax5), grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i, span);
+                        cudaStream_t s, bool pdl, bool xfer, bool turns, unsigned long long *span, bool vmax5,
+                        uint32_t *tile_ctr) {
+    launch_pdl(link_instance(turns, xfer, vmax5), grid, kLinkBlock, pdl, s, table, tiles, n_tiles, i, span,
+               tile_ctr);
 }
 
 void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t *n_tiles, uint32_t i, int grid,
@@ -1732,8 +1746,8 @@ void launch_node_kernel(const ScenDev *table, const uint4 *tiles, const uint32_t
 }
 
 void launch_advance_kernel(const ScenDev *table, uint32_t n_scen, uint32_t g, cudaStream_t s, bool pdl,
-                           unsigned long long *span) {
-    launch_pdl(advance_kernel, (int)n_scen, 128, pdl, s, table, g, span);
+                           unsigned long long *span, uint32_t *tile_ctr) {
+    launch_pdl(advance_kernel, (int)n_scen, 128, pdl, s, table, g, span, tile_ctr);
 }
 
 void launch_set_target(Ctrl *ctrl, unsigned long long target, cudaStream_t s) {

@@ -159,10 +159,11 @@ struct ScenDev {
 // changes) or yield approaches (gap acceptance); picks the instances that
 // apply those rules
 // span: kernel-span buffer (nullptr: no timing), see kSpanWords
-// grid: blocks of kLinkWarpsPerBlock warps; each warp takes the tile of its
-// index, then the tiles warp + all warps, ... or, with tile_ctr (kChunk
-// counters, one per chunk position, zero at the chunk's start), all warps +
-// the next value it claims from tile_ctr[i]
+// grid: blocks of kLinkWarpsPerBlock warps; each warp takes the tiles warp,
+// warp + all warps, ... or, with tile_ctr (kChunk counters, one per chunk
+// position, zero at the chunk's start) and more than two tiles per warp,
+// after its first two 2 * all warps + the next value it claims from
+// tile_ctr[i]
 // vmax5: every scenario of the table has vmax = 5 (the paper's value): picks
 // the instances compiled for that constant (a scenario that does not is
 // flagged, not stepped)

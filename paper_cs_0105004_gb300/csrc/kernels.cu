@@ -697,15 +697,16 @@ __device__ __forceinline__ void link_step(LinkSmem<NW> &SB, const ScenDev *__res
     // what the prefetch area holds for the tile about to start: its
     // descriptor, its column records, its columns' words of step t
     bool pf_td = false, pf_geo = false, pf_state = false;
-    // a warp's first tile is given by its index; after it, with a claim
-    // counter for this chunk position and more tiles than warps, it takes
-    // the next unclaimed tile (claimed while the current one runs, so warps
-    // whose tiles ran short take more), else every nwarps-th
-    uint32_t *const ctr = tile_ctr != nullptr && n_tiles > nwarps ? tile_ctr + pos : nullptr;
+    // a warp's first two tiles are given by its index (warp, warp + nwarps);
+    // after them, with a claim counter for this chunk position and more than
+    // two tiles per warp, it takes the next unclaimed tile (claimed while its
+    // second or later tile runs, when the warps no longer start together, so
+    // warps whose tiles ran short take more), else every nwarps-th
+    uint32_t *const ctr = tile_ctr != nullptr && n_tiles > 2u * nwarps ? tile_ctr + pos : nullptr;
     uint32_t claim = 0u;
     for (uint32_t tile = blockIdx.x * (uint32_t)NW + (uint32_t)warp; tile < n_tiles;
-         tile = ctr != nullptr ? nwarps + __shfl_sync(0xffffffffu, claim, 0) : tile + nwarps) {
-        if (ctr != nullptr && lane == 0) claim = atomicAdd(ctr, 1u);
+         tile = ctr != nullptr && tile >= nwarps ? 2u * nwarps + __shfl_sync(0xffffffffu, claim, 0) : tile + nwarps) {
+        if (ctr != nullptr && tile >= nwarps && lane == 0) claim = atomicAdd(ctr, 1u);
         // the next kernel may launch once every block has begun its last
         // round of tiles (warp 0 has the most tiles of its block): launched
         // earlier, its waiting blocks would hold registers and shared memory

@@ -57,8 +57,11 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
 }
 
 #ifdef TS_PHASE_TIMING
-// Debug builds only: %globaltimer stamps at the phase boundaries of the first
-// tile of every link_kernel block of the last launch.
+// Measurement builds only: stamp(phase, first) calls placed by hand at the
+// phase boundaries of link_step record %globaltimer for the first tile of
+// every link_kernel block of the last launch and sum each phase's time over
+// all tiles of warp 0 of every block (the source carries no calls; without
+// TS_PHASE_TIMING stamp() is empty).
 constexpr int kPhases = 10;
 constexpr int kPhaseBlocks = 4096;
 __device__ unsigned long long g_phase[kPhases][kPhaseBlocks];

@@ -1,0 +1,39 @@
+"""Host-side logic of bench.py: the DRAM traffic a bench line reports comes
+from an ncu summary under profiles/ only when that summary was taken from
+the kernel source being measured."""
+import bench
+
+
+def _write(tmp_path, lines):
+    d = tmp_path / "profiles"
+    d.mkdir()
+    (d / "k.md").write_text("\n".join(lines) + "\n")
+    return tmp_path
+
+
+def test_traffic_is_read_only_for_the_current_kernel_source(tmp_path, monkeypatch):
+    root = _write(tmp_path, [
+        "# summary",
+        "bench-traffic: kernel=link_kernel workload=config2 kernel_sha=aaaa dram_bytes_per_launch=5.2e7",
+        "bench-traffic-warm: kernel=link_kernel workload=config2 kernel_sha=aaaa dram_bytes_per_launch=14370000",
+        "bench-traffic: kernel=link_kernel workload=config1 kernel_sha=aaaa dram_bytes_per_launch=6000000",
+    ])
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    monkeypatch.setattr(bench, "kernel_sha", lambda: "aaaa")
+    assert bench._profile_traffic("link_kernel", "config2") == (5.2e7, "profiles/k.md")
+    assert bench._profile_traffic("link_kernel", "config2", "bench-traffic-warm")[0] == 14370000.0
+    assert bench._profile_traffic("link_kernel", "config1")[0] == 6000000.0
+    assert bench._profile_traffic("node_kernel", "config2") == (None, None)
+    # another kernel source: no figure at all
+    monkeypatch.setattr(bench, "kernel_sha", lambda: "bbbb")
+    assert bench._profile_traffic("link_kernel", "config2") == (None, None)
+
+
+def test_kernel_sha_follows_the_kernel_source(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    monkeypatch.setattr(bench, "KERNEL_SRC", str(src))
+    a = bench.kernel_sha()
+    assert len(a) == 16 and a == bench.kernel_sha()
+    src.write_text("__global__ void k() { }\n")
+    assert bench.kernel_sha() != a

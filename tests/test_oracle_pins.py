@@ -155,6 +155,43 @@ def test_lane_change_needs_room_behind():
     assert positions(o.get_state(), sc.net)[0] == (0, 0, 11, 1)
 
 
+def _near_end_case(end_state):
+    # link 0: 20 cells x 2 lanes into link 1 (1 lane).  Vehicle 0 stands in
+    # lane 0, cell 17 (two cells before the last), vehicle 1 stands right
+    # ahead of it in cell 18; lane 1 is empty.  end_state: "open" (free
+    # link-end buffers, no light), "red" (a light red for steps 0..19) or
+    # "full" (both link-end buffers taken by vehicles bound for link 1)
+    links = [(0, 1, 20, 2), (1, 2, 20, 1)]
+    routes = [[0, 1], [0, 1]]
+    bufs = None
+    if end_state == "full":
+        routes += [[0, 1], [0, 1]]
+        bufs = [(2, 0, 0, 0), (3, 0, 1, 0)]
+    sc = make_scenario(links, 3, routes, [0] * len(routes), p=0, placed=[(0, 0, 0, 17, 0), (1, 0, 0, 18, 0)],
+                       bufs=bufs)
+    if end_state == "red":
+        sc.net.link_signal = np.array([[40, 20, 20], [0, 0, 0]], np.uint32)
+    return sc
+
+
+@pytest.mark.parametrize("end_state", ["open", "red", "full"])
+def test_stopped_vehicle_near_the_end_changes_lane_whatever_the_end_state(end_state):
+    # Step 0 (d = +1): vehicle 0 has gap 0 (vehicle 1 ahead) < min(0+1, vmax)
+    # = 1, so it has a reason; in lane 1 its target cell and the 5 cells
+    # behind are empty and the next cell is free, so the target gap is at
+    # least 1 > 0 whether or not the link end lets anyone out: it changes
+    # lanes, then accelerates to 1 (the cell ahead in lane 1 is free).
+    # Vehicle 1, one cell before the last, has the last cell free ahead, so
+    # gap >= 1 = min(0+1, vmax): no reason to change; it moves to cell 19.
+    sc = _near_end_case(end_state)
+    o = oracle.Oracle(sc)
+    st = o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    assert int(st[0]["lane_changes"]) == 1
+    assert pos[0] == (0, 1, 18, 1)
+    assert pos[1] == (0, 0, 19, 1)
+
+
 # ------------------------------------------------------------------ 1-lane circle (Sec. 5)
 
 def _ring(L, n, mode, v0=0, lanes=1, p=0, vmax=5, seed=3, rng_seed=0):

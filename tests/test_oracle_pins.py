@@ -192,6 +192,19 @@ def test_stopped_vehicle_near_the_end_changes_lane_whatever_the_end_state(end_st
     assert pos[1] == (0, 0, 19, 1)
 
 
+def test_vehicle_with_vmax_free_cells_ahead_keeps_its_lane():
+    # Vehicle 0 in lane 0, cell 2, v = 4, with nothing ahead for 17 cells;
+    # lane 1 is empty too.  Its gap is vmax = 5 >= min(4+1, 5): no reason to
+    # change, on the even step (target lane 1) as on the odd one (no target
+    # from lane 0); it accelerates to 5 each step.
+    for start in (0, 1):
+        sc = make_scenario([(0, 1, 40, 2)], 2, [[0]], [0], p=0, placed=[(0, 0, 0, 2, 4)], start_step=start)
+        o = oracle.Oracle(sc)
+        st = o.step(2)
+        assert int(st["lane_changes"].sum()) == 0
+        assert positions(o.get_state(), sc.net)[0] == (0, 0, 12, 5)
+
+
 # ------------------------------------------------------------------ 1-lane circle (Sec. 5)
 
 def _ring(L, n, mode, v0=0, lanes=1, p=0, vmax=5, seed=3, rng_seed=0):

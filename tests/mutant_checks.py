@@ -27,6 +27,8 @@ def checks():
         ("transfer lane preference", P.test_transfer_lane_preference),
         ("lane change on even steps", P.test_lane_change_even_step_moves_up),
         ("lane change needs room behind", P.test_lane_change_needs_room_behind),
+        ("lane change near a link end", lambda: P.test_stopped_vehicle_near_the_end_changes_lane_whatever_the_end_state("red")),
+        ("free flow keeps its lane", P.test_vehicle_with_vmax_free_cells_ahead_keeps_its_lane),
         ("ring free flow", P.test_ring_free_flow_exact),
         ("ring jam", P.test_ring_jam_exact),
         ("megajam dissolves", P.test_megajam_dissolves_one_car_per_step),

@@ -41,6 +41,10 @@ MUTANTS = {
     "travel time one step long": ("o->lt_sum[l] += t - o->t_enter[id];\n                    o->lt_cnt[l]++;\n                    o->t_enter[id] = (uint32_t)t;",
                                   "o->lt_sum[l] += t + 1 - o->t_enter[id];\n                    o->lt_cnt[l]++;\n                    o->t_enter[id] = (uint32_t)t;"),
     "moving counts standing vehicles": ("if (o->vel[id] > 0) st->moving++;", "if (o->vel[id] >= 0) st->moving++;"),
+    "no lane change within vmax of a link end": (
+        "int32_t id = o->s_start[cell_index(o, l, k, x)];\n                    if (id < 0) continue;",
+        "int32_t id = o->s_start[cell_index(o, l, k, x)];\n"
+        "                    if (id < 0 || (!o->ring[l] && o->cells[l] - 1 - x < vmax)) continue;"),
     "digest drops the lane": ("uint64_t b = ((uint64_t)cell << 16) | ((uint64_t)lane << 8) | v;",
                               "uint64_t b = ((uint64_t)cell << 16) | v;"),
 }

@@ -37,3 +37,25 @@ def test_kernel_sha_follows_the_kernel_source(tmp_path, monkeypatch):
     assert len(a) == 16 and a == bench.kernel_sha()
     src.write_text("__global__ void k() { }\n")
     assert bench.kernel_sha() != a
+
+
+def test_reference_arm_prints_one_contract_line_on_the_host():
+    # the reference arm is the oracle on the host cores: it needs no GPU
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "config0", "--steps", "1",
+                        "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "vehicle-updates/s" and d["unit"] == d["metric"]
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

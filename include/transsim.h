@@ -272,7 +272,9 @@ const char *ts_last_error(void);
 ts_status ts_philox_words(uint32_t n, const uint32_t *host_step, const uint32_t *host_id, uint64_t seed,
                           uint32_t *host_out);
 
-/* Frees the context and its device memory (waits for its stream). */
+/* Frees the context and its device memory.  It first waits, without a
+ * deadline, for the work queued on its stream (that work uses the memory it
+ * frees); call ts_read_stats with a deadline first to bound the wait. */
 void ts_destroy(ts_ctx *ctx);
 
 /* ---- batching: many independent scenarios advanced by the same kernels.
@@ -294,6 +296,8 @@ ts_status ts_batch_reset(ts_batch *b, uint64_t target_step, void *cuda_stream);
 ts_status ts_batch_sync(ts_batch *b, uint32_t timeout_ms);
 /* Current step of a member (after ts_batch_sync). */
 ts_status ts_ctx_step(ts_ctx *ctx, uint64_t *step);
+/* Frees the batch (not its members); waits, without a deadline, for the
+ * batch's queued work first (ts_batch_sync bounds that wait). */
 void ts_batch_destroy(ts_batch *b);
 
 /* Kernel launch shape: at most this many occupancy words (32-cell columns

@@ -205,6 +205,29 @@ def test_vehicle_with_vmax_free_cells_ahead_keeps_its_lane():
         assert positions(o.get_state(), sc.net)[0] == (0, 0, 12, 5)
 
 
+@pytest.mark.parametrize("red", [False, True])
+def test_queue_at_a_link_end_moves_only_at_its_front(red):
+    # Five standing vehicles fill cells 15..19 of a 20-cell one-lane link
+    # bound for link 1.  Each one behind the front has gap 0 (the cell ahead
+    # is taken at the start of the step), so it keeps v = 0 and its cell; the
+    # front one, in the last cell, accelerates to 1 and enters the link-end
+    # buffer (then crosses to cell 0 of link 1) when the way out is open, and
+    # stays when the light is red.
+    n = 5
+    sc = make_scenario([(0, 1, 20, 1), (1, 2, 20, 1)], 3, [[0, 1]] * n, [0] * n, p=0,
+                       placed=[(i, 0, 0, 15 + i, 0) for i in range(n)])
+    if red:
+        sc.net.link_signal = np.array([[40, 20, 20], [0, 0, 0]], np.uint32)
+    o = oracle.Oracle(sc)
+    st = o.step(1)
+    pos = positions(o.get_state(), sc.net)
+    for i in range(n - 1):
+        assert pos[i] == (0, 0, 15 + i, 0)
+    assert pos[n - 1] == ((0, 0, 19, 0) if red else (1, 0, 0, 1))
+    assert int(st[0]["moving"]) == (0 if red else 1)
+    assert int(st[0]["transfers"]) == (0 if red else 1)
+
+
 # ------------------------------------------------------------------ 1-lane circle (Sec. 5)
 
 def _ring(L, n, mode, v0=0, lanes=1, p=0, vmax=5, seed=3, rng_seed=0):
